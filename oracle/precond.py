@@ -1,0 +1,69 @@
+"""Oracle block-Jacobi preconditioner (test infrastructure only).
+
+The "first solution" of Sect. 2.5.2 (background-scattering derivatives
+neglected), the choice the paper makes for its JFNK solvers: per depth k,
+
+  P^k_ij = Gamma^k_ij + A^kk_ij          (Sect. 2.5.1)
+  Gamma^k_ij = delta_ij sum_p (C_ip + R_ip) - (C_ji + R_ji)
+  A^kk_ij    = sum_nu sum_t s_it W_t(nu) chi_t(nu) [beta_j dJ/dchi^k + gamma_j dJ/deta^k]
+
+where chi_t = V_t (n_lo - g_t n_up) is the opacity of transition t, W_t the
+rate quadrature weight omega_t 4 pi / (h nu), s_it = +1 (-1) when i is the
+lower (upper) level of t, dJ/dchi^k and dJ/deta^k the angle averages of the
+App. A.2 coefficients, and the conservation row replaced by -1 (Sect. 2.5.1).
+
+Reading of beta_j (the printed sum_{s>j} V_js (1 - g_js) is garbled):
+beta_j = d chi / d n_j = sum_{t: lo=j} V_t - sum_{t: up=j} g_t V_t, derived from
+Eq. chi; gamma_j = d eta / d n_j = sum_{t: up=j} (2 h nu^3 / c^2) g_t V_t.
+
+With J^dagger frozen these blocks are exactly the diagonal blocks of the
+Jacobian of F; tests/test_oracle_residual.py checks that against the dense
+complex-step Jacobian.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .model import FOURPI, H, Model
+
+
+def block_jacobi(m: Model, n, res) -> np.ndarray:
+    """P[k] (nl x nl) from a residual evaluation made with ``want_lambda``."""
+    n = np.real(np.asarray(n))
+    nl, nq, nz = m.nl, m.nq, m.nz
+    Wnu = FOURPI / (H * m.nu)
+    alpha = np.zeros((nl, nq, nz))
+    beta = np.zeros((nl, nq, nz))
+    gamma = np.zeros((nl, nq, nz))
+    P = np.zeros((nz, nl, nl))
+    for t, tr in enumerate(m.trans):
+        lo, up = tr.lo, tr.up
+        chi_t = m.V[t] * (n[:, lo][None, :] - m.g[t] * n[:, up][None, :])
+        Wchi = m.omega[t][:, None] * Wnu[:, None] * chi_t
+        alpha[lo] += Wchi
+        alpha[up] -= Wchi
+        beta[lo] += m.V[t]
+        beta[up] -= m.g[t] * m.V[t]
+        gamma[up] += m.twohnu3c2[:, None] * m.g[t] * m.V[t]
+        # Gamma: direct dependence of kappa_t on n_lo, n_up
+        up_rate = m.Cmat[:, lo, up] + res.R_up[t]
+        dn_rate = m.Cmat[:, up, lo] + res.R_dn[t]
+        P[:, lo, lo] += up_rate
+        P[:, lo, up] -= dn_rate
+        P[:, up, lo] -= up_rate
+        P[:, up, up] += dn_rate
+    zeta = beta * np.real(res.lam_chi)[None] + gamma * np.real(res.lam_eta)[None]
+    P += np.einsum("iqk,jqk->kij", alpha, zeta)
+    P[np.arange(nz), res.istar, :] = -1.0
+    return P
+
+
+def lu_factor_blocks(P):
+    return [sla.lu_factor(P[k]) for k in range(P.shape[0])]
+
+
+def apply_inverse(lus, x):
+    """P^{-1} x, depth by depth."""
+    x = np.asarray(x).reshape(len(lus), -1)
+    return np.stack([sla.lu_solve(lus[k], x[k]) for k in range(len(lus))])

@@ -1,0 +1,147 @@
+"""Pins of the oracle residual, JVPs and block-Jacobi preconditioner (no GPU)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import model as OM
+from oracle.dense import dense_jacobian
+from oracle.precond import block_jacobi
+from oracle.residual import assemble, jvp_complex, jvp_fd, rates_from_J, residual
+
+
+@pytest.fixture(scope="module")
+def small_ca():
+    wl = W.config2(nu_scale=0.1, n_depth=10)
+    return OM.build_model(wl.atom, wl.columns[0], 2)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = W.tiny_workload(n_depth=5, n_nu_line=7, n_nu_cont=3)
+    return OM.build_model(wl.atom, wl.columns[0], 2)
+
+
+def test_detailed_balance_with_planck_radiation(small_ca):
+    """At n = n* and J = B_nu(T) every radiative net rate vanishes (Kirchhoff + Einstein + Milne).
+
+    Exact for bound-free (g_ij carries exp(-h nu/kT) per frequency); for a line
+    the Boltzmann factor is taken at the line centre, so the balance holds up to
+    the second order in (nu - nu_0)/nu_0 across the symmetric profile (~1e-9).
+    """
+    m = small_ca
+    R_up, R_dn = rates_from_J(m, m.B)
+    for t, tr in enumerate(m.trans):
+        up = m.nstar[:, tr.lo] * R_up[t]
+        dn = m.nstar[:, tr.up] * R_dn[t]
+        np.testing.assert_allclose(up, dn, rtol=1e-12 if tr.kind == "bf" else 1e-8)
+    F = assemble(m, m.nstar, R_up, R_dn, np.argmax(m.nstar, axis=1))
+    gross = np.zeros_like(m.nstar)
+    for t, tr in enumerate(m.trans):
+        gross[:, tr.lo] += m.nstar[:, tr.lo] * R_up[t]
+        gross[:, tr.up] += m.nstar[:, tr.lo] * R_up[t]
+    assert np.all(np.abs(F) <= 1e-8 * gross + 1e-300)
+
+
+def test_conservation_rows(small_ca):
+    m = small_ca
+    rng = np.random.default_rng(1)
+    n = W.perturbed_populations(m.nstar, rng)
+    r = residual(m, n, OM.initial_J(m))
+    np.testing.assert_array_equal(r.istar, np.argmax(n, axis=1))
+    np.testing.assert_allclose(r.F[np.arange(m.nz), r.istar], m.ntot - n.sum(axis=1), rtol=1e-14)
+    # the other rows sum to minus the conservation row's net-rate content: sum_i F_i = 0 before replacement
+    R_up, R_dn = r.R_up, r.R_dn
+    Fraw = np.zeros_like(n)
+    for t, tr in enumerate(m.trans):
+        kap = n[:, tr.lo] * (m.Cmat[:, tr.lo, tr.up] + R_up[t]) - n[:, tr.up] * (m.Cmat[:, tr.up, tr.lo] + R_dn[t])
+        Fraw[:, tr.lo] += kap
+        Fraw[:, tr.up] -= kap
+    assert np.max(np.abs(Fraw.sum(axis=1))) < 1e-12 * np.max(np.abs(Fraw))
+
+
+def test_complex_step_jvp_is_linear(small_ca):
+    m = small_ca
+    rng = np.random.default_rng(2)
+    n = W.perturbed_populations(m.nstar, rng, 0.2)
+    Jd = OM.initial_J(m)
+    v = rng.normal(size=n.shape) * n
+    w = rng.normal(size=n.shape) * n
+    Jv = jvp_complex(m, n, Jd, v)
+    Jw = jvp_complex(m, n, Jd, w)
+    Jc = jvp_complex(m, n, Jd, 2.5 * v - w)
+    np.testing.assert_allclose(Jc, 2.5 * Jv - Jw, rtol=1e-10, atol=1e-12 * np.max(np.abs(Jc)))
+
+
+def test_complex_step_matches_brute_force_differences(tiny):
+    """Complex-step JVP vs central differences with a scanned step (well-scaled tiny case)."""
+    m = tiny
+    rng = np.random.default_rng(3)
+    n = W.perturbed_populations(m.nstar, rng, 0.1)
+    Jd = OM.initial_J(m)
+    istar = np.argmax(n, axis=1)
+    for trial in range(3):
+        v = rng.normal(size=n.shape) * n
+        ref = jvp_complex(m, n, Jd, v, istar=istar)
+        best = np.inf
+        for h in [1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6]:
+            cd = jvp_fd(m, n, Jd, v, scheme="central", istar=istar, eps=h)
+            best = min(best, np.max(np.abs(cd - ref)) / np.max(np.abs(ref)))
+        assert best < 1e-7
+
+
+def test_block_jacobi_equals_dense_jacobian_diagonal_blocks(tiny):
+    """With J^dagger frozen, P^k is exactly the k-th diagonal block of J_F (Sect. 2.5)."""
+    m = tiny
+    rng = np.random.default_rng(4)
+    n = W.perturbed_populations(m.nstar, rng, 0.3)
+    Jd = OM.initial_J(m) * 0.7
+    res = residual(m, n, Jd, want_lambda=True)
+    P = block_jacobi(m, n, res)
+    Jm = dense_jacobian(m, n, Jd, istar=res.istar)
+    nl = m.nl
+    for k in range(m.nz):
+        blk = Jm[k * nl:(k + 1) * nl, k * nl:(k + 1) * nl]
+        np.testing.assert_allclose(P[k], blk, rtol=1e-9, atol=1e-11 * np.max(np.abs(blk)))
+    # conservation rows: -1 on the own depth, 0 elsewhere
+    for k in range(m.nz):
+        row = Jm[k * nl + res.istar[k]]
+        expect = np.zeros(m.nz * nl)
+        expect[k * nl:(k + 1) * nl] = -1.0
+        np.testing.assert_array_equal(row, expect)
+
+
+def test_dense_jacobian_structure_is_nonlocal(tiny):
+    """Off-diagonal blocks are nonzero (Fig. 1): the radiation couples all depths."""
+    m = tiny
+    n = m.nstar
+    Jm = dense_jacobian(m, n, OM.initial_J(m))
+    nl = m.nl
+    off = Jm[0:nl, (m.nz - 1) * nl:m.nz * nl]
+    assert np.max(np.abs(off)) > 0.0
+
+
+def test_finite_differences_are_less_accurate_than_complex_step(small_ca):
+    """Fig. 2: forward differences with eps_1 / eps_2 lose accuracy, the complex step does not."""
+    m = small_ca
+    n = m.nstar
+    Jd = OM.initial_J(m)
+    res = residual(m, n, Jd, want_lambda=True)
+    P = block_jacobi(m, n, res)
+    nl = m.nl
+    errs = {}
+    for scheme, choice in [("complex", None), ("forward", "eps1"), ("forward", "eps2")]:
+        worst = 0.0
+        for c in range(nl):
+            k = m.nz // 2
+            v = np.zeros_like(n)
+            v[k, c] = 1.0
+            if scheme == "complex":
+                col = jvp_complex(m, n, Jd, v, istar=res.istar)
+            else:
+                col = jvp_fd(m, n, Jd, v, scheme=scheme, choice=choice, F0=res.F, istar=res.istar)
+            ref = P[k][:, c]
+            worst = max(worst, np.max(np.abs(col[k] - ref)) / np.max(np.abs(P[k])))
+        errs[(scheme, choice)] = worst
+    assert errs[("complex", None)] < 1e-10
+    assert errs[("forward", "eps1")] > 1e3 * errs[("complex", None)]
+    assert errs[("forward", "eps2")] > 1e3 * errs[("complex", None)]

@@ -1,0 +1,137 @@
+"""Pins of the oracle solvers: Krylov, Algorithm 2, RH92, dense Newton (no GPU)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import krylov
+from oracle import model as OM
+from oracle.dense import dense_newton
+from oracle.hybrid import hybrid
+from oracle.jfnk import jfnk, zero_radiation_guess
+from oracle.residual import residual
+from oracle.rh92 import rh92
+
+
+def test_gmres_and_bicgstab_solve_linear_systems():
+    rng = np.random.default_rng(0)
+    A = np.eye(60) * 4 + rng.normal(size=(60, 60)) * 0.3
+    b = rng.normal(size=60)
+    x = np.linalg.solve(A, b)
+    g = krylov.gmres(lambda v: A @ v, b, 1e-12, m_max=60)
+    assert g.converged and np.allclose(g.x, x, rtol=1e-9, atol=1e-11)
+    g = krylov.gmres(lambda v: A @ v, b, 1e-12, m_max=7, max_restarts=200)   # restarted
+    assert g.converged and np.allclose(g.x, x, rtol=1e-8, atol=1e-10)
+    bi = krylov.bicgstab(lambda v: A @ v, b, 1e-12)
+    assert bi.converged and np.allclose(bi.x, x, rtol=1e-8, atol=1e-10)
+    # GMRES residual never increases (Sect. 2.3)
+    res = []
+    for m in range(1, 30):
+        r = krylov.gmres(lambda v: A @ v, b, 1e-30, m_max=m, max_restarts=0)
+        res.append(np.linalg.norm(b - A @ r.x))
+    assert all(res[i + 1] <= res[i] * (1 + 1e-12) for i in range(len(res) - 1))
+
+
+@pytest.mark.slow
+def test_sqrt_eps_law_under_depth_refinement():
+    """Isothermal two-level atom: S(0) -> sqrt(eps) B as the depth grid is refined (config 1 physics)."""
+    vals = []
+    for nz in (101, 201, 401):
+        atom = W.two_level_atom(n_nu=21)
+        col = W.two_level_slab(atom, n_depth=nz, tau_max=1e6)
+        m = OM.build_model(atom, col, 3)
+        s = jfnk(m, m.nstar, rtol=1e-4, ftol=1e-9)
+        assert s.converged
+        r = residual(m, s.n, s.J)
+        q0 = m.nq // 2
+        vals.append((r.eta / r.chi)[q0, 0] / m.B[q0, 0] / 1e-2)
+    assert vals[0] < vals[1] < vals[2] < 1.0
+    # first-order convergence in the log-depth step: Richardson extrapolation hits sqrt(eps)
+    extrap = 2 * vals[2] - vals[1]
+    assert abs(extrap - 1.0) < 0.05
+
+
+@pytest.mark.slow
+def test_config1_solution_and_conservation_of_every_iterate():
+    wl = W.config1()
+    m = OM.build_model(wl.atom, wl.columns[0], wl.n_mu)
+    s = jfnk(m, m.nstar, rtol=1e-2)
+    assert s.converged and s.F_norm <= 1e-2 * s.F_norm0
+    for h in s.history:
+        np.testing.assert_allclose(h["n"].sum(axis=1), m.ntot, rtol=1e-12)
+    r = residual(m, s.n, s.J)
+    q0 = m.nq // 2
+    ratio = (r.eta / r.chi)[q0, 0] / m.B[q0, 0]
+    assert 0.006 < ratio < 0.01   # 101 log-spaced depths: ~0.73 sqrt(eps) (see refinement test)
+
+
+def test_lte_limit_when_collisions_dominate():
+    """Departures from Saha-Boltzmann vanish like 1/(collision scale) when collisions dominate."""
+    wl = W.config2(nu_scale=0.1, n_depth=20)
+    rng = np.random.default_rng(5)
+    devs = []
+    for scale in (1e12, 1e16, 1e20):
+        m = OM.build_model(wl.atom, wl.columns[0], 3)
+        m.Cmat *= scale
+        n0 = W.perturbed_populations(m.nstar, rng, 0.3)
+        n0 *= (m.ntot / n0.sum(axis=1))[:, None]
+        s = jfnk(m, n0, rtol=1e-8, ftol=1e-10, J0=m.B)
+        assert s.converged
+        devs.append(np.max(np.abs(s.n / m.nstar - 1.0)))
+    assert 3e2 < devs[0] / devs[1] < 3e4
+    assert devs[2] < 1e-5
+
+
+def test_jfnk_with_tight_krylov_tolerance_follows_dense_newton():
+    """Fig. 4: JFNK approaches Newton-Raphson as r_tol -> 0."""
+    wl = W.tiny_workload(n_depth=6, n_nu_line=9, n_nu_cont=4)
+    m = OM.build_model(wl.atom, wl.columns[0], 2)
+    dn = dense_newton(m, m.nstar, maxiter=4, ftol=0.0)
+    jf = jfnk(m, m.nstar, rtol=1e-12, maxiter=4, ftol=0.0, fdrop=0.0)
+    for it in range(1, 4):
+        np.testing.assert_allclose(jf.history[it]["n"], dn.history[it]["n"], rtol=1e-7)
+
+
+def test_rh92_fixed_point_is_the_jfnk_solution():
+    """RH92's preconditioned rates are exact at n' = n: its fixed point is F(n) = 0 (Sect. 3.3)."""
+    from oracle.rh92 import rh92_update
+    wl = W.config2(nu_scale=0.1, n_depth=30)
+    m = OM.build_model(wl.atom, wl.columns[0], 3)
+    a = jfnk(m, m.nstar, rtol=1e-6, ftol=1e-11)
+    assert a.converged
+    res = residual(m, a.n, a.J, want_lambda=True)
+    np.testing.assert_allclose(rh92_update(m, a.n, res), a.n, rtol=1e-10)
+
+
+@pytest.mark.slow
+def test_rh92_and_jfnk_converge_to_the_same_solution_and_spectrum():
+    """Two-level slab (where RH92 converges): same populations and emergent spectrum (Figs. 9-10)."""
+    wl = W.config1(n_depth=41, n_nu=21)
+    m = OM.build_model(wl.atom, wl.columns[0], 3)
+    a = jfnk(m, m.nstar, rtol=1e-8, ftol=1e-11)
+    b = rh92(m, m.nstar, ftol=1e-11, maxiter=5000)
+    assert a.converged and b.converged
+    assert a.F_calls < b.iterations       # fewer formal solutions for JFNK
+    np.testing.assert_allclose(a.n, b.n, rtol=1e-8)
+    np.testing.assert_allclose(a.I_emergent, b.I_emergent, rtol=1e-8)
+
+
+@pytest.mark.slow
+def test_hybrid_start_converges_for_hydrogen():
+    """Sect. 3.5 hybrid (RH92 then JFNK) on the H I-like atom, where JFNK from LTE fails."""
+    wl = W.config3(nu_scale=0.1, n_depth=60)
+    m = OM.build_model(wl.atom, wl.columns[0], 3)
+    s = hybrid(m, m.nstar, rtol=1e-2)
+    assert s.converged
+    t = hybrid(m, m.nstar, rtol=1e-6, ftol=1e-10)
+    assert t.converged
+    np.testing.assert_allclose(s.n, t.n, rtol=1e-4)
+    for h in t.history:
+        np.testing.assert_allclose(h["n"].sum(axis=1), m.ntot, rtol=1e-11)
+
+
+def test_zero_radiation_guess_solves_its_equations():
+    wl = W.config2(nu_scale=0.1, n_depth=12)
+    m = OM.build_model(wl.atom, wl.columns[0], 2)
+    n = zero_radiation_guess(m)
+    assert np.all(n > 0)
+    np.testing.assert_allclose(n.sum(axis=1), m.ntot, rtol=1e-12)
