@@ -1,0 +1,238 @@
+/*
+ * jfnk.h -- C ABI of the GB300 JFNK NLTE library.
+ *
+ * The library evaluates the residual F(n) of the statistical-equilibrium
+ * equations of one model atom on plane-parallel columns (Arramy, de la Cruz
+ * Rodriguez & Leenaarts 2024, Sect. 2.1, Algorithm 1), its Jacobian-vector
+ * products (Sect. 2.4), the block-Jacobi preconditioner (Sect. 2.5.2), and
+ * solves F(n) = 0 with the Jacobian-free Newton-Krylov method of Algorithm 2,
+ * optionally started by RH92 iterations (Sect. 3.5). Every step of the
+ * computation runs in CUDA kernels built for sm_103a.
+ *
+ * Conventions
+ *   - Every function returns an int status: JFNK_OK (0) or a negative error
+ *     code; jfnk_last_error() returns a thread-local message for the last
+ *     failure on the calling thread.
+ *   - Handles are opaque and owned by the library; free them with the
+ *     matching jfnk_destroy_* call. Descriptor arrays are copied at creation
+ *     time and stay owned by the caller.
+ *   - Population vectors follow the paper's ordering (Sect. 2.1.1):
+ *     n[k * n_levels + l], depth index k = 0 at the top of the column.
+ *     Residuals F, directions v and products J v use the same layout.
+ *   - Mean intensities J[q * n_depth + k] use the atom's union frequency grid
+ *     (ascending, jfnk_atom_frequencies) and the column's depth index.
+ *   - Arrays passed with JFNK_MEM_HOST are host pointers (pageable or pinned)
+ *     and are copied in/out on ``stream``; with JFNK_MEM_DEVICE they are
+ *     device pointers on the context's device, read and written on
+ *     ``stream``. ``stream`` is a cudaStream_t (NULL = legacy default stream).
+ *     Host-memory calls synchronise the stream before returning; device-memory
+ *     calls return after enqueuing unless stated otherwise.
+ *   - cgs units throughout.
+ */
+#ifndef JFNK_H
+#define JFNK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define JFNK_OK            0
+#define JFNK_E_INVALID    -1   /* bad argument or descriptor                  */
+#define JFNK_E_NOMEM      -2   /* device or host allocation failed            */
+#define JFNK_E_CUDA       -3   /* a CUDA runtime call failed                  */
+#define JFNK_E_DIVERGED   -4   /* solver left the domain (negative opacity)   */
+#define JFNK_E_NAN        -5   /* non-finite residual or Krylov quantity      */
+#define JFNK_E_TIMEOUT    -6   /* tick budget exhausted before convergence    */
+#define JFNK_E_MAXITER    -7   /* Newton iteration limit reached              */
+
+#define JFNK_MAX_LEVELS   16   /* N_l limit (levels including continua)       */
+#define JFNK_MAX_MU        8   /* Gauss-Legendre points per hemisphere        */
+#define JFNK_MAX_DEPTH  1024
+
+typedef enum { JFNK_MEM_HOST = 0, JFNK_MEM_DEVICE = 1 } jfnk_mem;
+typedef enum { JFNK_FP64 = 0, JFNK_MIXED = 1 } jfnk_precision;
+typedef enum {
+  JFNK_INIT_LTE = 0,             /* Saha-Boltzmann populations (Sect. 2.2.1)     */
+  JFNK_INIT_USER = 1,            /* n_inout holds the initial guess              */
+  JFNK_INIT_ZERO_RADIATION = 2   /* rate equations with I = 0 (Sect. 2.2.1)      */
+} jfnk_init_kind;
+
+typedef struct jfnk_ctx jfnk_ctx;
+typedef struct jfnk_atom jfnk_atom;
+typedef struct jfnk_atmos jfnk_atmos;
+
+/* Bound-bound transition i -> j (0-based, i < j), Sect. 2.1.1 Eq. Vij.
+ * V_ij = (pi e^2 / m_e c) f phi(nu), phi a Voigt profile of damping a with the
+ * Doppler width of the local temperature and micro-turbulence, renormalised so
+ * that its quadrature sums to one. Collisions: C_ji = 8.63e-6 n_e Upsilon /
+ * (g_j sqrt(T)), or, if eps > 0, C_ji = eps A_ji / ((1 - eps)(1 - exp(-h nu/kT)))
+ * (two-level thermalisation parameter); C_ij by detailed balance.
+ * Frequency grid: n_nu (odd) points, offsets x in reference Doppler widths
+ * dnu_ref = nu_0 vchar / c: x = q_wing u for q_wing <= 2 q_core, otherwise
+ * x = q_wing sinh(beta u)/sinh(beta) with beta = 2 acosh(q_wing/(2 q_core)),
+ * u uniform on [-1, 1]. */
+typedef struct {
+  int i, j;
+  double f;          /* absorption oscillator strength                       */
+  double damping;    /* Voigt damping parameter a                            */
+  double upsilon;    /* effective collision strength                         */
+  double eps;        /* > 0 overrides upsilon (two-level eps law)            */
+  int n_nu;
+  double q_core, q_wing;
+} jfnk_bb_desc;
+
+/* Bound-free transition from bound level i to continuum level j, Eq. Vij2 and
+ * Eq. gij. alpha(nu) = alpha0 (nu_edge / nu)^3 on nu = nu_edge y_max^(s/(n_nu-1)).
+ * Collisional ionisation C_ij = n_e q0 sqrt(T) exp(-(E_j - E_i)/kT),
+ * recombination by detailed balance. */
+typedef struct {
+  int i, j;
+  double alpha0;     /* cross-section at the edge [cm^2]                      */
+  double q0;         /* [cm^3 s^-1 K^-1/2]                                    */
+  int n_nu;
+  double y_max;      /* nu_max / nu_edge                                      */
+} jfnk_bf_desc;
+
+typedef struct {
+  int n_levels;                 /* N_l <= JFNK_MAX_LEVELS                     */
+  const double* E_eV;           /* [n_levels] energies above the ground level */
+  const double* g;              /* [n_levels] statistical weights             */
+  const int* stage;             /* [n_levels] ionisation stage                */
+  int n_bb;
+  const jfnk_bb_desc* bb;
+  int n_bf;
+  const jfnk_bf_desc* bf;
+  double mass_amu;
+  double vchar;                 /* reference velocity of line grids [cm/s]    */
+} jfnk_atom_desc;
+
+/* One column. Background continuum (Sect. 2.1.1, Eqs. chi/eta):
+ * chi_c = kappa(nu) rho, kappa(nu) = kappa min(kappa_max, max(1, (nu/kappa_nu_ref)^kappa_power))
+ * (kappa_power = 0: grey), eta_c = chi_c B_nu(T), chi_sca = sigma_T n_e if
+ * thomson != 0, with the lagged mean intensity J^dagger in the scattering
+ * emissivity. Boundary conditions (Sect. 2.1.2): I = B_nu(T_bottom) entering
+ * at the bottom, I = 0 entering at the top. */
+typedef struct {
+  int n_depth;                  /* 2 <= N_z <= JFNK_MAX_DEPTH                 */
+  const double* z;              /* [n_depth] height, strictly monotonic       */
+  const double* T;
+  const double* ne;
+  const double* ntot;           /* total density of the active atom           */
+  const double* rho;            /* may be NULL when kappa == 0                */
+  const double* vturb;          /* may be NULL (no micro-turbulence) [cm/s]   */
+  double kappa, kappa_nu_ref, kappa_power, kappa_max;
+  int thomson;
+  int n_mu;                     /* Gauss-Legendre points on ]0,1[, 1..JFNK_MAX_MU */
+} jfnk_atmos_desc;
+
+/* Solver options (Algorithm 2; defaults from jfnk_default_options). */
+typedef struct {
+  double ftol;          /* 1/2 ||(n - n_prev)/(n + n_prev)||_inf threshold (1e-4)  */
+  double fdrop;         /* required ||F||_inf drop factor (1e-2)                   */
+  double rtol;          /* Krylov relative tolerance (1e-2)                        */
+  int maxiter;          /* Newton iterations (100)                                 */
+  int krylov_max;       /* GMRES basis size before restart (50, <= 64)             */
+  int max_restarts;     /* GMRES restarts per Newton step (20)                     */
+  int precision;        /* jfnk_precision                                          */
+  int init;             /* jfnk_init_kind                                          */
+  int clamp;            /* per-depth limiting of negative corrections (1)          */
+  int rh92_warmup;      /* > 0: hybrid start, at most this many RH92 iterations    */
+  double rh92_switch;   /* switch to JFNK when the RH92 change is below (1e-2)     */
+  int max_ticks;        /* F-class evaluations allowed per column (20000)          */
+} jfnk_options;
+
+typedef struct {
+  int status;           /* JFNK_OK when converged, else an error code               */
+  int newton_iters;
+  int rh92_iters;
+  int F_calls;          /* F-class evaluations: base F, JVPs and RH92 solutions    */
+  int jvp_calls;
+  double F_norm;        /* final ||F||_inf                                          */
+  double F_norm0;       /* ||F||_inf at the first JFNK base point                   */
+  double dn_norm;       /* last population change                                  */
+  double ray_points;    /* formal-solution ray-points evaluated (F_calls x rays)   */
+} jfnk_stats;
+
+/* ---- context ------------------------------------------------------------ */
+const char* jfnk_last_error(void);
+void jfnk_default_options(jfnk_options* o);
+/* Creates a context on CUDA device ``device``. */
+int jfnk_init(int device, jfnk_ctx** ctx);
+int jfnk_destroy_ctx(jfnk_ctx* ctx);
+
+/* ---- setup (Sect. 2.1, step a0) ------------------------------------------ */
+/* Validates the descriptor and builds the union frequency grid, the transition
+ * windows and their trapezoid quadrature weights. */
+int jfnk_create_atom(jfnk_ctx* ctx, const jfnk_atom_desc* d, jfnk_atom** out);
+int jfnk_destroy_atom(jfnk_atom* a);
+int jfnk_atom_info(const jfnk_atom* a, int* n_levels, int* n_transitions, int* n_nu);
+/* Copies the union frequency grid [n_nu] (Hz) to host memory. */
+int jfnk_atom_frequencies(const jfnk_atom* a, double* nu);
+
+/* Builds the depth-dependent tables of one column on the device: LTE
+ * populations, Voigt profiles, bound-free g_ij, Planck functions, background
+ * and collision rates. Enqueued on the context's internal stream and
+ * synchronised before returning. */
+int jfnk_create_atmosphere(jfnk_ctx* ctx, const jfnk_atom* atom, const jfnk_atmos_desc* d,
+                           jfnk_atmos** out);
+int jfnk_destroy_atmosphere(jfnk_atmos* a);
+/* n_depth, n_nu, n_levels, n_transitions, and ray-points per evaluation. */
+int jfnk_atmos_info(const jfnk_atmos* a, int* n_depth, int* n_nu, int* n_levels,
+                    int* n_transitions, double* ray_points);
+/* Table export for tests: which = 0 LTE populations [nz*nl], 1 Planck B [nq*nz],
+ * 2 collision rates C[k][i][j] [nz*nl*nl], 3 V_t on its window [sum_t w_t * nz]
+ * (transition-major, window-point-major, depth fastest), 4 g_t likewise,
+ * 5 quadrature weights omega_t on the window [sum_t w_t], 6 chi_c [nq*nz],
+ * 7 eta_c [nq*nz]. ``count`` is the capacity of ``out`` in doubles. */
+int jfnk_atmos_table(const jfnk_atmos* a, int which, double* out, size_t count);
+
+/* ---- the hot path --------------------------------------------------------- */
+/* Residual F(n) (Algorithm 1, Eqs. residuals_1/2) with the lagged mean
+ * intensity J_dagger in the background-scattering emissivity. The conservation
+ * row of each depth is the most populated level of n (lowest index on ties).
+ * J_new (nullable) receives the new mean intensity; I_emergent (nullable) the
+ * outgoing intensity at the top [nq * n_mu] (q-major). */
+int jfnk_residual(jfnk_ctx* ctx, const jfnk_atmos* a, int precision,
+                  const double* n, const double* J_dagger, double* F, double* J_new,
+                  double* I_emergent, jfnk_mem where, void* stream);
+
+/* Jacobian-vector product J_F(n) v (Sect. 2.4): exact first-order tangent
+ * propagation through every step of Algorithm 1, the value the complex-step
+ * scheme of Eq. complex converges to as eps -> 0. J_dagger and the
+ * conservation rows are taken at n and not perturbed. */
+int jfnk_jvp(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+             const double* J_dagger, const double* v, double* Jv, jfnk_mem where, void* stream);
+
+/* Block-Jacobi preconditioner P^k = Gamma^k + A^kk with the conservation row
+ * set to -1 (Sect. 2.5.1-2.5.2, first solution), unfactored, P[k][i][j]. */
+int jfnk_block_jacobi(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+                      const double* J_dagger, double* P, jfnk_mem where, void* stream);
+
+/* One RH92 population update (Rybicki & Hummer 1992 with full preconditioning,
+ * the paper's reference method): n_out from the formal solution at n. */
+int jfnk_rh92_update(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+                     const double* J_dagger, double* n_out, double* J_new, jfnk_mem where,
+                     void* stream);
+
+/* Solve F(n) = 0 with Algorithm 2 on the device. n_inout: initial guess when
+ * o->init == JFNK_INIT_USER, solution on return [nz*nl]. J_inout (nullable):
+ * initial J^dagger on input if non-NULL (else B_nu(T)), final mean intensity
+ * on return. Synchronises ``stream`` before returning. */
+int jfnk_solve(jfnk_ctx* ctx, const jfnk_atmos* a, const jfnk_options* o, double* n_inout,
+               double* J_inout, jfnk_stats* stats, jfnk_mem where, void* stream);
+
+/* Solves n_cols independent columns together: every residual of one JFNK
+ * tick (one F-class evaluation per in-flight column) runs in one launch
+ * sequence captured in a CUDA graph. n_inout[c] / J_inout[c] as above (the
+ * J_inout array itself may be NULL). */
+int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols,
+                     const jfnk_options* o, double* const* n_inout, double* const* J_inout,
+                     jfnk_stats* stats, jfnk_mem where, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JFNK_H */

@@ -1,0 +1,520 @@
+// C ABI of the library (include/jfnk.h): contexts, atoms, columns, explicit
+// residual / JVP / preconditioner / RH92 evaluations, and the solvers.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace jfnk {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+Batch::~Batch() {
+  if (graph) cudaGraphExecDestroy(graph);
+  if (h_status) cudaFreeHost(h_status);
+}
+
+// Work buffers and the tick graph of one column, cached in its handle.
+struct SingleWork {
+  std::unique_ptr<Batch> b[2];
+};
+
+static SingleWork* single_work(const jfnk_atmos* a) {
+  return reinterpret_cast<SingleWork*>(a->work);
+}
+
+static int get_single(const jfnk_atmos* a, int mixed, Batch** out) {
+  SingleWork* sw = single_work(a);
+  if (!sw->b[mixed]) {
+    std::unique_ptr<Batch> b(new Batch());
+    std::vector<const AtmosData*> cols{&a->d};
+    int rc = batch_create(b.get(), cols, mixed, kMaxKrylov);
+    if (rc) return rc;
+    sw->b[mixed] = std::move(b);
+  }
+  *out = sw->b[mixed].get();
+  return JFNK_OK;
+}
+
+static int copy_in(void* dst, const void* src, size_t bytes, jfnk_mem where, cudaStream_t s) {
+  JFNK_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                            where == JFNK_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return JFNK_OK;
+}
+
+static int copy_out(void* dst, const void* src, size_t bytes, jfnk_mem where, cudaStream_t s) {
+  JFNK_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                            where == JFNK_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  return JFNK_OK;
+}
+
+static int check_common(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, jfnk_mem where) {
+  if (!ctx || !a) return fail(JFNK_E_INVALID, "context and atmosphere are required");
+  if (a->ctx != ctx) return fail(JFNK_E_INVALID, "atmosphere belongs to another context");
+  if (precision != JFNK_FP64 && precision != JFNK_MIXED) return fail(JFNK_E_INVALID, "unknown precision");
+  if (where != JFNK_MEM_HOST && where != JFNK_MEM_DEVICE) return fail(JFNK_E_INVALID, "unknown memory kind");
+  JFNK_CUDA(cudaSetDevice(ctx->device));
+  return JFNK_OK;
+}
+
+// One explicit evaluation of the single-column batch in mode ``mode``.
+static int explicit_eval(jfnk_ctx* ctx, const jfnk_atmos* a, Batch* b, int mode, const double* n,
+                         const double* Jdag, jfnk_mem where, cudaStream_t s) {
+  const ColDesc& c = b->h_cols[0];
+  const AtmosData& M = a->d;
+  const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
+  int rc;
+  if (n && (rc = copy_in(c.w.n, n, N * 8, where, s))) return rc;
+  if (Jdag) {
+    if ((rc = copy_in(c.w.Jdag, Jdag, QZ * 8, where, s))) return rc;
+  } else {
+    JFNK_CUDA(cudaMemcpyAsync(c.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  if ((rc = batch_set_forced_mode(b, mode, s))) return rc;
+  return launch_evaluation(*b, s);
+}
+
+static void options_to_device(const jfnk_options* o, SolverOpts* so) {
+  so->ftol = o->ftol;
+  so->fdrop = o->fdrop;
+  so->rtol = o->rtol;
+  so->rh92_switch = o->rh92_switch;
+  so->maxiter = o->maxiter;
+  so->krylov_max = o->krylov_max;
+  so->max_restarts = o->max_restarts;
+  so->clamp = o->clamp;
+  so->rh92_warmup = o->rh92_warmup;
+  so->max_ticks = o->max_ticks;
+}
+
+static int validate_options(const jfnk_options* o) {
+  if (!o) return fail(JFNK_E_INVALID, "options are NULL");
+  if (!(o->rtol > 0.0 && o->rtol < 1.0)) return fail(JFNK_E_INVALID, "rtol must be in (0, 1)");
+  if (!(o->ftol >= 0.0) || !(o->fdrop >= 0.0)) return fail(JFNK_E_INVALID, "ftol, fdrop must be >= 0");
+  if (o->krylov_max < 1 || o->krylov_max > kMaxKrylov) return fail(JFNK_E_INVALID, "krylov_max must be in [1, 64]");
+  if (o->maxiter < 1 || o->max_restarts < 0 || o->max_ticks < 1) return fail(JFNK_E_INVALID, "iteration limits must be positive");
+  if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return fail(JFNK_E_INVALID, "unknown precision");
+  if (o->init != JFNK_INIT_LTE && o->init != JFNK_INIT_USER)
+    return fail(JFNK_E_INVALID, "init must be JFNK_INIT_LTE or JFNK_INIT_USER");
+  if (o->rh92_warmup < 0) return fail(JFNK_E_INVALID, "rh92_warmup must be >= 0");
+  return JFNK_OK;
+}
+
+__global__ void k_init_state(SolverState* st, int n, int phase) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  SolverState s{};
+  s.phase = phase;
+  s.status = 1;
+  st[c] = s;
+}
+
+constexpr int kTicksPerGraph = 8;
+
+static int ensure_graph(Batch* b, cudaStream_t s) {
+  if (b->graph) return JFNK_OK;
+  cudaGraph_t g;
+  JFNK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = JFNK_OK;
+  for (int t = 0; t < kTicksPerGraph && !rc; ++t) {
+    rc = launch_evaluation(*b, s);
+    if (!rc) rc = launch_lu(*b, s, true);
+    if (!rc) rc = launch_krylov_step(*b, s);
+  }
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(JFNK_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(JFNK_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->graph_ticks = kTicksPerGraph;
+  if (!b->h_status) JFNK_CUDA(cudaMallocHost(&b->h_status, sizeof(int) * std::max(1, b->ncols)));
+  return JFNK_OK;
+}
+
+// Runs the tick graph until every column has left the running state.
+static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
+  int rc = ensure_graph(b, s);
+  if (rc) return rc;
+  const long max_replays = (long)o->max_ticks / b->graph_ticks + 2;
+  for (long r = 0; r < max_replays; ++r) {
+    JFNK_CUDA(cudaGraphLaunch(b->graph, s));
+    JFNK_CUDA(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s));
+    JFNK_CUDA(cudaStreamSynchronize(s));
+    bool running = false;
+    for (int c = 0; c < b->ncols; ++c) running |= (b->h_status[c] == 1);
+    if (!running) return JFNK_OK;
+  }
+  return JFNK_OK;
+}
+
+static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
+                         const jfnk_options* o, double* const* n_in, double* const* J_in,
+                         jfnk_mem where, cudaStream_t s) {
+  SolverOpts so;
+  options_to_device(o, &so);
+  JFNK_CUDA(cudaMemcpyAsync(b->d_opts, &so, sizeof(so), cudaMemcpyHostToDevice, s));
+  int rc = batch_set_forced_mode(b, -1, s);
+  if (rc) return rc;
+  const int phase = o->rh92_warmup > 0 ? PH_RH92 : PH_BASE;
+  k_init_state<<<(b->ncols + 127) / 128, 128, 0, s>>>(b->d_state, b->ncols, phase);
+  JFNK_CUDA(cudaGetLastError());
+  JFNK_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int) * b->ncols, s));
+  for (int c = 0; c < b->ncols; ++c) {
+    const ColDesc& cd = b->h_cols[c];
+    const AtmosData& M = cols[c]->d;
+    const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
+    if (o->init == JFNK_INIT_USER) {
+      if (!n_in || !n_in[c]) return fail(JFNK_E_INVALID, "JFNK_INIT_USER needs n_inout");
+      if ((rc = copy_in(cd.w.n, n_in[c], N * 8, where, s))) return rc;
+    } else {
+      JFNK_CUDA(cudaMemcpyAsync(cd.w.n, M.tables.nstar, N * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    if (J_in && J_in[c]) {
+      if ((rc = copy_in(cd.w.Jdag, J_in[c], QZ * 8, where, s))) return rc;
+    } else {
+      JFNK_CUDA(cudaMemcpyAsync(cd.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  // mark every column as running for the host poll
+  std::vector<int> ones(b->ncols, 1);
+  JFNK_CUDA(cudaMemcpyAsync(b->d_status, ones.data(), sizeof(int) * b->ncols, cudaMemcpyHostToDevice, s));
+  JFNK_CUDA(cudaStreamSynchronize(s));
+  return JFNK_OK;
+}
+
+static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, double* const* n_out,
+                        double* const* J_out, jfnk_stats* stats, jfnk_mem where, cudaStream_t s,
+                        int* worst) {
+  std::vector<SolverState> st(b->ncols);
+  JFNK_CUDA(cudaMemcpyAsync(st.data(), b->d_state, sizeof(SolverState) * b->ncols, cudaMemcpyDeviceToHost, s));
+  int rc;
+  for (int c = 0; c < b->ncols; ++c) {
+    const ColDesc& cd = b->h_cols[c];
+    const AtmosData& M = cols[c]->d;
+    const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
+    if (n_out && n_out[c] && (rc = copy_out(n_out[c], cd.w.n, N * 8, where, s))) return rc;
+    if (J_out && J_out[c] && (rc = copy_out(J_out[c], cd.w.Jnew, QZ * 8, where, s))) return rc;
+  }
+  JFNK_CUDA(cudaStreamSynchronize(s));
+  *worst = JFNK_OK;
+  for (int c = 0; c < b->ncols; ++c) {
+    const SolverState& x = st[c];
+    int status = x.status == 1 ? JFNK_E_TIMEOUT : x.status;
+    if (stats) {
+      jfnk_stats& S = stats[c];
+      S.status = status;
+      S.newton_iters = x.newton_iter;
+      S.rh92_iters = x.rh92_iter;
+      S.F_calls = x.F_calls;
+      S.jvp_calls = x.jvp_calls;
+      S.F_norm = x.Fnorm;
+      S.F_norm0 = x.F0norm;
+      S.dn_norm = x.err;
+      S.ray_points = (double)x.F_calls * cols[c]->d.ray_points;
+    }
+    if (status != JFNK_OK && *worst == JFNK_OK) *worst = status;
+  }
+  return JFNK_OK;
+}
+
+// Runs ``body`` on the context's stream ordered after ``user``; the user stream
+// waits for the result. Host-memory calls are synchronised.
+template <typename F>
+int on_ctx_stream(jfnk_ctx* ctx, void* user, jfnk_mem where, F body) {
+  cudaStream_t us = reinterpret_cast<cudaStream_t>(user);
+  JFNK_CUDA(cudaEventRecord(ctx->ev_in, us));
+  JFNK_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  int rc = body(ctx->stream);
+  JFNK_CUDA(cudaEventRecord(ctx->ev_out, ctx->stream));
+  JFNK_CUDA(cudaStreamWaitEvent(us, ctx->ev_out, 0));
+  if (rc) return rc;
+  if (where == JFNK_MEM_HOST) JFNK_CUDA(cudaStreamSynchronize(ctx->stream));
+  return JFNK_OK;
+}
+
+}  // namespace jfnk
+
+using namespace jfnk;
+
+extern "C" {
+
+const char* jfnk_last_error(void) { return g_last_error.c_str(); }
+
+void jfnk_default_options(jfnk_options* o) {
+  if (!o) return;
+  o->ftol = 1e-4;
+  o->fdrop = 1e-2;
+  o->rtol = 1e-2;
+  o->maxiter = 100;
+  o->krylov_max = 50;
+  o->max_restarts = 20;
+  o->precision = JFNK_FP64;
+  o->init = JFNK_INIT_LTE;
+  o->clamp = 1;
+  o->rh92_warmup = 0;
+  o->rh92_switch = 1e-2;
+  o->max_ticks = 20000;
+}
+
+int jfnk_init(int device, jfnk_ctx** out) {
+  if (!out) return fail(JFNK_E_INVALID, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  JFNK_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(JFNK_E_INVALID, "no such CUDA device");
+  JFNK_CUDA(cudaSetDevice(device));
+  jfnk_ctx* c = new jfnk_ctx();
+  c->device = device;
+  cudaDeviceProp p;
+  cudaError_t e = cudaGetDeviceProperties(&p, device);
+  if (e != cudaSuccess) { delete c; return fail(JFNK_E_CUDA, cudaGetErrorString(e)); }
+  c->n_sm = p.multiProcessorCount;
+  e = cudaStreamCreateWithFlags(&c->setup_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) { delete c; return fail(JFNK_E_CUDA, cudaGetErrorString(e)); }
+  *out = c;
+  return JFNK_OK;
+}
+
+int jfnk_destroy_ctx(jfnk_ctx* c) {
+  if (!c) return JFNK_OK;
+  cudaSetDevice(c->device);
+  if (c->setup_stream) cudaStreamDestroy(c->setup_stream);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  delete c;
+  return JFNK_OK;
+}
+
+int jfnk_create_atom(jfnk_ctx* ctx, const jfnk_atom_desc* d, jfnk_atom** out) {
+  if (!ctx || !out) return fail(JFNK_E_INVALID, "context and out are required");
+  *out = nullptr;
+  jfnk_atom* a = new jfnk_atom();
+  a->ctx = ctx;
+  int rc = build_atom(d, &a->d);
+  if (rc) { delete a; return rc; }
+  *out = a;
+  return JFNK_OK;
+}
+
+int jfnk_destroy_atom(jfnk_atom* a) {
+  delete a;
+  return JFNK_OK;
+}
+
+int jfnk_atom_info(const jfnk_atom* a, int* n_levels, int* n_transitions, int* n_nu) {
+  if (!a) return fail(JFNK_E_INVALID, "atom is NULL");
+  if (n_levels) *n_levels = a->d.nl;
+  if (n_transitions) *n_transitions = a->d.nt;
+  if (n_nu) *n_nu = a->d.nq;
+  return JFNK_OK;
+}
+
+int jfnk_atom_frequencies(const jfnk_atom* a, double* nu) {
+  if (!a || !nu) return fail(JFNK_E_INVALID, "atom and nu are required");
+  std::memcpy(nu, a->d.nu.data(), sizeof(double) * a->d.nq);
+  return JFNK_OK;
+}
+
+int jfnk_create_atmosphere(jfnk_ctx* ctx, const jfnk_atom* atom, const jfnk_atmos_desc* d,
+                           jfnk_atmos** out) {
+  if (!ctx || !atom || !out) return fail(JFNK_E_INVALID, "context, atom and out are required");
+  if (atom->ctx != ctx) return fail(JFNK_E_INVALID, "atom belongs to another context");
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  JFNK_CUDA(cudaSetDevice(ctx->device));
+  jfnk_atmos* a = new jfnk_atmos();
+  a->ctx = ctx;
+  a->atom = atom;
+  int rc = build_atmosphere(ctx, atom->d, d, &a->d);
+  if (rc) { delete a; return rc; }
+  a->work = new SingleWork();
+  *out = a;
+  return JFNK_OK;
+}
+
+int jfnk_destroy_atmosphere(jfnk_atmos* a) {
+  if (!a) return JFNK_OK;
+  cudaSetDevice(a->ctx->device);
+  delete single_work(a);
+  delete a;
+  return JFNK_OK;
+}
+
+int jfnk_atmos_info(const jfnk_atmos* a, int* n_depth, int* n_nu, int* n_levels, int* n_transitions,
+                    double* ray_points) {
+  if (!a) return fail(JFNK_E_INVALID, "atmosphere is NULL");
+  if (n_depth) *n_depth = a->d.nz;
+  if (n_nu) *n_nu = a->d.nq;
+  if (n_levels) *n_levels = a->d.nl;
+  if (n_transitions) *n_transitions = a->d.nt;
+  if (ray_points) *ray_points = a->d.ray_points;
+  return JFNK_OK;
+}
+
+int jfnk_atmos_table(const jfnk_atmos* a, int which, double* out, size_t count) {
+  if (!a || !out) return fail(JFNK_E_INVALID, "atmosphere and out are required");
+  const AtmosData& M = a->d;
+  const ColTables& T = M.tables;
+  const double* src = nullptr;
+  size_t n = 0;
+  switch (which) {
+    case 0: src = T.nstar; n = (size_t)M.nz * M.nl; break;
+    case 1: src = T.Bn; n = (size_t)M.nq * M.nz; break;
+    case 2: src = T.C; n = (size_t)M.nz * M.nl * M.nl; break;
+    case 3: src = T.V; n = (size_t)M.nwin * M.nz; break;
+    case 4: src = T.G; n = (size_t)M.nwin * M.nz; break;
+    case 5: src = T.t_w; n = (size_t)M.nwin; break;
+    case 6: src = T.chi_c; n = (size_t)M.nq * M.nz; break;
+    case 7: src = T.eta_c; n = (size_t)M.nq * M.nz; break;
+    default: return fail(JFNK_E_INVALID, "unknown table");
+  }
+  if (count < n) return fail(JFNK_E_INVALID, "output buffer too small");
+  JFNK_CUDA(cudaSetDevice(a->ctx->device));
+  JFNK_CUDA(cudaMemcpy(out, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return JFNK_OK;
+}
+
+int jfnk_residual(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+                  const double* J_dagger, double* F, double* J_new, double* I_emergent,
+                  jfnk_mem where, void* stream) {
+  int rc = check_common(ctx, a, precision, where);
+  if (rc) return rc;
+  if (!n || !F) return fail(JFNK_E_INVALID, "n and F are required");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b;
+  if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;
+  return on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = explicit_eval(ctx, a, b, EV_BASE, n, J_dagger, where, s);
+    if (r) return r;
+    const ColDesc& c = b->h_cols[0];
+    const AtmosData& M = a->d;
+    if ((r = copy_out(F, c.w.F, (size_t)M.nz * M.nl * 8, where, s))) return r;
+    if (J_new && (r = copy_out(J_new, c.w.Jnew, (size_t)M.nq * M.nz * 8, where, s))) return r;
+    if (I_emergent && (r = copy_out(I_emergent, c.w.Iem, (size_t)M.nq * M.nmu * 8, where, s))) return r;
+    return 0;
+  });
+}
+
+int jfnk_jvp(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+             const double* J_dagger, const double* v, double* Jv, jfnk_mem where, void* stream) {
+  int rc = check_common(ctx, a, precision, where);
+  if (rc) return rc;
+  if (!n || !v || !Jv) return fail(JFNK_E_INVALID, "n, v and Jv are required");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b;
+  if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;
+  return on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = explicit_eval(ctx, a, b, EV_BASE, n, J_dagger, where, s);   // rates and rows at n
+    if (r) return r;
+    const ColDesc& c = b->h_cols[0];
+    const AtmosData& M = a->d;
+    const size_t N = (size_t)M.nz * M.nl;
+    if ((r = copy_in(c.w.v, v, N * 8, where, s))) return r;
+    if ((r = batch_set_forced_mode(b, EV_TANGENT, s))) return r;
+    if ((r = launch_evaluation(*b, s))) return r;
+    return copy_out(Jv, c.w.dF, N * 8, where, s);
+  });
+}
+
+int jfnk_block_jacobi(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+                      const double* J_dagger, double* P, jfnk_mem where, void* stream) {
+  int rc = check_common(ctx, a, precision, where);
+  if (rc) return rc;
+  if (!n || !P) return fail(JFNK_E_INVALID, "n and P are required");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b;
+  if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;
+  return on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = explicit_eval(ctx, a, b, EV_BASE, n, J_dagger, where, s);
+    if (r) return r;
+    const AtmosData& M = a->d;
+    return copy_out(P, b->h_cols[0].w.P, (size_t)M.nz * M.nl * M.nl * 8, where, s);
+  });
+}
+
+int jfnk_rh92_update(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
+                     const double* J_dagger, double* n_out, double* J_new, jfnk_mem where,
+                     void* stream) {
+  int rc = check_common(ctx, a, precision, where);
+  if (rc) return rc;
+  if (!n || !n_out) return fail(JFNK_E_INVALID, "n and n_out are required");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b;
+  if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;
+  return on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = explicit_eval(ctx, a, b, EV_RH92, n, J_dagger, where, s);
+    if (r) return r;
+    if ((r = launch_rh92_update(*b, s))) return r;
+    const ColDesc& c = b->h_cols[0];
+    const AtmosData& M = a->d;
+    if ((r = copy_out(n_out, c.w.n, (size_t)M.nz * M.nl * 8, where, s))) return r;
+    if (J_new && (r = copy_out(J_new, c.w.Jnew, (size_t)M.nq * M.nz * 8, where, s))) return r;
+    return 0;
+  });
+}
+
+int jfnk_solve(jfnk_ctx* ctx, const jfnk_atmos* a, const jfnk_options* o, double* n_inout,
+               double* J_inout, jfnk_stats* stats, jfnk_mem where, void* stream) {
+  int rc = check_common(ctx, a, o ? o->precision : 0, where);
+  if (rc) return rc;
+  if ((rc = validate_options(o))) return rc;
+  if (!n_inout) return fail(JFNK_E_INVALID, "n_inout is required");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b;
+  if ((rc = get_single(a, o->precision == JFNK_MIXED, &b))) return rc;
+  std::vector<const jfnk_atmos*> cols{a};
+  int worst = JFNK_OK;
+  rc = on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = prepare_solve(b, cols, o, &n_inout, &J_inout, where, s);
+    if (r) return r;
+    if ((r = run_to_completion(b, o, s))) return r;
+    return finish_solve(b, cols, &n_inout, &J_inout, stats, where, s, &worst);
+  });
+  if (rc) return rc;
+  if (worst != JFNK_OK) return fail(worst, "column did not converge (see stats.status)");
+  return JFNK_OK;
+}
+
+int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols_in,
+                     const jfnk_options* o, double* const* n_inout, double* const* J_inout,
+                     jfnk_stats* stats, jfnk_mem where, void* stream) {
+  if (!ctx) return fail(JFNK_E_INVALID, "context is NULL");
+  if (n_cols < 0 || (n_cols > 0 && (!cols_in || !n_inout))) return fail(JFNK_E_INVALID, "bad batch arguments");
+  if (n_cols == 0) return JFNK_OK;
+  int rc = validate_options(o);
+  if (rc) return rc;
+  std::vector<const jfnk_atmos*> cols(cols_in, cols_in + n_cols);
+  std::vector<const AtmosData*> data;
+  for (auto* a : cols) {
+    if ((rc = check_common(ctx, a, o->precision, where))) return rc;
+    data.push_back(&a->d);
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch b;
+  if ((rc = batch_create(&b, data, o->precision == JFNK_MIXED, std::max(o->krylov_max, 1)))) return rc;
+  int worst = JFNK_OK;
+  rc = on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = prepare_solve(&b, cols, o, n_inout, J_inout, where, s);
+    if (r) return r;
+    if ((r = run_to_completion(&b, o, s))) return r;
+    return finish_solve(&b, cols, n_inout, J_inout, stats, where, s, &worst);
+  });
+  if (rc) return rc;
+  if (worst != JFNK_OK) return fail(worst, "some columns did not converge (see stats[].status)");
+  return JFNK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// Shared definitions of the JFNK NLTE library (device structures, constants,
+// error handling). Internal header; the public interface is include/jfnk.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "jfnk.h"
+
+namespace jfnk {
+
+// cgs constants (CODATA 2018)
+constexpr double kH = 6.62607015e-27;
+constexpr double kC = 2.99792458e10;
+constexpr double kKB = 1.380649e-16;
+constexpr double kME = 9.1093837015e-28;
+constexpr double kQE = 4.80320471e-10;
+constexpr double kEV = 1.602176634e-12;
+constexpr double kAMU = 1.66053906660e-24;
+constexpr double kSigmaT = 6.6524587321e-25;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxL = JFNK_MAX_LEVELS;
+constexpr int kMaxMu = JFNK_MAX_MU;
+constexpr int kMaxKrylov = 64;
+constexpr int kMaxT = 32;      // transitions per atom
+
+// Evaluation modes of one F-class pass over a column.
+enum EvalMode : int {
+  EV_SKIP = 0,      // column finished: kernels return immediately
+  EV_BASE = 1,      // F(n), new J, preconditioner coefficients
+  EV_TANGENT = 2,   // J_F(n) v (tangent of every step)
+  EV_RH92 = 3,      // F(n), new J, Lambda_eta (RH92 update afterwards)
+};
+
+// Solver phases of the per-column state machine (one evaluation per tick).
+enum Phase : int {
+  PH_BASE = 0,      // next evaluation: base point of a Newton step
+  PH_JVP = 1,       // next evaluation: J v_j (Arnoldi direction)
+  PH_RESTART = 2,   // next evaluation: J x (GMRES restart residual)
+  PH_RH92 = 3,      // next evaluation: RH92 formal solution
+  PH_DONE = 4,
+};
+
+// Immutable tables of one column (device pointers), built at atmosphere creation.
+struct ColTables {
+  int nz, nq, nl, nt, nmu, nwin;  // nwin = sum over transitions of window points
+  const double* nu;       // [nq]
+  const double* c2;       // [nq] 2 h nu^3 / c^2
+  const double* rw;       // [nq] 4 pi / (h nu)
+  const int* q_off;       // [nq+1] CSR: transitions active at q
+  const int* q_t;         // [q_off[nq]]
+  const int* t_lo;        // [nt]
+  const int* t_up;
+  const int* t_q0;        // first union index of the window
+  const int* t_q1;        // last union index (inclusive)
+  const int* t_base;      // offset of transition t in window-point arrays
+  const double* t_w;      // [nwin] trapezoid weight omega_t(nu_q)
+  const double* V;        // [nwin][nz]
+  const double* G;        // [nwin][nz]
+  const double* dz;       // [nz-1] |z_k - z_{k+1}|
+  const double* mu;       // [nmu]
+  const double* wmu;      // [nmu]
+  const double* chi_c;    // [nq][nz]
+  const double* eta_c;    // [nq][nz]
+  const double* chi_sca;  // [nz]
+  const double* Bn;       // [nq][nz] Planck function
+  const double* C;        // [nz][nl][nl] collision rate i -> j
+  const double* ntot;     // [nz]
+  const double* nstar;    // [nz][nl]
+};
+
+struct SolverOpts {
+  double ftol, fdrop, rtol, rh92_switch;
+  int maxiter, krylov_max, max_restarts, clamp, rh92_warmup, max_ticks;
+};
+
+// Per-column solver state (device memory, written by the Krylov kernel only).
+struct SolverState {
+  int phase;
+  int status;          // 1 running, 0 converged, < 0 error code
+  int newton_iter;
+  int rh92_iter;
+  int j;               // current Arnoldi index
+  int restarts;
+  int F_calls;
+  int jvp_calls;
+  int ticks;
+  int pad;
+  double beta;         // norm of the current restart residual
+  double r0norm;       // norm of the Newton step's initial Krylov residual
+  double F0norm;
+  double Fnorm;
+  double err;
+};
+
+// Work buffers of one column (device pointers). ``real`` buffers hold float in
+// the mixed mode and double in the FP64 mode.
+struct ColWork {
+  double* n;        // [nz][nl] base populations
+  double* v;        // [nz][nl] tangent direction for explicit JVPs
+  double* Jdag;     // [nq][nz]
+  double* Jnew;     // [nq][nz]
+  int* istar;       // [nz]
+  void* chi;        // [nq][nz] real
+  void* S;          // [nq][nz] real (normalised by 2 h nu^3/c^2)
+  void* dchi;       // [nq][nz] real
+  void* dS;         // [nq][nz] real
+  void* H;          // [2 nmu][nq][nz] real: per-ray 1/2 w I  (value)
+  void* dH;         // tangent
+  void* LX;         // per-ray 1/2 w dI^k/dchi^k
+  void* LE;         // per-ray 1/2 w dI^k/deta^k
+  double* J;        // [nq][nz]
+  double* dJ;
+  double* Lchi;
+  double* Leta;
+  double* zeta;     // [nq][nz][nl] beta_j Lchi + gamma_j Leta (preconditioner)
+  double* Rup;      // [nt][nz]
+  double* Rdn;
+  double* dRup;
+  double* dRdn;
+  double* Apart;    // [nt][nz][nl]
+  double* rh;       // [nt][nz][RH_STRIDE] RH92 sums
+  double* F;        // [nz][nl]
+  double* dF;       // [nz][nl]
+  double* P;        // [nz][nl][nl] (LU factors after a base evaluation)
+  int* piv;         // [nz][nl]
+  double* Iem;      // [nq][nmu] emergent intensity
+  // Krylov
+  double* Vb;       // [(kmax+1)][N]
+  double* Hh;       // [(kmax+1)][kmax]
+  double* cs;       // [kmax]
+  double* sn;       // [kmax]
+  double* gv;       // [kmax+1]
+  double* x;        // [N]
+  double* w;        // [N]
+  double* nprev;    // [N]
+  SolverState* st;
+};
+
+struct ColDesc {
+  ColTables t;
+  ColWork w;
+  int forced_mode;   // >= 0: evaluation mode for explicit API calls; < 0: from st->phase
+  int mixed;         // 1: FP32 formal solution (buffers are float)
+};
+
+// RH92 per-transition sums: [0] sum W V Jeff, [1] sum W g V Jeff, [2] sum W U,
+// [3] sum W chi_t Psi eta_bg, [4 + s] sum W chi_t Psi U_s.
+constexpr int kRhFixed = 4;
+constexpr int kRhStride = kRhFixed + kMaxT;
+
+// ---- error handling --------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define JFNK_CUDA(expr)                                                        \
+  do {                                                                         \
+    cudaError_t _e = (expr);                                                   \
+    if (_e != cudaSuccess)                                                     \
+      return ::jfnk::fail(JFNK_E_CUDA, std::string(#expr) + ": " +             \
+                                           cudaGetErrorString(_e));            \
+  } while (0)
+
+// ---- device helpers --------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+}  // namespace jfnk

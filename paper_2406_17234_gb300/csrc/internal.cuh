@@ -1,0 +1,116 @@
+// Host-side objects of the library and the interfaces between its units.
+#pragma once
+
+#include <memory>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace jfnk {
+
+// Bump allocator over one cudaMalloc: callers reserve typed blocks, then
+// allocate once; every block is 256-byte aligned.
+struct DeviceArena {
+  char* base = nullptr;
+  size_t bytes = 0;
+  size_t cursor = 0;
+  void reset() { cursor = 0; }
+  template <typename T>
+  size_t take(size_t count) {
+    size_t off = cursor;
+    cursor += ((count * sizeof(T) + 255) / 256) * 256;
+    if (cursor == off) cursor += 256;
+    return off;
+  }
+  int allocate();
+  void release();
+  template <typename T>
+  T* ptr(size_t off) const {
+    return reinterpret_cast<T*>(base + off);
+  }
+  ~DeviceArena() { release(); }
+};
+
+struct AtomData {
+  int nl = 0, nt = 0, nq = 0, nwin = 0;
+  std::vector<double> E, g;
+  std::vector<int> stage;
+  double mass = 0, vchar = 0;
+  std::vector<jfnk_bb_desc> bb;
+  std::vector<jfnk_bf_desc> bf;
+  std::vector<double> nu;
+  std::vector<int> t_lo, t_up, t_kind, t_idx, t_q0, t_q1, t_base;
+  std::vector<double> t_nu0, t_w;
+  std::vector<int> q_off, q_t;
+};
+
+struct AtmosData {
+  int nz = 0, nq = 0, nl = 0, nt = 0, nmu = 0, nwin = 0;
+  double ray_points = 0;
+  DeviceArena arena;
+  ColTables tables{};
+  std::vector<double> host_t_w;
+};
+
+}  // namespace jfnk
+
+struct jfnk_ctx {
+  int device = 0;
+  int n_sm = 0;
+  cudaStream_t setup_stream = nullptr;
+  cudaStream_t stream = nullptr;      // stream of the evaluations and solves
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::mutex mu;
+};
+
+struct jfnk_atom {
+  jfnk_ctx* ctx;
+  jfnk::AtomData d;
+};
+
+struct jfnk_atmos {
+  jfnk_ctx* ctx;
+  const jfnk_atom* atom;
+  jfnk::AtmosData d;
+  void* work = nullptr;               // cached single-column work buffers
+};
+
+namespace jfnk {
+
+int build_atom(const jfnk_atom_desc* d, AtomData* A);
+int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d, AtmosData* M);
+
+// A batch of columns with their work buffers, resident on the device.
+struct Batch {
+  int ncols = 0;
+  int mixed = 0;
+  int kmax = 0;
+  int max_nz = 0, max_nq = 0, max_nt = 0, max_N = 0, max_nmu = 0;
+  DeviceArena arena;
+  ColDesc* d_cols = nullptr;          // device array [ncols]
+  std::vector<ColDesc> h_cols;        // host mirror
+  SolverState* d_state = nullptr;     // [ncols]
+  int* d_status = nullptr;            // [ncols] copy of st.status for polling
+  SolverOpts* d_opts = nullptr;       // solver options read by the Krylov kernel
+  cudaGraphExec_t graph = nullptr;    // captured tick sequence
+  int graph_ticks = 0;
+  int* h_status = nullptr;            // pinned host mirror of d_status
+  ~Batch();
+};
+
+// Allocates work buffers for columns ``tabs`` (precision: mixed or FP64).
+int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed, int kmax);
+// Launch sequence of one F-class evaluation for every column of the batch.
+int launch_evaluation(const Batch& b, cudaStream_t s);
+// Launch of the Krylov/Newton state machine step.
+int launch_krylov_step(const Batch& b, cudaStream_t s);
+// Sets every column's forced evaluation mode (explicit API calls) or -1.
+int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
+// Conservation rows from the current populations.
+int launch_istar(const Batch& b, cudaStream_t s);
+// Factorisation of the block-Jacobi blocks, in place.
+int launch_lu(const Batch& b, cudaStream_t s, bool factor);
+// RH92 per-depth update from an EV_RH92 evaluation (explicit API path).
+int launch_rh92_update(const Batch& b, cudaStream_t s);
+
+}  // namespace jfnk

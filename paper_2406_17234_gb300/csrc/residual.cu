@@ -1,0 +1,471 @@
+// The residual F(n) of Algorithm 1 and its tangent, for every column of a
+// batch: opacity/emissivity (Eqs. chi, eta), piecewise-linear formal solution
+// along every (nu, mu) ray (Eqs. Iplus/Iminus, App. A), the angle and
+// frequency integrals into radiative rates (Eqs. Rij/Rji), the per-depth
+// assembly with particle conservation (Eqs. residuals_1/2) and the
+// block-Jacobi preconditioner blocks (Sect. 2.5.2).
+//
+// Precision: ``real`` is double in the FP64 mode and float in the mixed mode
+// for chi, S, I and their tangents; every sum over rays and frequencies and
+// everything downstream of the rates is double. Intensities and source
+// functions are carried normalised by 2 h nu^3 / c^2 so that float keeps
+// range.
+#include "internal.cuh"
+
+namespace jfnk {
+
+__device__ __forceinline__ int eval_mode(const ColDesc& cd) {
+  if (cd.forced_mode >= 0) return cd.forced_mode;
+  switch (cd.w.st->phase) {
+    case PH_BASE: return EV_BASE;
+    case PH_JVP:
+    case PH_RESTART: return EV_TANGENT;
+    case PH_RH92: return EV_RH92;
+    default: return EV_SKIP;
+  }
+}
+
+__device__ __forceinline__ const double* tangent_dir(const ColDesc& cd) {
+  if (cd.forced_mode >= 0) return cd.w.v;
+  const int N = cd.t.nz * cd.t.nl;
+  return cd.w.st->phase == PH_RESTART ? cd.w.x : cd.w.Vb + (size_t)cd.w.st->j * N;
+}
+
+// ---------------------------------------------------------------------------
+// a1: opacity and source function per (nu, k), shared by every ray
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void k_opacity(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nl = T.nl;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.nq * nz) return;
+  const int q = i / nz, k = i - q * nz;
+  const double* n = cd.w.n + k * nl;
+  const double c2 = T.c2[q];
+  double chi = T.chi_c[i] + T.chi_sca[k];
+  double eta = T.eta_c[i] + T.chi_sca[k] * cd.w.Jdag[i];
+  const bool tan = (mode == EV_TANGENT);
+  const double* v = tan ? tangent_dir(cd) + k * nl : nullptr;
+  double dchi = 0.0, deta = 0.0;
+  for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+    const int t = T.q_t[s];
+    const int lo = T.t_lo[t], up = T.t_up[t];
+    const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+    const double V = T.V[p], g = T.G[p];
+    chi += V * (n[lo] - g * n[up]);
+    eta += c2 * g * V * n[up];
+    if (tan) {
+      dchi += V * (v[lo] - g * v[up]);
+      deta += c2 * g * V * v[up];
+    }
+  }
+  const double S = eta / chi;
+  reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
+  reinterpret_cast<real*>(cd.w.S)[i] = (real)(S / c2);
+  if (tan) {
+    reinterpret_cast<real*>(cd.w.dchi)[i] = (real)dchi;
+    reinterpret_cast<real*>(cd.w.dS)[i] = (real)((deta - S * dchi) / chi / c2);
+  }
+}
+
+// Piecewise-linear coefficients (App. A.1): e = exp(-x), a = 1 - (1-e)/x,
+// b = (1-e)/x - e and bq = b/x, by Taylor series below x = 0.1 where 1 - e
+// cancels, directly above.
+__device__ __forceinline__ void pl_coef(double x, double& e, double& a, double& b, double& bq) {
+  e = exp(-x);
+  if (x < 0.1) {
+    // a = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!, b = sum (-1)^{n+1} n x^n/(n+1)!
+    double pa = 0.0, pb = 0.0;
+    double fact = 1.0;
+    double ca[14], cb[14];
+    for (int m = 1; m <= 13; ++m) {
+      fact *= (m + 1);
+      double sgn = (m & 1) ? 1.0 : -1.0;
+      ca[m] = sgn / fact;
+      cb[m] = sgn * m / fact;
+    }
+    for (int m = 13; m >= 1; --m) {
+      pa = pa * x + ca[m];
+      pb = pb * x + cb[m];
+    }
+    a = pa * x;
+    bq = pb;
+    b = pb * x;
+  } else {
+    double r = 1.0 / x;
+    double w = (1.0 - e) * r;
+    a = 1.0 - w;
+    b = w - e;
+    bq = b * r;
+  }
+}
+
+__device__ __forceinline__ void pl_coef(float x, float& e, float& a, float& b, float& bq) {
+  e = __expf(-x);
+  if (x < 0.1f) {
+    // five terms of the same series: truncation below 3e-10 relative
+    const float a1 = 0.5f, a2 = -1.0f / 6.0f, a3 = 1.0f / 24.0f, a4 = -1.0f / 120.0f, a5 = 1.0f / 720.0f;
+    const float b1 = 0.5f, b2 = -1.0f / 3.0f, b3 = 1.0f / 8.0f, b4 = -1.0f / 30.0f, b5 = 1.0f / 144.0f;
+    float pa = fmaf(fmaf(fmaf(fmaf(a5, x, a4), x, a3), x, a2), x, a1);
+    float pb = fmaf(fmaf(fmaf(fmaf(b5, x, b4), x, b3), x, b2), x, b1);
+    a = pa * x;
+    bq = pb;
+    b = pb * x;
+  } else {
+    float r = 1.0f / x;
+    float w = (1.0f - e) * r;
+    a = 1.0f - w;
+    b = w - e;
+    bq = b * r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a2: formal solution, one thread per (nu, mu, hemisphere) ray
+// outputs per ray r and depth k: 1/2 w_mu I (value), its tangent, and in
+// base mode the local derivatives dI^k/dchi^k, dI^k/deta^k (App. A.2).
+// Layout of the per-ray outputs: [r][k][q].
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void k_formal(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nmu = T.nmu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq * 2 * nmu) return;
+  const int q = i % nq, r = i / nq;
+  const int up = r < nmu;
+  const int m = up ? r : r - nmu;
+  const real hw = (real)(0.5 * T.wmu[m]);
+  const real inv2mu = (real)(0.5 / T.mu[m]);
+  const real* chi = reinterpret_cast<const real*>(cd.w.chi) + (size_t)q * nz;
+  const real* S = reinterpret_cast<const real*>(cd.w.S) + (size_t)q * nz;
+  const bool tan = (mode == EV_TANGENT);
+  const bool der = (mode == EV_BASE || mode == EV_RH92);
+  const real* dchi = tan ? reinterpret_cast<const real*>(cd.w.dchi) + (size_t)q * nz : nullptr;
+  const real* dS = tan ? reinterpret_cast<const real*>(cd.w.dS) + (size_t)q * nz : nullptr;
+  real* H = reinterpret_cast<real*>(cd.w.H) + (size_t)r * nz * nq + q;
+  real* dH = tan ? reinterpret_cast<real*>(cd.w.dH) + (size_t)r * nz * nq + q : nullptr;
+  real* LX = der ? reinterpret_cast<real*>(cd.w.LX) + (size_t)r * nz * nq + q : nullptr;
+  real* LE = der ? reinterpret_cast<real*>(cd.w.LE) + (size_t)r * nz * nq + q : nullptr;
+  const int k0 = up ? nz - 1 : 0;
+  const int step = up ? -1 : 1;
+  real I = up ? (real)(T.Bn[(size_t)q * nz + nz - 1] / T.c2[q]) : (real)0;
+  real dI = 0;
+  real chi1 = chi[k0], S1 = S[k0];
+  real dchi1 = tan ? dchi[k0] : (real)0, dS1 = tan ? dS[k0] : (real)0;
+  H[(size_t)k0 * nq] = hw * I;
+  if (tan) dH[(size_t)k0 * nq] = 0;
+  if (der) { LX[(size_t)k0 * nq] = 0; LE[(size_t)k0 * nq] = 0; }
+  for (int s = 1; s < nz; ++s) {
+    const int k = k0 + step * s;
+    const int kd = up ? k : k - 1;   // layer index between k and its upstream neighbour
+    const real chi0 = chi[k], S0 = S[k];
+    const real h = (real)T.dz[kd] * inv2mu;
+    const real dtau = h * (chi0 + chi1);
+    real e, a, b, bq;
+    pl_coef(dtau, e, a, b, bq);
+    const real Inew = I * e + a * S0 + b * S1;
+    if (der) {
+      const real common = h * (e * (S1 - I) - (S1 - S0) * bq);
+      LX[(size_t)k * nq] = hw * (-(S0 / chi0) * a + common);
+      LE[(size_t)k * nq] = hw * (a / chi0);
+    }
+    if (tan) {
+      const real dchi0 = dchi[k], dS0 = dS[k];
+      const real ddtau = h * (dchi0 + dchi1);
+      const real dInew = dI * e + ddtau * (e * (S1 - I) - (S1 - S0) * bq) + a * dS0 + b * dS1;
+      dH[(size_t)k * nq] = hw * dInew;
+      dI = dInew;
+      dchi1 = dchi0;
+      dS1 = dS0;
+    }
+    I = Inew;
+    H[(size_t)k * nq] = hw * I;
+    chi1 = chi0;
+    S1 = S0;
+  }
+  if (up && mode != EV_TANGENT) cd.w.Iem[(size_t)q * nmu + m] = (double)I * T.c2[q];
+}
+
+// ---------------------------------------------------------------------------
+// a3 (part 1): sums over the 2 n_mu rays -> J, dJ, Lambda_chi, Lambda_eta
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nr = 2 * T.nmu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // i = k * nq + q
+  if (i >= nq * nz) return;
+  const int k = i / nq, q = i - k * nq;
+  const size_t plane = (size_t)nz * nq;
+  const size_t o = (size_t)q * nz + k;
+  const double c2 = T.c2[q];
+  double s = 0.0;
+  const real* H = reinterpret_cast<const real*>(cd.w.H) + i;
+  for (int r = 0; r < nr; ++r) s += (double)H[r * plane];
+  cd.w.J[o] = s * c2;
+  if (mode == EV_TANGENT) {
+    const real* dH = reinterpret_cast<const real*>(cd.w.dH) + i;
+    double ds = 0.0;
+    for (int r = 0; r < nr; ++r) ds += (double)dH[r * plane];
+    cd.w.dJ[o] = ds * c2;
+  } else {
+    cd.w.Jnew[o] = s * c2;
+    const real* LX = reinterpret_cast<const real*>(cd.w.LX) + i;
+    const real* LE = reinterpret_cast<const real*>(cd.w.LE) + i;
+    double sx = 0.0, se = 0.0;
+    for (int r = 0; r < nr; ++r) {
+      sx += (double)LX[r * plane];
+      se += (double)LE[r * plane];
+    }
+    cd.w.Lchi[o] = sx * c2;   // dJ/dchi in cgs
+    cd.w.Leta[o] = se;        // dJ/deta = a/chi needs no rescaling
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3 (part 2): frequency integrals per (transition, depth); in base mode also
+// the preconditioner sums A^kk_{t, j} = sum_nu W chi_t (beta_j Lchi + gamma_j Leta)
+// and in RH92 mode the sums of the preconditioned rate equations.
+// ---------------------------------------------------------------------------
+__global__ void k_rates(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nl = T.nl, nt = T.nt;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // i = t * nz + k
+  if (i >= nt * nz) return;
+  const int t = i / nz, k = i - t * nz;
+  const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
+  const int lo = T.t_lo[t], upl = T.t_up[t];
+  const double* n = cd.w.n + k * nl;
+  if (mode == EV_TANGENT) {
+    double dRu = 0.0, dRd = 0.0;
+    for (int q = q0; q <= q1; ++q) {
+      const size_t p = (size_t)(base + q - q0);
+      const double W = T.t_w[p] * T.rw[q];
+      const double WV = W * T.V[p * nz + k];
+      const double dJ = cd.w.dJ[(size_t)q * nz + k];
+      dRu += WV * dJ;
+      dRd += WV * T.G[p * nz + k] * dJ;
+    }
+    cd.w.dRup[i] = dRu;
+    cd.w.dRdn[i] = dRd;
+    return;
+  }
+  double Ru = 0.0, Rd = 0.0;
+  double A[kMaxL];
+  double rhs[kRhStride];
+  const bool base_mode = (mode == EV_BASE);
+  const bool rh = (mode == EV_RH92);
+  const int nrh = kRhFixed + nt;
+  for (int j = 0; j < nl; ++j) A[j] = 0.0;
+  if (rh)
+    for (int j = 0; j < nrh; ++j) rhs[j] = 0.0;
+  for (int q = q0; q <= q1; ++q) {
+    const size_t p = (size_t)(base + q - q0);
+    const double W = T.t_w[p] * T.rw[q];
+    const double V = T.V[p * nz + k], g = T.G[p * nz + k];
+    const size_t o = (size_t)q * nz + k;
+    const double J = cd.w.J[o];
+    const double c2 = T.c2[q];
+    Ru += W * V * J;
+    Rd += W * g * V * (c2 + J);
+    const double chi_t = V * (n[lo] - g * n[upl]);
+    if (base_mode) {
+      double zeta[kMaxL];
+      for (int j = 0; j < nl; ++j) zeta[j] = 0.0;
+      const double Lx = cd.w.Lchi[o], Le = cd.w.Leta[o];
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        const double Vs = T.V[ps], gs = T.G[ps];
+        zeta[T.t_lo[ts]] += Vs * Lx;                          // beta_j (Sect. 2.5.1, read from Eq. chi)
+        zeta[T.t_up[ts]] += -gs * Vs * Lx + c2 * gs * Vs * Le;  // and gamma_j (Eq. der_eta_n)
+      }
+      const double Wc = W * chi_t;
+      for (int j = 0; j < nl; ++j) A[j] += Wc * zeta[j];
+    }
+    if (rh) {
+      // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
+      const double Le = cd.w.Leta[o];
+      // eta(n) at this (q, k): background + lines
+      double eta_bg = T.eta_c[o] + T.chi_sca[k] * cd.w.Jdag[o];
+      double eta_l = 0.0;
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
+      }
+      const double Jeff = J - Le * (eta_bg + eta_l);
+      rhs[0] += W * V * Jeff;
+      rhs[1] += W * g * V * Jeff;
+      rhs[2] += W * c2 * g * V;
+      const double wcp = W * chi_t * Le;
+      rhs[3] += wcp * eta_bg;
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        rhs[kRhFixed + ts] += wcp * c2 * T.G[ps] * T.V[ps];
+      }
+    }
+  }
+  cd.w.Rup[i] = Ru;
+  cd.w.Rdn[i] = Rd;
+  if (base_mode)
+    for (int j = 0; j < nl; ++j) cd.w.Apart[(size_t)i * nl + j] = A[j];
+  if (rh)
+    for (int j = 0; j < nrh; ++j) cd.w.rh[(size_t)i * kRhStride + j] = rhs[j];
+}
+
+// ---------------------------------------------------------------------------
+// a4: per-depth assembly of F (or J_F v) and, in base mode, of P^k
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nl = T.nl, nt = T.nt;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nz) return;
+  const double* n = cd.w.n + k * nl;
+  const double* C = T.C + (size_t)k * nl * nl;
+  if (mode != EV_TANGENT) {
+    // conservation row at the most populated level (lowest index on ties)
+    int is = 0;
+    for (int l = 1; l < nl; ++l)
+      if (n[l] > n[is]) is = l;
+    cd.w.istar[k] = is;
+  }
+  const int is = cd.w.istar[k];
+  if (mode == EV_TANGENT) {
+    const double* v = tangent_dir(cd) + k * nl;
+    double dF[kMaxL];
+    for (int l = 0; l < nl; ++l) dF[l] = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const int lo = T.t_lo[t], up = T.t_up[t];
+      const size_t o = (size_t)t * nz + k;
+      const double dk = v[lo] * (C[lo * nl + up] + cd.w.Rup[o]) + n[lo] * cd.w.dRup[o] -
+                        v[up] * (C[up * nl + lo] + cd.w.Rdn[o]) - n[up] * cd.w.dRdn[o];
+      dF[lo] += dk;
+      dF[up] -= dk;
+    }
+    double sv = 0.0;
+    for (int l = 0; l < nl; ++l) sv += v[l];
+    dF[is] = -sv;
+    for (int l = 0; l < nl; ++l) cd.w.dF[k * nl + l] = dF[l];
+    return;
+  }
+  double F[kMaxL];
+  for (int l = 0; l < nl; ++l) F[l] = 0.0;
+  double* P = cd.w.P + (size_t)k * nl * nl;
+  const bool base_mode = (mode == EV_BASE);
+  if (base_mode)
+    for (int l = 0; l < nl * nl; ++l) P[l] = 0.0;
+  for (int t = 0; t < nt; ++t) {
+    const int lo = T.t_lo[t], up = T.t_up[t];
+    const size_t o = (size_t)t * nz + k;
+    const double urate = C[lo * nl + up] + cd.w.Rup[o];
+    const double drate = C[up * nl + lo] + cd.w.Rdn[o];
+    const double kap = n[lo] * urate - n[up] * drate;
+    F[lo] += kap;
+    F[up] -= kap;
+    if (base_mode) {
+      // Gamma^k (Sect. 2.5.1) and A^kk rows of the two levels of t
+      P[lo * nl + lo] += urate;
+      P[lo * nl + up] -= drate;
+      P[up * nl + lo] -= urate;
+      P[up * nl + up] += drate;
+      const double* Ap = cd.w.Apart + o * nl;
+      for (int j = 0; j < nl; ++j) {
+        P[lo * nl + j] += Ap[j];
+        P[up * nl + j] -= Ap[j];
+      }
+    }
+  }
+  double sn = 0.0;
+  for (int l = 0; l < nl; ++l) sn += n[l];
+  F[is] = T.ntot[k] - sn;
+  for (int l = 0; l < nl; ++l) cd.w.F[k * nl + l] = F[l];
+  if (base_mode)
+    for (int j = 0; j < nl; ++j) P[is * nl + j] = -1.0;
+}
+
+// LU factorisation with partial pivoting of every P^k, in place.
+__global__ void k_lu(const ColDesc* __restrict__ cols, int only_base) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (only_base && eval_mode(cd) != EV_BASE) return;
+  const int nz = cd.t.nz, nl = cd.t.nl;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nz) return;
+  double* A = cd.w.P + (size_t)k * nl * nl;
+  int* piv = cd.w.piv + k * nl;
+  for (int c = 0; c < nl; ++c) {
+    int pr = c;
+    double best = fabs(A[c * nl + c]);
+    for (int r = c + 1; r < nl; ++r) {
+      double vv = fabs(A[r * nl + c]);
+      if (vv > best) { best = vv; pr = r; }
+    }
+    piv[c] = pr;
+    if (pr != c)
+      for (int j = 0; j < nl; ++j) {
+        double tmp = A[c * nl + j];
+        A[c * nl + j] = A[pr * nl + j];
+        A[pr * nl + j] = tmp;
+      }
+    const double d = A[c * nl + c];
+    for (int r = c + 1; r < nl; ++r) {
+      const double f = A[r * nl + c] / d;
+      A[r * nl + c] = f;
+      for (int j = c + 1; j < nl; ++j) A[r * nl + j] -= f * A[c * nl + j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int launch_evaluation(const Batch& b, cudaStream_t s) {
+  const int nc = b.ncols;
+  if (nc == 0) return JFNK_OK;
+  const int tb = 256;
+  dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
+  dim3 g_ray((b.max_nq * 2 * b.max_nmu + 127) / 128, nc);
+  dim3 g_tk((b.max_nt * b.max_nz + 127) / 128, nc);
+  dim3 g_k((b.max_nz + 63) / 64, nc);
+  if (b.mixed) {
+    k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+    k_formal<float><<<g_ray, 128, 0, s>>>(b.d_cols);
+    k_ray_sum<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+  } else {
+    k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+    k_formal<double><<<g_ray, 128, 0, s>>>(b.d_cols);
+    k_ray_sum<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+  }
+  k_rates<<<g_tk, 128, 0, s>>>(b.d_cols);
+  k_assemble<<<g_k, 64, 0, s>>>(b.d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+int launch_lu(const Batch& b, cudaStream_t s, bool only_base) {
+  dim3 g_k((b.max_nz + 63) / 64, b.ncols);
+  k_lu<<<g_k, 64, 0, s>>>(b.d_cols, only_base ? 1 : 0);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+}  // namespace jfnk

@@ -1,0 +1,520 @@
+// On-device JFNK driver (Algorithm 2) and RH92 warm start, as a per-column
+// state machine: every tick performs one F-class evaluation per in-flight
+// column (a base evaluation, a Jacobian-vector product, a GMRES restart
+// product or an RH92 formal solution) followed by one Krylov/Newton step,
+// so that columns at different stages of their solves share each launch.
+// A tick sequence is captured once in a CUDA graph and replayed until every
+// column has finished; the host only polls a status word per column.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace jfnk {
+
+int DeviceArena::allocate() {
+  release();
+  bytes = cursor;
+  if (bytes == 0) return JFNK_OK;
+  cudaError_t e = cudaMalloc(&base, bytes);
+  if (e != cudaSuccess) {
+    base = nullptr;
+    return fail(JFNK_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return JFNK_OK;
+}
+
+void DeviceArena::release() {
+  if (base) cudaFree(base);
+  base = nullptr;
+  bytes = 0;
+}
+
+int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed, int kmax) {
+  const int nc = (int)cols.size();
+  b->ncols = nc;
+  b->mixed = mixed;
+  b->kmax = kmax;
+  b->max_nz = b->max_nq = b->max_nt = b->max_N = b->max_nmu = 0;
+  DeviceArena& ar = b->arena;
+  ar.reset();
+  const size_t rs = mixed ? sizeof(float) : sizeof(double);
+  struct Offs {
+    size_t n, v, Jdag, Jnew, istar, chi, S, dchi, dS, H, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
+        dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x, w, nprev;
+  };
+  std::vector<Offs> off(nc);
+  for (int c = 0; c < nc; ++c) {
+    const AtmosData& M = *cols[c];
+    const size_t nz = M.nz, nq = M.nq, nl = M.nl, nt = M.nt, nmu = M.nmu, N = nz * nl;
+    b->max_nz = std::max(b->max_nz, (int)nz);
+    b->max_nq = std::max(b->max_nq, (int)nq);
+    b->max_nt = std::max(b->max_nt, (int)nt);
+    b->max_N = std::max(b->max_N, (int)N);
+    b->max_nmu = std::max(b->max_nmu, (int)nmu);
+    Offs& o = off[c];
+    o.n = ar.take<double>(N); o.v = ar.take<double>(N);
+    o.Jdag = ar.take<double>(nq * nz); o.Jnew = ar.take<double>(nq * nz);
+    o.istar = ar.take<int>(nz);
+    o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<char>(rs * nq * nz);
+    o.dchi = ar.take<char>(rs * nq * nz); o.dS = ar.take<char>(rs * nq * nz);
+    o.H = ar.take<char>(rs * 2 * nmu * nq * nz); o.dH = ar.take<char>(rs * 2 * nmu * nq * nz);
+    o.LX = ar.take<char>(rs * 2 * nmu * nq * nz); o.LE = ar.take<char>(rs * 2 * nmu * nq * nz);
+    o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(nq * nz);
+    o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
+    o.Rup = ar.take<double>(nt * nz); o.Rdn = ar.take<double>(nt * nz);
+    o.dRup = ar.take<double>(nt * nz); o.dRdn = ar.take<double>(nt * nz);
+    o.Apart = ar.take<double>(nt * nz * nl);
+    o.rh = ar.take<double>(nt * nz * kRhStride);
+    o.F = ar.take<double>(N); o.dF = ar.take<double>(N);
+    o.P = ar.take<double>(nz * nl * nl); o.piv = ar.take<int>(nz * nl);
+    o.Iem = ar.take<double>(nq * nmu);
+    o.Vb = ar.take<double>((kmax + 1) * N); o.Hh = ar.take<double>((kmax + 1) * kmax);
+    o.cs = ar.take<double>(kmax); o.sn = ar.take<double>(kmax); o.gv = ar.take<double>(kmax + 1);
+    o.x = ar.take<double>(N); o.w = ar.take<double>(N); o.nprev = ar.take<double>(N);
+  }
+  size_t o_cols = ar.take<ColDesc>(nc);
+  size_t o_state = ar.take<SolverState>(nc);
+  size_t o_status = ar.take<int>(nc);
+  size_t o_opts = ar.take<SolverOpts>(1);
+  int rc = ar.allocate();
+  if (rc) return rc;
+  b->h_cols.resize(nc);
+  b->d_cols = ar.ptr<ColDesc>(o_cols);
+  b->d_state = ar.ptr<SolverState>(o_state);
+  b->d_status = ar.ptr<int>(o_status);
+  b->d_opts = ar.ptr<SolverOpts>(o_opts);
+  for (int c = 0; c < nc; ++c) {
+    const Offs& o = off[c];
+    ColDesc& d = b->h_cols[c];
+    d.t = cols[c]->tables;
+    d.forced_mode = -1;
+    d.mixed = mixed;
+    ColWork& w = d.w;
+    w.n = ar.ptr<double>(o.n); w.v = ar.ptr<double>(o.v);
+    w.Jdag = ar.ptr<double>(o.Jdag); w.Jnew = ar.ptr<double>(o.Jnew);
+    w.istar = ar.ptr<int>(o.istar);
+    w.chi = ar.ptr<void>(o.chi); w.S = ar.ptr<void>(o.S);
+    w.dchi = ar.ptr<void>(o.dchi); w.dS = ar.ptr<void>(o.dS);
+    w.H = ar.ptr<void>(o.H); w.dH = ar.ptr<void>(o.dH);
+    w.LX = ar.ptr<void>(o.LX); w.LE = ar.ptr<void>(o.LE);
+    w.J = ar.ptr<double>(o.J); w.dJ = ar.ptr<double>(o.dJ);
+    w.Lchi = ar.ptr<double>(o.Lchi); w.Leta = ar.ptr<double>(o.Leta);
+    w.zeta = nullptr;
+    w.Rup = ar.ptr<double>(o.Rup); w.Rdn = ar.ptr<double>(o.Rdn);
+    w.dRup = ar.ptr<double>(o.dRup); w.dRdn = ar.ptr<double>(o.dRdn);
+    w.Apart = ar.ptr<double>(o.Apart); w.rh = ar.ptr<double>(o.rh);
+    w.F = ar.ptr<double>(o.F); w.dF = ar.ptr<double>(o.dF);
+    w.P = ar.ptr<double>(o.P); w.piv = ar.ptr<int>(o.piv); w.Iem = ar.ptr<double>(o.Iem);
+    w.Vb = ar.ptr<double>(o.Vb); w.Hh = ar.ptr<double>(o.Hh);
+    w.cs = ar.ptr<double>(o.cs); w.sn = ar.ptr<double>(o.sn); w.gv = ar.ptr<double>(o.gv);
+    w.x = ar.ptr<double>(o.x); w.w = ar.ptr<double>(o.w); w.nprev = ar.ptr<double>(o.nprev);
+    w.st = b->d_state + c;
+  }
+  JFNK_CUDA(cudaMemcpy(b->d_cols, b->h_cols.data(), nc * sizeof(ColDesc), cudaMemcpyHostToDevice));
+  JFNK_CUDA(cudaMemset(b->d_state, 0, nc * sizeof(SolverState)));
+  return JFNK_OK;
+}
+
+__global__ void k_set_forced(ColDesc* cols, int mode) { cols[blockIdx.x].forced_mode = mode; }
+
+int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s) {
+  for (auto& c : b->h_cols) c.forced_mode = mode;
+  k_set_forced<<<b->ncols, 1, 0, s>>>(b->d_cols, mode);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// block reductions
+// ---------------------------------------------------------------------------
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < nw; ++i) r += sh[i];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = sh[0];
+  for (int i = 1; i < nw; ++i) r = fmax(r, sh[i]);
+  __syncthreads();
+  return r;
+}
+
+// x <- P^{-1} x for the nl-vector of one depth (LU with row interchanges).
+__device__ void lu_solve(const double* LU, const int* piv, double* x, int nl) {
+  for (int c = 0; c < nl; ++c) {
+    const int p = piv[c];
+    if (p != c) { double t = x[c]; x[c] = x[p]; x[p] = t; }
+  }
+  for (int r = 1; r < nl; ++r) {
+    double s = x[r];
+    for (int c = 0; c < r; ++c) s -= LU[r * nl + c] * x[c];
+    x[r] = s;
+  }
+  for (int r = nl - 1; r >= 0; --r) {
+    double s = x[r];
+    for (int c = r + 1; c < nl; ++c) s -= LU[r * nl + c] * x[c];
+    x[r] = s / LU[r * nl + r];
+  }
+}
+
+// Dense solve with partial pivoting of one small system (RH92 per depth).
+__device__ bool small_solve(double* A, double* b, int nl) {
+  for (int c = 0; c < nl; ++c) {
+    int pr = c;
+    double best = fabs(A[c * nl + c]);
+    for (int r = c + 1; r < nl; ++r)
+      if (fabs(A[r * nl + c]) > best) { best = fabs(A[r * nl + c]); pr = r; }
+    if (!(best > 0.0)) return false;
+    if (pr != c) {
+      for (int j = 0; j < nl; ++j) { double t = A[c * nl + j]; A[c * nl + j] = A[pr * nl + j]; A[pr * nl + j] = t; }
+      double t = b[c]; b[c] = b[pr]; b[pr] = t;
+    }
+    for (int r = c + 1; r < nl; ++r) {
+      double f = A[r * nl + c] / A[c * nl + c];
+      for (int j = c; j < nl; ++j) A[r * nl + j] -= f * A[c * nl + j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = nl - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int j = r + 1; j < nl; ++j) s -= A[r * nl + j] * b[j];
+    b[r] = s / A[r * nl + r];
+  }
+  return true;
+}
+
+// RH92 update of depth k from the sums of an EV_RH92 evaluation; returns the
+// population change measure of the depth (or NaN on a singular system).
+__device__ double rh92_depth(const ColDesc& cd, int k) {
+  const ColTables& T = cd.t;
+  const int nl = T.nl, nt = T.nt, nz = T.nz;
+  double M[kMaxL * kMaxL], c0[kMaxL];
+  for (int i = 0; i < nl * nl; ++i) M[i] = 0.0;
+  for (int i = 0; i < nl; ++i) c0[i] = 0.0;
+  const double* C = T.C + (size_t)k * nl * nl;
+  for (int t = 0; t < nt; ++t) {
+    const int lo = T.t_lo[t], up = T.t_up[t];
+    const double* r = cd.w.rh + ((size_t)t * nz + k) * kRhStride;
+    double coef[kMaxL];
+    for (int j = 0; j < nl; ++j) coef[j] = 0.0;
+    coef[lo] += r[0] + C[lo * nl + up];
+    coef[up] -= r[1] + r[2] + C[up * nl + lo];
+    for (int s = 0; s < nt; ++s) coef[T.t_up[s]] += r[kRhFixed + s];
+    for (int j = 0; j < nl; ++j) {
+      M[lo * nl + j] += coef[j];
+      M[up * nl + j] -= coef[j];
+    }
+    c0[lo] += r[3];
+    c0[up] -= r[3];
+  }
+  const int is = cd.w.istar[k];
+  double rhs[kMaxL];
+  for (int i = 0; i < nl; ++i) rhs[i] = -c0[i];
+  for (int j = 0; j < nl; ++j) M[is * nl + j] = 1.0;
+  rhs[is] = T.ntot[k];
+  if (!small_solve(M, rhs, nl)) return nan("");
+  double* n = cd.w.n + k * nl;
+  double err = 0.0;
+  for (int l = 0; l < nl; ++l) {
+    err = fmax(err, 0.5 * fabs((rhs[l] - n[l]) / (rhs[l] + n[l])));
+    n[l] = rhs[l];
+  }
+  return err;
+}
+
+// ---------------------------------------------------------------------------
+// Krylov / Newton step: one CTA per column
+// ---------------------------------------------------------------------------
+__device__ void apply_pinv(const ColDesc& cd, const double* in, double sign_in, const double* in2,
+                           double sign_in2, double* out) {
+  // out = P^{-1} (sign_in in + sign_in2 in2), depth by depth
+  const int nz = cd.t.nz, nl = cd.t.nl;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    double x[kMaxL];
+    for (int l = 0; l < nl; ++l) {
+      x[l] = sign_in * in[k * nl + l];
+      if (in2) x[l] += sign_in2 * in2[k * nl + l];
+    }
+    lu_solve(cd.w.P + (size_t)k * nl * nl, cd.w.piv + k * nl, x, nl);
+    for (int l = 0; l < nl; ++l) out[k * nl + l] = x[l];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_krylov(const ColDesc* __restrict__ cols,
+                                                const SolverOpts* __restrict__ opts,
+                                                int* status_out) {
+  const ColDesc& cd = cols[blockIdx.x];
+  const SolverOpts o = *opts;
+  SolverState* st = cd.w.st;
+  __shared__ double sh[32];
+  __shared__ double s_h[kMaxKrylov + 1];
+  __shared__ double s_y[kMaxKrylov];
+  __shared__ int s_next;      // decision broadcast
+  __shared__ double s_val;
+  const int phase = st->phase;
+  if (phase == PH_DONE) return;
+  const int nz = cd.t.nz, nl = cd.t.nl, N = nz * nl;
+  const int kmax = o.krylov_max;
+  double* w = cd.w.w;
+  double* x = cd.w.x;
+  double* Vb = cd.w.Vb;
+  enum { NX_NONE, NX_NEWTON, NX_START_GMRES, NX_DONE };
+  int next = NX_NONE;
+  double start_beta = 0.0;
+
+  if (phase == PH_RH92) {
+    double err = 0.0;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+      double e = rh92_depth(cd, k);
+      err = (e == e) ? fmax(err, e) : INFINITY;
+    }
+    err = block_max(err, sh);
+    for (int i = threadIdx.x; i < cd.t.nq * nz; i += blockDim.x) cd.w.Jdag[i] = cd.w.Jnew[i];
+    if (threadIdx.x == 0) {
+      st->F_calls++;
+      st->ticks++;
+      st->rh92_iter++;
+      st->err = err;
+      if (!(err < INFINITY)) { st->status = JFNK_E_NAN; st->phase = PH_DONE; }
+      else if (err < o.rh92_switch || st->rh92_iter >= o.rh92_warmup) st->phase = PH_BASE;
+      else if (st->ticks >= o.max_ticks) { st->status = JFNK_E_TIMEOUT; st->phase = PH_DONE; }
+      status_out[blockIdx.x] = st->status;
+    }
+    return;
+  }
+
+  if (phase == PH_BASE) {
+    double fm = 0.0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double f = cd.w.F[i];
+      if (!(fabs(f) < INFINITY)) bad = true;
+      fm = fmax(fm, fabs(f));
+    }
+    fm = block_max(bad ? INFINITY : fm, sh);
+    if (threadIdx.x == 0) {
+      st->F_calls++;
+      st->ticks++;
+      st->Fnorm = fm;
+      int nx = NX_START_GMRES;
+      if (!(fm < INFINITY)) { st->status = JFNK_E_NAN; nx = NX_DONE; }
+      else if (st->newton_iter == 0) st->F0norm = fm;
+      else if (st->err <= o.ftol && fm <= o.fdrop * st->F0norm) { st->status = JFNK_OK; nx = NX_DONE; }
+      if (nx != NX_DONE && st->newton_iter >= o.maxiter) { st->status = JFNK_E_MAXITER; nx = NX_DONE; }
+      if (nx != NX_DONE && st->ticks >= o.max_ticks) { st->status = JFNK_E_TIMEOUT; nx = NX_DONE; }
+      s_next = nx;
+    }
+    __syncthreads();
+    next = s_next;
+    if (next == NX_DONE) {
+      if (threadIdx.x == 0) { st->phase = PH_DONE; status_out[blockIdx.x] = st->status; }
+      return;
+    }
+    // r0 = -P^{-1} F (x0 = 0)
+    apply_pinv(cd, cd.w.F, -1.0, nullptr, 0.0, w);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = 0.0;
+    __syncthreads();
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) ss += w[i] * w[i];
+    double beta = sqrt(block_sum(ss, sh));
+    if (threadIdx.x == 0) {
+      st->r0norm = beta;
+      st->restarts = 0;
+    }
+    next = NX_START_GMRES;
+    if (!(beta > 0.0)) {
+      // F is exactly zero: nothing to correct
+      if (threadIdx.x == 0) { st->status = (beta == 0.0) ? JFNK_OK : JFNK_E_NAN; st->phase = PH_DONE; status_out[blockIdx.x] = st->status; }
+      return;
+    }
+    start_beta = beta;
+  } else {
+    // a Jacobian-vector product J u is in dF (u = V_j or u = x)
+    if (threadIdx.x == 0) { st->F_calls++; st->jvp_calls++; st->ticks++; }
+    if (phase == PH_RESTART) {
+      apply_pinv(cd, cd.w.F, -1.0, cd.w.dF, -1.0, w);   // r = P^{-1}(-F - J x)
+      __syncthreads();
+      double ss = 0.0;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) ss += w[i] * w[i];
+      double beta = sqrt(block_sum(ss, sh));
+      if (threadIdx.x == 0) {
+        if (!(beta == beta)) { st->status = JFNK_E_NAN; s_next = NX_DONE; }
+        else if (beta < o.rtol * st->r0norm) s_next = NX_NEWTON;
+        else { st->restarts++; s_next = NX_START_GMRES; }
+        s_val = beta;
+      }
+      __syncthreads();
+      next = s_next;
+      start_beta = s_val;
+      if (next == NX_DONE) {
+        if (threadIdx.x == 0) { st->phase = PH_DONE; status_out[blockIdx.x] = st->status; }
+        return;
+      }
+    } else {
+      const int j = st->j;
+      apply_pinv(cd, cd.w.dF, 1.0, nullptr, 0.0, w);
+      __syncthreads();
+      // classical Gram-Schmidt, twice (CGS2)
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) s_h[i] = 0.0;
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i = wid; i <= j; i += nwarp) {
+          const double* vi = Vb + (size_t)i * N;
+          double s = 0.0;
+          for (int e = lane; e < N; e += 32) s += vi[e] * w[e];
+          s = warp_sum(s);
+          if (lane == 0) s_y[i] = s;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < N; e += blockDim.x) {
+          double acc = w[e];
+          for (int i = 0; i <= j; ++i) acc -= s_y[i] * Vb[(size_t)i * N + e];
+          w[e] = acc;
+        }
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_h[i] += s_y[i];
+        __syncthreads();
+      }
+      double ss = 0.0;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) ss += w[i] * w[i];
+      const double hnext = sqrt(block_sum(ss, sh));
+      if (threadIdx.x == 0) {
+        double* Hh = cd.w.Hh;
+        double* cs = cd.w.cs;
+        double* sn = cd.w.sn;
+        double* gv = cd.w.gv;
+        for (int i = 0; i <= j; ++i) Hh[i * kmax + j] = s_h[i];
+        Hh[(j + 1) * kmax + j] = hnext;
+        for (int i = 0; i < j; ++i) {   // previous Givens rotations
+          double a = Hh[i * kmax + j], bb = Hh[(i + 1) * kmax + j];
+          Hh[i * kmax + j] = cs[i] * a + sn[i] * bb;
+          Hh[(i + 1) * kmax + j] = -sn[i] * a + cs[i] * bb;
+        }
+        double a = Hh[j * kmax + j], bb = Hh[(j + 1) * kmax + j];
+        double rr = hypot(a, bb);
+        cs[j] = rr == 0.0 ? 1.0 : a / rr;
+        sn[j] = rr == 0.0 ? 0.0 : bb / rr;
+        Hh[j * kmax + j] = rr;
+        Hh[(j + 1) * kmax + j] = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        const double resid = fabs(gv[j + 1]);
+        const bool conv = resid < o.rtol * st->r0norm || !(hnext > 1e-300 * st->r0norm);
+        const bool full = (j + 1 >= kmax);
+        int nx;
+        if (!(resid == resid) || !(rr == rr)) { st->status = JFNK_E_NAN; nx = NX_DONE; }
+        else if (!conv && !full) nx = NX_NONE;       // continue Arnoldi
+        else {
+          // y = H^{-1} g (upper triangular, j+1)
+          for (int r = j; r >= 0; --r) {
+            double s = gv[r];
+            for (int c = r + 1; c <= j; ++c) s -= Hh[r * kmax + c] * s_y[c];
+            s_y[r] = s / Hh[r * kmax + r];
+          }
+          nx = (conv || st->restarts >= o.max_restarts) ? NX_NEWTON : 100;   // 100: restart
+        }
+        s_next = nx;
+        s_val = hnext;
+      }
+      __syncthreads();
+      next = s_next;
+      if (next == NX_DONE) {
+        if (threadIdx.x == 0) { st->phase = PH_DONE; status_out[blockIdx.x] = st->status; }
+        return;
+      }
+      if (next == NX_NONE) {
+        const double hn = s_val;
+        double* vn = Vb + (size_t)(j + 1) * N;
+        for (int e = threadIdx.x; e < N; e += blockDim.x) vn[e] = w[e] / hn;
+        if (threadIdx.x == 0) { st->j = j + 1; st->phase = PH_JVP; status_out[blockIdx.x] = st->status; }
+        return;
+      }
+      // x += V y
+      for (int e = threadIdx.x; e < N; e += blockDim.x) {
+        double acc = x[e];
+        for (int i = 0; i <= j; ++i) acc += s_y[i] * Vb[(size_t)i * N + e];
+        x[e] = acc;
+      }
+      __syncthreads();
+      if (next == 100) {
+        if (threadIdx.x == 0) { st->phase = PH_RESTART; status_out[blockIdx.x] = st->status; }
+        return;
+      }
+    }
+  }
+
+  if (next == NX_START_GMRES) {
+    const double beta = start_beta;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) Vb[e] = w[e] / beta;
+    if (threadIdx.x == 0) {
+      for (int i = 0; i <= kmax; ++i) cd.w.gv[i] = 0.0;
+      cd.w.gv[0] = beta;
+      st->j = 0;
+      st->phase = PH_JVP;
+      status_out[blockIdx.x] = st->status;
+    }
+    return;
+  }
+
+  // Newton update with per-depth limiting (Sect. 2.2.2): n += alpha_k x^k
+  double err = 0.0;
+  double* n = cd.w.n;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    double alpha = 1.0;
+    if (o.clamp)
+      for (int l = 0; l < nl; ++l) {
+        const double dx = x[k * nl + l];
+        if (dx < 0.0) alpha = fmin(alpha, 0.9 * n[k * nl + l] / (-dx));
+      }
+    for (int l = 0; l < nl; ++l) {
+      const double np = n[k * nl + l];
+      const double nn = np + alpha * x[k * nl + l];
+      cd.w.nprev[k * nl + l] = np;
+      n[k * nl + l] = nn;
+      err = fmax(err, 0.5 * fabs((nn - np) / (nn + np)));
+    }
+  }
+  err = block_max(err, sh);
+  for (int i = threadIdx.x; i < cd.t.nq * nz; i += blockDim.x) cd.w.Jdag[i] = cd.w.Jnew[i];
+  if (threadIdx.x == 0) {
+    st->err = err;
+    st->newton_iter++;
+    st->phase = PH_BASE;
+    status_out[blockIdx.x] = st->status;
+  }
+}
+
+int launch_krylov_step(const Batch& b, cudaStream_t s) {
+  k_krylov<<<b.ncols, 256, 0, s>>>(b.d_cols, b.d_opts, b.d_status);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+__global__ void k_rh92_apply(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cd.t.nz) return;
+  rh92_depth(cd, k);
+}
+
+int launch_rh92_update(const Batch& b, cudaStream_t s) {
+  dim3 g((b.max_nz + 63) / 64, b.ncols);
+  k_rh92_apply<<<g, 64, 0, s>>>(b.d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+}  // namespace jfnk

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA library through its C ABI against the CPU oracle.
+
+Tolerances (FP64 mode): tables 1e-12 relative (Voigt profiles 1e-9, the
+accuracy of the Weideman expansion against the Faddeeva function); F and
+J_F v compared per element against the gross rate scale of their depth
+(F cancels towards zero at the solution, so a relative error per element is
+meaningless there); converged populations 1e-5 relative (the stated FP64 bar,
+both solved far past it). Mixed mode: converged populations 1e-3 relative.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import model as OM
+from oracle.jfnk import jfnk
+from oracle.precond import block_jacobi as ora_P
+from oracle.residual import jvp_complex, residual as ora_residual
+from oracle.rh92 import rh92_update as ora_rh92
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_2406_17234_gb300.binding")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return B.Context(0)
+
+
+def _pair(ctx, wl, n_mu=None, col=0):
+    n_mu = n_mu or wl.n_mu
+    atom = B.Atom(ctx, wl.atom)
+    atm = B.Atmosphere(ctx, atom, wl.columns[col], n_mu=n_mu)
+    m = OM.build_model(wl.atom, wl.columns[col], n_mu)
+    return atom, atm, m
+
+
+CASES = {
+    "two-level": lambda: W.config1(),
+    "ca-small": lambda: W.config2(nu_scale=0.2, n_depth=37),
+    "h-small": lambda: W.config3(nu_scale=0.15, n_depth=41),
+    "tiny": lambda: W.tiny_workload(n_depth=5, n_nu_line=7, n_nu_cont=3),
+}
+
+
+def _gross(m, n, R_up, R_dn):
+    g = np.zeros_like(n)
+    for t, tr in enumerate(m.trans):
+        up = n[:, tr.lo] * (m.Cmat[:, tr.lo, tr.up] + R_up[t])
+        dn = n[:, tr.up] * (m.Cmat[:, tr.up, tr.lo] + R_dn[t])
+        g[:, tr.lo] += up + dn
+        g[:, tr.up] += up + dn
+    g += np.abs(n).sum(axis=1, keepdims=True) * 1e-30
+    return g
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_tables_match_oracle(ctx, case):
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    np.testing.assert_allclose(atom.frequencies(), m.nu, rtol=1e-14)
+    assert (atm.n_depth, atm.n_nu, atm.n_levels, atm.n_transitions) == (m.nz, m.nq, m.nl, m.nt)
+    np.testing.assert_allclose(atm.lte(), m.nstar, rtol=1e-12)
+    np.testing.assert_allclose(atm.planck(), m.B, rtol=1e-12)
+    C = atm.table(2, m.nz * m.nl * m.nl).reshape(m.nz, m.nl, m.nl)
+    np.testing.assert_allclose(C, m.Cmat, rtol=1e-12, atol=0)
+    nwin = sum(tr.q1 - tr.q0 + 1 for tr in m.trans)
+    V = atm.table(3, nwin * m.nz).reshape(nwin, m.nz)
+    G = atm.table(4, nwin * m.nz).reshape(nwin, m.nz)
+    w = atm.table(5, nwin)
+    base = 0
+    for t, tr in enumerate(m.trans):
+        nw = tr.q1 - tr.q0 + 1
+        np.testing.assert_allclose(w[base:base + nw], m.omega[t, tr.q0:tr.q1 + 1], rtol=1e-13)
+        np.testing.assert_allclose(V[base:base + nw], m.V[t, tr.q0:tr.q1 + 1], rtol=1e-9 if tr.kind == "bb" else 1e-13)
+        np.testing.assert_allclose(G[base:base + nw], m.g[t, tr.q0:tr.q1 + 1], rtol=1e-12)
+        base += nw
+    np.testing.assert_allclose(atm.table(6, m.nq * m.nz).reshape(m.nq, m.nz), m.chi_c, rtol=1e-12)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("perturb", [0.0, 0.3])
+def test_residual_matches_oracle(ctx, case, perturb):
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    rng = np.random.default_rng(11)
+    n = m.nstar if perturb == 0.0 else W.perturbed_populations(m.nstar, rng, perturb)
+    Jd = m.B * np.exp(rng.normal(0, 0.2, m.B.shape))
+    F, J, Ie = B.residual(atm, n, Jd, want_J=True, want_emergent=True)
+    r = ora_residual(m, n, Jd)
+    gross = _gross(m, n, r.R_up, r.R_dn)
+    assert np.all(np.abs(F - r.F) <= 1e-10 * gross + 1e-12 * np.abs(r.F))
+    k = np.arange(m.nz)
+    np.testing.assert_allclose(F[k, r.istar], r.F[k, r.istar], rtol=1e-13)
+    np.testing.assert_allclose(J, r.J, rtol=1e-10, atol=1e-14 * np.max(np.abs(r.J)))
+    np.testing.assert_allclose(Ie, r.I_emergent, rtol=1e-10, atol=1e-14 * np.max(np.abs(r.I_emergent)))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_jvp_matches_complex_step(ctx, case):
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    rng = np.random.default_rng(12)
+    n = W.perturbed_populations(m.nstar, rng, 0.2)
+    Jd = m.B
+    for trial in range(2):
+        v = rng.normal(size=n.shape) * n
+        g = B.jvp(atm, n, v, Jd)
+        ref = jvp_complex(m, n, Jd, v)
+        scale = np.max(np.abs(ref), axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(g - ref) / scale) < 1e-9
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_block_jacobi_matches_oracle(ctx, case):
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    rng = np.random.default_rng(13)
+    n = W.perturbed_populations(m.nstar, rng, 0.2)
+    P = B.block_jacobi(atm, n, m.B)
+    r = ora_residual(m, n, m.B, want_lambda=True)
+    ref = ora_P(m, n, r)
+    scale = np.max(np.abs(ref), axis=(1, 2), keepdims=True)
+    assert np.max(np.abs(P - ref) / scale) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["two-level", "ca-small", "h-small"])
+def test_rh92_update_matches_oracle(ctx, case):
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    n_gpu, J_gpu = B.rh92_update(atm, m.nstar, m.B)
+    r = ora_residual(m, m.nstar, m.B, want_lambda=True)
+    ref = ora_rh92(m, m.nstar, r)
+    np.testing.assert_allclose(n_gpu, ref, rtol=1e-8, atol=1e-12 * np.max(ref))
+
+
+def test_solve_two_level_matches_oracle_and_conserves(ctx):
+    wl = W.config1()
+    atom, atm, m = _pair(ctx, wl)
+    n, J, st = B.solve(atm, B.default_options(rtol=1e-6, ftol=1e-10))
+    ref = jfnk(m, m.nstar, rtol=1e-6, ftol=1e-10)
+    assert st["status"] == 0
+    np.testing.assert_allclose(n, ref.n, rtol=1e-5)
+    np.testing.assert_allclose(n.sum(axis=1), m.ntot, rtol=1e-12)
+    # the sqrt(eps) observable: S(0)/B at line centre
+    r = ora_residual(m, n, J)
+    q0 = m.nq // 2
+    ratio = (r.eta / r.chi)[q0, 0] / m.B[q0, 0]
+    r2 = ora_residual(m, ref.n, ref.J)
+    assert ratio == pytest.approx((r2.eta / r2.chi)[q0, 0] / m.B[q0, 0], rel=1e-5)
+
+
+def test_solve_paper_tolerances_two_level(ctx):
+    wl = W.config1()
+    atom, atm, m = _pair(ctx, wl)
+    n, J, st = B.solve(atm, B.default_options())
+    ref = jfnk(m, m.nstar)
+    assert st["status"] == 0 and ref.converged
+    assert st["F_norm"] <= 1e-2 * st["F_norm0"]
+    np.testing.assert_allclose(n, ref.n, rtol=1e-3)
+
+
+def test_solve_ca_small_matches_oracle(ctx):
+    wl = CASES["ca-small"]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    n, J, st = B.solve(atm, B.default_options(rtol=1e-6, ftol=1e-10))
+    ref = jfnk(m, m.nstar, rtol=1e-6, ftol=1e-10)
+    assert st["status"] == 0 and ref.converged
+    np.testing.assert_allclose(n, ref.n, rtol=1e-5)
+
+
+def test_solve_mixed_precision_against_fp64_oracle(ctx):
+    wl = CASES["ca-small"]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    n, J, st = B.solve(atm, B.default_options(rtol=1e-4, ftol=1e-7, precision=B.JFNK_MIXED))
+    ref = jfnk(m, m.nstar, rtol=1e-6, ftol=1e-10)
+    assert st["status"] == 0
+    np.testing.assert_allclose(n, ref.n, rtol=1e-3)
+
+
+def test_hybrid_solve_hydrogen(ctx):
+    wl = W.config3(nu_scale=0.1, n_depth=60)
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    from oracle.hybrid import hybrid
+    n, J, st = B.solve(atm, B.default_options(rtol=1e-6, ftol=1e-10, rh92_warmup=200))
+    ref = hybrid(m, m.nstar, rtol=1e-6, ftol=1e-10)
+    assert st["status"] == 0 and st["rh92_iters"] > 0
+    np.testing.assert_allclose(n, ref.n, rtol=1e-5)
+
+
+def test_batch_equals_single(ctx):
+    wl = W.config4(n_columns=5, nz_min=20, nz_max=45, nu_scale=0.1)
+    atom = B.Atom(ctx, wl.atom)
+    atms = [B.Atmosphere(ctx, atom, c, n_mu=3) for c in wl.columns]
+    opts = B.default_options(rtol=1e-6, ftol=1e-9)
+    ns, stats = B.batch_solve(ctx, atms, opts)
+    for a, nb, s in zip(atms, ns, stats):
+        n1, _, s1 = B.solve(a, B.default_options(rtol=1e-6, ftol=1e-9))
+        assert s["status"] == 0 and s1["status"] == 0
+        np.testing.assert_array_equal(nb, n1)
+        assert s["F_calls"] == s1["F_calls"]
+
+
+def test_edge_cases(ctx):
+    # minimum depth count, a single angle, a single transition
+    wl = W.config1(n_depth=2, n_nu=3)
+    atom, atm, m = _pair(ctx, wl, n_mu=1)
+    F, _, _ = B.residual(atm, m.nstar)
+    r = ora_residual(m, m.nstar, m.B)
+    gross = _gross(m, m.nstar, r.R_up, r.R_dn)
+    assert np.all(np.abs(F - r.F) <= 1e-10 * gross)
+    # empty batch is a no-op
+    ns, st = B.batch_solve(ctx, [])
+    assert ns == [] and st == []
+
+
+def test_invalid_descriptors_are_rejected(ctx):
+    wl = W.config1()
+    bad = W.two_level_atom()
+    bad.lines[0] = W.replace(bad.lines[0], n_nu=4)
+    with pytest.raises(B.JFNKError) as e:
+        B.Atom(ctx, bad)
+    assert e.value.code == B.JFNK_E_INVALID
+    atom = B.Atom(ctx, wl.atom)
+    col = wl.columns[0]
+    col2 = W.replace(col, T=-col.T)
+    with pytest.raises(B.JFNKError):
+        B.Atmosphere(ctx, atom, col2)
