@@ -1,0 +1,351 @@
+"""Benchmark: converged JFNK NLTE column solves on the GPU (one JSON line).
+
+Default workload: the six-level Ca II-like atom on the 82-depth synthetic
+chromosphere (about 1,000 frequencies, 5 mu per hemisphere), FP64, solved from
+LTE populations with the paper's stopping rule (Sect. 3.1). One step = one
+full solve: every F-class evaluation (opacity, formal solution, rates,
+assembly, preconditioner) and every Krylov/Newton update, on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ca|two-level|h] [--precision fp64|mixed]
+
+Metric: formal-solution ray-points/s (= F-class evaluations x N_nu x 2 N_mu x
+N_z per second); also converged columns/s and p50/p99 solve latency.
+N > 1 (torchrun): every rank solves its own column (weak scaling, no
+collective on the data path); value = ray-points of all ranks / max time.
+``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "formal-solution ray-points/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="ca", choices=["ca", "two-level", "h"])
+    p.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(name):
+    if name == "two-level":
+        return W.config1(), "fp64"
+    if name == "h":
+        return W.config3(), "mixed"
+    return W.config2(), "fp64"
+
+
+def workload_config(wl, m_info, precision):
+    nq, nz, nmu = m_info
+    return {"workload": f"{wl.name}: {wl.atom.name} atom, {nz} depths, {nq} frequencies, "
+                        f"{nmu} mu per hemisphere, JFNK from {wl.init.upper()} to the paper's "
+                        f"stopping rule ({precision})",
+            "atom": wl.atom.name, "n_levels": int(wl.atom.n_levels), "n_depth": nz, "n_nu": nq,
+            "n_mu": nmu, "init": wl.init, "rtol": 1e-2, "ftol": 1e-4, "fdrop": 1e-2,
+            "l2": "flushed by a 256 MiB device write before every timed step"}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, local, dist
+
+
+def clocks_start():
+    try:
+        return subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return None
+
+
+def clocks_stop(proc, device):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except Exception:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or f[0] != str(device):
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2406_17234_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_key):
+    """DRAM bytes per launch of the formal kernel from a committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", "formal_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_ray_point")
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    """The oracle as it stands, on the host cores: a bounded sample of the same workload."""
+    from oracle import model as OM
+    from oracle.residual import jvp_complex, residual
+    m = OM.build_model(wl.atom, wl.columns[0], wl.n_mu)
+    J0 = OM.initial_J(m)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    evals = 0
+    residual(m, m.nstar, J0)
+    evals += 1
+    while time.perf_counter() - t0 < budget_s:
+        v = rng.normal(size=m.nstar.shape) * m.nstar
+        jvp_complex(m, m.nstar, J0, v)
+        evals += 1
+    dt = time.perf_counter() - t0
+    return {"value": evals * m.ray_points / dt, "unit": "ray-points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{evals} oracle F-class evaluations (1 residual + {evals - 1} complex-step JVPs) "
+                      f"of the same column at LTE, {dt:.1f} s, numpy FP64/complex128 single thread"}
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    wl, prec = workload(args.workload)
+    from oracle import model as OM
+    from oracle.residual import jvp_complex, residual
+    m = OM.build_model(wl.atom, wl.columns[0], wl.n_mu)
+    J0 = OM.initial_J(m)
+    rng = np.random.default_rng(0)
+
+    def step():
+        residual(m, m.nstar, J0)
+        for _ in range(3):
+            jvp_complex(m, m.nstar, J0, rng.normal(size=m.nstar.shape) * m.nstar)
+        return 4 * m.ray_points
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    pts = 0.0
+    for _ in range(args.steps):
+        pts += step()
+    dt = time.perf_counter() - t0
+    value = pts / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ray-points/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, (m.nq, m.nz, m.nmu), "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": "ray-points/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: 1 residual + 3 complex-step JVPs of the column at LTE"},
+            "e2e": {"value": value, "unit": "ray-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, ws, local, dist):
+    import torch
+    from paper_2406_17234_gb300 import binding as B
+
+    wl, default_prec = workload(args.workload)
+    prec = args.precision or default_prec
+    precision = B.JFNK_MIXED if prec == "mixed" else B.JFNK_FP64
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = B.Context(local)
+    atom = B.Atom(ctx, wl.atom)
+    atm = B.Atmosphere(ctx, atom, wl.columns[0], n_mu=wl.n_mu)
+    N = atm.n_depth * atm.n_levels
+    rh92 = 200 if wl.init == "hybrid" else 0
+    lib = ctx.lib
+    import ctypes as C
+
+    def opts(profile=1):
+        return B.default_options(precision=precision, profile=profile, rh92_warmup=rh92)
+
+    n_dev = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = B.jfnk_stats()
+
+    def solve_device(o):
+        rc = lib.jfnk_solve(ctx.h, atm.h, C.byref(o), n_dev.data_ptr(), None, C.byref(st),
+                            B.JFNK_MEM_DEVICE, stream.cuda_stream)
+        B.check(rc, "jfnk_solve")
+        return st.as_dict()
+
+    o = opts()
+    for _ in range(args.warmup):
+        flush.zero_()
+        solve_device(o)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start() if rank == 0 else None
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s = solve_device(o)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(s)
+    torch.cuda.synchronize()
+    clocks = clocks_stop(clk, local) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    total_ms = float(sum(times))
+    pts = float(sum(s["ray_points"] for s in stats))
+    # e2e: host buffers through the public API (pinned in / out), wall clock
+    n_host = torch.from_numpy(atm.lte().ravel().copy()).pin_memory()
+    n_out = torch.empty_like(n_host).pin_memory()
+    e2e_times, e2e_pts = [], 0.0
+    oe = opts(profile=0)
+    oe.init = B.JFNK_INIT_USER
+    st2 = B.jfnk_stats()
+    for _ in range(max(1, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        n_out.copy_(n_host)
+        t0 = time.perf_counter()
+        rc = lib.jfnk_solve(ctx.h, atm.h, C.byref(oe), n_out.data_ptr(), None, C.byref(st2),
+                            B.JFNK_MEM_HOST, stream.cuda_stream)
+        e2e_times.append(time.perf_counter() - t0)
+        B.check(rc, "jfnk_solve (host)")
+        e2e_pts += st2.ray_points
+    if dist is not None:
+        t = torch.tensor([total_ms, pts, sum(e2e_times), e2e_pts], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms, pts = float(tmax[0]), float(tsum[1])
+        e2e_s, e2e_pts_all = float(tmax[2]), float(tsum[3])
+    else:
+        e2e_s, e2e_pts_all = sum(e2e_times), e2e_pts
+    if rank != 0:
+        return
+    value = pts / (total_ms * 1e-3)
+    lat = np.array(times)
+    cols_per_s = ws * args.steps / (total_ms * 1e-3)
+    s0 = stats[-1]
+    # roofline of the formal-solution kernel (dominant): algorithmic work per launch / event time
+    launches = sum(s["formal_launches"] for s in stats)
+    kern_ms = sum(s["formal_ms"] for s in stats)
+    fp64 = precision == B.JFNK_FP64
+    fma_peak = B.probe_alu(ctx, 0 if fp64 else 1)
+    exp_rate = B.probe_alu(ctx, 2 if fp64 else 3)
+    exp_cost = fma_peak / exp_rate          # exp in FMA-pipe flop equivalents (measured)
+    n_jvp = sum(s["jvp_calls"] for s in stats)
+    n_all = sum(s["F_calls"] for s in stats)
+    n_base = n_all - n_jvp
+    flops_pt = (n_base * (9 + 13) + n_jvp * (9 + 12)) / max(1, n_all) + exp_cost
+    per_launch_pts = atm.ray_points
+    achieved = per_launch_pts * flops_pt / (kern_ms / max(1, launches) * 1e-3)
+    key = "formal_fp64" if fp64 else "formal_fp32"
+    traffic_pp = measured_traffic(key)
+    roofline = {"bound": "alu", "kernel": f"k_formal<{'double' if fp64 else 'float'}>",
+                "achieved": achieved / 1e9, "peak": fma_peak / 1e9, "unit": "GFLOP/s",
+                "frac": achieved / fma_peak,
+                "traffic": None if traffic_pp is None else traffic_pp * per_launch_pts,
+                "flops_per_ray_point": flops_pt, "exp_cost_flops": exp_cost,
+                "avg_launch_us": 1e3 * kern_ms / max(1, launches), "launches": launches,
+                "share_of_step": kern_ms / total_ms,
+                "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA throughput (jfnk_probe_alu) on this GPU"}
+    ticks = [s["F_calls"] for s in stats]
+    gpu_launches = int(sum(8 * 8 * math.ceil(t / 8) + 2 for t in ticks))
+    line = {"metric": METRIC, "value": value, "unit": "ray-points/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if fp64 else "f32 formal solution / f64 rates, Krylov, Newton",
+            "data": "synthetic",
+            "config": workload_config(wl, (atm.n_nu, atm.n_depth, atm.n_mu), prec),
+            "columns_per_s": cols_per_s,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "solve": {"newton_iters": s0["newton_iters"], "rh92_iters": s0["rh92_iters"],
+                      "F_calls": s0["F_calls"], "jvp_calls": s0["jvp_calls"],
+                      "F_norm_drop": s0["F_norm"] / s0["F_norm0"], "dn_norm": s0["dn_norm"],
+                      "status": s0["status"]},
+            "roofline": roofline,
+            "e2e": {"value": e2e_pts_all / e2e_s, "unit": "ray-points/s",
+                    "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8 + 0},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local, dist = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+    else:
+        run_ours(args, rank, ws, local, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -142,6 +142,7 @@ typedef struct {
   int rh92_warmup;      /* > 0: hybrid start, at most this many RH92 iterations    */
   double rh92_switch;   /* switch to JFNK when the RH92 change is below (1e-2)     */
   int max_ticks;        /* F-class evaluations allowed per column (20000)          */
+  int profile;          /* 1: time the formal-solution kernel of every active tick */
 } jfnk_options;
 
 typedef struct {
@@ -154,6 +155,8 @@ typedef struct {
   double F_norm0;       /* ||F||_inf at the first JFNK base point                   */
   double dn_norm;       /* last population change                                  */
   double ray_points;    /* formal-solution ray-points evaluated (F_calls x rays)   */
+  double formal_ms;     /* profile: summed duration of the formal-solution kernel  */
+  int formal_launches;  /* profile: number of timed launches (active ticks)        */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -231,6 +234,14 @@ int jfnk_solve(jfnk_ctx* ctx, const jfnk_atmos* a, const jfnk_options* o, double
 int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols,
                      const jfnk_options* o, double* const* n_inout, double* const* J_inout,
                      jfnk_stats* stats, jfnk_mem where, void* stream);
+
+/* ---- measurement ----------------------------------------------------------- */
+/* Throughput probe of one arithmetic pipe on the context's device, for roofline
+ * denominators: kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add,
+ * 2 = FP64 exp(), 3 = FP32 __expf (MUFU). Runs a fixed dependent-chain workload
+ * over every SM and returns operations per second (an FMA counts as 2 flops;
+ * an exp as 1 operation). */
+int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s);
 
 #ifdef __cplusplus
 }

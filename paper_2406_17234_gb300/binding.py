@@ -64,13 +64,15 @@ class jfnk_options(C.Structure):
     _fields_ = [("ftol", C.c_double), ("fdrop", C.c_double), ("rtol", C.c_double),
                 ("maxiter", C.c_int), ("krylov_max", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("init", C.c_int), ("clamp", C.c_int),
-                ("rh92_warmup", C.c_int), ("rh92_switch", C.c_double), ("max_ticks", C.c_int)]
+                ("rh92_warmup", C.c_int), ("rh92_switch", C.c_double), ("max_ticks", C.c_int),
+                ("profile", C.c_int)]
 
 
 class jfnk_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("rh92_iters", C.c_int),
                 ("F_calls", C.c_int), ("jvp_calls", C.c_int), ("F_norm", C.c_double),
-                ("F_norm0", C.c_double), ("dn_norm", C.c_double), ("ray_points", C.c_double)]
+                ("F_norm0", C.c_double), ("dn_norm", C.c_double), ("ray_points", C.c_double),
+                ("formal_ms", C.c_double), ("formal_launches", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -101,6 +103,7 @@ _SIGNATURES = {
                                    C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "jfnk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(jfnk_options), C.c_void_p,
                              C.c_void_p, C.POINTER(jfnk_stats), C.c_int, C.c_void_p]),
+    "jfnk_probe_alu": (C.c_int, [C.c_void_p, C.c_int, _dp]),
     "jfnk_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p),
                                    C.POINTER(jfnk_options), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(jfnk_stats), C.c_int,
@@ -319,6 +322,12 @@ def solve(atm: Atmosphere, opts: Optional[jfnk_options] = None, n0=None, J0=None
     if raise_on_fail:
         check(rc, "jfnk_solve")
     return n, J, st.as_dict()
+
+
+def probe_alu(ctx: Context, kind: int) -> float:
+    v = C.c_double()
+    check(ctx.lib.jfnk_probe_alu(ctx.h, kind, C.byref(v)), "jfnk_probe_alu")
+    return v.value
 
 
 def batch_solve(ctx: Context, atms: Sequence[Atmosphere], opts: Optional[jfnk_options] = None,

@@ -20,6 +20,7 @@ int fail(int code, const std::string& msg) {
 Batch::~Batch() {
   if (graph) cudaGraphExecDestroy(graph);
   if (h_status) cudaFreeHost(h_status);
+  for (cudaEvent_t e : tick_ev) cudaEventDestroy(e);
 }
 
 // Work buffers and the tick graph of one column, cached in its handle.
@@ -119,13 +120,22 @@ __global__ void k_init_state(SolverState* st, int n, int phase) {
 
 constexpr int kTicksPerGraph = 8;
 
-static int ensure_graph(Batch* b, cudaStream_t s) {
-  if (b->graph) return JFNK_OK;
+static int ensure_graph(Batch* b, cudaStream_t s, bool profile) {
+  if (b->graph && b->graph_profiled == profile) return JFNK_OK;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (profile && b->tick_ev.empty()) {
+    b->tick_ev.resize(2 * kTicksPerGraph);
+    for (auto& e : b->tick_ev) JFNK_CUDA(cudaEventCreate(&e));
+  }
   cudaGraph_t g;
   JFNK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = JFNK_OK;
   for (int t = 0; t < kTicksPerGraph && !rc; ++t) {
-    rc = launch_evaluation(*b, s);
+    rc = profile ? launch_evaluation(*b, s, b->tick_ev[2 * t], b->tick_ev[2 * t + 1])
+                 : launch_evaluation(*b, s);
     if (!rc) rc = launch_lu(*b, s, true);
     if (!rc) rc = launch_krylov_step(*b, s);
   }
@@ -136,19 +146,28 @@ static int ensure_graph(Batch* b, cudaStream_t s) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(JFNK_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   b->graph_ticks = kTicksPerGraph;
+  b->graph_profiled = profile;
   if (!b->h_status) JFNK_CUDA(cudaMallocHost(&b->h_status, sizeof(int) * std::max(1, b->ncols)));
   return JFNK_OK;
 }
 
 // Runs the tick graph until every column has left the running state.
 static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
-  int rc = ensure_graph(b, s);
+  const bool profile = o->profile != 0;
+  int rc = ensure_graph(b, s, profile);
   if (rc) return rc;
+  b->tick_ms.clear();
   const long max_replays = (long)o->max_ticks / b->graph_ticks + 2;
   for (long r = 0; r < max_replays; ++r) {
     JFNK_CUDA(cudaGraphLaunch(b->graph, s));
     JFNK_CUDA(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s));
     JFNK_CUDA(cudaStreamSynchronize(s));
+    if (profile)
+      for (int t = 0; t < b->graph_ticks; ++t) {
+        float ms = 0.f;
+        JFNK_CUDA(cudaEventElapsedTime(&ms, b->tick_ev[2 * t], b->tick_ev[2 * t + 1]));
+        b->tick_ms.push_back(ms);
+      }
     bool running = false;
     for (int c = 0; c < b->ncols; ++c) running |= (b->h_status[c] == 1);
     if (!running) return JFNK_OK;
@@ -206,6 +225,11 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
   }
   JFNK_CUDA(cudaStreamSynchronize(s));
   *worst = JFNK_OK;
+  int active = 0;
+  for (int c = 0; c < b->ncols; ++c) active = std::max(active, st[c].ticks);
+  active = std::min(active, (int)b->tick_ms.size());
+  double kernel_ms = 0.0;
+  for (int t = 0; t < active; ++t) kernel_ms += b->tick_ms[t];
   for (int c = 0; c < b->ncols; ++c) {
     const SolverState& x = st[c];
     int status = x.status == 1 ? JFNK_E_TIMEOUT : x.status;
@@ -220,6 +244,8 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.F_norm0 = x.F0norm;
       S.dn_norm = x.err;
       S.ray_points = (double)x.F_calls * cols[c]->d.ray_points;
+      S.formal_ms = kernel_ms;
+      S.formal_launches = active;
     }
     if (status != JFNK_OK && *worst == JFNK_OK) *worst = status;
   }
@@ -263,6 +289,7 @@ void jfnk_default_options(jfnk_options* o) {
   o->rh92_warmup = 0;
   o->rh92_switch = 1e-2;
   o->max_ticks = 20000;
+  o->profile = 0;
 }
 
 int jfnk_init(int device, jfnk_ctx** out) {

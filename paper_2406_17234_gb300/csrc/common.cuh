@@ -106,10 +106,12 @@ struct ColWork {
   double* Jnew;     // [nq][nz]
   int* istar;       // [nz]
   void* chi;        // [nq][nz] real
-  void* S;          // [nq][nz] real (normalised by 2 h nu^3/c^2)
+  double* S;        // [nq][nz] source function normalised by 2 h nu^3/c^2
+  void* dSk;        // [nq][nz] real: S^{k+1} - S^k formed in FP64 (0 at the bottom)
   void* dchi;       // [nq][nz] real
-  void* dS;         // [nq][nz] real
-  void* H;          // [2 nmu][nq][nz] real: per-ray 1/2 w I  (value)
+  double* dS;       // [nq][nz] tangent of S (normalised)
+  void* ddSk;       // [nq][nz] real: dS^{k+1} - dS^k
+  void* H;          // [2 nmu][nz][nq] real: per-ray 1/2 w (I - S)  (value)
   void* dH;         // tangent
   void* LX;         // per-ray 1/2 w dI^k/dchi^k
   void* LE;         // per-ray 1/2 w dI^k/deta^k

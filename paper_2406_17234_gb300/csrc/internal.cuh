@@ -94,6 +94,9 @@ struct Batch {
   SolverOpts* d_opts = nullptr;       // solver options read by the Krylov kernel
   cudaGraphExec_t graph = nullptr;    // captured tick sequence
   int graph_ticks = 0;
+  bool graph_profiled = false;
+  std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel of each tick
+  std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve
   int* h_status = nullptr;            // pinned host mirror of d_status
   ~Batch();
 };
@@ -101,7 +104,9 @@ struct Batch {
 // Allocates work buffers for columns ``tabs`` (precision: mixed or FP64).
 int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed, int kmax);
 // Launch sequence of one F-class evaluation for every column of the batch.
-int launch_evaluation(const Batch& b, cudaStream_t s);
+// ev0/ev1 (optional) are recorded around the formal-solution kernel.
+int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                      cudaEvent_t ev1 = nullptr);
 // Launch of the Krylov/Newton state machine step.
 int launch_krylov_step(const Batch& b, cudaStream_t s);
 // Sets every column's forced evaluation mode (explicit API calls) or -1.

@@ -1,0 +1,94 @@
+// Arithmetic-pipe throughput probe (roofline denominators for ALU-bound
+// kernels): every thread runs independent dependent chains of one operation.
+#include "internal.cuh"
+
+namespace jfnk {
+
+constexpr int kChains = 8;
+constexpr int kIters = 4096;
+
+template <typename T>
+__global__ void k_probe_fma(T* out, T a, T b) {
+  T x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = x[c] * a + b;
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == (T)12345.678) out[0] = s;   // keeps the chains alive
+}
+
+__global__ void k_probe_exp64(double* out) {
+  double x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = -1e-3 * (threadIdx.x + c);
+  for (int it = 0; it < kIters / 8; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = -exp(x[c]) * 0.5;
+  }
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == 12345.678) out[0] = s;
+}
+
+__global__ void k_probe_exp32(float* out) {
+  float x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = -1e-3f * (threadIdx.x + c);
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = -__expf(x[c]);
+  }
+  float s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == 12345.678f) out[0] = s;
+}
+
+}  // namespace jfnk
+
+using namespace jfnk;
+
+extern "C" int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s) {
+  if (!ctx || !ops_per_s || kind < 0 || kind > 3) return fail(JFNK_E_INVALID, "bad probe arguments");
+  JFNK_CUDA(cudaSetDevice(ctx->device));
+  double* d;
+  JFNK_CUDA(cudaMalloc(&d, 64));
+  const int threads = 256, blocks = ctx->n_sm * 8;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStream_t s = ctx->stream;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, s);
+    switch (kind) {
+      case 0: k_probe_fma<double><<<blocks, threads, 0, s>>>(d, 0.999999, 1e-7); break;
+      case 1: k_probe_fma<float><<<blocks, threads, 0, s>>>((float*)d, 0.999999f, 1e-7f); break;
+      case 2: k_probe_exp64<<<blocks, threads, 0, s>>>(d); break;
+      case 3: k_probe_exp32<<<blocks, threads, 0, s>>>((float*)d); break;
+    }
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;   // first launch is a warm-up
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (err != cudaSuccess) return fail(JFNK_E_CUDA, cudaGetErrorString(err));
+  const double threads_total = (double)threads * blocks;
+  double ops;
+  if (kind <= 1) ops = threads_total * kChains * kIters * 2.0;
+  else if (kind == 2) ops = threads_total * kChains * (kIters / 8);
+  else ops = threads_total * kChains * kIters;
+  *ops_per_s = ops / (best * 1e-3);
+  return JFNK_OK;
+}

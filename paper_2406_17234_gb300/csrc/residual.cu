@@ -65,69 +65,78 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
   }
   const double S = eta / chi;
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
-  reinterpret_cast<real*>(cd.w.S)[i] = (real)(S / c2);
+  cd.w.S[i] = S / c2;
   if (tan) {
     reinterpret_cast<real*>(cd.w.dchi)[i] = (real)dchi;
-    reinterpret_cast<real*>(cd.w.dS)[i] = (real)((deta - S * dchi) / chi / c2);
+    cd.w.dS[i] = (deta - S * dchi) / chi / c2;
   }
 }
 
-// Piecewise-linear coefficients (App. A.1): e = exp(-x), a = 1 - (1-e)/x,
-// b = (1-e)/x - e and bq = b/x, by Taylor series below x = 0.1 where 1 - e
-// cancels, directly above.
-__device__ __forceinline__ void pl_coef(double x, double& e, double& a, double& b, double& bq) {
+// Differences of the source function (and of its tangent) between adjacent
+// depths, formed in FP64 before any rounding to ``real``.
+template <typename real>
+__global__ void k_source_diff(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode(cd);
+  if (mode == EV_SKIP) return;
+  const int nz = cd.t.nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cd.t.nq * nz) return;
+  const int k = i % nz;
+  const bool last = (k == nz - 1);
+  reinterpret_cast<real*>(cd.w.dSk)[i] = last ? (real)0 : (real)(cd.w.S[i + 1] - cd.w.S[i]);
+  if (mode == EV_TANGENT)
+    reinterpret_cast<real*>(cd.w.ddSk)[i] = last ? (real)0 : (real)(cd.w.dS[i + 1] - cd.w.dS[i]);
+}
+
+// Piecewise-linear coefficients (App. A.1) in the form the difference
+// recurrence needs: e = exp(-x), w = (1 - e)/x (so a = 1 - w, b = w - e) and
+// bq = b/x, by Taylor series below x = 0.1 where 1 - e cancels.
+__device__ __forceinline__ void pl_coef(double x, double& e, double& w, double& bq) {
   e = exp(-x);
   if (x < 0.1) {
-    // a = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!, b = sum (-1)^{n+1} n x^n/(n+1)!
-    double pa = 0.0, pb = 0.0;
-    double fact = 1.0;
-    double ca[14], cb[14];
-    for (int m = 1; m <= 13; ++m) {
-      fact *= (m + 1);
-      double sgn = (m & 1) ? 1.0 : -1.0;
-      ca[m] = sgn / fact;
-      cb[m] = sgn * m / fact;
+    // w = sum_{n>=0} (-x)^n/(n+1)!, bq = sum_{n>=1} (-1)^{n+1} n x^{n-1}/(n+1)!
+    double pw = 0.0, pb = 0.0;
+    double inv_fact[16];
+    inv_fact[0] = 1.0;
+    for (int m = 1; m < 16; ++m) inv_fact[m] = inv_fact[m - 1] / m;
+    for (int m = 13; m >= 0; --m) {
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      pw = pw * x + sg * inv_fact[m + 1];
+      pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
     }
-    for (int m = 13; m >= 1; --m) {
-      pa = pa * x + ca[m];
-      pb = pb * x + cb[m];
-    }
-    a = pa * x;
+    w = pw;
     bq = pb;
-    b = pb * x;
   } else {
-    double r = 1.0 / x;
-    double w = (1.0 - e) * r;
-    a = 1.0 - w;
-    b = w - e;
-    bq = b * r;
+    const double r = 1.0 / x;
+    w = (1.0 - e) * r;
+    bq = (w - e) * r;
   }
 }
 
-__device__ __forceinline__ void pl_coef(float x, float& e, float& a, float& b, float& bq) {
+__device__ __forceinline__ void pl_coef(float x, float& e, float& w, float& bq) {
   e = __expf(-x);
   if (x < 0.1f) {
-    // five terms of the same series: truncation below 3e-10 relative
-    const float a1 = 0.5f, a2 = -1.0f / 6.0f, a3 = 1.0f / 24.0f, a4 = -1.0f / 120.0f, a5 = 1.0f / 720.0f;
-    const float b1 = 0.5f, b2 = -1.0f / 3.0f, b3 = 1.0f / 8.0f, b4 = -1.0f / 30.0f, b5 = 1.0f / 144.0f;
-    float pa = fmaf(fmaf(fmaf(fmaf(a5, x, a4), x, a3), x, a2), x, a1);
-    float pb = fmaf(fmaf(fmaf(fmaf(b5, x, b4), x, b3), x, b2), x, b1);
-    a = pa * x;
-    bq = pb;
-    b = pb * x;
+    // the same series to x^5 (truncation below 3e-10 relative)
+    w = fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
+    bq = fmaf(fmaf(fmaf(fmaf(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
   } else {
-    float r = 1.0f / x;
-    float w = (1.0f - e) * r;
-    a = 1.0f - w;
-    b = w - e;
-    bq = b * r;
+    const float r = __frcp_rn(x);
+    w = (1.0f - e) * r;
+    bq = (w - e) * r;
   }
 }
 
 // ---------------------------------------------------------------------------
-// a2: formal solution, one thread per (nu, mu, hemisphere) ray
-// outputs per ray r and depth k: 1/2 w_mu I (value), its tangent, and in
-// base mode the local derivatives dI^k/dchi^k, dI^k/deta^k (App. A.2).
+// a2: formal solution, one thread per (nu, mu, hemisphere) ray.
+// The piecewise-linear recurrence of Eqs. Iplus/Iminus is carried for
+// D = I - S: with a = 1 - w and b = w - e it becomes
+//   D^k = D^{k+1} e^{-dtau^k} + w^k (S^{k+1} - S^k)          (mu > 0)
+//   D^k = D^{k-1} e^{-dtau^{k-1}} + w^{k-1} (S^{k-1} - S^k)  (mu < 0)
+// identical in exact arithmetic; in FP32 it keeps the precision of I - S,
+// which is what the net rates of nearly thermalised layers depend on.
+// Outputs per ray r and depth k: 1/2 w_mu D, its tangent, and in base mode
+// the local derivatives dI^k/dchi^k and dI^k/deta^k (App. A.2).
 // Layout of the per-ray outputs: [r][k][q].
 // ---------------------------------------------------------------------------
 template <typename real>
@@ -144,58 +153,64 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
   const int m = up ? r : r - nmu;
   const real hw = (real)(0.5 * T.wmu[m]);
   const real inv2mu = (real)(0.5 / T.mu[m]);
-  const real* chi = reinterpret_cast<const real*>(cd.w.chi) + (size_t)q * nz;
-  const real* S = reinterpret_cast<const real*>(cd.w.S) + (size_t)q * nz;
+  const size_t row = (size_t)q * nz;
+  const real* chi = reinterpret_cast<const real*>(cd.w.chi) + row;
+  const real* dSk = reinterpret_cast<const real*>(cd.w.dSk) + row;
+  const double* S64 = cd.w.S + row;
   const bool tan = (mode == EV_TANGENT);
   const bool der = (mode == EV_BASE || mode == EV_RH92);
-  const real* dchi = tan ? reinterpret_cast<const real*>(cd.w.dchi) + (size_t)q * nz : nullptr;
-  const real* dS = tan ? reinterpret_cast<const real*>(cd.w.dS) + (size_t)q * nz : nullptr;
+  const real* dchi = tan ? reinterpret_cast<const real*>(cd.w.dchi) + row : nullptr;
+  const real* ddSk = tan ? reinterpret_cast<const real*>(cd.w.ddSk) + row : nullptr;
   real* H = reinterpret_cast<real*>(cd.w.H) + (size_t)r * nz * nq + q;
   real* dH = tan ? reinterpret_cast<real*>(cd.w.dH) + (size_t)r * nz * nq + q : nullptr;
   real* LX = der ? reinterpret_cast<real*>(cd.w.LX) + (size_t)r * nz * nq + q : nullptr;
   real* LE = der ? reinterpret_cast<real*>(cd.w.LE) + (size_t)r * nz * nq + q : nullptr;
   const int k0 = up ? nz - 1 : 0;
   const int step = up ? -1 : 1;
-  real I = up ? (real)(T.Bn[(size_t)q * nz + nz - 1] / T.c2[q]) : (real)0;
-  real dI = 0;
-  real chi1 = chi[k0], S1 = S[k0];
-  real dchi1 = tan ? dchi[k0] : (real)0, dS1 = tan ? dS[k0] : (real)0;
-  H[(size_t)k0 * nq] = hw * I;
-  if (tan) dH[(size_t)k0 * nq] = 0;
+  // boundary values: I = B_nu(T_bottom) entering at the bottom, I = 0 at the top
+  real D = up ? (real)(T.Bn[row + nz - 1] / T.c2[q] - S64[k0]) : (real)(-S64[k0]);
+  real dD = tan ? (real)(-cd.w.dS[row + k0]) : (real)0;
+  real chi1 = chi[k0];
+  real dchi1 = tan ? dchi[k0] : (real)0;
+  H[(size_t)k0 * nq] = hw * D;
+  if (tan) dH[(size_t)k0 * nq] = hw * dD;
   if (der) { LX[(size_t)k0 * nq] = 0; LE[(size_t)k0 * nq] = 0; }
   for (int s = 1; s < nz; ++s) {
     const int k = k0 + step * s;
-    const int kd = up ? k : k - 1;   // layer index between k and its upstream neighbour
-    const real chi0 = chi[k], S0 = S[k];
+    const int kd = up ? k : k - 1;             // layer between k and its upstream neighbour
+    const real chi0 = chi[k];
+    const real dS = up ? dSk[k] : -dSk[k - 1];  // S_upstream - S^k
     const real h = (real)T.dz[kd] * inv2mu;
     const real dtau = h * (chi0 + chi1);
-    real e, a, b, bq;
-    pl_coef(dtau, e, a, b, bq);
-    const real Inew = I * e + a * S0 + b * S1;
+    real e, w, bq;
+    pl_coef(dtau, e, w, bq);
+    const real Dnew = D * e + w * dS;
     if (der) {
-      const real common = h * (e * (S1 - I) - (S1 - S0) * bq);
-      LX[(size_t)k * nq] = hw * (-(S0 / chi0) * a + common);
+      // App. A.2 with S_up - I_up = -D_up
+      const real a = (real)1 - w;
+      const real S0 = (real)S64[k];
+      LX[(size_t)k * nq] = hw * (-(S0 / chi0) * a - h * (e * D + dS * bq));
       LE[(size_t)k * nq] = hw * (a / chi0);
     }
     if (tan) {
-      const real dchi0 = dchi[k], dS0 = dS[k];
+      const real dchi0 = dchi[k];
+      const real ddS = up ? ddSk[k] : -ddSk[k - 1];
       const real ddtau = h * (dchi0 + dchi1);
-      const real dInew = dI * e + ddtau * (e * (S1 - I) - (S1 - S0) * bq) + a * dS0 + b * dS1;
-      dH[(size_t)k * nq] = hw * dInew;
-      dI = dInew;
+      const real dDnew = dD * e - ddtau * (e * D + bq * dS) + w * ddS;
+      dH[(size_t)k * nq] = hw * dDnew;
+      dD = dDnew;
       dchi1 = dchi0;
-      dS1 = dS0;
     }
-    I = Inew;
-    H[(size_t)k * nq] = hw * I;
+    D = Dnew;
+    H[(size_t)k * nq] = hw * D;
     chi1 = chi0;
-    S1 = S0;
   }
-  if (up && mode != EV_TANGENT) cd.w.Iem[(size_t)q * nmu + m] = (double)I * T.c2[q];
+  if (up && mode != EV_TANGENT) cd.w.Iem[(size_t)q * nmu + m] = ((double)D + S64[0]) * T.c2[q];
 }
 
 // ---------------------------------------------------------------------------
-// a3 (part 1): sums over the 2 n_mu rays -> J, dJ, Lambda_chi, Lambda_eta
+// a3 (part 1): sums over the 2 n_mu rays -> J, dJ, Lambda_chi, Lambda_eta;
+// J = S + sum_r 1/2 w_r D_r (the Gauss-Legendre weights sum to one).
 // ---------------------------------------------------------------------------
 template <typename real>
 __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
@@ -213,14 +228,15 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
   double s = 0.0;
   const real* H = reinterpret_cast<const real*>(cd.w.H) + i;
   for (int r = 0; r < nr; ++r) s += (double)H[r * plane];
-  cd.w.J[o] = s * c2;
+  const double J = (cd.w.S[o] + s) * c2;
+  cd.w.J[o] = J;
   if (mode == EV_TANGENT) {
     const real* dH = reinterpret_cast<const real*>(cd.w.dH) + i;
     double ds = 0.0;
     for (int r = 0; r < nr; ++r) ds += (double)dH[r * plane];
-    cd.w.dJ[o] = ds * c2;
+    cd.w.dJ[o] = (cd.w.dS[o] + ds) * c2;
   } else {
-    cd.w.Jnew[o] = s * c2;
+    cd.w.Jnew[o] = J;
     const real* LX = reinterpret_cast<const real*>(cd.w.LX) + i;
     const real* LE = reinterpret_cast<const real*>(cd.w.LE) + i;
     double sx = 0.0, se = 0.0;
@@ -438,7 +454,7 @@ __global__ void k_lu(const ColDesc* __restrict__ cols, int only_base) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int launch_evaluation(const Batch& b, cudaStream_t s) {
+int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   const int nc = b.ncols;
   if (nc == 0) return JFNK_OK;
   const int tb = 256;
@@ -448,11 +464,17 @@ int launch_evaluation(const Batch& b, cudaStream_t s) {
   dim3 g_k((b.max_nz + 63) / 64, nc);
   if (b.mixed) {
     k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+    k_source_diff<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     k_formal<float><<<g_ray, 128, 0, s>>>(b.d_cols);
+    if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     k_ray_sum<float><<<g_qk, tb, 0, s>>>(b.d_cols);
   } else {
     k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+    k_source_diff<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     k_formal<double><<<g_ray, 128, 0, s>>>(b.d_cols);
+    if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     k_ray_sum<double><<<g_qk, tb, 0, s>>>(b.d_cols);
   }
   k_rates<<<g_tk, 128, 0, s>>>(b.d_cols);

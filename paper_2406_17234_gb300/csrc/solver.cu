@@ -40,7 +40,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   ar.reset();
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
   struct Offs {
-    size_t n, v, Jdag, Jnew, istar, chi, S, dchi, dS, H, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
+    size_t n, v, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
         dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x, w, nprev;
   };
   std::vector<Offs> off(nc);
@@ -56,8 +56,10 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     o.n = ar.take<double>(N); o.v = ar.take<double>(N);
     o.Jdag = ar.take<double>(nq * nz); o.Jnew = ar.take<double>(nq * nz);
     o.istar = ar.take<int>(nz);
-    o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<char>(rs * nq * nz);
-    o.dchi = ar.take<char>(rs * nq * nz); o.dS = ar.take<char>(rs * nq * nz);
+    o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<double>(nq * nz);
+    o.dSk = ar.take<char>(rs * nq * nz);
+    o.dchi = ar.take<char>(rs * nq * nz); o.dS = ar.take<double>(nq * nz);
+    o.ddSk = ar.take<char>(rs * nq * nz);
     o.H = ar.take<char>(rs * 2 * nmu * nq * nz); o.dH = ar.take<char>(rs * 2 * nmu * nq * nz);
     o.LX = ar.take<char>(rs * 2 * nmu * nq * nz); o.LE = ar.take<char>(rs * 2 * nmu * nq * nz);
     o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(nq * nz);
@@ -94,8 +96,8 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     w.n = ar.ptr<double>(o.n); w.v = ar.ptr<double>(o.v);
     w.Jdag = ar.ptr<double>(o.Jdag); w.Jnew = ar.ptr<double>(o.Jnew);
     w.istar = ar.ptr<int>(o.istar);
-    w.chi = ar.ptr<void>(o.chi); w.S = ar.ptr<void>(o.S);
-    w.dchi = ar.ptr<void>(o.dchi); w.dS = ar.ptr<void>(o.dS);
+    w.chi = ar.ptr<void>(o.chi); w.S = ar.ptr<double>(o.S); w.dSk = ar.ptr<void>(o.dSk);
+    w.dchi = ar.ptr<void>(o.dchi); w.dS = ar.ptr<double>(o.dS); w.ddSk = ar.ptr<void>(o.ddSk);
     w.H = ar.ptr<void>(o.H); w.dH = ar.ptr<void>(o.dH);
     w.LX = ar.ptr<void>(o.LX); w.LE = ar.ptr<void>(o.LE);
     w.J = ar.ptr<double>(o.J); w.dJ = ar.ptr<double>(o.dJ);
