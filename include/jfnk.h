@@ -235,6 +235,28 @@ int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols,
                      const jfnk_options* o, double* const* n_inout, double* const* J_inout,
                      jfnk_stats* stats, jfnk_mem where, void* stream);
 
+/* ---- residual without device allocation -------------------------------------- */
+/* The paper has no counterpart to this entry point: it is a deployment aid.
+ * Same result as jfnk_residual(ctx, a, JFNK_FP64, n, J_dagger, F, J_new, NULL,
+ * JFNK_MEM_DEVICE, stream), but every work buffer comes from one fixed device
+ * array of JFNK_STATIC_SCRATCH_BYTES built into the library (held on every GPU
+ * that loads it until the process exits), so the call never allocates device
+ * memory. For callers that cannot allocate: code running under a memory budget
+ * owned by another allocator, or latency-critical loops that must not pay for
+ * cudaMalloc (which can synchronise the device and fail mid-run).
+ *   n [nz*nl], J_dagger [nq*nz] (nullable: B_nu(T)), F [nz*nl], J_new [nq*nz]
+ *   (nullable): device pointers on the context's device; the work is enqueued
+ *   on ``stream`` and the call returns without synchronising.
+ * A column whose buffers exceed the array (roughly nq * nz * (6 n_mu + 9) * 8
+ * bytes) is rejected with JFNK_E_INVALID and a message giving the size needed.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. Every call shares
+ * the array: calls that overlap on the GPU race and must be serialised by the
+ * caller. */
+#define JFNK_STATIC_SCRATCH_BYTES (32u << 20)
+int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const double* n,
+                         const double* J_dagger, double* F, double* J_new, void* stream);
+
 /* ---- measurement ----------------------------------------------------------- */
 /* Throughput probe of one arithmetic pipe on the context's device, for roofline
  * denominators: kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add,

@@ -104,6 +104,8 @@ _SIGNATURES = {
     "jfnk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(jfnk_options), C.c_void_p,
                              C.c_void_p, C.POINTER(jfnk_stats), C.c_int, C.c_void_p]),
     "jfnk_probe_alu": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "jfnk_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
     "jfnk_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p),
                                    C.POINTER(jfnk_options), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(jfnk_stats), C.c_int,
