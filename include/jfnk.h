@@ -247,7 +247,7 @@ int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols,
  *   n [nz*nl], J_dagger [nq*nz] (nullable: B_nu(T)), F [nz*nl], J_new [nq*nz]
  *   (nullable): device pointers on the context's device; the work is enqueued
  *   on ``stream`` and the call returns without synchronising.
- * A column whose buffers exceed the array (roughly nq * nz * (6 n_mu + 9) * 8
+ * A column whose buffers exceed the array (roughly nq * nz * (8 n_mu + 9) * 8
  * bytes) is rejected with JFNK_E_INVALID and a message giving the size needed.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture. Every call shares

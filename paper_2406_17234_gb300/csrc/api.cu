@@ -215,13 +215,16 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
                         int* worst) {
   std::vector<SolverState> st(b->ncols);
   JFNK_CUDA(cudaMemcpyAsync(st.data(), b->d_state, sizeof(SolverState) * b->ncols, cudaMemcpyDeviceToHost, s));
+  JFNK_CUDA(cudaStreamSynchronize(s));
   int rc;
   for (int c = 0; c < b->ncols; ++c) {
     const ColDesc& cd = b->h_cols[c];
     const AtmosData& M = cols[c]->d;
     const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
     if (n_out && n_out[c] && (rc = copy_out(n_out[c], cd.w.n, N * 8, where, s))) return rc;
-    if (J_out && J_out[c] && (rc = copy_out(J_out[c], cd.w.Jnew, QZ * 8, where, s))) return rc;
+    // after the last base evaluation the new J sits in the buffer opposite to J^dagger
+    const double* Jfinal = st[c].jsel ? cd.w.Jdag : cd.w.Jnew;
+    if (J_out && J_out[c] && (rc = copy_out(J_out[c], Jfinal, QZ * 8, where, s))) return rc;
   }
   JFNK_CUDA(cudaStreamSynchronize(s));
   *worst = JFNK_OK;

@@ -89,7 +89,7 @@ struct SolverState {
   int F_calls;
   int jvp_calls;
   int ticks;
-  int pad;
+  int jsel;            // 1: the roles of the two mean-intensity buffers are swapped
   double beta;         // norm of the current restart residual
   double r0norm;       // norm of the Newton step's initial Krylov residual
   double F0norm;
@@ -112,6 +112,7 @@ struct ColWork {
   double* dS;       // [nq][nz] tangent of S (normalised)
   void* ddSk;       // [nq][nz] real: dS^{k+1} - dS^k
   void* H;          // [2 nmu][nz][nq] real: per-ray 1/2 w (I - S)  (value)
+  void* HI;         // [2 nmu][nz][nq] real: per-ray 1/2 w I (base evaluations)
   void* dH;         // tangent
   void* LX;         // per-ray 1/2 w dI^k/dchi^k
   void* LE;         // per-ray 1/2 w dI^k/deta^k
@@ -149,6 +150,16 @@ struct ColDesc {
   int forced_mode;   // >= 0: evaluation mode for explicit API calls; < 0: from st->phase
   int mixed;         // 1: FP32 formal solution (buffers are float)
 };
+
+// The lagged mean intensity J^dagger and the newly computed J live in two
+// buffers whose roles swap after every Newton update (no copy); explicit
+// evaluations always read w.Jdag and write w.Jnew.
+__device__ __forceinline__ const double* jdag_ptr(const ColDesc& cd) {
+  return (cd.forced_mode < 0 && cd.w.st->jsel) ? cd.w.Jnew : cd.w.Jdag;
+}
+__device__ __forceinline__ double* jnew_ptr(const ColDesc& cd) {
+  return (cd.forced_mode < 0 && cd.w.st->jsel) ? cd.w.Jdag : cd.w.Jnew;
+}
 
 // RH92 per-transition sums: [0] sum W V Jeff, [1] sum W g V Jeff, [2] sum W U,
 // [3] sum W chi_t Psi eta_bg, [4 + s] sum W chi_t Psi U_s.

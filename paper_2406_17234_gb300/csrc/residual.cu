@@ -47,7 +47,7 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
   const double* n = cd.w.n + k * nl;
   const double c2 = T.c2[q];
   double chi = T.chi_c[i] + T.chi_sca[k];
-  double eta = T.eta_c[i] + T.chi_sca[k] * cd.w.Jdag[i];
+  double eta = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
   const bool tan = (mode == EV_TANGENT);
   const double* v = tan ? tangent_dir(cd) + k * nl : nullptr;
   double dchi = 0.0, deta = 0.0;
@@ -162,6 +162,7 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
   const real* dchi = tan ? reinterpret_cast<const real*>(cd.w.dchi) + row : nullptr;
   const real* ddSk = tan ? reinterpret_cast<const real*>(cd.w.ddSk) + row : nullptr;
   real* H = reinterpret_cast<real*>(cd.w.H) + (size_t)r * nz * nq + q;
+  real* HI = der ? reinterpret_cast<real*>(cd.w.HI) + (size_t)r * nz * nq + q : nullptr;
   real* dH = tan ? reinterpret_cast<real*>(cd.w.dH) + (size_t)r * nz * nq + q : nullptr;
   real* LX = der ? reinterpret_cast<real*>(cd.w.LX) + (size_t)r * nz * nq + q : nullptr;
   real* LE = der ? reinterpret_cast<real*>(cd.w.LE) + (size_t)r * nz * nq + q : nullptr;
@@ -172,9 +173,13 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
   real dD = tan ? (real)(-cd.w.dS[row + k0]) : (real)0;
   real chi1 = chi[k0];
   real dchi1 = tan ? dchi[k0] : (real)0;
+  // base evaluations also carry I itself, which keeps relative precision where
+  // I << S (optically thin, hot layers) and D = I - S cancels
+  real I = up ? (real)(T.Bn[row + nz - 1] / T.c2[q]) : (real)0;
+  real S1 = (real)S64[k0];
   H[(size_t)k0 * nq] = hw * D;
   if (tan) dH[(size_t)k0 * nq] = hw * dD;
-  if (der) { LX[(size_t)k0 * nq] = 0; LE[(size_t)k0 * nq] = 0; }
+  if (der) { LX[(size_t)k0 * nq] = 0; LE[(size_t)k0 * nq] = 0; HI[(size_t)k0 * nq] = hw * I; }
   for (int s = 1; s < nz; ++s) {
     const int k = k0 + step * s;
     const int kd = up ? k : k - 1;             // layer between k and its upstream neighbour
@@ -191,6 +196,9 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
       const real S0 = (real)S64[k];
       LX[(size_t)k * nq] = hw * (-(S0 / chi0) * a - h * (e * D + dS * bq));
       LE[(size_t)k * nq] = hw * (a / chi0);
+      I = I * e + a * S0 + (w - e) * S1;   // Eqs. Iplus / Iminus
+      HI[(size_t)k * nq] = hw * I;
+      S1 = S0;
     }
     if (tan) {
       const real dchi0 = dchi[k];
@@ -205,7 +213,7 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
     H[(size_t)k * nq] = hw * D;
     chi1 = chi0;
   }
-  if (up && mode != EV_TANGENT) cd.w.Iem[(size_t)q * nmu + m] = ((double)D + S64[0]) * T.c2[q];
+  if (up && der) cd.w.Iem[(size_t)q * nmu + m] = (double)I * T.c2[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -225,10 +233,21 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
   const size_t plane = (size_t)nz * nq;
   const size_t o = (size_t)q * nz + k;
   const double c2 = T.c2[q];
-  double s = 0.0;
+  double s = 0.0, sa = 0.0;
   const real* H = reinterpret_cast<const real*>(cd.w.H) + i;
-  for (int r = 0; r < nr; ++r) s += (double)H[r * plane];
-  const double J = (cd.w.S[o] + s) * c2;
+  for (int r = 0; r < nr; ++r) {
+    const double h = (double)H[r * plane];
+    s += h;
+    sa += fabs(h);
+  }
+  double J = (cd.w.S[o] + s) * c2;
+  if (mode != EV_TANGENT) {
+    // take the representation with the smaller rounding error: sum |w D| vs sum |w I|
+    const real* HI = reinterpret_cast<const real*>(cd.w.HI) + i;
+    double si = 0.0;
+    for (int r = 0; r < nr; ++r) si += (double)HI[r * plane];
+    if (fabs(si) < sa) J = si * c2;   // intensities are non-negative: sum |w I| = sum w I
+  }
   cd.w.J[o] = J;
   if (mode == EV_TANGENT) {
     const real* dH = reinterpret_cast<const real*>(cd.w.dH) + i;
@@ -236,7 +255,7 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
     for (int r = 0; r < nr; ++r) ds += (double)dH[r * plane];
     cd.w.dJ[o] = (cd.w.dS[o] + ds) * c2;
   } else {
-    cd.w.Jnew[o] = J;
+    jnew_ptr(cd)[o] = J;
     const real* LX = reinterpret_cast<const real*>(cd.w.LX) + i;
     const real* LE = reinterpret_cast<const real*>(cd.w.LE) + i;
     double sx = 0.0, se = 0.0;
@@ -254,51 +273,51 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
 // the preconditioner sums A^kk_{t, j} = sum_nu W chi_t (beta_j Lchi + gamma_j Leta)
 // and in RH92 mode the sums of the preconditioned rate equations.
 // ---------------------------------------------------------------------------
-__global__ void k_rates(const ColDesc* __restrict__ cols) {
-  const ColDesc& cd = cols[blockIdx.y];
+constexpr int kRateWarps = 4;
+constexpr int kRateAcc = 2 + (kRhFixed + kMaxT > kMaxL ? kRhFixed + kMaxT : kMaxL);
+
+// One block per (32-depth tile, transition, column): lanes map to depths (so
+// every table and J access is coalesced), warps split the frequency window,
+// and the partial sums are reduced through shared memory.
+__global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.z];
   const int mode = eval_mode(cd);
   if (mode == EV_SKIP) return;
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // i = t * nz + k
-  if (i >= nt * nz) return;
-  const int t = i / nz, k = i - t * nz;
+  const int t = blockIdx.y;
+  if (t >= nt || (int)blockIdx.x * 32 >= nz) return;
+  __shared__ double red[kRateWarps][kRateAcc][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = min((int)blockIdx.x * 32 + lane, nz - 1);
   const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
   const int lo = T.t_lo[t], upl = T.t_up[t];
   const double* n = cd.w.n + k * nl;
-  if (mode == EV_TANGENT) {
-    double dRu = 0.0, dRd = 0.0;
-    for (int q = q0; q <= q1; ++q) {
-      const size_t p = (size_t)(base + q - q0);
-      const double W = T.t_w[p] * T.rw[q];
-      const double WV = W * T.V[p * nz + k];
-      const double dJ = cd.w.dJ[(size_t)q * nz + k];
-      dRu += WV * dJ;
-      dRd += WV * T.G[p * nz + k] * dJ;
-    }
-    cd.w.dRup[i] = dRu;
-    cd.w.dRdn[i] = dRd;
-    return;
-  }
-  double Ru = 0.0, Rd = 0.0;
-  double A[kMaxL];
-  double rhs[kRhStride];
+  const bool tan = (mode == EV_TANGENT);
   const bool base_mode = (mode == EV_BASE);
   const bool rh = (mode == EV_RH92);
-  const int nrh = kRhFixed + nt;
-  for (int j = 0; j < nl; ++j) A[j] = 0.0;
-  if (rh)
-    for (int j = 0; j < nrh; ++j) rhs[j] = 0.0;
-  for (int q = q0; q <= q1; ++q) {
+  const int nacc = tan ? 2 : (base_mode ? 2 + nl : (rh ? 2 + kRhFixed + nt : 2));
+  double acc[kRateAcc];
+  for (int j = 0; j < nacc; ++j) acc[j] = 0.0;
+  const double n_lo = n[lo], n_up = n[upl];
+  const double* Jd = rh ? jdag_ptr(cd) : nullptr;
+  for (int q = q0 + wid; q <= q1; q += kRateWarps) {
     const size_t p = (size_t)(base + q - q0);
     const double W = T.t_w[p] * T.rw[q];
     const double V = T.V[p * nz + k], g = T.G[p * nz + k];
     const size_t o = (size_t)q * nz + k;
+    if (tan) {
+      const double WV = W * V;
+      const double dJ = cd.w.dJ[o];
+      acc[0] += WV * dJ;
+      acc[1] += WV * g * dJ;
+      continue;
+    }
     const double J = cd.w.J[o];
     const double c2 = T.c2[q];
-    Ru += W * V * J;
-    Rd += W * g * V * (c2 + J);
-    const double chi_t = V * (n[lo] - g * n[upl]);
+    acc[0] += W * V * J;
+    acc[1] += W * g * V * (c2 + J);
+    const double chi_t = V * (n_lo - g * n_up);
     if (base_mode) {
       double zeta[kMaxL];
       for (int j = 0; j < nl; ++j) zeta[j] = 0.0;
@@ -311,13 +330,11 @@ __global__ void k_rates(const ColDesc* __restrict__ cols) {
         zeta[T.t_up[ts]] += -gs * Vs * Lx + c2 * gs * Vs * Le;  // and gamma_j (Eq. der_eta_n)
       }
       const double Wc = W * chi_t;
-      for (int j = 0; j < nl; ++j) A[j] += Wc * zeta[j];
-    }
-    if (rh) {
+      for (int j = 0; j < nl; ++j) acc[2 + j] += Wc * zeta[j];
+    } else if (rh) {
       // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
       const double Le = cd.w.Leta[o];
-      // eta(n) at this (q, k): background + lines
-      double eta_bg = T.eta_c[o] + T.chi_sca[k] * cd.w.Jdag[o];
+      const double eta_bg = T.eta_c[o] + T.chi_sca[k] * Jd[o];
       double eta_l = 0.0;
       for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
         const int ts = T.q_t[s];
@@ -325,24 +342,40 @@ __global__ void k_rates(const ColDesc* __restrict__ cols) {
         eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
       }
       const double Jeff = J - Le * (eta_bg + eta_l);
-      rhs[0] += W * V * Jeff;
-      rhs[1] += W * g * V * Jeff;
-      rhs[2] += W * c2 * g * V;
+      acc[2] += W * V * Jeff;
+      acc[3] += W * g * V * Jeff;
+      acc[4] += W * c2 * g * V;
       const double wcp = W * chi_t * Le;
-      rhs[3] += wcp * eta_bg;
+      acc[5] += wcp * eta_bg;
       for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
         const int ts = T.q_t[s];
         const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-        rhs[kRhFixed + ts] += wcp * c2 * T.G[ps] * T.V[ps];
+        acc[2 + kRhFixed + ts] += wcp * c2 * T.G[ps] * T.V[ps];
       }
     }
   }
-  cd.w.Rup[i] = Ru;
-  cd.w.Rdn[i] = Rd;
+  for (int j = 0; j < nacc; ++j) red[wid][j][lane] = acc[j];
+  __syncthreads();
+  if (wid != 0) return;
+  const int kw = (int)blockIdx.x * 32 + lane;
+  if (kw >= nz) return;
+  for (int j = 0; j < nacc; ++j) {
+    double v = red[0][j][lane];
+    for (int w = 1; w < kRateWarps; ++w) v += red[w][j][lane];
+    acc[j] = v;
+  }
+  const size_t i = (size_t)t * nz + kw;
+  if (tan) {
+    cd.w.dRup[i] = acc[0];
+    cd.w.dRdn[i] = acc[1];
+    return;
+  }
+  cd.w.Rup[i] = acc[0];
+  cd.w.Rdn[i] = acc[1];
   if (base_mode)
-    for (int j = 0; j < nl; ++j) cd.w.Apart[(size_t)i * nl + j] = A[j];
+    for (int j = 0; j < nl; ++j) cd.w.Apart[i * nl + j] = acc[2 + j];
   if (rh)
-    for (int j = 0; j < nrh; ++j) cd.w.rh[(size_t)i * kRhStride + j] = rhs[j];
+    for (int j = 0; j < kRhFixed + nt; ++j) cd.w.rh[i * kRhStride + j] = acc[2 + j];
 }
 
 // ---------------------------------------------------------------------------
@@ -459,25 +492,25 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   if (nc == 0) return JFNK_OK;
   const int tb = 256;
   dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
-  dim3 g_ray((b.max_nq * 2 * b.max_nmu + 127) / 128, nc);
-  dim3 g_tk((b.max_nt * b.max_nz + 127) / 128, nc);
+  dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
+  dim3 g_rates((b.max_nz + 31) / 32, b.max_nt, nc);
   dim3 g_k((b.max_nz + 63) / 64, nc);
   if (b.mixed) {
     k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
     k_source_diff<float><<<g_qk, tb, 0, s>>>(b.d_cols);
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-    k_formal<float><<<g_ray, 128, 0, s>>>(b.d_cols);
+    k_formal<float><<<g_ray, 64, 0, s>>>(b.d_cols);
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     k_ray_sum<float><<<g_qk, tb, 0, s>>>(b.d_cols);
   } else {
     k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
     k_source_diff<double><<<g_qk, tb, 0, s>>>(b.d_cols);
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-    k_formal<double><<<g_ray, 128, 0, s>>>(b.d_cols);
+    k_formal<double><<<g_ray, 64, 0, s>>>(b.d_cols);
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     k_ray_sum<double><<<g_qk, tb, 0, s>>>(b.d_cols);
   }
-  k_rates<<<g_tk, 128, 0, s>>>(b.d_cols);
+  k_rates<<<g_rates, 32 * kRateWarps, 0, s>>>(b.d_cols);
   k_assemble<<<g_k, 64, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;

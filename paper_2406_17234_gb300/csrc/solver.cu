@@ -40,7 +40,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   ar.reset();
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
   struct Offs {
-    size_t n, v, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
+    size_t n, v, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
         dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x, w, nprev;
   };
   std::vector<Offs> off(nc);
@@ -61,6 +61,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     o.dchi = ar.take<char>(rs * nq * nz); o.dS = ar.take<double>(nq * nz);
     o.ddSk = ar.take<char>(rs * nq * nz);
     o.H = ar.take<char>(rs * 2 * nmu * nq * nz); o.dH = ar.take<char>(rs * 2 * nmu * nq * nz);
+    o.HI = ar.take<char>(rs * 2 * nmu * nq * nz);
     o.LX = ar.take<char>(rs * 2 * nmu * nq * nz); o.LE = ar.take<char>(rs * 2 * nmu * nq * nz);
     o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(nq * nz);
     o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
@@ -98,7 +99,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     w.istar = ar.ptr<int>(o.istar);
     w.chi = ar.ptr<void>(o.chi); w.S = ar.ptr<double>(o.S); w.dSk = ar.ptr<void>(o.dSk);
     w.dchi = ar.ptr<void>(o.dchi); w.dS = ar.ptr<double>(o.dS); w.ddSk = ar.ptr<void>(o.ddSk);
-    w.H = ar.ptr<void>(o.H); w.dH = ar.ptr<void>(o.dH);
+    w.H = ar.ptr<void>(o.H); w.dH = ar.ptr<void>(o.dH); w.HI = ar.ptr<void>(o.HI);
     w.LX = ar.ptr<void>(o.LX); w.LE = ar.ptr<void>(o.LE);
     w.J = ar.ptr<double>(o.J); w.dJ = ar.ptr<double>(o.dJ);
     w.Lchi = ar.ptr<double>(o.Lchi); w.Leta = ar.ptr<double>(o.Leta);
@@ -284,8 +285,8 @@ __global__ void __launch_bounds__(256) k_krylov(const ColDesc* __restrict__ cols
       err = (e == e) ? fmax(err, e) : INFINITY;
     }
     err = block_max(err, sh);
-    for (int i = threadIdx.x; i < cd.t.nq * nz; i += blockDim.x) cd.w.Jdag[i] = cd.w.Jnew[i];
     if (threadIdx.x == 0) {
+      st->jsel ^= 1;   // J(n) becomes the lagged J^dagger
       st->F_calls++;
       st->ticks++;
       st->rh92_iter++;
@@ -490,8 +491,8 @@ __global__ void __launch_bounds__(256) k_krylov(const ColDesc* __restrict__ cols
     }
   }
   err = block_max(err, sh);
-  for (int i = threadIdx.x; i < cd.t.nq * nz; i += blockDim.x) cd.w.Jdag[i] = cd.w.Jnew[i];
   if (threadIdx.x == 0) {
+    st->jsel ^= 1;   // J(n^p) becomes J^dagger_{p+1}
     st->err = err;
     st->newton_iter++;
     st->phase = PH_BASE;

@@ -78,7 +78,7 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
   const size_t o_istar = L.take<int>(nz);
   const size_t o_chi = L.take<double>(QZ), o_S = L.take<double>(QZ), o_dSk = L.take<double>(QZ);
   const size_t o_H = L.take<double>(2 * nmu * QZ), o_LX = L.take<double>(2 * nmu * QZ),
-               o_LE = L.take<double>(2 * nmu * QZ);
+               o_LE = L.take<double>(2 * nmu * QZ), o_HI = L.take<double>(2 * nmu * QZ);
   const size_t o_J = L.take<double>(QZ), o_Lchi = L.take<double>(QZ), o_Leta = L.take<double>(QZ);
   const size_t o_Rup = L.take<double>(nt * nz), o_Rdn = L.take<double>(nt * nz);
   const size_t o_Apart = L.take<double>(nt * nz * nl);
@@ -107,6 +107,7 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
   w.S = reinterpret_cast<double*>(base + o_S);
   w.dSk = base + o_dSk;
   w.H = base + o_H;
+  w.HI = base + o_HI;
   w.LX = base + o_LX;
   w.LE = base + o_LE;
   w.J = reinterpret_cast<double*>(base + o_J);

@@ -175,7 +175,9 @@ def test_solve_ca_small_matches_oracle(ctx):
 def test_solve_mixed_precision_against_fp64_oracle(ctx):
     wl = CASES["ca-small"]()
     atom, atm, m = _pair(ctx, wl, n_mu=3)
-    n, J, st = B.solve(atm, B.default_options(rtol=1e-4, ftol=1e-6, precision=B.JFNK_MIXED))
+    # FP32 formal solutions put a floor near 1e-6 under the population change,
+    # so the mixed mode is converged to 1e-5 here
+    n, J, st = B.solve(atm, B.default_options(rtol=1e-4, ftol=1e-5, precision=B.JFNK_MIXED))
     ref = jfnk(m, m.nstar, rtol=1e-6, ftol=1e-10)
     assert st["status"] == 0
     np.testing.assert_allclose(n, ref.n, rtol=1e-3)
@@ -201,12 +203,12 @@ def test_batch_equals_single(ctx, precision):
     wl = W.config4(n_columns=5, nz_min=60, nz_max=90, nu_scale=0.1)
     atom = B.Atom(ctx, wl.atom)
     atms = [B.Atmosphere(ctx, atom, c, n_mu=3) for c in wl.columns]
-    opts = B.default_options(rtol=1e-6, ftol=1e-9, precision=precision)
+    tol = dict(rtol=1e-6, ftol=1e-9) if precision == 0 else dict(rtol=1e-4, ftol=1e-5)
+    opts = B.default_options(precision=precision, **tol)
     ns, stats = B.batch_solve(ctx, atms, opts, raise_on_fail=False)
     assert sum(s["status"] == 0 for s in stats) >= 3
     for a, nb, s in zip(atms, ns, stats):
-        n1, _, s1 = B.solve(a, B.default_options(rtol=1e-6, ftol=1e-9, precision=precision),
-                            raise_on_fail=False)
+        n1, _, s1 = B.solve(a, B.default_options(precision=precision, **tol), raise_on_fail=False)
         assert s["status"] == s1["status"]
         assert s["F_calls"] == s1["F_calls"]
         if s["status"] == 0:
