@@ -1,0 +1,283 @@
+// Fused formal solution + ray sums (steps a2 and the angle integral of a3),
+// one block per (block of Qb frequencies, column).
+//
+// Everything transcendental in the piecewise-linear recurrence (App. A.1:
+// exp(-dtau), w, a, b/dtau, and the tangent and preconditioner coefficients of
+// App. A.2) depends on the opacities only, never on the intensity. So the
+// block first computes those coefficients for every (depth, ray) pair in
+// parallel into shared memory (phase A); one thread per ray then runs the
+// sequential recurrence, which is a fused multiply-add per step (phase B);
+// finally the rays are summed per (frequency, depth) in shared memory into
+// J, dJ, Lambda_chi and Lambda_eta (phase C). No per-ray array reaches
+// global memory.
+//
+// The recurrences (exactly those of Eqs. Iplus/Iminus, rewritten):
+//   D = I - S:  D^k = D^u e + w (S^u - S^k)                   (all modes)
+//   tangent:    dD^k = dD^u e - ddtau (e D^u + bq (S^u - S^k)) + w (dS^u - dS^k)
+//   base:       I^k = I^u e + a S^k + b S^u ;  dI^k/dchi^k = hw-scaled a_chi
+//               with S^u - I^u = -D^u ; dI^k/deta^k = a / chi^k
+// where u is the upstream depth (k+1 for mu > 0, k-1 for mu < 0).
+#include "internal.cuh"
+
+namespace jfnk {
+
+__device__ __forceinline__ int eval_mode_f(const ColDesc& cd) {
+  if (cd.forced_mode >= 0) return cd.forced_mode;
+  switch (cd.w.st->phase) {
+    case PH_BASE: return EV_BASE;
+    case PH_JVP:
+    case PH_RESTART: return EV_TANGENT;
+    case PH_RH92: return EV_RH92;
+    default: return EV_SKIP;
+  }
+}
+
+// Taylor-series / direct coefficients (see residual.cu for the derivation).
+__device__ __forceinline__ void pl_coef_f(double x, double& e, double& w, double& a, double& bq) {
+  e = exp(-x);
+  if (x < 0.1) {
+    double pw = 0.0, pa = 0.0, pb = 0.0;
+    double inv_fact[17];
+    inv_fact[0] = 1.0;
+#pragma unroll
+    for (int m = 1; m < 17; ++m) inv_fact[m] = inv_fact[m - 1] / m;
+#pragma unroll
+    for (int m = 13; m >= 0; --m) {
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      pw = pw * x + sg * inv_fact[m + 1];
+      pa = pa * x + sg * inv_fact[m + 2];
+      pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
+    }
+    w = pw;
+    a = pa * x;
+    bq = pb;
+  } else {
+    const double r = 1.0 / x;
+    w = (1.0 - e) * r;
+    a = 1.0 - w;
+    bq = (w - e) * r;
+  }
+}
+
+__device__ __forceinline__ void pl_coef_f(float x, float& e, float& w, float& a, float& bq) {
+  e = __expf(-x);
+  if (x < 0.1f) {
+    w = fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
+    a = x * fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f);
+    bq = fmaf(fmaf(fmaf(fmaf(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
+  } else {
+    const float r = __frcp_rn(x);
+    w = (1.0f - e) * r;
+    a = 1.0f - w;
+    bq = (w - e) * r;
+  }
+}
+
+constexpr int kFusedThreads = 256;
+constexpr int kFusedSlots = 6;   // E, X(D), P1(dD coef | I), P2(dD | LX), LB, LE
+constexpr int kFusedStage = 5;   // chi, S, dS, dchi, ddS per (q, k)
+
+__host__ __device__ inline size_t round16(size_t bytes) { return (bytes + 15) / 16 * 16; }
+
+size_t fused_smem_bytes(int qb, int nz, int nmu, bool mixed) {
+  const size_t rs = mixed ? 4 : 8;
+  const size_t stage = round16(rs * ((size_t)kFusedStage * qb * nz + qb));
+  const size_t slots = rs * (size_t)kFusedSlots * nz * qb * 2 * nmu;
+  return stage + slots;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* __restrict__ cols, int Qb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode_f(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nmu = T.nmu, nr = 2 * nmu;
+  const int qb0 = blockIdx.x * Qb;
+  if (qb0 >= nq) return;
+  const int nqb = min(Qb, nq - qb0);
+  const int R = Qb * nr;
+  const int nray = nqb * nr;
+  const bool tan = (mode == EV_TANGENT);
+  const bool der = (mode == EV_BASE || mode == EV_RH92);
+  real* st = reinterpret_cast<real*>(smem_raw);
+  real* s_chi = st;
+  real* s_S = s_chi + Qb * nz;
+  real* s_dS = s_S + Qb * nz;
+  real* s_dchi = s_dS + Qb * nz;
+  real* s_ddS = s_dchi + Qb * nz;
+  real* s_Bb = s_ddS + Qb * nz;
+  real* slot = reinterpret_cast<real*>(smem_raw + round16(sizeof(real) * ((size_t)kFusedStage * Qb * nz + Qb)));
+  const size_t plane = (size_t)nz * R;
+  real* E = slot;
+  real* X = E + plane;
+  real* P1 = X + plane;    // tangent: -ddtau e        | base: a S^k + b S^u, then hw I
+  real* P2 = P1 + plane;   // tangent: coefficient, then hw dD | base: LX constant, then hw dI/dchi
+  real* LB = P2 + plane;   // base: LX slope on D^u
+  real* LE = LB + plane;   // base: hw dI/deta
+  const real* chi_g = reinterpret_cast<const real*>(cd.w.chi);
+  const real* dchi_g = reinterpret_cast<const real*>(cd.w.dchi);
+  const double* S64 = cd.w.S;
+  const double* dS64 = cd.w.dS;
+
+  // phase 0: stage the block's opacities and source-function differences
+  for (int i = threadIdx.x; i < nqb * nz; i += blockDim.x) {
+    const int ql = i / nz, k = i - ql * nz;
+    const size_t o = (size_t)(qb0 + ql) * nz + k;
+    s_chi[i] = chi_g[o];
+    s_S[i] = (real)S64[o];
+    s_dS[i] = (k < nz - 1) ? (real)(S64[o + 1] - S64[o]) : (real)0;   // formed in FP64
+    if (tan) {
+      s_dchi[i] = dchi_g[o];
+      s_ddS[i] = (k < nz - 1) ? (real)(dS64[o + 1] - dS64[o]) : (real)0;
+    }
+  }
+  for (int ql = threadIdx.x; ql < nqb; ql += blockDim.x) {
+    const int q = qb0 + ql;
+    s_Bb[ql] = (real)(T.Bn[(size_t)q * nz + nz - 1] / T.c2[q]);
+  }
+  __syncthreads();
+
+  // phase A: coefficients of every (depth, ray) step, in parallel
+  for (int i = threadIdx.x; i < nz * nray; i += blockDim.x) {
+    const int k = i / nray, ray = i - k * nray;
+    const int ql = ray / nr, rr = ray - ql * nr;
+    const bool up = rr < nmu;
+    if ((up && k == nz - 1) || (!up && k == 0)) continue;
+    const int m = up ? rr : rr - nmu;
+    const int ku = up ? k + 1 : k - 1;
+    const int kd = up ? k : k - 1;
+    const real inv2mu = (real)(0.5 / T.mu[m]);
+    const real hw = (real)(0.5 * T.wmu[m]);
+    const real* ch = s_chi + ql * nz;
+    const real c0 = ch[k], cu = ch[ku];
+    const real h = (real)T.dz[kd] * inv2mu;
+    const real dtau = h * (c0 + cu);
+    real e, w, a, bq;
+    pl_coef_f(dtau, e, w, a, bq);
+    const real dSin = up ? s_dS[ql * nz + k] : -s_dS[ql * nz + k - 1];
+    const size_t si = (size_t)k * R + ray;
+    E[si] = e;
+    X[si] = w * dSin;
+    if (tan) {
+      const real ddtau = h * (s_dchi[ql * nz + k] + s_dchi[ql * nz + ku]);
+      const real ddSin = up ? s_ddS[ql * nz + k] : -s_ddS[ql * nz + k - 1];
+      P1[si] = -ddtau * e;
+      P2[si] = -ddtau * bq * dSin + w * ddSin;
+    } else if (der) {
+      const real S0 = s_S[ql * nz + k], Su = s_S[ql * nz + ku];
+      P1[si] = a * S0 + bq * dtau * Su;
+      P2[si] = hw * (-(S0 / c0) * a - h * dSin * bq);
+      LB[si] = -hw * h * e;
+      LE[si] = hw * (a / c0);
+    }
+  }
+  __syncthreads();
+
+  // phase B: the sequential recurrence, one thread per ray
+  for (int ray = threadIdx.x; ray < nray; ray += blockDim.x) {
+    const int ql = ray / nr, rr = ray - ql * nr;
+    const bool up = rr < nmu;
+    const int m = up ? rr : rr - nmu;
+    const int q = qb0 + ql;
+    const real hw = (real)(0.5 * T.wmu[m]);
+    const int k0 = up ? nz - 1 : 0;
+    const int step = up ? -1 : 1;
+    const size_t o0 = (size_t)q * nz + k0;
+    real D = up ? (real)(T.Bn[(size_t)q * nz + nz - 1] / T.c2[q] - S64[o0]) : (real)(-S64[o0]);
+    real dD = tan ? (real)(-dS64[o0]) : (real)0;
+    real I = up ? s_Bb[ql] : (real)0;
+    size_t si = (size_t)k0 * R + ray;
+    X[si] = hw * D;
+    if (tan) P2[si] = hw * dD;
+    if (der) { P1[si] = hw * I; P2[si] = 0; LE[si] = 0; }
+    for (int s = 1; s < nz; ++s) {
+      si = (size_t)(k0 + step * s) * R + ray;
+      const real e = E[si];
+      const real Dn = D * e + X[si];
+      if (tan) {
+        const real dDn = dD * e + P1[si] * D + P2[si];
+        P2[si] = hw * dDn;
+        dD = dDn;
+      } else if (der) {
+        I = I * e + P1[si];
+        P1[si] = hw * I;
+        P2[si] = P2[si] + LB[si] * D;
+      }
+      D = Dn;
+      X[si] = hw * D;
+    }
+    if (up && der) cd.w.Iem[(size_t)q * nmu + m] = (double)I * T.c2[q];
+  }
+  __syncthreads();
+
+  // phase C: sums over the rays of each (frequency, depth)
+  double* Jout = cd.w.J;
+  for (int i = threadIdx.x; i < nqb * nz; i += blockDim.x) {
+    const int ql = i / nz, k = i - ql * nz;
+    const int q = qb0 + ql;
+    const size_t o = (size_t)q * nz + k;
+    const size_t b0 = (size_t)k * R + ql * nr;
+    const double c2 = T.c2[q];
+    double sD = 0.0, sa = 0.0;
+    for (int rr = 0; rr < nr; ++rr) {
+      const double v = (double)X[b0 + rr];
+      sD += v;
+      sa += fabs(v);
+    }
+    double J = (S64[o] + sD) * c2;
+    if (tan) {
+      double sd = 0.0;
+      for (int rr = 0; rr < nr; ++rr) sd += (double)P2[b0 + rr];
+      cd.w.dJ[o] = (dS64[o] + sd) * c2;
+    } else if (der) {
+      double sI = 0.0, sx = 0.0, se = 0.0;
+      for (int rr = 0; rr < nr; ++rr) {
+        sI += (double)P1[b0 + rr];
+        sx += (double)P2[b0 + rr];
+        se += (double)LE[b0 + rr];
+      }
+      // the representation with the smaller rounding error (intensities are >= 0)
+      if (fabs(sI) < sa) J = sI * c2;
+      jnew_ptr(cd)[o] = J;
+      cd.w.Lchi[o] = sx * c2;
+      cd.w.Leta[o] = se;
+    }
+    Jout[o] = J;
+  }
+}
+
+int fused_prepare(Batch* b) {
+  if (b->formal_qb <= 0) return JFNK_OK;
+  const size_t bytes = fused_smem_bytes(b->formal_qb, b->max_nz, b->max_nmu, b->mixed != 0);
+  if (b->mixed)
+    JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  else
+    JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return JFNK_OK;
+}
+
+int launch_formal_fused(const Batch& b, cudaStream_t s) {
+  const int qb = b.formal_qb;
+  const size_t bytes = fused_smem_bytes(qb, b.max_nz, b.max_nmu, b.mixed != 0);
+  dim3 g((b.max_nq + qb - 1) / qb, b.ncols);
+  if (b.mixed)
+    k_formal_fused<float><<<g, kFusedThreads, bytes, s>>>(b.d_cols, qb);
+  else
+    k_formal_fused<double><<<g, kFusedThreads, bytes, s>>>(b.d_cols, qb);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+// Largest frequency block whose shared memory still lets two blocks share an SM
+// (0 when even one frequency does not fit: the unfused kernels are used).
+int fused_default_qb(int max_nz, int max_nmu, bool mixed) {
+  const size_t cap = 227 * 1024;
+  for (int qb : {8, 4, 2, 1})
+    if (2 * fused_smem_bytes(qb, max_nz, max_nmu, mixed) <= cap) return qb;
+  if (fused_smem_bytes(1, max_nz, max_nmu, mixed) <= cap) return 1;
+  return 0;
+}
+
+}  // namespace jfnk

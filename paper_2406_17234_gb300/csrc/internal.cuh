@@ -95,6 +95,7 @@ struct Batch {
   cudaGraphExec_t graph = nullptr;    // captured tick sequence
   int graph_ticks = 0;
   bool graph_profiled = false;
+  int formal_qb = 0;                  // frequencies per block of the fused formal kernel (0: unfused)
   std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel of each tick
   std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve
   int* h_status = nullptr;            // pinned host mirror of d_status
@@ -109,6 +110,11 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                       cudaEvent_t ev1 = nullptr);
 // Launch of the Krylov/Newton state machine step.
 int launch_krylov_step(const Batch& b, cudaStream_t s);
+// Fused formal solution + ray sums (formal_fused.cu).
+size_t fused_smem_bytes(int qb, int nz, int nmu, bool mixed);
+int fused_default_qb(int max_nz, int max_nmu, bool mixed);
+int fused_prepare(Batch* b);
+int launch_formal_fused(const Batch& b, cudaStream_t s);
 // Sets every column's forced evaluation mode (explicit API calls) or -1.
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.

@@ -90,39 +90,47 @@ __global__ void k_source_diff(const ColDesc* __restrict__ cols) {
 }
 
 // Piecewise-linear coefficients (App. A.1) in the form the difference
-// recurrence needs: e = exp(-x), w = (1 - e)/x (so a = 1 - w, b = w - e) and
-// bq = b/x, by Taylor series below x = 0.1 where 1 - e cancels.
-__device__ __forceinline__ void pl_coef(double x, double& e, double& w, double& bq) {
+// recurrence needs: e = exp(-x), w = (1 - e)/x, a = 1 - w and bq = b/x with
+// b = w - e. Below x = 0.1 every one of them comes from its own Taylor series,
+// since 1 - e, 1 - w and w - e all cancel there (a = 1 - w loses all FP32
+// digits at x ~ 1e-6).
+__device__ __forceinline__ void pl_coef(double x, double& e, double& w, double& a, double& bq) {
   e = exp(-x);
   if (x < 0.1) {
-    // w = sum_{n>=0} (-x)^n/(n+1)!, bq = sum_{n>=1} (-1)^{n+1} n x^{n-1}/(n+1)!
-    double pw = 0.0, pb = 0.0;
-    double inv_fact[16];
+    // w = sum_{n>=0} (-x)^n/(n+1)!, a = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!,
+    // bq = sum_{n>=1} (-1)^{n+1} n x^{n-1}/(n+1)!
+    double pw = 0.0, pa = 0.0, pb = 0.0;
+    double inv_fact[17];
     inv_fact[0] = 1.0;
-    for (int m = 1; m < 16; ++m) inv_fact[m] = inv_fact[m - 1] / m;
+    for (int m = 1; m < 17; ++m) inv_fact[m] = inv_fact[m - 1] / m;
     for (int m = 13; m >= 0; --m) {
       const double sg = (m & 1) ? -1.0 : 1.0;
       pw = pw * x + sg * inv_fact[m + 1];
+      pa = pa * x + sg * inv_fact[m + 2];
       pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
     }
     w = pw;
+    a = pa * x;
     bq = pb;
   } else {
     const double r = 1.0 / x;
     w = (1.0 - e) * r;
+    a = 1.0 - w;
     bq = (w - e) * r;
   }
 }
 
-__device__ __forceinline__ void pl_coef(float x, float& e, float& w, float& bq) {
+__device__ __forceinline__ void pl_coef(float x, float& e, float& w, float& a, float& bq) {
   e = __expf(-x);
   if (x < 0.1f) {
     // the same series to x^5 (truncation below 3e-10 relative)
     w = fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
+    a = x * fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f);
     bq = fmaf(fmaf(fmaf(fmaf(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
   } else {
     const float r = __frcp_rn(x);
     w = (1.0f - e) * r;
+    a = 1.0f - w;
     bq = (w - e) * r;
   }
 }
@@ -187,16 +195,15 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
     const real dS = up ? dSk[k] : -dSk[k - 1];  // S_upstream - S^k
     const real h = (real)T.dz[kd] * inv2mu;
     const real dtau = h * (chi0 + chi1);
-    real e, w, bq;
-    pl_coef(dtau, e, w, bq);
+    real e, w, a, bq;
+    pl_coef(dtau, e, w, a, bq);
     const real Dnew = D * e + w * dS;
     if (der) {
       // App. A.2 with S_up - I_up = -D_up
-      const real a = (real)1 - w;
       const real S0 = (real)S64[k];
       LX[(size_t)k * nq] = hw * (-(S0 / chi0) * a - h * (e * D + dS * bq));
       LE[(size_t)k * nq] = hw * (a / chi0);
-      I = I * e + a * S0 + (w - e) * S1;   // Eqs. Iplus / Iminus
+      I = I * e + a * S0 + (bq * dtau) * S1;   // Eqs. Iplus / Iminus, b = bq dtau
       HI[(size_t)k * nq] = hw * I;
       S1 = S0;
     }
@@ -495,7 +502,15 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
   dim3 g_rates((b.max_nz + 31) / 32, b.max_nt, nc);
   dim3 g_k((b.max_nz + 63) / 64, nc);
-  if (b.mixed) {
+  if (b.formal_qb > 0) {
+    // opacity, then the fused formal solution with in-block ray sums
+    if (b.mixed) k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+    else k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+    int rc = launch_formal_fused(b, s);
+    if (rc) return rc;
+    if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+  } else if (b.mixed) {
     k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
     k_source_diff<float><<<g_qk, tb, 0, s>>>(b.d_cols);
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));

@@ -39,6 +39,10 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   DeviceArena& ar = b->arena;
   ar.reset();
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
+  int mnz = 0, mnmu = 0;
+  for (auto* c : cols) { mnz = std::max(mnz, c->nz); mnmu = std::max(mnmu, c->nmu); }
+  b->formal_qb = fused_default_qb(mnz, mnmu, mixed != 0);
+  const bool per_ray = (b->formal_qb == 0);   // unfused kernels need per-ray buffers
   struct Offs {
     size_t n, v, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
         dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x, w, nprev;
@@ -57,12 +61,12 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     o.Jdag = ar.take<double>(nq * nz); o.Jnew = ar.take<double>(nq * nz);
     o.istar = ar.take<int>(nz);
     o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<double>(nq * nz);
-    o.dSk = ar.take<char>(rs * nq * nz);
+    o.dSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
     o.dchi = ar.take<char>(rs * nq * nz); o.dS = ar.take<double>(nq * nz);
-    o.ddSk = ar.take<char>(rs * nq * nz);
-    o.H = ar.take<char>(rs * 2 * nmu * nq * nz); o.dH = ar.take<char>(rs * 2 * nmu * nq * nz);
-    o.HI = ar.take<char>(rs * 2 * nmu * nq * nz);
-    o.LX = ar.take<char>(rs * 2 * nmu * nq * nz); o.LE = ar.take<char>(rs * 2 * nmu * nq * nz);
+    o.ddSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
+    const size_t pr = per_ray ? rs * 2 * nmu * nq * nz : 0;
+    o.H = ar.take<char>(pr); o.dH = ar.take<char>(pr); o.HI = ar.take<char>(pr);
+    o.LX = ar.take<char>(pr); o.LE = ar.take<char>(pr);
     o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(nq * nz);
     o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
     o.Rup = ar.take<double>(nt * nz); o.Rdn = ar.take<double>(nt * nz);
@@ -116,7 +120,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   }
   JFNK_CUDA(cudaMemcpy(b->d_cols, b->h_cols.data(), nc * sizeof(ColDesc), cudaMemcpyHostToDevice));
   JFNK_CUDA(cudaMemset(b->d_state, 0, nc * sizeof(SolverState)));
-  return JFNK_OK;
+  return fused_prepare(b);
 }
 
 __global__ void k_set_forced(ColDesc* cols, int mode) { cols[blockIdx.x].forced_mode = mode; }
