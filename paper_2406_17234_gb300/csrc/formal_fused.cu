@@ -192,10 +192,16 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     X[si] = hw * D;
     if (tan) P2[si] = hw * dD;
     if (der) { P1[si] = hw * I; P2[si] = 0; LE[si] = 0; }
+    // In base evaluations D is re-anchored on I - S whenever that is the
+    // better-conditioned value: D carries an absolute error of the order of
+    // the largest |D| met upstream (attenuated along the ray), I - S one of
+    // the order of |I| + |S|.
+    real M = D < (real)0 ? -D : D;
     for (int s = 1; s < nz; ++s) {
-      si = (size_t)(k0 + step * s) * R + ray;
+      const int k = k0 + step * s;
+      si = (size_t)k * R + ray;
       const real e = E[si];
-      const real Dn = D * e + X[si];
+      real Dn = D * e + X[si];
       if (tan) {
         const real dDn = dD * e + P1[si] * D + P2[si];
         P2[si] = hw * dDn;
@@ -204,6 +210,14 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
         I = I * e + P1[si];
         P1[si] = hw * I;
         P2[si] = P2[si] + LB[si] * D;
+        const real Sk = s_S[ql * nz + k];
+        const real aD = Dn < (real)0 ? -Dn : Dn;
+        M = fmax(M * e, aD);
+        const real anchor = (I < (real)0 ? -I : I) + (Sk < (real)0 ? -Sk : Sk);
+        if (anchor < M) {
+          Dn = I - Sk;
+          M = anchor;
+        }
       }
       D = Dn;
       X[si] = hw * D;

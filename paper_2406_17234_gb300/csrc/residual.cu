@@ -188,6 +188,7 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
   H[(size_t)k0 * nq] = hw * D;
   if (tan) dH[(size_t)k0 * nq] = hw * dD;
   if (der) { LX[(size_t)k0 * nq] = 0; LE[(size_t)k0 * nq] = 0; HI[(size_t)k0 * nq] = hw * I; }
+  real M = D < (real)0 ? -D : D;   // attenuated bound of |D| upstream (base re-anchoring)
   for (int s = 1; s < nz; ++s) {
     const int k = k0 + step * s;
     const int kd = up ? k : k - 1;             // layer between k and its upstream neighbour
@@ -197,7 +198,7 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
     const real dtau = h * (chi0 + chi1);
     real e, w, a, bq;
     pl_coef(dtau, e, w, a, bq);
-    const real Dnew = D * e + w * dS;
+    real Dnew = D * e + w * dS;
     if (der) {
       // App. A.2 with S_up - I_up = -D_up
       const real S0 = (real)S64[k];
@@ -206,6 +207,14 @@ __global__ void k_formal(const ColDesc* __restrict__ cols) {
       I = I * e + a * S0 + (bq * dtau) * S1;   // Eqs. Iplus / Iminus, b = bq dtau
       HI[(size_t)k * nq] = hw * I;
       S1 = S0;
+      // re-anchor D on I - S where that is better conditioned
+      const real aD = Dnew < (real)0 ? -Dnew : Dnew;
+      M = fmax(M * e, aD);
+      const real anchor = (I < (real)0 ? -I : I) + (S0 < (real)0 ? -S0 : S0);
+      if (anchor < M) {
+        Dnew = I - S0;
+        M = anchor;
+      }
     }
     if (tan) {
       const real dchi0 = dchi[k];
