@@ -32,8 +32,9 @@ __device__ __forceinline__ int eval_mode_f(const ColDesc& cd) {
   }
 }
 
-// Taylor-series / direct coefficients (see residual.cu for the derivation).
-__device__ __forceinline__ void pl_coef_f(double x, double& e, double& w, double& a, double& bq) {
+// Taylor-series / direct coefficients (see residual.cu for the derivation);
+// r = 1/x is supplied by the caller (shared between the rays of a layer).
+__device__ __forceinline__ void pl_coef_f(double x, double r, double& e, double& w, double& a, double& bq) {
   e = exp(-x);
   if (x < 0.1) {
     double pw = 0.0, pa = 0.0, pb = 0.0;
@@ -52,21 +53,19 @@ __device__ __forceinline__ void pl_coef_f(double x, double& e, double& w, double
     a = pa * x;
     bq = pb;
   } else {
-    const double r = 1.0 / x;
     w = (1.0 - e) * r;
     a = 1.0 - w;
     bq = (w - e) * r;
   }
 }
 
-__device__ __forceinline__ void pl_coef_f(float x, float& e, float& w, float& a, float& bq) {
+__device__ __forceinline__ void pl_coef_f(float x, float r, float& e, float& w, float& a, float& bq) {
   e = __expf(-x);
   if (x < 0.1f) {
     w = fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
     a = x * fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f);
     bq = fmaf(fmaf(fmaf(fmaf(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
   } else {
-    const float r = __frcp_rn(x);
     w = (1.0f - e) * r;
     a = 1.0f - w;
     bq = (w - e) * r;
@@ -75,14 +74,21 @@ __device__ __forceinline__ void pl_coef_f(float x, float& e, float& w, float& a,
 
 constexpr int kFusedThreads = 256;
 constexpr int kFusedSlots = 6;   // E, X(D), P1(dD coef | I), P2(dD | LX), LB, LE
-constexpr int kFusedStage = 5;   // chi, S, dS, dchi, ddS per (q, k)
+constexpr int kFusedStage = 6;   // chi, S, dS, dchi, ddS, 1/(chi^k + chi^{k+1}) per (q, k)
 
 __host__ __device__ inline size_t round16(size_t bytes) { return (bytes + 15) / 16 * 16; }
 
+// Slot row stride: the rays of the block, padded to an odd count so that
+// threads walking depths (phase C) hit distinct shared-memory banks.
+__host__ __device__ inline int slot_stride(int qb, int nmu) {
+  const int r = qb * 2 * nmu;
+  return r | 1;
+}
+
 size_t fused_smem_bytes(int qb, int nz, int nmu, bool mixed) {
   const size_t rs = mixed ? 4 : 8;
-  const size_t stage = round16(rs * ((size_t)kFusedStage * qb * nz + qb));
-  const size_t slots = rs * (size_t)kFusedSlots * nz * qb * 2 * nmu;
+  const size_t stage = round16(rs * ((size_t)kFusedStage * qb * nz + qb + 2 * nz + 4 * kMaxMu));
+  const size_t slots = rs * (size_t)kFusedSlots * nz * slot_stride(qb, nmu);
   return stage + slots;
 }
 
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
   const int qb0 = blockIdx.x * Qb;
   if (qb0 >= nq) return;
   const int nqb = min(Qb, nq - qb0);
-  const int R = Qb * nr;
+  const int R = slot_stride(Qb, nmu);
   const int nray = nqb * nr;
   const bool tan = (mode == EV_TANGENT);
   const bool der = (mode == EV_BASE || mode == EV_RH92);
@@ -107,8 +113,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
   real* s_dS = s_S + Qb * nz;
   real* s_dchi = s_dS + Qb * nz;
   real* s_ddS = s_dchi + Qb * nz;
-  real* s_Bb = s_ddS + Qb * nz;
-  real* slot = reinterpret_cast<real*>(smem_raw + round16(sizeof(real) * ((size_t)kFusedStage * Qb * nz + Qb)));
+  real* s_rs = s_ddS + Qb * nz;   // 1/(chi^k + chi^{k+1}) of layer k
+  real* s_Bb = s_rs + Qb * nz;
+  real* s_idz = s_Bb + Qb;        // 1/|z_k - z_{k+1}|
+  real* s_dz = s_idz + nz;        // |z_k - z_{k+1}|
+  real* s_mu = s_dz + nz;         // per angle: 1/(2 mu), 1/2 w_mu, 2 mu
+  real* slot = reinterpret_cast<real*>(smem_raw + round16(sizeof(real) * ((size_t)kFusedStage * Qb * nz + Qb + 2 * nz + 4 * kMaxMu)));
   const size_t plane = (size_t)nz * R;
   real* E = slot;
   real* X = E + plane;
@@ -126,6 +136,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     const int ql = i / nz, k = i - ql * nz;
     const size_t o = (size_t)(qb0 + ql) * nz + k;
     s_chi[i] = chi_g[o];
+    if (k < nz - 1) s_rs[i] = (real)1 / (chi_g[o] + chi_g[o + 1]);   // shared by the 2 n_mu rays of the layer
     s_S[i] = (real)S64[o];
     s_dS[i] = (k < nz - 1) ? (real)(S64[o + 1] - S64[o]) : (real)0;   // formed in FP64
     if (tan) {
@@ -136,6 +147,15 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
   for (int ql = threadIdx.x; ql < nqb; ql += blockDim.x) {
     const int q = qb0 + ql;
     s_Bb[ql] = (real)(T.Bn[(size_t)q * nz + nz - 1] / T.c2[q]);
+  }
+  for (int k = threadIdx.x; k < nz - 1; k += blockDim.x) {
+    s_idz[k] = (real)(1.0 / T.dz[k]);
+    s_dz[k] = (real)T.dz[k];
+  }
+  for (int m = threadIdx.x; m < nmu; m += blockDim.x) {
+    s_mu[3 * m] = (real)(0.5 / T.mu[m]);
+    s_mu[3 * m + 1] = (real)(0.5 * T.wmu[m]);
+    s_mu[3 * m + 2] = (real)(2.0 * T.mu[m]);
   }
   __syncthreads();
 
@@ -148,14 +168,16 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     const int m = up ? rr : rr - nmu;
     const int ku = up ? k + 1 : k - 1;
     const int kd = up ? k : k - 1;
-    const real inv2mu = (real)(0.5 / T.mu[m]);
-    const real hw = (real)(0.5 * T.wmu[m]);
+    const real inv2mu = s_mu[3 * m];
+    const real hw = s_mu[3 * m + 1];
     const real* ch = s_chi + ql * nz;
     const real c0 = ch[k], cu = ch[ku];
-    const real h = (real)T.dz[kd] * inv2mu;
+    const real h = s_dz[kd] * inv2mu;
     const real dtau = h * (c0 + cu);
+    // 1/dtau = (2 mu / dz) / (chi^k + chi^u): the layer reciprocal is shared
+    const real rdt = s_rs[ql * nz + kd] * (s_idz[kd] * s_mu[3 * m + 2]);
     real e, w, a, bq;
-    pl_coef_f(dtau, e, w, a, bq);
+    pl_coef_f(dtau, rdt, e, w, a, bq);
     const real dSin = up ? s_dS[ql * nz + k] : -s_dS[ql * nz + k - 1];
     const size_t si = (size_t)k * R + ray;
     E[si] = e;
@@ -181,7 +203,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     const bool up = rr < nmu;
     const int m = up ? rr : rr - nmu;
     const int q = qb0 + ql;
-    const real hw = (real)(0.5 * T.wmu[m]);
+    const real hw = s_mu[3 * m + 1];
     const int k0 = up ? nz - 1 : 0;
     const int step = up ? -1 : 1;
     const size_t o0 = (size_t)q * nz + k0;
@@ -197,6 +219,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     // the largest |D| met upstream (attenuated along the ray), I - S one of
     // the order of |I| + |S|.
     real M = D < (real)0 ? -D : D;
+#pragma unroll 4
     for (int s = 1; s < nz; ++s) {
       const int k = k0 + step * s;
       si = (size_t)k * R + ray;
@@ -234,29 +257,30 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     const size_t o = (size_t)q * nz + k;
     const size_t b0 = (size_t)k * R + ql * nr;
     const double c2 = T.c2[q];
-    double sD = 0.0, sa = 0.0;
+    // ray sums in the working precision; only J = S + sum carries FP64
+    real sD = 0, sa = 0;
     for (int rr = 0; rr < nr; ++rr) {
-      const double v = (double)X[b0 + rr];
+      const real v = X[b0 + rr];
       sD += v;
-      sa += fabs(v);
+      sa += (v < (real)0 ? -v : v);
     }
-    double J = (S64[o] + sD) * c2;
+    double J = (S64[o] + (double)sD) * c2;
     if (tan) {
-      double sd = 0.0;
-      for (int rr = 0; rr < nr; ++rr) sd += (double)P2[b0 + rr];
-      cd.w.dJ[o] = (dS64[o] + sd) * c2;
+      real sd = 0;
+      for (int rr = 0; rr < nr; ++rr) sd += P2[b0 + rr];
+      cd.w.dJ[o] = (dS64[o] + (double)sd) * c2;
     } else if (der) {
-      double sI = 0.0, sx = 0.0, se = 0.0;
+      real sI = 0, sx = 0, se = 0;
       for (int rr = 0; rr < nr; ++rr) {
-        sI += (double)P1[b0 + rr];
-        sx += (double)P2[b0 + rr];
-        se += (double)LE[b0 + rr];
+        sI += P1[b0 + rr];
+        sx += P2[b0 + rr];
+        se += LE[b0 + rr];
       }
       // the representation with the smaller rounding error (intensities are >= 0)
-      if (fabs(sI) < sa) J = sI * c2;
+      if ((sI < (real)0 ? -sI : sI) < sa) J = (double)sI * c2;
       jnew_ptr(cd)[o] = J;
-      cd.w.Lchi[o] = sx * c2;
-      cd.w.Leta[o] = se;
+      cd.w.Lchi[o] = (double)sx * c2;
+      cd.w.Leta[o] = (double)se;
     }
     Jout[o] = J;
   }
