@@ -311,8 +311,7 @@ def run_ours(args, rank, ws, local, dist):
                 "avg_launch_us": 1e3 * kern_ms / max(1, launches), "launches": launches,
                 "share_of_step": kern_ms / total_ms,
                 "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA throughput (jfnk_probe_alu) on this GPU"}
-    ticks = [s["F_calls"] for s in stats]
-    gpu_launches = int(sum(8 * 8 * math.ceil(t / 8) + 2 for t in ticks))
+    gpu_launches = int(sum(s["kernel_launches"] for s in stats))
     line = {"metric": METRIC, "value": value, "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -157,6 +157,7 @@ typedef struct {
   double ray_points;    /* formal-solution ray-points evaluated (F_calls x rays)   */
   double formal_ms;     /* profile: summed duration of the formal-solution kernel  */
   int formal_launches;  /* profile: number of timed launches (active ticks)        */
+  int kernel_launches;  /* CUDA kernels launched by the solve (graph nodes included) */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */

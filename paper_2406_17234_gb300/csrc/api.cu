@@ -136,12 +136,20 @@ static int ensure_graph(Batch* b, cudaStream_t s, bool profile) {
   for (int t = 0; t < kTicksPerGraph && !rc; ++t) {
     rc = profile ? launch_evaluation(*b, s, b->tick_ev[2 * t], b->tick_ev[2 * t + 1])
                  : launch_evaluation(*b, s);
-    if (!rc) rc = launch_lu(*b, s, true);
-    if (!rc) rc = launch_krylov_step(*b, s);
+    if (!rc) rc = launch_krylov_step(*b, s);   // P^k was factorised by the assembly
   }
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (rc) return rc;
   if (e != cudaSuccess) return fail(JFNK_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  size_t nnodes = 0;
+  cudaGraphGetNodes(g, nullptr, &nnodes);
+  std::vector<cudaGraphNode_t> nodes(nnodes);
+  cudaGraphGetNodes(g, nodes.data(), &nnodes);
+  b->graph_kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) b->graph_kernels++;
+  }
   e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(JFNK_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -157,9 +165,11 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   int rc = ensure_graph(b, s, profile);
   if (rc) return rc;
   b->tick_ms.clear();
+  b->replays = 0;
   const long max_replays = (long)o->max_ticks / b->graph_ticks + 2;
   for (long r = 0; r < max_replays; ++r) {
     JFNK_CUDA(cudaGraphLaunch(b->graph, s));
+    b->replays++;
     JFNK_CUDA(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s));
     JFNK_CUDA(cudaStreamSynchronize(s));
     if (profile)
@@ -249,6 +259,7 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.ray_points = (double)x.F_calls * cols[c]->d.ray_points;
       S.formal_ms = kernel_ms;
       S.formal_launches = active;
+      S.kernel_launches = (int)(b->replays * b->graph_kernels) + 2;   // + state init, mode reset
     }
     if (status != JFNK_OK && *worst == JFNK_OK) *worst = status;
   }

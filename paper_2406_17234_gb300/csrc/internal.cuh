@@ -96,6 +96,8 @@ struct Batch {
   int graph_ticks = 0;
   bool graph_profiled = false;
   int formal_qb = 0;                  // frequencies per block of the fused formal kernel (0: unfused)
+  int graph_kernels = 0;              // kernel nodes in the captured tick graph
+  long replays = 0;                   // graph replays of the last solve
   std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel of each tick
   std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve
   int* h_status = nullptr;            // pinned host mirror of d_status

@@ -10,7 +10,11 @@
 // everything downstream of the rates is double. Intensities and source
 // functions are carried normalised by 2 h nu^3 / c^2 so that float keeps
 // range.
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace jfnk {
 
@@ -44,13 +48,30 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= T.nq * nz) return;
   const int q = i / nz, k = i - q * nz;
-  const double* n = cd.w.n + k * nl;
   const double c2 = T.c2[q];
+  if (mode == EV_TANGENT) {
+    // chi and S at the base point are those of the Newton step's base
+    // evaluation (n and J^dagger are unchanged): only their tangents are new,
+    // in the working precision.
+    const double* v = tangent_dir(cd) + k * nl;
+    real dchi = 0, deta = 0;
+    for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+      const int t = T.q_t[s];
+      const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+      const real V = (real)T.V[p], g = (real)T.G[p];
+      const real vlo = (real)v[T.t_lo[t]], vup = (real)v[T.t_up[t]];
+      dchi += V * (vlo - g * vup);
+      deta += g * V * vup;                 // normalised by 2 h nu^3 / c^2
+    }
+    const real chi = reinterpret_cast<const real*>(cd.w.chi)[i];
+    const real S = (real)cd.w.S[i];
+    reinterpret_cast<real*>(cd.w.dchi)[i] = dchi;
+    cd.w.dS[i] = (double)((deta - S * dchi) / chi);
+    return;
+  }
+  const double* n = cd.w.n + k * nl;
   double chi = T.chi_c[i] + T.chi_sca[k];
   double eta = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
-  const bool tan = (mode == EV_TANGENT);
-  const double* v = tan ? tangent_dir(cd) + k * nl : nullptr;
-  double dchi = 0.0, deta = 0.0;
   for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
     const int t = T.q_t[s];
     const int lo = T.t_lo[t], up = T.t_up[t];
@@ -58,18 +79,9 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
     const double V = T.V[p], g = T.G[p];
     chi += V * (n[lo] - g * n[up]);
     eta += c2 * g * V * n[up];
-    if (tan) {
-      dchi += V * (v[lo] - g * v[up]);
-      deta += c2 * g * V * v[up];
-    }
   }
-  const double S = eta / chi;
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
-  cd.w.S[i] = S / c2;
-  if (tan) {
-    reinterpret_cast<real*>(cd.w.dchi)[i] = (real)dchi;
-    cd.w.dS[i] = (deta - S * dchi) / chi / c2;
-  }
+  cd.w.S[i] = eta / (chi * c2);
 }
 
 // Differences of the source function (and of its tangent) between adjacent
@@ -290,182 +302,264 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
 // and in RH92 mode the sums of the preconditioned rate equations.
 // ---------------------------------------------------------------------------
 constexpr int kRateWarps = 4;
+constexpr int kRateSplit = 4;   // blocks of a cluster sharing one (transition, depth tile)
 constexpr int kRateAcc = 2 + (kRhFixed + kMaxT > kMaxL ? kRhFixed + kMaxT : kMaxL);
 
-// One block per (32-depth tile, transition, column): lanes map to depths (so
-// every table and J access is coalesced), warps split the frequency window,
-// and the partial sums are reduced through shared memory.
+// One cluster of kRateSplit blocks per (32-depth tile, transition, column):
+// lanes map to depths (every table and J access is coalesced), the blocks of
+// the cluster split the frequency window into contiguous chunks and their
+// warps stride through the chunk; partial sums are reduced through shared
+// memory inside a block and through distributed shared memory across the
+// cluster, in a fixed order (bit-reproducible, no atomics).
 __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __restrict__ cols) {
-  const ColDesc& cd = cols[blockIdx.z];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const ColDesc& cd = cols[blockIdx.z / kRateSplit];
   const int mode = eval_mode(cd);
-  if (mode == EV_SKIP) return;
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
   const int t = blockIdx.y;
-  if (t >= nt || (int)blockIdx.x * 32 >= nz) return;
+  // uniform over the cluster: every block takes the same branch
+  const bool active = (mode != EV_SKIP) && t < nt && (int)blockIdx.x * 32 < nz;
   __shared__ double red[kRateWarps][kRateAcc][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int k = min((int)blockIdx.x * 32 + lane, nz - 1);
-  const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
-  const int lo = T.t_lo[t], upl = T.t_up[t];
-  const double* n = cd.w.n + k * nl;
   const bool tan = (mode == EV_TANGENT);
   const bool base_mode = (mode == EV_BASE);
   const bool rh = (mode == EV_RH92);
   const int nacc = tan ? 2 : (base_mode ? 2 + nl : (rh ? 2 + kRhFixed + nt : 2));
-  double acc[kRateAcc];
-  for (int j = 0; j < nacc; ++j) acc[j] = 0.0;
-  const double n_lo = n[lo], n_up = n[upl];
-  const double* Jd = rh ? jdag_ptr(cd) : nullptr;
-  for (int q = q0 + wid; q <= q1; q += kRateWarps) {
-    const size_t p = (size_t)(base + q - q0);
-    const double W = T.t_w[p] * T.rw[q];
-    const double V = T.V[p * nz + k], g = T.G[p * nz + k];
-    const size_t o = (size_t)q * nz + k;
-    if (tan) {
-      const double WV = W * V;
-      const double dJ = cd.w.dJ[o];
-      acc[0] += WV * dJ;
-      acc[1] += WV * g * dJ;
-      continue;
+  if (active) {
+    const int k = min((int)blockIdx.x * 32 + lane, nz - 1);
+    const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
+    const int nw = q1 - q0 + 1;
+    const int qa = q0 + (int)(((long)nw * rank) / kRateSplit);
+    const int qb = q0 + (int)(((long)nw * (rank + 1)) / kRateSplit) - 1;
+    const int lo = T.t_lo[t], upl = T.t_up[t];
+    const double* n = cd.w.n + k * nl;
+    double acc[kRateAcc];
+    for (int j = 0; j < nacc; ++j) acc[j] = 0.0;
+    const double n_lo = n[lo], n_up = n[upl];
+    const double* Jd = rh ? jdag_ptr(cd) : nullptr;
+    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+      const size_t p = (size_t)(base + q - q0);
+      const double W = T.t_w[p] * T.rw[q];
+      const double V = T.V[p * nz + k], g = T.G[p * nz + k];
+      const size_t o = (size_t)q * nz + k;
+      if (tan) {
+        const double WV = W * V;
+        const double dJ = cd.w.dJ[o];
+        acc[0] += WV * dJ;
+        acc[1] += WV * g * dJ;
+        continue;
+      }
+      const double J = cd.w.J[o];
+      const double c2 = T.c2[q];
+      acc[0] += W * V * J;
+      acc[1] += W * g * V * (c2 + J);
+      const double chi_t = V * (n_lo - g * n_up);
+      if (base_mode) {
+        double zeta[kMaxL];
+        for (int j = 0; j < nl; ++j) zeta[j] = 0.0;
+        const double Lx = cd.w.Lchi[o], Le = cd.w.Leta[o];
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          const double Vs = T.V[ps], gs = T.G[ps];
+          zeta[T.t_lo[ts]] += Vs * Lx;                          // beta_j (Sect. 2.5.1, read from Eq. chi)
+          zeta[T.t_up[ts]] += -gs * Vs * Lx + c2 * gs * Vs * Le;  // and gamma_j (Eq. der_eta_n)
+        }
+        const double Wc = W * chi_t;
+        for (int j = 0; j < nl; ++j) acc[2 + j] += Wc * zeta[j];
+      } else if (rh) {
+        // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
+        const double Le = cd.w.Leta[o];
+        const double eta_bg = T.eta_c[o] + T.chi_sca[k] * Jd[o];
+        double eta_l = 0.0;
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
+        }
+        const double Jeff = J - Le * (eta_bg + eta_l);
+        acc[2] += W * V * Jeff;
+        acc[3] += W * g * V * Jeff;
+        acc[4] += W * c2 * g * V;
+        const double wcp = W * chi_t * Le;
+        acc[5] += wcp * eta_bg;
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          acc[2 + kRhFixed + ts] += wcp * c2 * T.G[ps] * T.V[ps];
+        }
+      }
     }
-    const double J = cd.w.J[o];
-    const double c2 = T.c2[q];
-    acc[0] += W * V * J;
-    acc[1] += W * g * V * (c2 + J);
-    const double chi_t = V * (n_lo - g * n_up);
-    if (base_mode) {
-      double zeta[kMaxL];
-      for (int j = 0; j < nl; ++j) zeta[j] = 0.0;
-      const double Lx = cd.w.Lchi[o], Le = cd.w.Leta[o];
-      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-        const int ts = T.q_t[s];
-        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-        const double Vs = T.V[ps], gs = T.G[ps];
-        zeta[T.t_lo[ts]] += Vs * Lx;                          // beta_j (Sect. 2.5.1, read from Eq. chi)
-        zeta[T.t_up[ts]] += -gs * Vs * Lx + c2 * gs * Vs * Le;  // and gamma_j (Eq. der_eta_n)
+    for (int j = 0; j < nacc; ++j) red[wid][j][lane] = acc[j];
+    __syncthreads();
+    if (wid == 0)
+      for (int j = 0; j < nacc; ++j) {
+        double v = red[0][j][lane];
+        for (int w = 1; w < kRateWarps; ++w) v += red[w][j][lane];
+        red[0][j][lane] = v;
       }
-      const double Wc = W * chi_t;
-      for (int j = 0; j < nl; ++j) acc[2 + j] += Wc * zeta[j];
-    } else if (rh) {
-      // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
-      const double Le = cd.w.Leta[o];
-      const double eta_bg = T.eta_c[o] + T.chi_sca[k] * Jd[o];
-      double eta_l = 0.0;
-      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-        const int ts = T.q_t[s];
-        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-        eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
+  }
+  cluster.sync();
+  if (active && rank == 0 && wid == 0) {
+    const int kw = (int)blockIdx.x * 32 + lane;
+    if (kw < nz) {
+      double acc[kRateAcc];
+      for (int j = 0; j < nacc; ++j) acc[j] = red[0][j][lane];
+      for (int r = 1; r < kRateSplit; ++r) {
+        const double* peer = cluster.map_shared_rank(&red[0][0][0], r);
+        for (int j = 0; j < nacc; ++j) acc[j] += peer[j * 32 + lane];
       }
-      const double Jeff = J - Le * (eta_bg + eta_l);
-      acc[2] += W * V * Jeff;
-      acc[3] += W * g * V * Jeff;
-      acc[4] += W * c2 * g * V;
-      const double wcp = W * chi_t * Le;
-      acc[5] += wcp * eta_bg;
-      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-        const int ts = T.q_t[s];
-        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-        acc[2 + kRhFixed + ts] += wcp * c2 * T.G[ps] * T.V[ps];
+      const size_t i = (size_t)t * nz + kw;
+      if (tan) {
+        cd.w.dRup[i] = acc[0];
+        cd.w.dRdn[i] = acc[1];
+      } else {
+        cd.w.Rup[i] = acc[0];
+        cd.w.Rdn[i] = acc[1];
+        if (base_mode)
+          for (int j = 0; j < nl; ++j) cd.w.Apart[i * nl + j] = acc[2 + j];
+        if (rh)
+          for (int j = 0; j < kRhFixed + nt; ++j) cd.w.rh[i * kRhStride + j] = acc[2 + j];
       }
     }
   }
-  for (int j = 0; j < nacc; ++j) red[wid][j][lane] = acc[j];
-  __syncthreads();
-  if (wid != 0) return;
-  const int kw = (int)blockIdx.x * 32 + lane;
-  if (kw >= nz) return;
-  for (int j = 0; j < nacc; ++j) {
-    double v = red[0][j][lane];
-    for (int w = 1; w < kRateWarps; ++w) v += red[w][j][lane];
-    acc[j] = v;
-  }
-  const size_t i = (size_t)t * nz + kw;
-  if (tan) {
-    cd.w.dRup[i] = acc[0];
-    cd.w.dRdn[i] = acc[1];
-    return;
-  }
-  cd.w.Rup[i] = acc[0];
-  cd.w.Rdn[i] = acc[1];
-  if (base_mode)
-    for (int j = 0; j < nl; ++j) cd.w.Apart[i * nl + j] = acc[2 + j];
-  if (rh)
-    for (int j = 0; j < kRhFixed + nt; ++j) cd.w.rh[i * kRhStride + j] = acc[2 + j];
+  cluster.sync();   // peers keep their shared memory until rank 0 has read it
+}
+
+static int launch_rates(const Batch& b, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((b.max_nz + 31) / 32, b.max_nt, b.ncols * kRateSplit);
+  cfg.blockDim = dim3(32 * kRateWarps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = kRateSplit;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_rates, (const ColDesc*)b.d_cols));
+  return JFNK_OK;
 }
 
 // ---------------------------------------------------------------------------
-// a4: per-depth assembly of F (or J_F v) and, in base mode, of P^k
+// a4: per-depth assembly of F (or J_F v) and, in base mode, of P^k; one warp
+// per depth: lanes first take transitions (net rates), then levels (F) and
+// matrix entries (P), each sum in a fixed order. Solver evaluations also
+// LU-factorise P^k in place (lane 0), explicit evaluations leave it as is.
 // ---------------------------------------------------------------------------
-__global__ void k_assemble(const ColDesc* __restrict__ cols) {
+constexpr int kAsmWarps = 4;
+
+__global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __restrict__ cols) {
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode(cd);
   if (mode == EV_SKIP) return;
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = blockIdx.x * kAsmWarps + wid;
   if (k >= nz) return;
+  __shared__ double s_up[kAsmWarps][kMaxT], s_dn[kAsmWarps][kMaxT], s_kap[kAsmWarps][kMaxT];
+  __shared__ double s_P[kAsmWarps][kMaxL * kMaxL];
+  __shared__ int s_piv[kAsmWarps][kMaxL];
   const double* n = cd.w.n + k * nl;
   const double* C = T.C + (size_t)k * nl * nl;
-  if (mode != EV_TANGENT) {
+  const bool tan = (mode == EV_TANGENT);
+  int is;
+  if (!tan) {
     // conservation row at the most populated level (lowest index on ties)
-    int is = 0;
+    is = 0;
     for (int l = 1; l < nl; ++l)
       if (n[l] > n[is]) is = l;
-    cd.w.istar[k] = is;
+    if (lane == 0) cd.w.istar[k] = is;
+  } else {
+    is = cd.w.istar[k];
   }
-  const int is = cd.w.istar[k];
-  if (mode == EV_TANGENT) {
-    const double* v = tangent_dir(cd) + k * nl;
-    double dF[kMaxL];
-    for (int l = 0; l < nl; ++l) dF[l] = 0.0;
-    for (int t = 0; t < nt; ++t) {
-      const int lo = T.t_lo[t], up = T.t_up[t];
-      const size_t o = (size_t)t * nz + k;
-      const double dk = v[lo] * (C[lo * nl + up] + cd.w.Rup[o]) + n[lo] * cd.w.dRup[o] -
-                        v[up] * (C[up * nl + lo] + cd.w.Rdn[o]) - n[up] * cd.w.dRdn[o];
-      dF[lo] += dk;
-      dF[up] -= dk;
-    }
-    double sv = 0.0;
-    for (int l = 0; l < nl; ++l) sv += v[l];
-    dF[is] = -sv;
-    for (int l = 0; l < nl; ++l) cd.w.dF[k * nl + l] = dF[l];
-    return;
-  }
-  double F[kMaxL];
-  for (int l = 0; l < nl; ++l) F[l] = 0.0;
-  double* P = cd.w.P + (size_t)k * nl * nl;
-  const bool base_mode = (mode == EV_BASE);
-  if (base_mode)
-    for (int l = 0; l < nl * nl; ++l) P[l] = 0.0;
-  for (int t = 0; t < nt; ++t) {
+  const double* v = tan ? tangent_dir(cd) + k * nl : nullptr;
+  for (int t = lane; t < nt; t += 32) {
     const int lo = T.t_lo[t], up = T.t_up[t];
     const size_t o = (size_t)t * nz + k;
-    const double urate = C[lo * nl + up] + cd.w.Rup[o];
-    const double drate = C[up * nl + lo] + cd.w.Rdn[o];
-    const double kap = n[lo] * urate - n[up] * drate;
-    F[lo] += kap;
-    F[up] -= kap;
-    if (base_mode) {
-      // Gamma^k (Sect. 2.5.1) and A^kk rows of the two levels of t
-      P[lo * nl + lo] += urate;
-      P[lo * nl + up] -= drate;
-      P[up * nl + lo] -= urate;
-      P[up * nl + up] += drate;
-      const double* Ap = cd.w.Apart + o * nl;
-      for (int j = 0; j < nl; ++j) {
-        P[lo * nl + j] += Ap[j];
-        P[up * nl + j] -= Ap[j];
+    const double ur = C[lo * nl + up] + cd.w.Rup[o];
+    const double dr = C[up * nl + lo] + cd.w.Rdn[o];
+    if (tan)
+      s_kap[wid][t] = v[lo] * ur + n[lo] * cd.w.dRup[o] - v[up] * dr - n[up] * cd.w.dRdn[o];
+    else
+      s_kap[wid][t] = n[lo] * ur - n[up] * dr;
+    s_up[wid][t] = ur;
+    s_dn[wid][t] = dr;
+  }
+  __syncwarp();
+  if (lane < nl) {
+    double f = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      if (T.t_lo[t] == lane) f += s_kap[wid][t];
+      if (T.t_up[t] == lane) f -= s_kap[wid][t];
+    }
+    if (lane == is) {
+      double sv = 0.0;
+      if (tan) {
+        for (int l = 0; l < nl; ++l) sv += v[l];
+        f = -sv;
+      } else {
+        for (int l = 0; l < nl; ++l) sv += n[l];
+        f = T.ntot[k] - sv;
+      }
+    }
+    (tan ? cd.w.dF : cd.w.F)[k * nl + lane] = f;
+  }
+  if (mode != EV_BASE) return;
+  // P^k = Gamma^k + A^kk (Sect. 2.5.1), conservation row -1
+  for (int e = lane; e < nl * nl; e += 32) {
+    const int i = e / nl, j = e - i * nl;
+    double pv = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      const int lo = T.t_lo[t], up = T.t_up[t];
+      const double sg = (lo == i) ? 1.0 : ((up == i) ? -1.0 : 0.0);
+      if (sg == 0.0) continue;
+      double g = cd.w.Apart[((size_t)t * nz + k) * nl + j];
+      if (j == lo) g += s_up[wid][t];
+      if (j == up) g -= s_dn[wid][t];
+      pv += sg * g;
+    }
+    s_P[wid][e] = (i == is) ? -1.0 : pv;
+  }
+  __syncwarp();
+  double* P = cd.w.P + (size_t)k * nl * nl;
+  if (cd.forced_mode >= 0) {
+    for (int e = lane; e < nl * nl; e += 32) P[e] = s_P[wid][e];
+    return;
+  }
+  if (lane == 0) {
+    // LU with partial pivoting, in shared memory
+    double* A = s_P[wid];
+    for (int c = 0; c < nl; ++c) {
+      int pr = c;
+      double best = fabs(A[c * nl + c]);
+      for (int r = c + 1; r < nl; ++r) {
+        const double vv = fabs(A[r * nl + c]);
+        if (vv > best) { best = vv; pr = r; }
+      }
+      s_piv[wid][c] = pr;
+      if (pr != c)
+        for (int j = 0; j < nl; ++j) {
+          const double tmp = A[c * nl + j];
+          A[c * nl + j] = A[pr * nl + j];
+          A[pr * nl + j] = tmp;
+        }
+      const double d = A[c * nl + c];
+      for (int r = c + 1; r < nl; ++r) {
+        const double f = A[r * nl + c] / d;
+        A[r * nl + c] = f;
+        for (int j = c + 1; j < nl; ++j) A[r * nl + j] -= f * A[c * nl + j];
       }
     }
   }
-  double sn = 0.0;
-  for (int l = 0; l < nl; ++l) sn += n[l];
-  F[is] = T.ntot[k] - sn;
-  for (int l = 0; l < nl; ++l) cd.w.F[k * nl + l] = F[l];
-  if (base_mode)
-    for (int j = 0; j < nl; ++j) P[is * nl + j] = -1.0;
+  __syncwarp();
+  for (int e = lane; e < nl * nl; e += 32) P[e] = s_P[wid][e];
+  if (lane < nl) cd.w.piv[k * nl + lane] = s_piv[wid][lane];
 }
 
 // LU factorisation with partial pivoting of every P^k, in place.
@@ -509,8 +603,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   const int tb = 256;
   dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
   dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
-  dim3 g_rates((b.max_nz + 31) / 32, b.max_nt, nc);
-  dim3 g_k((b.max_nz + 63) / 64, nc);
+  dim3 g_asm((b.max_nz + kAsmWarps - 1) / kAsmWarps, nc);
   if (b.formal_qb > 0) {
     // opacity, then the fused formal solution with in-block ray sums
     if (b.mixed) k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
@@ -534,8 +627,11 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     k_ray_sum<double><<<g_qk, tb, 0, s>>>(b.d_cols);
   }
-  k_rates<<<g_rates, 32 * kRateWarps, 0, s>>>(b.d_cols);
-  k_assemble<<<g_k, 64, 0, s>>>(b.d_cols);
+  {
+    int rc = launch_rates(b, s);
+    if (rc) return rc;
+  }
+  k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
