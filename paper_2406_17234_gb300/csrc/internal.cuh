@@ -121,8 +121,6 @@ int launch_formal_fused(const Batch& b, cudaStream_t s);
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.
 int launch_istar(const Batch& b, cudaStream_t s);
-// Factorisation of the block-Jacobi blocks, in place.
-int launch_lu(const Batch& b, cudaStream_t s, bool factor);
 // RH92 per-depth update from an EV_RH92 evaluation (explicit API path).
 int launch_rh92_update(const Batch& b, cudaStream_t s);
 

@@ -558,40 +558,31 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
     }
   }
   __syncwarp();
-  for (int e = lane; e < nl * nl; e += 32) P[e] = s_P[wid][e];
-  if (lane < nl) cd.w.piv[k * nl + lane] = s_piv[wid][lane];
-}
-
-// LU factorisation with partial pivoting of every P^k, in place.
-__global__ void k_lu(const ColDesc* __restrict__ cols, int only_base) {
-  const ColDesc& cd = cols[blockIdx.y];
-  if (only_base && eval_mode(cd) != EV_BASE) return;
-  const int nz = cd.t.nz, nl = cd.t.nl;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nz) return;
-  double* A = cd.w.P + (size_t)k * nl * nl;
-  int* piv = cd.w.piv + k * nl;
-  for (int c = 0; c < nl; ++c) {
-    int pr = c;
-    double best = fabs(A[c * nl + c]);
-    for (int r = c + 1; r < nl; ++r) {
-      double vv = fabs(A[r * nl + c]);
-      if (vv > best) { best = vv; pr = r; }
+  // explicit inverse of P^k: lane j solves P x = e_j with the factors, so that
+  // the Krylov step applies P^{-1} as a fully parallel small mat-vec
+  __shared__ double s_inv[kAsmWarps][kMaxL * kMaxL];
+  if (lane < nl) {
+    const double* A = s_P[wid];
+    double x[kMaxL];
+    for (int r = 0; r < nl; ++r) x[r] = (r == lane) ? 1.0 : 0.0;
+    for (int c = 0; c < nl; ++c) {
+      const int p = s_piv[wid][c];
+      if (p != c) { const double t = x[c]; x[c] = x[p]; x[p] = t; }
     }
-    piv[c] = pr;
-    if (pr != c)
-      for (int j = 0; j < nl; ++j) {
-        double tmp = A[c * nl + j];
-        A[c * nl + j] = A[pr * nl + j];
-        A[pr * nl + j] = tmp;
-      }
-    const double d = A[c * nl + c];
-    for (int r = c + 1; r < nl; ++r) {
-      const double f = A[r * nl + c] / d;
-      A[r * nl + c] = f;
-      for (int j = c + 1; j < nl; ++j) A[r * nl + j] -= f * A[c * nl + j];
+    for (int r = 1; r < nl; ++r) {
+      double acc = x[r];
+      for (int c = 0; c < r; ++c) acc -= A[r * nl + c] * x[c];
+      x[r] = acc;
     }
+    for (int r = nl - 1; r >= 0; --r) {
+      double acc = x[r];
+      for (int c = r + 1; c < nl; ++c) acc -= A[r * nl + c] * x[c];
+      x[r] = acc / A[r * nl + r];
+    }
+    for (int r = 0; r < nl; ++r) s_inv[wid][r * nl + lane] = x[r];
   }
+  __syncwarp();
+  for (int e = lane; e < nl * nl; e += 32) P[e] = s_inv[wid][e];
 }
 
 // ---------------------------------------------------------------------------
@@ -636,11 +627,5 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   return JFNK_OK;
 }
 
-int launch_lu(const Batch& b, cudaStream_t s, bool only_base) {
-  dim3 g_k((b.max_nz + 63) / 64, b.ncols);
-  k_lu<<<g_k, 64, 0, s>>>(b.d_cols, only_base ? 1 : 0);
-  JFNK_CUDA(cudaGetLastError());
-  return JFNK_OK;
-}
 
 }  // namespace jfnk

@@ -159,24 +159,6 @@ __device__ double block_max(double v, double* sh) {
   return r;
 }
 
-// x <- P^{-1} x for the nl-vector of one depth (LU with row interchanges).
-__device__ void lu_solve(const double* LU, const int* piv, double* x, int nl) {
-  for (int c = 0; c < nl; ++c) {
-    const int p = piv[c];
-    if (p != c) { double t = x[c]; x[c] = x[p]; x[p] = t; }
-  }
-  for (int r = 1; r < nl; ++r) {
-    double s = x[r];
-    for (int c = 0; c < r; ++c) s -= LU[r * nl + c] * x[c];
-    x[r] = s;
-  }
-  for (int r = nl - 1; r >= 0; --r) {
-    double s = x[r];
-    for (int c = r + 1; c < nl; ++c) s -= LU[r * nl + c] * x[c];
-    x[r] = s / LU[r * nl + r];
-  }
-}
-
 // Dense solve with partial pivoting of one small system (RH92 per depth).
 __device__ bool small_solve(double* A, double* b, int nl) {
   for (int c = 0; c < nl; ++c) {
@@ -247,20 +229,27 @@ __device__ double rh92_depth(const ColDesc& cd, int k) {
 // ---------------------------------------------------------------------------
 __device__ void apply_pinv(const ColDesc& cd, const double* in, double sign_in, const double* in2,
                            double sign_in2, double* out) {
-  // out = P^{-1} (sign_in in + sign_in2 in2), depth by depth
+  // out = P^{-1} (sign_in in + sign_in2 in2): w.P holds the explicit block
+  // inverses after a solver base evaluation; one thread per (depth, row)
   const int nz = cd.t.nz, nl = cd.t.nl;
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-    double x[kMaxL];
-    for (int l = 0; l < nl; ++l) {
-      x[l] = sign_in * in[k * nl + l];
-      if (in2) x[l] += sign_in2 * in2[k * nl + l];
+  for (int idx = threadIdx.x; idx < nz * nl; idx += blockDim.x) {
+    const int k = idx / nl, i = idx - k * nl;
+    const double* Pi = cd.w.P + ((size_t)k * nl + i) * nl;
+    const double* a = in + k * nl;
+    const double* b2 = in2 ? in2 + k * nl : nullptr;
+    double acc = 0.0;
+    for (int j = 0; j < nl; ++j) {
+      double xj = sign_in * a[j];
+      if (b2) xj += sign_in2 * b2[j];
+      acc += Pi[j] * xj;
     }
-    lu_solve(cd.w.P + (size_t)k * nl * nl, cd.w.piv + k * nl, x, nl);
-    for (int l = 0; l < nl; ++l) out[k * nl + l] = x[l];
+    out[idx] = acc;
   }
 }
 
-__global__ void __launch_bounds__(256) k_krylov(const ColDesc* __restrict__ cols,
+constexpr int kKrylovThreads = 512;
+
+__global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __restrict__ cols,
                                                 const SolverOpts* __restrict__ opts,
                                                 int* status_out) {
   const ColDesc& cd = cols[blockIdx.x];
@@ -505,7 +494,7 @@ __global__ void __launch_bounds__(256) k_krylov(const ColDesc* __restrict__ cols
 }
 
 int launch_krylov_step(const Batch& b, cudaStream_t s) {
-  k_krylov<<<b.ncols, 256, 0, s>>>(b.d_cols, b.d_opts, b.d_status);
+  k_krylov<<<b.ncols, kKrylovThreads, 0, s>>>(b.d_cols, b.d_opts, b.d_status);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
