@@ -158,6 +158,8 @@ typedef struct {
   double formal_ms;     /* profile: summed duration of the formal-solution kernel  */
   int formal_launches;  /* profile: number of timed launches (active ticks)        */
   int kernel_launches;  /* CUDA kernels launched by the solve (graph nodes included) */
+  int formal_qb;        /* autotuned frequencies per block of the formal kernel     */
+  int formal_threads;   /* autotuned threads per block of the formal kernel         */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -235,6 +237,19 @@ int jfnk_solve(jfnk_ctx* ctx, const jfnk_atmos* a, const jfnk_options* o, double
 int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols,
                      const jfnk_options* o, double* const* n_inout, double* const* J_inout,
                      jfnk_stats* stats, jfnk_mem where, void* stream);
+
+/* ---- persistent batches -------------------------------------------------------- */
+/* A batch plan owns the device work buffers of n_cols columns (precision and
+ * Krylov size fixed at creation) and its tick graph, so that repeated solves
+ * pay for allocation, autotuning and graph capture once. The atmospheres must
+ * outlive the plan. jfnk_batch_run solves every column like jfnk_batch_solve
+ * (o->precision must equal the plan's, o->krylov_max <= its krylov_max). */
+typedef struct jfnk_batch jfnk_batch;
+int jfnk_batch_create(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols, int precision,
+                      int krylov_max, jfnk_batch** out);
+int jfnk_batch_run(jfnk_batch* b, const jfnk_options* o, double* const* n_inout,
+                   double* const* J_inout, jfnk_stats* stats, jfnk_mem where, void* stream);
+int jfnk_batch_destroy(jfnk_batch* b);
 
 /* ---- residual without device allocation -------------------------------------- */
 /* The paper has no counterpart to this entry point: it is a deployment aid.

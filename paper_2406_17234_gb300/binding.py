@@ -72,7 +72,8 @@ class jfnk_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_iters", C.c_int), ("rh92_iters", C.c_int),
                 ("F_calls", C.c_int), ("jvp_calls", C.c_int), ("F_norm", C.c_double),
                 ("F_norm0", C.c_double), ("dn_norm", C.c_double), ("ray_points", C.c_double),
-                ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int)]
+                ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int),
+                ("formal_qb", C.c_int), ("formal_threads", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -104,6 +105,11 @@ _SIGNATURES = {
     "jfnk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(jfnk_options), C.c_void_p,
                              C.c_void_p, C.POINTER(jfnk_stats), C.c_int, C.c_void_p]),
     "jfnk_probe_alu": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "jfnk_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.c_int, C.c_int,
+                                    C.POINTER(C.c_void_p)]),
+    "jfnk_batch_run": (C.c_int, [C.c_void_p, C.POINTER(jfnk_options), C.POINTER(C.c_void_p),
+                                 C.POINTER(C.c_void_p), C.POINTER(jfnk_stats), C.c_int, C.c_void_p]),
+    "jfnk_batch_destroy": (C.c_int, [C.c_void_p]),
     "jfnk_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
     "jfnk_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p),
@@ -344,3 +350,40 @@ def batch_solve(ctx: Context, atms: Sequence[Atmosphere], opts: Optional[jfnk_op
     if raise_on_fail:
         check(rc, "jfnk_batch_solve")
     return ns, [s.as_dict() for s in stats]
+
+
+class BatchPlan:
+    """Persistent batch of columns (jfnk_batch_*): buffers, tuning and graph built once."""
+
+    def __init__(self, ctx: Context, atms: Sequence[Atmosphere], precision: int = JFNK_FP64,
+                 krylov_max: int = 50):
+        self.ctx, self.atms, self.precision = ctx, list(atms), precision
+        nc = len(self.atms)
+        self._hs = (C.c_void_p * nc)(*[a.h for a in self.atms])
+        h = C.c_void_p()
+        check(ctx.lib.jfnk_batch_create(ctx.h, nc, self._hs, precision, krylov_max, C.byref(h)),
+              "jfnk_batch_create")
+        self.h = h
+        self.ns = [np.zeros((a.n_depth, a.n_levels)) for a in self.atms]
+        self._nps = (C.c_void_p * nc)(*[n.ctypes.data for n in self.ns])
+        self.stats = (jfnk_stats * nc)()
+
+    def run(self, opts: Optional[jfnk_options] = None, raise_on_fail: bool = True, stream=None):
+        o = opts or default_options(precision=self.precision)
+        o.precision = self.precision
+        rc = self.ctx.lib.jfnk_batch_run(self.h, C.byref(o), self._nps, None, self.stats,
+                                         JFNK_MEM_HOST, _stream(stream))
+        if raise_on_fail:
+            check(rc, "jfnk_batch_run")
+        return self.ns, [s.as_dict() for s in self.stats]
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.jfnk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -213,6 +213,26 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
       JFNK_CUDA(cudaMemcpyAsync(cd.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
+  if (!b->tuned && b->formal_qb > 0) {
+    // tune the fused formal kernel once per batch, on its own columns: a base
+    // evaluation at the initial state, then tangent data along v = n
+    if ((rc = batch_set_forced_mode(b, EV_BASE, s))) return rc;
+    if ((rc = launch_evaluation(*b, s))) return rc;
+    for (int c = 0; c < b->ncols; ++c) {
+      const AtmosData& M = cols[c]->d;
+      JFNK_CUDA(cudaMemcpyAsync(b->h_cols[c].w.v, b->h_cols[c].w.n, (size_t)M.nz * M.nl * 8,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    if ((rc = batch_set_forced_mode(b, EV_TANGENT, s))) return rc;
+    if ((rc = launch_evaluation(*b, s))) return rc;
+    if ((rc = fused_autotune(b, s))) return rc;
+    b->tuned = true;
+    if (b->graph) {   // a graph captured with other launch shapes is stale
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    if ((rc = batch_set_forced_mode(b, -1, s))) return rc;
+  }
   // mark every column as running for the host poll
   std::vector<int> ones(b->ncols, 1);
   JFNK_CUDA(cudaMemcpyAsync(b->d_status, ones.data(), sizeof(int) * b->ncols, cudaMemcpyHostToDevice, s));
@@ -260,6 +280,8 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.formal_ms = kernel_ms;
       S.formal_launches = active;
       S.kernel_launches = (int)(b->replays * b->graph_kernels) + 2;   // + state init, mode reset
+      S.formal_qb = b->formal_qb;
+      S.formal_threads = b->formal_threads;
     }
     if (status != JFNK_OK && *worst == JFNK_OK) *worst = status;
   }
@@ -529,6 +551,71 @@ int jfnk_solve(jfnk_ctx* ctx, const jfnk_atmos* a, const jfnk_options* o, double
   return JFNK_OK;
 }
 
+}  // extern "C"
+
+struct jfnk_batch {
+  jfnk_ctx* ctx;
+  std::vector<const jfnk_atmos*> cols;
+  jfnk::Batch b;
+  int precision;
+};
+
+extern "C" {
+
+int jfnk_batch_create(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols_in, int precision,
+                      int krylov_max, jfnk_batch** out) {
+  if (!ctx || !out) return fail(JFNK_E_INVALID, "context and out are required");
+  *out = nullptr;
+  if (n_cols < 1 || !cols_in) return fail(JFNK_E_INVALID, "a batch needs at least one column");
+  if (krylov_max < 1 || krylov_max > kMaxKrylov) return fail(JFNK_E_INVALID, "krylov_max must be in [1, 64]");
+  std::unique_ptr<jfnk_batch> h(new jfnk_batch());
+  h->ctx = ctx;
+  h->precision = precision;
+  h->cols.assign(cols_in, cols_in + n_cols);
+  std::vector<const AtmosData*> data;
+  int rc;
+  for (auto* a : h->cols) {
+    if ((rc = check_common(ctx, a, precision, JFNK_MEM_HOST))) return rc;
+    data.push_back(&a->d);
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if ((rc = batch_create(&h->b, data, precision == JFNK_MIXED, krylov_max))) return rc;
+  *out = h.release();
+  return JFNK_OK;
+}
+
+int jfnk_batch_destroy(jfnk_batch* b) {
+  if (!b) return JFNK_OK;
+  cudaSetDevice(b->ctx->device);
+  delete b;
+  return JFNK_OK;
+}
+
+int jfnk_batch_run(jfnk_batch* h, const jfnk_options* o, double* const* n_inout,
+                   double* const* J_inout, jfnk_stats* stats, jfnk_mem where, void* stream) {
+  if (!h) return fail(JFNK_E_INVALID, "batch is NULL");
+  int rc = validate_options(o);
+  if (rc) return rc;
+  if (o->precision != h->precision) return fail(JFNK_E_INVALID, "options precision differs from the batch's");
+  if (o->krylov_max > h->b.kmax) return fail(JFNK_E_INVALID, "krylov_max exceeds the batch's");
+  if (!n_inout) return fail(JFNK_E_INVALID, "n_inout is required");
+  if (where != JFNK_MEM_HOST && where != JFNK_MEM_DEVICE) return fail(JFNK_E_INVALID, "unknown memory kind");
+  jfnk_ctx* ctx = h->ctx;
+  JFNK_CUDA(cudaSetDevice(ctx->device));
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  int worst = JFNK_OK;
+  Batch* b = &h->b;
+  rc = on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    int r = prepare_solve(b, h->cols, o, n_inout, J_inout, where, s);
+    if (r) return r;
+    if ((r = run_to_completion(b, o, s))) return r;
+    return finish_solve(b, h->cols, n_inout, J_inout, stats, where, s, &worst);
+  });
+  if (rc) return rc;
+  if (worst != JFNK_OK) return fail(worst, "some columns did not converge (see stats[].status)");
+  return JFNK_OK;
+}
+
 int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols_in,
                      const jfnk_options* o, double* const* n_inout, double* const* J_inout,
                      jfnk_stats* stats, jfnk_mem where, void* stream) {
@@ -537,25 +624,11 @@ int jfnk_batch_solve(jfnk_ctx* ctx, int n_cols, const jfnk_atmos* const* cols_in
   if (n_cols == 0) return JFNK_OK;
   int rc = validate_options(o);
   if (rc) return rc;
-  std::vector<const jfnk_atmos*> cols(cols_in, cols_in + n_cols);
-  std::vector<const AtmosData*> data;
-  for (auto* a : cols) {
-    if ((rc = check_common(ctx, a, o->precision, where))) return rc;
-    data.push_back(&a->d);
-  }
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  Batch b;
-  if ((rc = batch_create(&b, data, o->precision == JFNK_MIXED, std::max(o->krylov_max, 1)))) return rc;
-  int worst = JFNK_OK;
-  rc = on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
-    int r = prepare_solve(&b, cols, o, n_inout, J_inout, where, s);
-    if (r) return r;
-    if ((r = run_to_completion(&b, o, s))) return r;
-    return finish_solve(&b, cols, n_inout, J_inout, stats, where, s, &worst);
-  });
-  if (rc) return rc;
-  if (worst != JFNK_OK) return fail(worst, "some columns did not converge (see stats[].status)");
-  return JFNK_OK;
+  jfnk_batch* h = nullptr;
+  if ((rc = jfnk_batch_create(ctx, n_cols, cols_in, o->precision, std::max(o->krylov_max, 1), &h))) return rc;
+  rc = jfnk_batch_run(h, o, n_inout, J_inout, stats, where, stream);
+  jfnk_batch_destroy(h);
+  return rc;
 }
 
 }  // extern "C"

@@ -73,7 +73,7 @@ __device__ __forceinline__ void pl_coef_f(float x, float r, float& e, float& w, 
 }
 
 constexpr int kFusedThreads = 256;
-constexpr int kFusedSlots = 6;   // E, X(D), P1(dD coef | I), P2(dD | LX), LB, LE
+constexpr int kFusedSlots = 5;   // E, X(D), P1(dD coef | I), P2(dD | LX), LE
 constexpr int kFusedStage = 6;   // chi, S, dS, dchi, ddS, 1/(chi^k + chi^{k+1}) per (q, k)
 
 __host__ __device__ inline size_t round16(size_t bytes) { return (bytes + 15) / 16 * 16; }
@@ -124,8 +124,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
   real* X = E + plane;
   real* P1 = X + plane;    // tangent: -ddtau e        | base: a S^k + b S^u, then hw I
   real* P2 = P1 + plane;   // tangent: coefficient, then hw dD | base: LX constant, then hw dI/dchi
-  real* LB = P2 + plane;   // base: LX slope on D^u
-  real* LE = LB + plane;   // base: hw dI/deta
+  real* LE = P2 + plane;   // base: hw dI/deta
   const real* chi_g = reinterpret_cast<const real*>(cd.w.chi);
   const real* dchi_g = reinterpret_cast<const real*>(cd.w.dchi);
   const double* S64 = cd.w.S;
@@ -159,40 +158,47 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
   }
   __syncthreads();
 
-  // phase A: coefficients of every (depth, ray) step, in parallel
-  for (int i = threadIdx.x; i < nz * nray; i += blockDim.x) {
-    const int k = i / nray, ray = i - k * nray;
+  // phase A: coefficients of every (depth, ray) step, in parallel; each
+  // thread keeps one ray and strides over depths (no index division in the loop)
+  const int klanes = blockDim.x / nray;
+  if ((int)threadIdx.x < klanes * nray) {
+    const int ray = threadIdx.x % nray;
+    const int kl = threadIdx.x / nray;
     const int ql = ray / nr, rr = ray - ql * nr;
     const bool up = rr < nmu;
-    if ((up && k == nz - 1) || (!up && k == 0)) continue;
     const int m = up ? rr : rr - nmu;
-    const int ku = up ? k + 1 : k - 1;
-    const int kd = up ? k : k - 1;
     const real inv2mu = s_mu[3 * m];
     const real hw = s_mu[3 * m + 1];
+    const real two_mu = s_mu[3 * m + 2];
     const real* ch = s_chi + ql * nz;
-    const real c0 = ch[k], cu = ch[ku];
-    const real h = s_dz[kd] * inv2mu;
-    const real dtau = h * (c0 + cu);
-    // 1/dtau = (2 mu / dz) / (chi^k + chi^u): the layer reciprocal is shared
-    const real rdt = s_rs[ql * nz + kd] * (s_idz[kd] * s_mu[3 * m + 2]);
-    real e, w, a, bq;
-    pl_coef_f(dtau, rdt, e, w, a, bq);
-    const real dSin = up ? s_dS[ql * nz + k] : -s_dS[ql * nz + k - 1];
-    const size_t si = (size_t)k * R + ray;
-    E[si] = e;
-    X[si] = w * dSin;
-    if (tan) {
-      const real ddtau = h * (s_dchi[ql * nz + k] + s_dchi[ql * nz + ku]);
-      const real ddSin = up ? s_ddS[ql * nz + k] : -s_ddS[ql * nz + k - 1];
-      P1[si] = -ddtau * e;
-      P2[si] = -ddtau * bq * dSin + w * ddSin;
-    } else if (der) {
-      const real S0 = s_S[ql * nz + k], Su = s_S[ql * nz + ku];
-      P1[si] = a * S0 + bq * dtau * Su;
-      P2[si] = hw * (-(S0 / c0) * a - h * dSin * bq);
-      LB[si] = -hw * h * e;
-      LE[si] = hw * (a / c0);
+    const real* rs = s_rs + ql * nz;
+    const real* dSq = s_dS + ql * nz;
+    const int kbeg = up ? 0 : 1, kend = up ? nz - 1 : nz;   // steps into depth k
+    for (int k = kbeg + kl; k < kend; k += klanes) {
+      const int ku = up ? k + 1 : k - 1;
+      const int kd = up ? k : k - 1;
+      const real c0 = ch[k], cu = ch[ku];
+      const real h = s_dz[kd] * inv2mu;
+      const real dtau = h * (c0 + cu);
+      // 1/dtau = (2 mu / dz) / (chi^k + chi^u): the layer reciprocal is shared
+      const real rdt = rs[kd] * (s_idz[kd] * two_mu);
+      real e, w, a, bq;
+      pl_coef_f(dtau, rdt, e, w, a, bq);
+      const real dSin = up ? dSq[k] : -dSq[k - 1];
+      const size_t si = (size_t)k * R + ray;
+      E[si] = e;
+      X[si] = w * dSin;
+      if (tan) {
+        const real ddtau = h * (s_dchi[ql * nz + k] + s_dchi[ql * nz + ku]);
+        const real ddSin = up ? s_ddS[ql * nz + k] : -s_ddS[ql * nz + k - 1];
+        P1[si] = -ddtau * e;
+        P2[si] = -ddtau * bq * dSin + w * ddSin;
+      } else if (der) {
+        const real S0 = s_S[ql * nz + k], Su = s_S[ql * nz + ku];
+        P1[si] = a * S0 + bq * dtau * Su;
+        P2[si] = hw * (-(S0 / c0) * a - h * dSin * bq);
+        LE[si] = hw * (a / c0);
+      }
     }
   }
   __syncthreads();
@@ -232,7 +238,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
       } else if (der) {
         I = I * e + P1[si];
         P1[si] = hw * I;
-        P2[si] = P2[si] + LB[si] * D;
+        // dI^k/dchi^k: its slope on the upstream D is -hw h e (App. A.2)
+        const int kd = up ? k : k - 1;
+        P2[si] = P2[si] - hw * (s_dz[kd] * s_mu[3 * m]) * e * D;
         const real Sk = s_S[ql * nz + k];
         const real aD = Dn < (real)0 ? -Dn : Dn;
         M = fmax(M * e, aD);
@@ -288,6 +296,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
 
 int fused_prepare(Batch* b) {
   if (b->formal_qb <= 0) return JFNK_OK;
+  if (b->formal_threads <= 0) b->formal_threads = kFusedThreads;
   const size_t bytes = fused_smem_bytes(b->formal_qb, b->max_nz, b->max_nmu, b->mixed != 0);
   if (b->mixed)
     JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -296,16 +305,60 @@ int fused_prepare(Batch* b) {
   return JFNK_OK;
 }
 
-int launch_formal_fused(const Batch& b, cudaStream_t s) {
-  const int qb = b.formal_qb;
+static int launch_fused_cfg(const Batch& b, cudaStream_t s, int qb, int threads) {
   const size_t bytes = fused_smem_bytes(qb, b.max_nz, b.max_nmu, b.mixed != 0);
   dim3 g((b.max_nq + qb - 1) / qb, b.ncols);
   if (b.mixed)
-    k_formal_fused<float><<<g, kFusedThreads, bytes, s>>>(b.d_cols, qb);
+    k_formal_fused<float><<<g, threads, bytes, s>>>(b.d_cols, qb);
   else
-    k_formal_fused<double><<<g, kFusedThreads, bytes, s>>>(b.d_cols, qb);
+    k_formal_fused<double><<<g, threads, bytes, s>>>(b.d_cols, qb);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
+}
+
+int launch_formal_fused(const Batch& b, cudaStream_t s) {
+  return launch_fused_cfg(b, s, b.formal_qb, b.formal_threads);
+}
+
+// Autotuner: times the fused kernel in tangent mode (the bulk of a solve) on
+// the batch's own columns for every (frequencies per block, threads per block)
+// pair that fits, and keeps the fastest. Requires the columns' base evaluation
+// buffers to be filled (chi, S) and a direction in w.v.
+int fused_autotune(Batch* b, cudaStream_t s) {
+  if (b->formal_qb <= 0) return JFNK_OK;
+  const size_t cap = 227 * 1024;
+  cudaEvent_t e0, e1;
+  JFNK_CUDA(cudaEventCreate(&e0));
+  JFNK_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bq = b->formal_qb, bt = b->formal_threads;
+  for (int qb : {1, 2, 4, 8}) {
+    const size_t bytes = fused_smem_bytes(qb, b->max_nz, b->max_nmu, b->mixed != 0);
+    if (bytes > cap) continue;
+    const int nray = qb * 2 * b->max_nmu;
+    for (int threads : {64, 128, 256}) {
+      if (threads < nray) continue;
+      if (b->mixed)
+        JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      else
+        JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      int rc = launch_fused_cfg(*b, s, qb, threads);   // warm-up
+      if (rc) return rc;
+      JFNK_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r)
+        if ((rc = launch_fused_cfg(*b, s, qb, threads))) return rc;
+      JFNK_CUDA(cudaEventRecord(e1, s));
+      JFNK_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      JFNK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bq = qb; bt = threads; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->formal_qb = bq;
+  b->formal_threads = bt;
+  return fused_prepare(b);
 }
 
 // Largest frequency block whose shared memory still lets two blocks share an SM

@@ -96,6 +96,8 @@ struct Batch {
   int graph_ticks = 0;
   bool graph_profiled = false;
   int formal_qb = 0;                  // frequencies per block of the fused formal kernel (0: unfused)
+  int formal_threads = 0;             // threads per block of the fused formal kernel
+  bool tuned = false;                 // autotuner has run on this batch
   int graph_kernels = 0;              // kernel nodes in the captured tick graph
   long replays = 0;                   // graph replays of the last solve
   std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel of each tick
@@ -117,6 +119,7 @@ size_t fused_smem_bytes(int qb, int nz, int nmu, bool mixed);
 int fused_default_qb(int max_nz, int max_nmu, bool mixed);
 int fused_prepare(Batch* b);
 int launch_formal_fused(const Batch& b, cudaStream_t s);
+int fused_autotune(Batch* b, cudaStream_t s);
 // Sets every column's forced evaluation mode (explicit API calls) or -1.
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.

@@ -240,3 +240,21 @@ def test_invalid_descriptors_are_rejected(ctx):
     col2 = W.replace(col, T=-col.T)
     with pytest.raises(B.JFNKError):
         B.Atmosphere(ctx, atom, col2)
+
+
+def test_batch_plan_is_reusable_and_matches_single(ctx):
+    """A persistent batch plan gives the same populations on repeated runs and alone."""
+    wl = W.config4(n_columns=3, nz_min=64, nz_max=80, nu_scale=0.1)
+    atom = B.Atom(ctx, wl.atom)
+    atms = [B.Atmosphere(ctx, atom, c, n_mu=3) for c in wl.columns]
+    plan = B.BatchPlan(ctx, atms, precision=B.JFNK_MIXED)
+    opts = B.default_options(precision=B.JFNK_MIXED)
+    ns1, st1 = plan.run(opts, raise_on_fail=False)
+    ns1 = [n.copy() for n in ns1]
+    ns2, st2 = plan.run(opts, raise_on_fail=False)
+    for a, b_, s1, s2, atm in zip(ns1, ns2, st1, st2, atms):
+        assert s1["status"] == s2["status"]
+        np.testing.assert_array_equal(a, b_)
+        if s1["status"] == 0:
+            n_single, _, s = B.solve(atm, B.default_options(precision=B.JFNK_MIXED))
+            np.testing.assert_array_equal(a, n_single)
