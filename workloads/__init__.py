@@ -187,12 +187,14 @@ _T_NODES = np.array([[-5.0, 1e5], [-4.6, 2.5e4], [-4.4, 8000.0], [-3.0, 6500.0],
 
 def chromosphere(n_depth: int = 82, m_top: float = 1e-5, m_bot: float = 10.0,
                  rng: Optional[np.random.Generator] = None, t_sigma: float = 0.0,
-                 abundance: float = 2.2e-6) -> Column:
+                 abundance: float = 2.2e-6, noise: str = "nodes") -> Column:
     """Hydrostatic column log-spaced in column mass.
 
     log T is piecewise linear in x = log10 m through fixed nodes (1e5 K at the
-    top, a 4,400 K minimum, 9,400 K at the bottom), optionally multiplied by
-    exp(N(0, t_sigma^2)) per depth; log10 n_e = 9 + (x + 5); p = g m;
+    top, a 4,400 K minimum, 9,400 K at the bottom). With t_sigma > 0 the
+    profile is perturbed by exp(N(0, t_sigma^2)): on each node (``noise="nodes"``,
+    a smooth perturbed profile) or on every depth point (``noise="depth"``);
+    log10 n_e = 9 + (x + 5); p = g m;
     n_H = (p/kT - n_e)/1.1; rho = 1.4 m_H n_H; z from dz = dm / rho.
 
     Background continuum: kappa(nu) = 1 cm^2/g up to 400 nm, rising as
@@ -205,9 +207,13 @@ def chromosphere(n_depth: int = 82, m_top: float = 1e-5, m_bot: float = 10.0,
     """
     m = np.logspace(np.log10(m_top), np.log10(m_bot), n_depth)
     x = np.log10(m)
-    logT = np.interp(x, _T_NODES[:, 0], np.log10(_T_NODES[:, 1]))
+    nodes_T = _T_NODES[:, 1].copy()
+    if t_sigma > 0.0 and noise == "nodes":
+        assert rng is not None
+        nodes_T = nodes_T * np.exp(rng.normal(0.0, t_sigma, size=len(nodes_T)))
+    logT = np.interp(x, _T_NODES[:, 0], np.log10(nodes_T))
     T = 10.0 ** logT
-    if t_sigma > 0.0:
+    if t_sigma > 0.0 and noise == "depth":
         assert rng is not None
         T = T * np.exp(rng.normal(0.0, t_sigma, size=n_depth))
     ne = 10.0 ** (9.0 + (x + 5.0))
@@ -304,12 +310,13 @@ def config3(seed: int = 1, n_depth: int = 82, nu_scale: float = 1.0,
 
 
 def config4(n_columns: int = 4096, seed: int = 20240624, nz_min: int = 64,
-            nz_max: int = 256, nu_scale: float = 1.0) -> Workload:
-    """Batch of independent columns: uniform depth counts, T noise sigma = 5 %."""
+            nz_max: int = 256, nu_scale: float = 1.0, noise: str = "nodes") -> Workload:
+    """Batch of independent columns: uniform depth counts, T noise sigma = 5 %
+    (on the temperature nodes by default; per depth point with noise="depth")."""
     rng = np.random.default_rng(seed)
     atom = ca_like_atom(0, nu_scale)
     nzs = rng.integers(nz_min, nz_max + 1, size=n_columns)
-    cols = [chromosphere(int(nz), rng=rng, t_sigma=0.05, abundance=2.2e-6) for nz in nzs]
+    cols = [chromosphere(int(nz), rng=rng, t_sigma=0.05, abundance=2.2e-6, noise=noise) for nz in nzs]
     return Workload(name="batched 1.5D Ca II-like columns", atom=atom, columns=cols,
                     n_mu=5, precision="mixed", init="lte")
 
