@@ -138,7 +138,8 @@ typedef struct {
   int max_restarts;     /* GMRES restarts per Newton step (20)                     */
   int precision;        /* jfnk_precision                                          */
   int init;             /* jfnk_init_kind                                          */
-  int clamp;            /* per-depth limiting of negative corrections (1)          */
+  int clamp;            /* per-depth limiting of negative corrections (1), applied
+                           to Newton and to hybrid-start RH92 corrections         */
   int rh92_warmup;      /* > 0: hybrid start, at most this many RH92 iterations    */
   double rh92_switch;   /* switch to JFNK when the RH92 change is below (1e-2)     */
   int max_ticks;        /* F-class evaluations allowed per column (20000)          */
@@ -218,7 +219,9 @@ int jfnk_block_jacobi(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const d
                       const double* J_dagger, double* P, jfnk_mem where, void* stream);
 
 /* One RH92 population update (Rybicki & Hummer 1992 with full preconditioning,
- * the paper's reference method): n_out from the formal solution at n. */
+ * the paper's reference method): n_out from the formal solution at n. The
+ * update is returned as solved, without the per-depth limiting that
+ * jfnk_solve applies to the RH92 corrections of a hybrid start. */
 int jfnk_rh92_update(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
                      const double* J_dagger, double* n_out, double* J_new, jfnk_mem where,
                      void* stream);

@@ -20,6 +20,13 @@ linear in the new populations n' (angle averages only, the atmosphere being
 static). Together with the collision terms and the conservation row, one
 N_l x N_l linear solve per depth gives n'. At the fixed point n' = n the rates
 are exact, so RH92 and JFNK share the same solution.
+
+Far from the solution (LTE start in a hot, strongly ionised layer) the solve
+can return negative populations. With ``clamp`` the correction n' - n is then
+limited per depth exactly like a Newton correction (Sect. 2.2.2, the same
+``depth_clamp``): the paper states that limiting for the Newton step only, and
+applying it to the RH92 correction is this implementation's reading; it leaves
+every iteration that stays positive unchanged.
 """
 from __future__ import annotations
 
@@ -28,7 +35,7 @@ from typing import List
 
 import numpy as np
 
-from .jfnk import pop_change
+from .jfnk import depth_clamp, pop_change
 from .model import FOURPI, H, Model, initial_J
 from .residual import residual
 
@@ -86,7 +93,8 @@ def rh92_update(m: Model, n, res):
     return n_new
 
 
-def rh92(m: Model, n0, J0=None, ftol: float = 1e-4, maxiter: int = 500) -> RH92Result:
+def rh92(m: Model, n0, J0=None, ftol: float = 1e-4, maxiter: int = 500,
+         clamp: bool = True) -> RH92Result:
     n = np.array(n0, dtype=float)
     Jdag = initial_J(m) if J0 is None else np.array(J0, dtype=float)
     hist = []
@@ -96,6 +104,8 @@ def rh92(m: Model, n0, J0=None, ftol: float = 1e-4, maxiter: int = 500) -> RH92R
     res = residual(m, n, Jdag, want_lambda=True)
     for it in range(1, maxiter + 1):
         n_new = rh92_update(m, n, res)
+        if clamp:
+            n_new, _ = depth_clamp(n, n_new - n)
         err = pop_change(n_new, n)
         Jdag = res.J
         n = n_new

@@ -19,6 +19,7 @@ int fail(int code, const std::string& msg) {
 
 Batch::~Batch() {
   if (graph) cudaGraphExecDestroy(graph);
+  if (graph_view) cudaGraphExecDestroy(graph_view);
   if (h_status) cudaFreeHost(h_status);
   for (cudaEvent_t e : tick_ev) cudaEventDestroy(e);
 }
@@ -120,12 +121,9 @@ __global__ void k_init_state(SolverState* st, int n, int phase) {
 
 constexpr int kTicksPerGraph = 8;
 
-static int ensure_graph(Batch* b, cudaStream_t s, bool profile) {
-  if (b->graph && b->graph_profiled == profile) return JFNK_OK;
-  if (b->graph) {
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+// Captures kTicksPerGraph ticks (evaluation + Krylov step) of the batch's
+// current launch view into an executable graph.
+static int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out) {
   if (profile && b->tick_ev.empty()) {
     b->tick_ev.resize(2 * kTicksPerGraph);
     for (auto& e : b->tick_ev) JFNK_CUDA(cudaEventCreate(&e));
@@ -150,39 +148,89 @@ static int ensure_graph(Batch* b, cudaStream_t s, bool profile) {
     cudaGraphNodeType ty;
     if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) b->graph_kernels++;
   }
-  e = cudaGraphInstantiate(&b->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(JFNK_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   b->graph_ticks = kTicksPerGraph;
+  return JFNK_OK;
+}
+
+static int ensure_graph(Batch* b, cudaStream_t s, bool profile) {
+  if (b->graph && b->graph_profiled == profile) return JFNK_OK;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  int rc = capture_ticks(b, s, profile, &b->graph);
+  if (rc) return rc;
   b->graph_profiled = profile;
   if (!b->h_status) JFNK_CUDA(cudaMallocHost(&b->h_status, sizeof(int) * std::max(1, b->ncols)));
   return JFNK_OK;
 }
 
-// Runs the tick graph until every column has left the running state.
+// Runs the tick graph until every column has left the running state. When at
+// most half of the columns of the current launch view are still running, the
+// view is rebuilt over those columns only (their descriptors are gathered
+// into d_view, the launch extents shrink) and its tick graph recaptured, so
+// that finished columns stop costing launched blocks.
 static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   const bool profile = o->profile != 0;
   int rc = ensure_graph(b, s, profile);
   if (rc) return rc;
   b->tick_ms.clear();
   b->replays = 0;
+  b->compactions = 0;
+  // the full view, restored before returning
+  const int nfull = b->ncols;
+  ColDesc* dfull = b->d_cols;
+  const int fz = b->max_nz, fq = b->max_nq, ft = b->max_nt, fN = b->max_N, fm = b->max_nmu;
+  std::vector<int> view(nfull);
+  for (int c = 0; c < nfull; ++c) view[c] = c;
+  cudaGraphExec_t cur = b->graph;
   const long max_replays = (long)o->max_ticks / b->graph_ticks + 2;
-  for (long r = 0; r < max_replays; ++r) {
-    JFNK_CUDA(cudaGraphLaunch(b->graph, s));
+  rc = JFNK_OK;
+  for (long r = 0; r < max_replays && !rc; ++r) {
+    if (cudaGraphLaunch(cur, s) != cudaSuccess) { rc = fail(JFNK_E_CUDA, "cudaGraphLaunch failed"); break; }
     b->replays++;
-    JFNK_CUDA(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s));
-    JFNK_CUDA(cudaStreamSynchronize(s));
+    if (cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(JFNK_E_CUDA, "status poll failed"); break; }
     if (profile)
       for (int t = 0; t < b->graph_ticks; ++t) {
         float ms = 0.f;
-        JFNK_CUDA(cudaEventElapsedTime(&ms, b->tick_ev[2 * t], b->tick_ev[2 * t + 1]));
+        cudaEventElapsedTime(&ms, b->tick_ev[2 * t], b->tick_ev[2 * t + 1]);
         b->tick_ms.push_back(ms);
       }
-    bool running = false;
-    for (int c = 0; c < b->ncols; ++c) running |= (b->h_status[c] == 1);
-    if (!running) return JFNK_OK;
+    std::vector<int> running;
+    for (int c = 0; c < b->ncols; ++c)
+      if (b->h_status[c] == 1) running.push_back(view[c]);
+    if (running.empty()) break;
+    if (b->ncols > 1 && (int)running.size() * 2 <= b->ncols) {
+      std::vector<ColDesc> hv;
+      int mz = 0, mq = 0, mt = 0, mN = 0, mm = 0;
+      for (int c : running) {
+        const ColDesc& d = b->h_cols[c];
+        hv.push_back(d);
+        mz = std::max(mz, d.t.nz); mq = std::max(mq, d.t.nq); mt = std::max(mt, d.t.nt);
+        mN = std::max(mN, d.t.nz * d.t.nl); mm = std::max(mm, d.t.nmu);
+      }
+      std::vector<int> ones(running.size(), 1);
+      if (cudaMemcpyAsync(b->d_view, hv.data(), sizeof(ColDesc) * hv.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaMemcpyAsync(b->d_status, ones.data(), sizeof(int) * ones.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(JFNK_E_CUDA, "view rebuild failed"); break; }
+      b->d_cols = b->d_view;
+      b->ncols = (int)running.size();
+      b->max_nz = mz; b->max_nq = mq; b->max_nt = mt; b->max_N = mN; b->max_nmu = mm;
+      if (b->graph_view) { cudaGraphExecDestroy(b->graph_view); b->graph_view = nullptr; }
+      if ((rc = capture_ticks(b, s, profile, &b->graph_view))) break;
+      cur = b->graph_view;
+      view = running;
+      b->compactions++;
+    }
   }
-  return JFNK_OK;
+  b->d_cols = dfull;
+  b->ncols = nfull;
+  b->max_nz = fz; b->max_nq = fq; b->max_nt = ft; b->max_N = fN; b->max_nmu = fm;
+  return rc;
 }
 
 static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,

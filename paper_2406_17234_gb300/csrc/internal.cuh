@@ -103,6 +103,10 @@ struct Batch {
   std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel of each tick
   std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve
   int* h_status = nullptr;            // pinned host mirror of d_status
+  // launch view over the columns still running (straggler compaction)
+  ColDesc* d_view = nullptr;          // device array [ncols] of the view's descriptors
+  cudaGraphExec_t graph_view = nullptr;
+  int compactions = 0;                // view rebuilds in the last solve
   ~Batch();
 };
 

@@ -84,6 +84,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   size_t o_state = ar.take<SolverState>(nc);
   size_t o_status = ar.take<int>(nc);
   size_t o_opts = ar.take<SolverOpts>(1);
+  size_t o_view = ar.take<ColDesc>(nc);
   int rc = ar.allocate();
   if (rc) return rc;
   b->h_cols.resize(nc);
@@ -91,6 +92,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   b->d_state = ar.ptr<SolverState>(o_state);
   b->d_status = ar.ptr<int>(o_status);
   b->d_opts = ar.ptr<SolverOpts>(o_opts);
+  b->d_view = ar.ptr<ColDesc>(o_view);
   for (int c = 0; c < nc; ++c) {
     const Offs& o = off[c];
     ColDesc& d = b->h_cols[c];
@@ -186,8 +188,10 @@ __device__ bool small_solve(double* A, double* b, int nl) {
 }
 
 // RH92 update of depth k from the sums of an EV_RH92 evaluation; returns the
-// population change measure of the depth (or NaN on a singular system).
-__device__ double rh92_depth(const ColDesc& cd, int k) {
+// population change measure of the depth (or NaN on a singular system). With
+// clamp the correction is limited like a Newton correction (Sect. 2.2.2), so
+// that no population of the depth falls below a tenth of its old value.
+__device__ double rh92_depth(const ColDesc& cd, int k, bool clamp) {
   const ColTables& T = cd.t;
   const int nl = T.nl, nt = T.nt, nz = T.nz;
   double M[kMaxL * kMaxL], c0[kMaxL];
@@ -216,10 +220,17 @@ __device__ double rh92_depth(const ColDesc& cd, int k) {
   rhs[is] = T.ntot[k];
   if (!small_solve(M, rhs, nl)) return nan("");
   double* n = cd.w.n + k * nl;
+  double alpha = 1.0;
+  if (clamp)
+    for (int l = 0; l < nl; ++l) {
+      const double d = rhs[l] - n[l];
+      if (d < 0.0) alpha = fmin(alpha, 0.9 * n[l] / (-d));
+    }
   double err = 0.0;
   for (int l = 0; l < nl; ++l) {
-    err = fmax(err, 0.5 * fabs((rhs[l] - n[l]) / (rhs[l] + n[l])));
-    n[l] = rhs[l];
+    const double nn = clamp ? n[l] + alpha * (rhs[l] - n[l]) : rhs[l];
+    err = fmax(err, 0.5 * fabs((nn - n[l]) / (nn + n[l])));
+    n[l] = nn;
   }
   return err;
 }
@@ -274,7 +285,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
   if (phase == PH_RH92) {
     double err = 0.0;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-      double e = rh92_depth(cd, k);
+      double e = rh92_depth(cd, k, o.clamp != 0);
       err = (e == e) ? fmax(err, e) : INFINITY;
     }
     err = block_max(err, sh);
@@ -503,7 +514,7 @@ __global__ void k_rh92_apply(const ColDesc* __restrict__ cols) {
   const ColDesc& cd = cols[blockIdx.y];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= cd.t.nz) return;
-  rh92_depth(cd, k);
+  rh92_depth(cd, k, false);   // the plain update: jfnk_rh92_update applies no limiting
 }
 
 int launch_rh92_update(const Batch& b, cudaStream_t s) {

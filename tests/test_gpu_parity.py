@@ -198,6 +198,26 @@ def test_hybrid_solve_hydrogen(ctx):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_limited_hybrid_solve(ctx, precision):
+    """Capped hybrid start on a column whose plain RH92 step goes negative: the
+    limited RH92 warm-up and the JFNK phase match the oracle's."""
+    from oracle.hybrid import hybrid
+    atom = W.ca_like_atom(0, 0.12)
+    col = W.chromosphere(40, rng=np.random.default_rng(0), t_sigma=0.05, abundance=2.2e-6)
+    a = B.Atom(ctx, atom)
+    atm = B.Atmosphere(ctx, a, col, n_mu=3)
+    m = OM.build_model(atom, col, 3)
+    ref = hybrid(m, m.nstar, switch_tol=0.1, rh92_max=10, rtol=1e-6, ftol=1e-10)
+    tol = dict(rtol=1e-6, ftol=1e-10) if precision == 0 else dict(rtol=1e-4, ftol=1e-5)
+    n, J, st = B.solve(atm, B.default_options(precision=precision, rh92_warmup=10, rh92_switch=0.1, **tol))
+    assert st["status"] == 0 and 0 < st["rh92_iters"] <= 10
+    if precision == 0:
+        assert st["rh92_iters"] == ref.rh92_iters
+    assert (n > 0).all()
+    np.testing.assert_allclose(n, ref.n, rtol=1e-5 if precision == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_batch_equals_single(ctx, precision):
     """Each column's result in a batch is bit-identical to its result alone."""
     wl = W.config4(n_columns=5, nz_min=60, nz_max=90, nu_scale=0.1)

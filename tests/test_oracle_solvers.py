@@ -7,9 +7,9 @@ from oracle import krylov
 from oracle import model as OM
 from oracle.dense import dense_newton
 from oracle.hybrid import hybrid
-from oracle.jfnk import jfnk, zero_radiation_guess
+from oracle.jfnk import depth_clamp, jfnk, zero_radiation_guess
 from oracle.residual import residual
-from oracle.rh92 import rh92
+from oracle.rh92 import rh92, rh92_update
 
 
 def test_gmres_and_bicgstab_solve_linear_systems():
@@ -127,6 +127,44 @@ def test_hybrid_start_converges_for_hydrogen():
     np.testing.assert_allclose(s.n, t.n, rtol=1e-4)
     for h in t.history:
         np.testing.assert_allclose(h["n"].sum(axis=1), m.ntot, rtol=1e-11)
+
+
+def _hot_top_column():
+    """Coarse Ca II-like column whose LTE start sends the plain RH92 solve negative."""
+    atom = W.ca_like_atom(0, 0.12)
+    col = W.chromosphere(40, rng=np.random.default_rng(0), t_sigma=0.05, abundance=2.2e-6)
+    return OM.build_model(atom, col, 3)
+
+
+def test_limited_rh92_correction_stays_positive_and_conserves():
+    """Sect. 2.2.2 per-depth limiting applied to the RH92 correction: alpha = 1
+    exactly where no population falls below a tenth of its old value, every
+    limited population keeps at least a tenth of it, and each depth still sums
+    to its total particle density (both n and the plain update do)."""
+    m = _hot_top_column()
+    res = residual(m, m.nstar, OM.initial_J(m), want_lambda=True)
+    raw = rh92_update(m, m.nstar, res)
+    assert (raw <= 0).any()                      # the plain update leaves the domain
+    np.testing.assert_allclose(raw.sum(axis=1), m.ntot, rtol=1e-10)
+    lim, alpha = depth_clamp(m.nstar, raw - m.nstar)
+    free = (raw >= 0.1 * m.nstar).all(axis=1)
+    assert (alpha[free] == 1.0).all() and (alpha[~free] < 1.0).all()
+    assert (lim >= 0.1 * m.nstar * (1 - 1e-12)).all()
+    np.testing.assert_allclose(lim.sum(axis=1), m.ntot, rtol=1e-10)
+    for k in range(1, 5):                        # every limited iterate stays positive
+        w = rh92(m, m.nstar, ftol=0.0, maxiter=k)
+        assert (w.n > 0).all()
+        np.testing.assert_allclose(w.n.sum(axis=1), m.ntot, rtol=1e-10)
+
+
+def test_limited_hybrid_start_reaches_the_jfnk_solution():
+    """A capped, limited RH92 warm-up followed by Algorithm 2 lands on the same
+    fixed point as Algorithm 2 from LTE (two different iterations, one solution)."""
+    m = _hot_top_column()
+    a = jfnk(m, m.nstar, rtol=1e-6, ftol=1e-10)
+    b = hybrid(m, m.nstar, switch_tol=0.1, rh92_max=10, rtol=1e-6, ftol=1e-10)
+    assert a.converged and b.converged and 0 < b.rh92_iters <= 10
+    np.testing.assert_allclose(b.n, a.n, rtol=1e-8)
 
 
 def test_zero_radiation_guess_solves_its_equations():
