@@ -128,6 +128,15 @@ typedef struct {
   int n_mu;                     /* Gauss-Legendre points on ]0,1[, 1..JFNK_MAX_MU */
 } jfnk_atmos_desc;
 
+/* Formal-solution kernel of a batch (all give the solution of Eqs. Iplus/
+ * Iminus; the two sweep kernels of the mixed mode are bit-identical). */
+typedef enum {
+  JFNK_FORMAL_PER_RAY = 0,       /* per-ray buffers, separate ray-sum kernel      */
+  JFNK_FORMAL_FUSED = 1,         /* FP64: block per frequency group, shared memory */
+  JFNK_FORMAL_SWEEP_THREAD = 2,  /* mixed: thread per frequency, all angles        */
+  JFNK_FORMAL_SWEEP_WARP = 3     /* mixed: warp per frequency pair, lane per ray   */
+} jfnk_formal_kernel;
+
 /* Solver options (Algorithm 2; defaults from jfnk_default_options). */
 typedef struct {
   double ftol;          /* 1/2 ||(n - n_prev)/(n + n_prev)||_inf threshold (1e-4)  */
@@ -144,6 +153,8 @@ typedef struct {
   double rh92_switch;   /* switch to JFNK when the RH92 change is below (1e-2)     */
   int max_ticks;        /* F-class evaluations allowed per column (20000)          */
   int profile;          /* 1: time the formal-solution kernel of every active tick */
+  int formal_variant;   /* mixed mode: 0 autotuned, JFNK_FORMAL_SWEEP_THREAD or
+                           JFNK_FORMAL_SWEEP_WARP forced (identical results)      */
 } jfnk_options;
 
 typedef struct {
@@ -159,8 +170,9 @@ typedef struct {
   double formal_ms;     /* profile: summed duration of the formal-solution kernel  */
   int formal_launches;  /* profile: number of timed launches (active ticks)        */
   int kernel_launches;  /* CUDA kernels launched by the solve (graph nodes included) */
-  int formal_qb;        /* autotuned frequencies per block of the formal kernel     */
-  int formal_threads;   /* autotuned threads per block of the formal kernel         */
+  int formal_qb;        /* fused kernel: frequencies per block (0 for the others)   */
+  int formal_threads;   /* threads per block (warps per block: JFNK_FORMAL_SWEEP_WARP) */
+  int formal_kernel;    /* jfnk_formal_kernel that ran the formal solution          */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */

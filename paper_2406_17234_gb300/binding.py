@@ -31,6 +31,10 @@ JFNK_FP64 = 0
 JFNK_MIXED = 1
 JFNK_INIT_LTE = 0
 JFNK_INIT_USER = 1
+JFNK_FORMAL_PER_RAY = 0
+JFNK_FORMAL_FUSED = 1
+JFNK_FORMAL_SWEEP_THREAD = 2
+JFNK_FORMAL_SWEEP_WARP = 3
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -65,7 +69,7 @@ class jfnk_options(C.Structure):
                 ("maxiter", C.c_int), ("krylov_max", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("init", C.c_int), ("clamp", C.c_int),
                 ("rh92_warmup", C.c_int), ("rh92_switch", C.c_double), ("max_ticks", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("formal_variant", C.c_int)]
 
 
 class jfnk_stats(C.Structure):
@@ -73,7 +77,7 @@ class jfnk_stats(C.Structure):
                 ("F_calls", C.c_int), ("jvp_calls", C.c_int), ("F_norm", C.c_double),
                 ("F_norm0", C.c_double), ("dn_norm", C.c_double), ("ray_points", C.c_double),
                 ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int),
-                ("formal_qb", C.c_int), ("formal_threads", C.c_int)]
+                ("formal_qb", C.c_int), ("formal_threads", C.c_int), ("formal_kernel", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -107,6 +107,9 @@ static int validate_options(const jfnk_options* o) {
   if (o->init != JFNK_INIT_LTE && o->init != JFNK_INIT_USER)
     return fail(JFNK_E_INVALID, "init must be JFNK_INIT_LTE or JFNK_INIT_USER");
   if (o->rh92_warmup < 0) return fail(JFNK_E_INVALID, "rh92_warmup must be >= 0");
+  if (o->formal_variant != 0 && o->formal_variant != JFNK_FORMAL_SWEEP_THREAD &&
+      o->formal_variant != JFNK_FORMAL_SWEEP_WARP)
+    return fail(JFNK_E_INVALID, "formal_variant must be 0, JFNK_FORMAL_SWEEP_THREAD or JFNK_FORMAL_SWEEP_WARP");
   return JFNK_OK;
 }
 
@@ -233,6 +236,26 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   return rc;
 }
 
+static void drop_graphs(Batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (b->graph_view) {
+    cudaGraphExecDestroy(b->graph_view);
+    b->graph_view = nullptr;
+  }
+}
+
+// Selects a sweep variant and block size; captured graphs with other shapes are dropped.
+static int set_sweep_config(Batch* b, int variant, int size) {
+  if (b->sweep_variant == variant && b->formal_threads == size) return JFNK_OK;
+  b->sweep_variant = variant;
+  b->formal_threads = size;
+  drop_graphs(b);
+  return JFNK_OK;
+}
+
 static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
                          const jfnk_options* o, double* const* n_in, double* const* J_in,
                          jfnk_mem where, cudaStream_t s) {
@@ -261,8 +284,14 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
       JFNK_CUDA(cudaMemcpyAsync(cd.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
-  if (!b->tuned && b->formal_qb > 0) {
-    // tune the fused formal kernel once per batch, on its own columns: a base
+  if (b->formal_kind == FORMAL_SWEEP && o->formal_variant != 0) {
+    // a forced sweep variant (results are the same as with the tuned one)
+    const int v = o->formal_variant == JFNK_FORMAL_SWEEP_WARP ? 2 : 1;
+    const int size = v == 2 ? sweep_warp_size(b->max_nz) : 128;
+    if (size == 0) return fail(JFNK_E_INVALID, "JFNK_FORMAL_SWEEP_WARP: the column is too deep for its shared memory");
+    if ((rc = set_sweep_config(b, v, size))) return rc;
+  } else if (!b->tuned && b->formal_kind != FORMAL_UNFUSED) {
+    // tune the formal kernel once per batch, on its own columns: a base
     // evaluation at the initial state, then tangent data along v = n
     if ((rc = batch_set_forced_mode(b, EV_BASE, s))) return rc;
     if ((rc = launch_evaluation(*b, s))) return rc;
@@ -273,13 +302,14 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
     }
     if ((rc = batch_set_forced_mode(b, EV_TANGENT, s))) return rc;
     if ((rc = launch_evaluation(*b, s))) return rc;
-    if ((rc = fused_autotune(b, s))) return rc;
+    if ((rc = b->formal_kind == FORMAL_SWEEP ? sweep_autotune(b, s) : fused_autotune(b, s))) return rc;
     b->tuned = true;
-    if (b->graph) {   // a graph captured with other launch shapes is stale
-      cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
-    }
+    b->tuned_variant = b->sweep_variant;
+    b->tuned_size = b->formal_threads;
+    drop_graphs(b);   // graphs captured with other launch shapes are stale
     if ((rc = batch_set_forced_mode(b, -1, s))) return rc;
+  } else if (b->tuned && b->formal_kind == FORMAL_SWEEP) {
+    if ((rc = set_sweep_config(b, b->tuned_variant, b->tuned_size))) return rc;
   }
   // mark every column as running for the host poll
   std::vector<int> ones(b->ncols, 1);
@@ -328,8 +358,11 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.formal_ms = kernel_ms;
       S.formal_launches = active;
       S.kernel_launches = (int)(b->replays * b->graph_kernels) + 2;   // + state init, mode reset
-      S.formal_qb = b->formal_qb;
+      S.formal_qb = b->formal_kind == FORMAL_FUSED ? b->formal_qb : 0;
       S.formal_threads = b->formal_threads;
+      S.formal_kernel = b->formal_kind == FORMAL_SWEEP
+                            ? (b->sweep_variant == 2 ? JFNK_FORMAL_SWEEP_WARP : JFNK_FORMAL_SWEEP_THREAD)
+                            : (b->formal_kind == FORMAL_FUSED ? JFNK_FORMAL_FUSED : JFNK_FORMAL_PER_RAY);
     }
     if (status != JFNK_OK && *worst == JFNK_OK) *worst = status;
   }
@@ -374,6 +407,7 @@ void jfnk_default_options(jfnk_options* o) {
   o->rh92_switch = 1e-2;
   o->max_ticks = 20000;
   o->profile = 0;
+  o->formal_variant = 0;
 }
 
 int jfnk_init(int device, jfnk_ctx** out) {

@@ -61,6 +61,11 @@ struct ColTables {
   const double* t_w;      // [nwin] trapezoid weight omega_t(nu_q)
   const double* V;        // [nwin][nz]
   const double* G;        // [nwin][nz]
+  const float* V32;       // [nwin][nz] float copies (mixed-mode tangent evaluations)
+  const float* G32;       // [nwin][nz]
+  const float* V32T;      // [nz][nwin] the same, depth-major
+  const float* G32T;      // [nz][nwin]
+  const float* W32;       // [nwin] omega_t(nu_q) 4 pi/(h nu_q) 2 h nu_q^3/c^2 in float
   const double* dz;       // [nz-1] |z_k - z_{k+1}|
   const double* mu;       // [nmu]
   const double* wmu;      // [nmu]
@@ -116,6 +121,15 @@ struct ColWork {
   void* dH;         // tangent
   void* LX;         // per-ray 1/2 w dI^k/dchi^k
   void* LE;         // per-ray 1/2 w dI^k/deta^k
+  void* part;       // [5][nz][pitch] float: down-sweep ray sums of the sweep kernel
+  // mixed mode, FP32 tangent path; depth-major [nz][col_pitch(nq)] arrays
+  float* v32;       // [N] float copy of the tangent direction
+  float* chiT;      // chi at the base point
+  float* S32T;      // S at the base point (normalised)
+  float* dSkT;      // row k: S^{k+1} - S^k, formed in FP64 and rounded
+  float* dchiT;     // tangent of chi
+  float* dS32T;     // tangent of S (normalised)
+  float* dJ32T;     // tangent of J (normalised)
   double* J;        // [nq][nz]
   double* dJ;
   double* Lchi;
@@ -143,6 +157,9 @@ struct ColWork {
   double* nprev;    // [N]
   SolverState* st;
 };
+
+// Row pitch of the depth-major float arrays: frequencies rounded up to 32.
+__host__ __device__ inline int col_pitch(int nq) { return (nq + 31) & ~31; }
 
 struct ColDesc {
   ColTables t;

@@ -1,0 +1,63 @@
+// Shared pieces of the formal-solution kernels: the evaluation mode of a
+// column and the piecewise-linear coefficients of App. A.1 in the form the
+// difference recurrences use.
+#pragma once
+
+#include "internal.cuh"
+
+namespace jfnk {
+
+__device__ __forceinline__ int eval_mode_f(const ColDesc& cd) {
+  if (cd.forced_mode >= 0) return cd.forced_mode;
+  switch (cd.w.st->phase) {
+    case PH_BASE: return EV_BASE;
+    case PH_JVP:
+    case PH_RESTART: return EV_TANGENT;
+    case PH_RH92: return EV_RH92;
+    default: return EV_SKIP;
+  }
+}
+
+// Coefficients of one step of optical depth x: e = exp(-x), w = (1 - e)/x,
+// a = 1 - w and bq = (w - e)/x, each from its own Taylor series below
+// x = 0.1 (where 1 - e, 1 - w and w - e cancel); r = 1/x is supplied by the
+// caller (shared between the rays of a layer).
+__device__ __forceinline__ void pl_coef_f(double x, double r, double& e, double& w, double& a, double& bq) {
+  e = exp(-x);
+  if (x < 0.1) {
+    double pw = 0.0, pa = 0.0, pb = 0.0;
+    double inv_fact[17];
+    inv_fact[0] = 1.0;
+#pragma unroll
+    for (int m = 1; m < 17; ++m) inv_fact[m] = inv_fact[m - 1] / m;
+#pragma unroll
+    for (int m = 13; m >= 0; --m) {
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      pw = pw * x + sg * inv_fact[m + 1];
+      pa = pa * x + sg * inv_fact[m + 2];
+      pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
+    }
+    w = pw;
+    a = pa * x;
+    bq = pb;
+  } else {
+    w = (1.0 - e) * r;
+    a = 1.0 - w;
+    bq = (w - e) * r;
+  }
+}
+
+__device__ __forceinline__ void pl_coef_f(float x, float r, float& e, float& w, float& a, float& bq) {
+  e = __expf(-x);
+  if (x < 0.1f) {
+    w = fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
+    a = x * fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f);
+    bq = fmaf(fmaf(fmaf(fmaf(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
+  } else {
+    w = (1.0f - e) * r;
+    a = 1.0f - w;
+    bq = (w - e) * r;
+  }
+}
+
+}  // namespace jfnk

@@ -17,60 +17,9 @@
 //   base:       I^k = I^u e + a S^k + b S^u ;  dI^k/dchi^k = hw-scaled a_chi
 //               with S^u - I^u = -D^u ; dI^k/deta^k = a / chi^k
 // where u is the upstream depth (k+1 for mu > 0, k-1 for mu < 0).
-#include "internal.cuh"
+#include "formal_coef.cuh"
 
 namespace jfnk {
-
-__device__ __forceinline__ int eval_mode_f(const ColDesc& cd) {
-  if (cd.forced_mode >= 0) return cd.forced_mode;
-  switch (cd.w.st->phase) {
-    case PH_BASE: return EV_BASE;
-    case PH_JVP:
-    case PH_RESTART: return EV_TANGENT;
-    case PH_RH92: return EV_RH92;
-    default: return EV_SKIP;
-  }
-}
-
-// Taylor-series / direct coefficients (see residual.cu for the derivation);
-// r = 1/x is supplied by the caller (shared between the rays of a layer).
-__device__ __forceinline__ void pl_coef_f(double x, double r, double& e, double& w, double& a, double& bq) {
-  e = exp(-x);
-  if (x < 0.1) {
-    double pw = 0.0, pa = 0.0, pb = 0.0;
-    double inv_fact[17];
-    inv_fact[0] = 1.0;
-#pragma unroll
-    for (int m = 1; m < 17; ++m) inv_fact[m] = inv_fact[m - 1] / m;
-#pragma unroll
-    for (int m = 13; m >= 0; --m) {
-      const double sg = (m & 1) ? -1.0 : 1.0;
-      pw = pw * x + sg * inv_fact[m + 1];
-      pa = pa * x + sg * inv_fact[m + 2];
-      pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
-    }
-    w = pw;
-    a = pa * x;
-    bq = pb;
-  } else {
-    w = (1.0 - e) * r;
-    a = 1.0 - w;
-    bq = (w - e) * r;
-  }
-}
-
-__device__ __forceinline__ void pl_coef_f(float x, float r, float& e, float& w, float& a, float& bq) {
-  e = __expf(-x);
-  if (x < 0.1f) {
-    w = fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
-    a = x * fmaf(fmaf(fmaf(fmaf(fmaf(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f);
-    bq = fmaf(fmaf(fmaf(fmaf(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
-  } else {
-    w = (1.0f - e) * r;
-    a = 1.0f - w;
-    bq = (w - e) * r;
-  }
-}
 
 constexpr int kFusedThreads = 256;
 constexpr int kFusedSlots = 5;   // E, X(D), P1(dD coef | I), P2(dD | LX), LE
@@ -298,20 +247,14 @@ int fused_prepare(Batch* b) {
   if (b->formal_qb <= 0) return JFNK_OK;
   if (b->formal_threads <= 0) b->formal_threads = kFusedThreads;
   const size_t bytes = fused_smem_bytes(b->formal_qb, b->max_nz, b->max_nmu, b->mixed != 0);
-  if (b->mixed)
-    JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  else
-    JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return JFNK_OK;
 }
 
 static int launch_fused_cfg(const Batch& b, cudaStream_t s, int qb, int threads) {
   const size_t bytes = fused_smem_bytes(qb, b.max_nz, b.max_nmu, b.mixed != 0);
   dim3 g((b.max_nq + qb - 1) / qb, b.ncols);
-  if (b.mixed)
-    k_formal_fused<float><<<g, threads, bytes, s>>>(b.d_cols, qb);
-  else
-    k_formal_fused<double><<<g, threads, bytes, s>>>(b.d_cols, qb);
+  k_formal_fused<double><<<g, threads, bytes, s>>>(b.d_cols, qb);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
@@ -338,10 +281,7 @@ int fused_autotune(Batch* b, cudaStream_t s) {
     const int nray = qb * 2 * b->max_nmu;
     for (int threads : {64, 128, 256}) {
       if (threads < nray) continue;
-      if (b->mixed)
-        JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-      else
-        JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      JFNK_CUDA(cudaFuncSetAttribute(k_formal_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
       int rc = launch_fused_cfg(*b, s, qb, threads);   // warm-up
       if (rc) return rc;
       JFNK_CUDA(cudaEventRecord(e0, s));

@@ -1,0 +1,610 @@
+// Mixed-precision formal solution + ray sums, one thread per (frequency,
+// column): the thread carries every angle of a hemisphere at once (n_mu
+// independent recurrences, the instruction-level parallelism of the sweep)
+// and walks the column twice.
+//
+//   down sweep (mu < 0 rays, top to bottom): the per-depth sums of the
+//     hemisphere over its angles go to a scratch array laid out [k][q], so
+//     that the threads of a warp (consecutive frequencies) write one
+//     contiguous segment per depth;
+//   up sweep (mu > 0 rays, bottom to top): the hemisphere's own sums are added
+//     to the stored ones and the depth's outputs are written (J, J_new,
+//     Lambda_chi, Lambda_eta in base evaluations, dJ in tangent ones).
+//
+// No per-ray value is stored anywhere: the coefficients of a step (App. A.1,
+// App. A.2) are formed in registers right where the recurrence needs them,
+// and the optical-depth reciprocal of a layer is shared by the angles.
+//
+// The recurrences are those of the fused kernel (Eqs. Iplus/Iminus in the
+// difference form D = I - S, the tangent dD, and in base evaluations the
+// intensity form I with the re-anchoring of D on I - S); only the order of
+// the ray sums differs: each hemisphere is summed over its angles first and
+// the two hemisphere sums are then added.
+#include "formal_coef.cuh"
+
+namespace jfnk {
+
+constexpr int kSweepParts = 5;   // base: sum D, sum |D|, sum I, sum dI/dchi, sum dI/deta (x 1/2 w)
+
+// Scratch of the down sweep: [kSweepParts][nz][col_pitch(nq)] floats.
+__host__ __device__ inline int sweep_pitch(int nq) { return col_pitch(nq); }
+
+size_t sweep_scratch_bytes(int nq, int nz) {
+  return sizeof(float) * (size_t)kSweepParts * nz * sweep_pitch(nq);
+}
+
+// Every operation of a ray step is an explicitly rounded intrinsic: the
+// compiler may not contract or reorder any of them, so the two kernel
+// variants below (which see the same values in different registers, lanes
+// and orders of issue) produce bit-identical results.
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fma3(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// App. A.1 coefficients of a step of optical depth x (r = 1/x): e = exp(-x),
+// w = (1 - e)/x, a = 1 - w, bq = (w - e)/x; below x = 0.1 each comes from its
+// Taylor series (truncated after x^5, below 3e-10 relative).
+__device__ __forceinline__ void pl_coef_rn(float x, float r, float& e, float& w, float& a, float& bq) {
+  e = __expf(-x);
+  if (x < 0.1f) {
+    w = fma3(fma3(fma3(fma3(fma3(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
+    a = mul(x, fma3(fma3(fma3(fma3(fma3(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f));
+    bq = fma3(fma3(fma3(fma3(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
+  } else {
+    w = mul(sub(1.0f, e), r);
+    a = sub(1.0f, w);
+    bq = mul(sub(w, e), r);
+  }
+}
+
+// Quantities of one depth step shared by all angles of a hemisphere.
+struct StepIn {
+  float csum;    // chi^k + chi^u
+  float rs;      // 1/(chi^k + chi^u)
+  float dzk;     // |z_k - z_u|
+  float idzk;    // 1/|z_k - z_u|
+  float dSin;    // S^u - S^k (formed in FP64)
+  float S0, Su;  // S^k, S^u
+  float rc0;     // 1/chi^k
+  float dcs;     // dchi^k + dchi^u
+  float ddSin;   // dS^u - dS^k (formed in FP64)
+};
+
+// Contributions of one ray to the sums of its depth, each already x 1/2 w_mu.
+struct RayOut {
+  float xD, xI, xx, xe, xd;
+};
+
+// One step of one ray into depth k from its upstream neighbour u:
+//   D^k  = D^u e + w (S^u - S^k)                                  (D = I - S)
+//   dD^k = dD^u e - ddtau (e D^u + bq (S^u - S^k)) + w (dS^u - dS^k)
+//   I^k  = I^u e + a S^k + b S^u,  b = bq dtau                      (base)
+//   dI^k/dchi^k = -(S^k/chi^k) a - h (S^u - S^k) bq - h e D^u,      (App. A.2)
+//   dI^k/deta^k = a/chi^k,  h = |dz|/(2 mu), dtau = h (chi^k + chi^u)
+// In base evaluations D is re-anchored on I - S whenever that is the
+// better-conditioned value: D carries an absolute error of the order of the
+// largest |D| met upstream (attenuated along the ray), I - S one of the order
+// of |I| + |S|.
+template <bool TAN>
+__device__ __forceinline__ RayOut ray_step(const StepIn& in, float inv2mu, float two_mu, float hw, float& D,
+                                           float& I, float& M, float& dD) {
+  RayOut o;
+  const float h = mul(in.dzk, inv2mu);
+  const float dtau = mul(h, in.csum);
+  const float rdt = mul(in.rs, mul(in.idzk, two_mu));
+  float e, w, a, bq;
+  pl_coef_rn(dtau, rdt, e, w, a, bq);
+  const float Du = D;
+  float Dn = fma3(Du, e, mul(w, in.dSin));
+  if (TAN) {
+    const float ddtau = mul(h, in.dcs);
+    const float dDn = fma3(dD, e, fma3(-ddtau, fma3(e, Du, mul(bq, in.dSin)), mul(w, in.ddSin)));
+    dD = dDn;
+    o.xd = mul(hw, dDn);
+    o.xD = o.xI = o.xx = o.xe = 0.f;
+  } else {
+    const float In = fma3(I, e, fma3(a, in.S0, mul(mul(bq, dtau), in.Su)));
+    const float lx = -fma3(mul(in.S0, in.rc0), a, mul(h, fma3(in.dSin, bq, mul(e, Du))));
+    o.xI = mul(hw, In);
+    o.xx = mul(hw, lx);
+    o.xe = mul(hw, mul(a, in.rc0));
+    M = fmaxf(mul(M, e), fabsf(Dn));
+    const float anchor = add(fabsf(In), fabsf(in.S0));
+    if (anchor < M) {
+      Dn = sub(In, in.S0);
+      M = anchor;
+    }
+    I = In;
+    o.xD = mul(hw, Dn);
+    o.xd = 0.f;
+  }
+  D = Dn;
+  return o;
+}
+
+// Sum of eight angle contributions in the fixed tree of a 3-level xor
+// butterfly over 8 lanes (absent angles contribute 0).
+__device__ __forceinline__ float tree8(const float* x) {
+  return add(add(add(x[0], x[4]), add(x[2], x[6])), add(add(x[1], x[5]), add(x[3], x[7])));
+}
+__device__ __forceinline__ float butterfly8(float v) {
+  v = add(v, __shfl_xor_sync(0xffffffffu, v, 4));
+  v = add(v, __shfl_xor_sync(0xffffffffu, v, 2));
+  v = add(v, __shfl_xor_sync(0xffffffffu, v, 1));
+  return v;
+}
+
+// Output of one depth from the two hemisphere sums (base: D, |D|, I, Lchi, Leta).
+__device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, double Sk64, double c2, float fD, float fa,
+                                           float fI, float fx, float fe) {
+  // the representation with the smaller rounding error (intensities are >= 0)
+  double J = __dmul_rn(__dadd_rn(Sk64, (double)fD), c2);
+  if (fabsf(fI) < fa) J = __dmul_rn((double)fI, c2);
+  cd.w.J[o] = J;
+  jnew_ptr(cd)[o] = J;
+  cd.w.Lchi[o] = __dmul_rn((double)fx, c2);
+  cd.w.Leta[o] = (double)fe;
+}
+// Tangent output: dJ (normalised by 2 h nu^3/c^2) in float, depth-major, read
+// by the FP32 tangent rate integrals; o indexes the depth-major arrays.
+__device__ __forceinline__ void write_tan(const ColDesc& cd, size_t o, float dS, float fd) {
+  cd.w.dJ32T[o] = add(dS, fd);
+}
+
+// Stages |dz| and 1/|dz| of the block's column in shared memory.
+__device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float* s_idz) {
+  for (int k = threadIdx.x; k < T.nz - 1; k += blockDim.x) {
+    s_dz[k] = (float)T.dz[k];
+    s_idz[k] = (float)(1.0 / T.dz[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Variant 1: one thread per frequency, all angles of a hemisphere in registers.
+// ---------------------------------------------------------------------------
+// Base evaluations read chi and S per frequency row ([q][k], S in FP64), form
+// S^u - S^k in FP64, and leave depth-major float copies of chi, S and the
+// rounded differences for the tangent evaluations of the same Newton step;
+// those then read and write depth-major float arrays only (one 128-byte line
+// per warp and depth) and run entirely in FP32.
+template <int MU, bool TAN, bool UP>
+__device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const float* __restrict__ s_dz,
+                                             const float* __restrict__ s_idz) {
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nmu = T.nmu;
+  const size_t pitch = (size_t)col_pitch(nq);
+  const size_t pstride = (size_t)nz * pitch;
+  const size_t row = (size_t)q * nz;
+  const float* __restrict__ chi = reinterpret_cast<const float*>(cd.w.chi) + row;
+  const double* __restrict__ S64 = cd.w.S + row;
+  float* __restrict__ chiT = cd.w.chiT + q;
+  float* __restrict__ S32T = cd.w.S32T + q;
+  float* __restrict__ dSkT = cd.w.dSkT + q;
+  const float* __restrict__ dchiT = cd.w.dchiT + q;
+  const float* __restrict__ dS32T = cd.w.dS32T + q;
+  float* __restrict__ part = reinterpret_cast<float*>(cd.w.part) + q;
+  const double c2 = T.c2[q];
+
+  float inv2mu[MU], hw[MU], two_mu[MU];
+#pragma unroll
+  for (int m = 0; m < MU; ++m) {
+    const bool on = m < nmu;
+    inv2mu[m] = on ? (float)(0.5 / T.mu[m]) : 0.f;
+    hw[m] = on ? (float)(0.5 * T.wmu[m]) : 0.f;
+    two_mu[m] = on ? (float)(2.0 * T.mu[m]) : 0.f;
+  }
+
+  // boundary depth: I = 0 at the top, I = B at the bottom (Sect. 2.1)
+  const int k0 = UP ? nz - 1 : 0;
+  double Sp = S64[k0];
+  float cp = TAN ? chiT[k0 * pitch] : chi[k0];
+  float dSp = TAN ? dS32T[k0 * pitch] : 0.f;
+  float dcp = TAN ? dchiT[k0 * pitch] : 0.f;
+  float Su = __double2float_rn(Sp);
+  if (!TAN && !UP) {
+    chiT[0] = cp;
+    S32T[0] = Su;
+  }
+  const double Ib64 = UP ? T.Bn[row + nz - 1] / c2 : 0.0;
+  const float D0 = __double2float_rn(__dsub_rn(Ib64, Sp));
+  const float I0 = __double2float_rn(Ib64);
+  const float dD0 = -dSp;
+  float D[MU], I[MU], M[MU], dD[MU];
+  float xD[8], xa[8], xI[8], xx[8], xe[8], xd[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) xD[m] = xa[m] = xI[m] = xx[m] = xe[m] = xd[m] = 0.f;
+#pragma unroll
+  for (int m = 0; m < MU; ++m) {
+    D[m] = D0;
+    I[m] = I0;
+    M[m] = fabsf(D0);
+    dD[m] = dD0;
+    if (m < nmu) {
+      xD[m] = mul(hw[m], D0);
+      xa[m] = fabsf(xD[m]);
+      xI[m] = mul(hw[m], I0);
+      xd[m] = mul(hw[m], dD0);
+    }
+  }
+  auto emit = [&](int k, double Sk64, float dS) {
+    float* pp = part + (size_t)k * pitch;
+    if (TAN) {
+      const float td = tree8(xd);
+      if (!UP) pp[0] = td;
+      else write_tan(cd, (size_t)k * pitch + q, dS, add(td, pp[0]));
+      return;
+    }
+    const float tD = tree8(xD), ta = tree8(xa), tI = tree8(xI), tx = tree8(xx), te = tree8(xe);
+    if (!UP) {
+      pp[0] = tD;
+      pp[pstride] = ta;
+      pp[2 * pstride] = tI;
+      pp[3 * pstride] = tx;
+      pp[4 * pstride] = te;
+    } else {
+      write_base(cd, row + k, Sk64, c2, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
+                 add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]));
+    }
+  };
+  emit(k0, Sp, dSp);
+
+  // the next depth's inputs are loaded one step ahead
+  int kn = UP ? nz - 2 : 1;
+  float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f;
+  double S_n = 0.0;
+  auto load = [&](int kk) {
+    if (TAN) {
+      const size_t o = (size_t)kk * pitch;
+      c_n = chiT[o];
+      dc_n = dchiT[o];
+      dS_n = dS32T[o];
+      dSl_n = dSkT[(size_t)(UP ? kk : kk - 1) * pitch];
+    } else {
+      c_n = chi[kk];
+      S_n = S64[kk];
+    }
+  };
+  if (nz > 1) load(kn);
+  for (int s = 1; s < nz; ++s) {
+    const int k = kn;
+    const int kd = UP ? k : k - 1;   // layer between k and its upstream neighbour
+    const float c0 = c_n, dc0 = dc_n, dS0 = dS_n, dSl = dSl_n;
+    const double Sk64 = S_n;
+    if (s + 1 < nz) {
+      kn = UP ? k - 1 : k + 1;
+      load(kn);
+    }
+    StepIn in;
+    in.csum = add(c0, cp);
+    in.rs = __frcp_rn(in.csum);
+    in.dzk = s_dz[kd];
+    in.idzk = s_idz[kd];
+    if (TAN) {
+      in.dSin = UP ? dSl : -dSl;
+      in.S0 = in.Su = in.rc0 = 0.f;
+      in.dcs = add(dc0, dcp);
+      in.ddSin = sub(dSp, dS0);
+    } else {
+      in.dSin = __double2float_rn(__dsub_rn(Sp, Sk64));
+      in.S0 = __double2float_rn(Sk64);
+      if (!UP) {
+        // depth-major copies for the tangent evaluations
+        chiT[(size_t)k * pitch] = c0;
+        S32T[(size_t)k * pitch] = in.S0;
+        dSkT[(size_t)kd * pitch] = -in.dSin;   // S^{k} - S^{k-1}
+      }
+      in.Su = Su;
+      in.rc0 = __frcp_rn(c0);
+      in.dcs = in.ddSin = 0.f;
+    }
+#pragma unroll
+    for (int m = 0; m < MU; ++m) {
+      if (m < nmu) {
+        const RayOut r = ray_step<TAN>(in, inv2mu[m], two_mu[m], hw[m], D[m], I[m], M[m], dD[m]);
+        xD[m] = r.xD;
+        xa[m] = fabsf(r.xD);
+        xI[m] = r.xI;
+        xx[m] = r.xx;
+        xe[m] = r.xe;
+        xd[m] = r.xd;
+      }
+    }
+    emit(k, Sk64, dS0);
+    Sp = Sk64;
+    Su = in.S0;
+    cp = c0;
+    dSp = dS0;
+    dcp = dc0;
+  }
+  if (UP && !TAN) {
+#pragma unroll
+    for (int m = 0; m < MU; ++m)
+      if (m < nmu) cd.w.Iem[(size_t)q * nmu + m] = __dmul_rn((double)I[m], c2);
+  }
+}
+
+// One kernel per evaluation kind (its own register allocation): blocks of
+// columns in the other kind return at once.
+template <int MU, bool TAN>
+__global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict__ cols) {
+  extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode_f(cd);
+  if (mode == EV_SKIP || (mode == EV_TANGENT) != TAN) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq;
+  if ((int)(blockIdx.x * blockDim.x) >= nq) return;   // uniform over the block
+  float* s_dz = s_tab;
+  float* s_idz = s_tab + nz;
+  stage_dz(T, s_dz, s_idz);
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  sweep_thread<MU, TAN, false>(cd, q, s_dz, s_idz);
+  sweep_thread<MU, TAN, true>(cd, q, s_dz, s_idz);
+}
+
+// ---------------------------------------------------------------------------
+// Variant 2 (small launches): one warp per two frequencies; lane = (frequency
+// of the pair, hemisphere, angle), so both hemispheres advance together and
+// every lane runs one ray. A hemisphere's sums come from an xor butterfly
+// over its 8 angle lanes (the tree of tree8), land in shared memory per
+// depth, and the 16 lanes of a frequency then combine the two hemispheres
+// depth by depth (coalesced output rows).
+// ---------------------------------------------------------------------------
+constexpr int kWarpParts = kSweepParts;
+
+__host__ __device__ inline size_t warp_variant_smem(int nz, int warps) {
+  return sizeof(float) * (2 * (size_t)nz + (size_t)warps * 2 * 2 * kWarpParts * nz);
+}
+
+template <bool TAN>
+__device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __restrict__ wp,
+                                           const float* __restrict__ s_dz, const float* __restrict__ s_idz) {
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nmu = T.nmu;
+  const int lane = threadIdx.x & 31;
+  const int qi = lane >> 4, hemi = (lane >> 3) & 1, m = lane & 7;
+  const int leader = lane & ~7;
+  const bool up = hemi == 1;
+  const bool valid = q < nq;
+  const int qq = valid ? q : nq - 1;
+  const size_t row = (size_t)qq * nz;
+  const size_t pitch = (size_t)col_pitch(nq);
+  const float* __restrict__ chi = reinterpret_cast<const float*>(cd.w.chi) + row;
+  const double* __restrict__ S64 = cd.w.S + row;
+  float* __restrict__ chiT = cd.w.chiT + qq;
+  float* __restrict__ S32T = cd.w.S32T + qq;
+  float* __restrict__ dSkT = cd.w.dSkT + qq;
+  const float* __restrict__ dchiT = cd.w.dchiT + qq;
+  const float* __restrict__ dS32T = cd.w.dS32T + qq;
+  const double c2 = T.c2[qq];
+  const bool on = m < nmu;
+  const float inv2mu = on ? (float)(0.5 / T.mu[m]) : 0.f;
+  const float hw = on ? (float)(0.5 * T.wmu[m]) : 0.f;
+  const float two_mu = on ? (float)(2.0 * T.mu[m]) : 0.f;
+  float* hp = wp + (size_t)(qi * 2 + hemi) * kWarpParts * nz;   // this hemisphere's sums [v][k]
+  const bool writer = !TAN && !up && m == 0 && valid;           // depth-major copies
+
+  const int k0 = up ? nz - 1 : 0;
+  double Sp = S64[k0];
+  float cp = TAN ? chiT[k0 * pitch] : chi[k0];
+  float dSp = TAN ? dS32T[k0 * pitch] : 0.f;
+  float dcp = TAN ? dchiT[k0 * pitch] : 0.f;
+  float Su = __double2float_rn(Sp);
+  if (writer) {
+    chiT[0] = cp;
+    S32T[0] = Su;
+  }
+  const double Ib64 = up ? T.Bn[row + nz - 1] / c2 : 0.0;
+  const float D0 = __double2float_rn(__dsub_rn(Ib64, Sp));
+  const float I0 = __double2float_rn(Ib64);
+  const float dD0 = -dSp;
+  float D = D0, I = I0, M = fabsf(D0), dD = dD0;
+  RayOut r;
+  r.xD = on ? mul(hw, D0) : 0.f;
+  r.xI = on ? mul(hw, I0) : 0.f;
+  r.xx = r.xe = 0.f;
+  r.xd = on ? mul(hw, dD0) : 0.f;
+  auto store = [&](int k) {
+    if (TAN) {
+      const float td = butterfly8(r.xd);
+      if (m == 0) hp[k] = td;
+    } else {
+      const float tD = butterfly8(r.xD), ta = butterfly8(fabsf(r.xD)), tI = butterfly8(r.xI);
+      const float tx = butterfly8(r.xx), te = butterfly8(r.xe);
+      if (m == 0) {
+        hp[k] = tD;
+        hp[nz + k] = ta;
+        hp[2 * nz + k] = tI;
+        hp[3 * nz + k] = tx;
+        hp[4 * nz + k] = te;
+      }
+    }
+  };
+  store(k0);
+  for (int s = 1; s < nz; ++s) {
+    const int k = up ? nz - 1 - s : s;
+    const int kd = up ? k : k - 1;
+    StepIn in;
+    float c0, dc0 = 0.f, dS0 = 0.f;
+    if (TAN) {
+      const size_t o = (size_t)k * pitch;
+      c0 = chiT[o];
+      dc0 = dchiT[o];
+      dS0 = dS32T[o];
+      const float dSl = dSkT[(size_t)kd * pitch];
+      in.dSin = up ? dSl : -dSl;
+      in.S0 = in.Su = in.rc0 = 0.f;
+      in.dcs = add(dc0, dcp);
+      in.ddSin = sub(dSp, dS0);
+    } else {
+      c0 = chi[k];
+      // the FP64 difference is formed once per hemisphere (angle lane 0)
+      float dSin = 0.f, S0 = 0.f;
+      if (m == 0) {
+        const double Sk64 = S64[k];
+        dSin = __double2float_rn(__dsub_rn(Sp, Sk64));
+        S0 = __double2float_rn(Sk64);
+        Sp = Sk64;
+        if (writer) {
+          chiT[(size_t)k * pitch] = c0;
+          S32T[(size_t)k * pitch] = S0;
+          dSkT[(size_t)kd * pitch] = -dSin;   // S^{k} - S^{k-1}
+        }
+      }
+      in.dSin = __shfl_sync(0xffffffffu, dSin, leader);
+      in.S0 = __shfl_sync(0xffffffffu, S0, leader);
+      in.Su = Su;
+      in.rc0 = __frcp_rn(c0);
+      in.dcs = in.ddSin = 0.f;
+    }
+    in.csum = add(c0, cp);
+    in.rs = __frcp_rn(in.csum);
+    in.dzk = s_dz[kd];
+    in.idzk = s_idz[kd];
+    if (on) {
+      r = ray_step<TAN>(in, inv2mu, two_mu, hw, D, I, M, dD);
+    } else {
+      r.xD = r.xI = r.xx = r.xe = r.xd = 0.f;
+    }
+    store(k);
+    Su = in.S0;
+    cp = c0;
+    dcp = dc0;
+    dSp = dS0;
+  }
+  if (up && on && valid && !TAN) cd.w.Iem[(size_t)q * nmu + m] = __dmul_rn((double)I, c2);
+  __syncwarp();
+  if (!valid) return;
+  // combine the hemispheres of frequency q, depths strided over its 16 lanes
+  const float* dn = wp + (size_t)(qi * 2 + 0) * kWarpParts * nz;
+  const float* upp = wp + (size_t)(qi * 2 + 1) * kWarpParts * nz;
+  for (int k = lane & 15; k < nz; k += 16) {
+    if (TAN) {
+      const size_t o = (size_t)k * pitch + q;
+      write_tan(cd, o, cd.w.dS32T[o], add(upp[k], dn[k]));
+    } else {
+      write_base(cd, row + k, S64[k], c2, add(upp[k], dn[k]), add(upp[nz + k], dn[nz + k]),
+                 add(upp[2 * nz + k], dn[2 * nz + k]), add(upp[3 * nz + k], dn[3 * nz + k]),
+                 add(upp[4 * nz + k], dn[4 * nz + k]));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_formal_sweep_warp(const ColDesc* __restrict__ cols) {
+  extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|, per warp [2][2][parts][nz]
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = eval_mode_f(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq;
+  const int warps = blockDim.x >> 5;
+  if ((int)blockIdx.x * warps * 2 >= nq) return;   // uniform over the block
+  float* s_dz = s_tab;
+  float* s_idz = s_tab + nz;
+  stage_dz(T, s_dz, s_idz);
+  __syncthreads();
+  const int wid = threadIdx.x >> 5;
+  float* wp = s_tab + 2 * nz + (size_t)wid * 2 * 2 * kWarpParts * nz;
+  const int q = ((int)blockIdx.x * warps + wid) * 2 + ((threadIdx.x & 31) >> 4);
+  if (mode == EV_TANGENT) sweep_warp<true>(cd, q, wp, s_dz, s_idz);
+  else sweep_warp<false>(cd, q, wp, s_dz, s_idz);
+}
+
+// Angle counts with their own instantiation; a launch uses the smallest one
+// that covers every column of the batch (columns with fewer angles predicate
+// the rest off).
+static int sweep_mu_class(int nmu) {
+  if (nmu <= 2) return 2;
+  if (nmu <= 3) return 3;
+  if (nmu <= 4) return 4;
+  if (nmu <= 5) return 5;
+  return 8;
+}
+
+template <int MU>
+static void launch_mu(const Batch& b, cudaStream_t s, int threads) {
+  dim3 g((b.max_nq + threads - 1) / threads, b.ncols);
+  const size_t bytes = sizeof(float) * 2 * (size_t)b.max_nz;
+  k_formal_sweep<MU, true><<<g, threads, bytes, s>>>(b.d_cols);
+  k_formal_sweep<MU, false><<<g, threads, bytes, s>>>(b.d_cols);
+}
+
+// variant 1: ``size`` threads per block; variant 2: ``size`` warps per block
+static int launch_sweep_cfg(const Batch& b, cudaStream_t s, int variant, int size) {
+  if (variant == 2) {
+    const int fpb = 2 * size;   // frequencies per block
+    dim3 g((b.max_nq + fpb - 1) / fpb, b.ncols);
+    k_formal_sweep_warp<<<g, 32 * size, warp_variant_smem(b.max_nz, size), s>>>(b.d_cols);
+  } else {
+    switch (sweep_mu_class(b.max_nmu)) {
+      case 2: launch_mu<2>(b, s, size); break;
+      case 3: launch_mu<3>(b, s, size); break;
+      case 4: launch_mu<4>(b, s, size); break;
+      case 5: launch_mu<5>(b, s, size); break;
+      default: launch_mu<8>(b, s, size); break;
+    }
+  }
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+static bool warp_variant_fits(int nz, int warps) {
+  return warp_variant_smem(nz, warps) <= (size_t)227 * 1024;
+}
+
+int sweep_prepare(Batch* b) {
+  const size_t bytes = warp_variant_smem(b->max_nz, 8);
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::min(bytes, (size_t)227 * 1024)));
+  if (b->sweep_variant == 0) {
+    b->sweep_variant = 1;
+    b->formal_threads = 128;
+  }
+  return JFNK_OK;
+}
+
+int launch_formal_sweep(const Batch& b, cudaStream_t s) {
+  return launch_sweep_cfg(b, s, b.sweep_variant == 2 ? 2 : 1, b.formal_threads > 0 ? b.formal_threads : 128);
+}
+
+int sweep_warp_size(int nz) {
+  for (int w : {4, 2, 1})
+    if (warp_variant_fits(nz, w)) return w;
+  return 0;
+}
+
+// Autotuner of the sweep kernels, timed in tangent mode on the batch's own
+// columns: variant 1 with 32..256 threads per block, variant 2 with 1..8 warps
+// per block (where its shared memory fits). Both variants give bit-identical
+// results, so the choice changes the speed only.
+int sweep_autotune(Batch* b, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  JFNK_CUDA(cudaEventCreate(&e0));
+  JFNK_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bv = 1, bs = 128;
+  const std::pair<int, int> cands[] = {{1, 32}, {1, 64}, {1, 128}, {1, 256}, {2, 1}, {2, 2}, {2, 4}, {2, 8}};
+  for (const auto& c : cands) {
+    if (c.first == 2 && !warp_variant_fits(b->max_nz, c.second)) continue;
+    int rc = launch_sweep_cfg(*b, s, c.first, c.second);   // warm-up
+    if (rc) return rc;
+    JFNK_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r)
+      if ((rc = launch_sweep_cfg(*b, s, c.first, c.second))) return rc;
+    JFNK_CUDA(cudaEventRecord(e1, s));
+    JFNK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    JFNK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; bv = c.first; bs = c.second; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->sweep_variant = bv;
+  b->formal_threads = bs;
+  return JFNK_OK;
+}
+
+}  // namespace jfnk

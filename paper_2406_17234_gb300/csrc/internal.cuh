@@ -80,6 +80,10 @@ namespace jfnk {
 int build_atom(const jfnk_atom_desc* d, AtomData* A);
 int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d, AtmosData* M);
 
+// Formal-solution kernels: per-ray buffers + ray-sum kernel (any size),
+// in-block fused kernel (FP64), per-frequency sweep kernel (mixed precision).
+enum FormalKind { FORMAL_UNFUSED = 0, FORMAL_FUSED = 1, FORMAL_SWEEP = 2 };
+
 // A batch of columns with their work buffers, resident on the device.
 struct Batch {
   int ncols = 0;
@@ -95,8 +99,11 @@ struct Batch {
   cudaGraphExec_t graph = nullptr;    // captured tick sequence
   int graph_ticks = 0;
   bool graph_profiled = false;
-  int formal_qb = 0;                  // frequencies per block of the fused formal kernel (0: unfused)
-  int formal_threads = 0;             // threads per block of the fused formal kernel
+  int formal_kind = 0;                // FORMAL_UNFUSED, FORMAL_FUSED or FORMAL_SWEEP
+  int formal_qb = 0;                  // frequencies per block of the fused formal kernel
+  int formal_threads = 0;             // fused: threads per block; sweep: threads (variant 1) or warps (2)
+  int sweep_variant = 0;              // sweep kernel: 1 thread per frequency, 2 warp per frequency pair
+  int tuned_variant = 0, tuned_size = 0;   // autotuner's choice (a forced variant may replace it for a solve)
   bool tuned = false;                 // autotuner has run on this batch
   int graph_kernels = 0;              // kernel nodes in the captured tick graph
   long replays = 0;                   // graph replays of the last solve
@@ -124,6 +131,13 @@ int fused_default_qb(int max_nz, int max_nmu, bool mixed);
 int fused_prepare(Batch* b);
 int launch_formal_fused(const Batch& b, cudaStream_t s);
 int fused_autotune(Batch* b, cudaStream_t s);
+// Per-frequency sweep kernel of the mixed mode (formal_sweep.cu).
+size_t sweep_scratch_bytes(int nq, int nz);
+int sweep_prepare(Batch* b);
+int launch_formal_sweep(const Batch& b, cudaStream_t s);
+// Warps per block of the warp variant whose shared memory fits depth nz (0: none).
+int sweep_warp_size(int nz);
+int sweep_autotune(Batch* b, cudaStream_t s);
 // Sets every column's forced evaluation mode (explicit API calls) or -1.
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.

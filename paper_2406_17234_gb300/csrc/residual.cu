@@ -44,15 +44,35 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
   const int mode = eval_mode(cd);
   if (mode == EV_SKIP) return;
   const ColTables& T = cd.t;
-  const int nz = T.nz, nl = T.nl;
+  const int nz = T.nz, nl = T.nl, nq = T.nq;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T.nq * nz) return;
-  const int q = i / nz, k = i - q * nz;
-  const double c2 = T.c2[q];
+  if (i >= nq * nz) return;
   if (mode == EV_TANGENT) {
     // chi and S at the base point are those of the Newton step's base
     // evaluation (n and J^dagger are unchanged): only their tangents are new,
     // in the working precision.
+    if (cd.mixed) {
+      // mixed mode: threads run over (k, q) with q fastest, on float tables,
+      // the float direction and the depth-major base-point arrays
+      const int k = i / nq, q = i - k * nq;
+      const float* v = cd.w.v32 + k * nl;
+      const float* V32 = T.V32T + (size_t)k * T.nwin;
+      const float* G32 = T.G32T + (size_t)k * T.nwin;
+      float dchi = 0.f, deta = 0.f;
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int t = T.q_t[s];
+        const int p = T.t_base[t] + q - T.t_q0[t];
+        const float V = V32[p], g = G32[p];
+        const float vlo = v[T.t_lo[t]], vup = v[T.t_up[t]];
+        dchi += V * (vlo - g * vup);
+        deta += g * V * vup;               // normalised by 2 h nu^3 / c^2
+      }
+      const size_t o = (size_t)k * col_pitch(nq) + q;
+      cd.w.dchiT[o] = dchi;
+      cd.w.dS32T[o] = (deta - cd.w.S32T[o] * dchi) / cd.w.chiT[o];
+      return;
+    }
+    const int q = i / nz, k = i - q * nz;
     const double* v = tangent_dir(cd) + k * nl;
     real dchi = 0, deta = 0;
     for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
@@ -69,6 +89,8 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
     cd.w.dS[i] = (double)((deta - S * dchi) / chi);
     return;
   }
+  const int q = i / nz, k = i - q * nz;
+  const double c2 = T.c2[q];
   const double* n = cd.w.n + k * nl;
   double chi = T.chi_c[i] + T.chi_sca[k];
   double eta = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
@@ -82,6 +104,17 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
   }
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
   cd.w.S[i] = eta / (chi * c2);
+}
+
+// Mixed mode: float copy of the tangent direction of every column in a
+// tangent evaluation (the opacity tangent then runs entirely in FP32).
+__global__ void k_dir32(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
+  const int N = cd.t.nz * cd.t.nl;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  cd.w.v32[i] = (float)tangent_dir(cd)[i];
 }
 
 // Differences of the source function (and of its tangent) between adjacent
@@ -339,6 +372,19 @@ __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __rest
     for (int j = 0; j < nacc; ++j) acc[j] = 0.0;
     const double n_lo = n[lo], n_up = n[upl];
     const double* Jd = rh ? jdag_ptr(cd) : nullptr;
+    if (tan && cd.mixed) {
+      // mixed mode: the tangent rate integrals in FP32 (float tables and dJ)
+      float a0 = 0.f, a1 = 0.f;
+      for (int q = qa + wid; q <= qb; q += kRateWarps) {
+        const size_t p = (size_t)(base + q - q0);
+        const float WV = T.W32[p] * T.V32[p * nz + k];
+        const float dJ = cd.w.dJ32T[(size_t)k * col_pitch(T.nq) + q];
+        a0 = fmaf(WV, dJ, a0);
+        a1 = fmaf(WV * T.G32[p * nz + k], dJ, a1);
+      }
+      acc[0] = a0;
+      acc[1] = a1;
+    } else
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
       const size_t p = (size_t)(base + q - q0);
       const double W = T.t_w[p] * T.rw[q];
@@ -595,7 +641,15 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
   dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
   dim3 g_asm((b.max_nz + kAsmWarps - 1) / kAsmWarps, nc);
-  if (b.formal_qb > 0) {
+  if (b.formal_kind == FORMAL_SWEEP) {
+    // (float tangent direction,) opacity, then the per-frequency sweeps
+    k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
+    k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+    int rc = launch_formal_sweep(b, s);
+    if (rc) return rc;
+    if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+  } else if (b.formal_kind == FORMAL_FUSED) {
     // opacity, then the fused formal solution with in-block ray sums
     if (b.mixed) k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
     else k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
@@ -603,13 +657,6 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     int rc = launch_formal_fused(b, s);
     if (rc) return rc;
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
-  } else if (b.mixed) {
-    k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
-    k_source_diff<float><<<g_qk, tb, 0, s>>>(b.d_cols);
-    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-    k_formal<float><<<g_ray, 64, 0, s>>>(b.d_cols);
-    if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
-    k_ray_sum<float><<<g_qk, tb, 0, s>>>(b.d_cols);
   } else {
     k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
     k_source_diff<double><<<g_qk, tb, 0, s>>>(b.d_cols);

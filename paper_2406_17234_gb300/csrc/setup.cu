@@ -299,6 +299,19 @@ __global__ void k_window_tables(int nt, const TransDev* tr, const int* t_q0, con
   }
 }
 
+// Float copies of the (normalised) window tables for mixed-mode tangents.
+__global__ void k_float_copy(int nwin, int nz, const double* V, const double* G, float* V32, float* G32,
+                             float* V32T, float* G32T) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nwin * nz) return;
+  const size_t p = i / nz, k = i % nz;
+  const float v = (float)V[i], g = (float)G[i];
+  V32[i] = v;
+  G32[i] = g;
+  V32T[k * nwin + p] = v;
+  G32T[k * nwin + p] = g;
+}
+
 // Renormalise each line profile so that sum_q omega_t(q) phi(q, k) = 1.
 __global__ void k_normalise_lines(int nt, const TransDev* tr, const int* t_q0, const int* t_q1,
                                   const int* t_base, const double* t_w, int nz, double* V) {
@@ -403,6 +416,9 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   size_t o_T = ar.take<double>(nz), o_ne = ar.take<double>(nz), o_rho = ar.take<double>(nz),
          o_vt = ar.take<double>(nz);
   size_t o_tr = ar.take<TransDev>(nt), o_cd = ar.take<CollDev>(nt);
+  size_t o_V32 = ar.take<float>((size_t)nwin * nz), o_G32 = ar.take<float>((size_t)nwin * nz),
+         o_W32 = ar.take<float>(nwin);
+  size_t o_V32T = ar.take<float>((size_t)nwin * nz), o_G32T = ar.take<float>((size_t)nwin * nz);
   int rc = ar.allocate();
   if (rc) return rc;
   // host-side staging
@@ -414,8 +430,13 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   for (int k = 0; k + 1 < nz; ++k) dzv[k] = std::fabs(d->z[k] - d->z[k + 1]);
   gauss_legendre_01(nmu, mu.data(), wmu.data());
   std::vector<int> winT(nwin);
+  std::vector<float> w32(nwin);
   for (int t = 0; t < nt; ++t)
-    for (int p = 0; p <= A.t_q1[t] - A.t_q0[t]; ++p) winT[A.t_base[t] + p] = t;
+    for (int p = 0; p <= A.t_q1[t] - A.t_q0[t]; ++p) {
+      const int q = A.t_q0[t] + p;
+      winT[A.t_base[t] + p] = t;
+      w32[A.t_base[t] + p] = (float)(A.t_w[A.t_base[t] + p] * rw[q] * c2[q]);
+    }
   std::vector<TransDev> tr(nt);
   std::vector<CollDev> cd(nt);
   for (int t = 0; t < nt; ++t) {
@@ -452,6 +473,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(up(o_tbase, A.t_base.data(), nt * 4));
   JFNK_CUDA(up(o_winT, winT.data(), nwin * 4));
   JFNK_CUDA(up(o_tw, A.t_w.data(), nwin * 8));
+  JFNK_CUDA(up(o_W32, w32.data(), nwin * 4));
   JFNK_CUDA(up(o_dz, dzv.data(), (nz - 1) * 8));
   JFNK_CUDA(up(o_mu, mu.data(), nmu * 8));
   JFNK_CUDA(up(o_wmu, wmu.data(), nmu * 8));
@@ -482,6 +504,9 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
       ar.ptr<double>(o_tw), nz, ar.ptr<double>(o_V));
   k_collisions<<<(nz + tb - 1) / tb, tb, 0, s>>>(nt, ar.ptr<CollDev>(o_cd), at, nz, T, ne,
                                                   ar.ptr<double>(o_C));
+  k_float_copy<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
+      nwin, nz, ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<float>(o_V32), ar.ptr<float>(o_G32),
+      ar.ptr<float>(o_V32T), ar.ptr<float>(o_G32T));
   JFNK_CUDA(cudaGetLastError());
   JFNK_CUDA(cudaStreamSynchronize(s));
   ColTables& tb_ = M->tables;
@@ -491,6 +516,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   tb_.t_lo = ar.ptr<int>(o_tlo); tb_.t_up = ar.ptr<int>(o_tup); tb_.t_q0 = ar.ptr<int>(o_tq0);
   tb_.t_q1 = ar.ptr<int>(o_tq1); tb_.t_base = ar.ptr<int>(o_tbase); tb_.t_w = ar.ptr<double>(o_tw);
   tb_.V = ar.ptr<double>(o_V); tb_.G = ar.ptr<double>(o_G); tb_.dz = ar.ptr<double>(o_dz);
+  tb_.V32 = ar.ptr<float>(o_V32); tb_.G32 = ar.ptr<float>(o_G32); tb_.W32 = ar.ptr<float>(o_W32);
+  tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);
   tb_.mu = ar.ptr<double>(o_mu); tb_.wmu = ar.ptr<double>(o_wmu);
   tb_.chi_c = ar.ptr<double>(o_chic); tb_.eta_c = ar.ptr<double>(o_etac);
   tb_.chi_sca = ar.ptr<double>(o_sca); tb_.Bn = ar.ptr<double>(o_B); tb_.C = ar.ptr<double>(o_C);

@@ -41,10 +41,12 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
   int mnz = 0, mnmu = 0;
   for (auto* c : cols) { mnz = std::max(mnz, c->nz); mnmu = std::max(mnmu, c->nmu); }
-  b->formal_qb = fused_default_qb(mnz, mnmu, mixed != 0);
-  const bool per_ray = (b->formal_qb == 0);   // unfused kernels need per-ray buffers
+  b->formal_qb = mixed ? 0 : fused_default_qb(mnz, mnmu, false);
+  b->formal_kind = mixed ? FORMAL_SWEEP : (b->formal_qb > 0 ? FORMAL_FUSED : FORMAL_UNFUSED);
+  const bool per_ray = (b->formal_kind == FORMAL_UNFUSED);   // unfused kernels need per-ray buffers
   struct Offs {
-    size_t n, v, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH, LX, LE, J, dJ, Lchi, Leta, Rup, Rdn,
+    size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH, LX, LE, part, J, dJ,
+        Lchi, Leta, Rup, Rdn,
         dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x, w, nprev;
   };
   std::vector<Offs> off(nc);
@@ -61,13 +63,19 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     o.Jdag = ar.take<double>(nq * nz); o.Jnew = ar.take<double>(nq * nz);
     o.istar = ar.take<int>(nz);
     o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<double>(nq * nz);
+    const bool sweep = (b->formal_kind == FORMAL_SWEEP);
     o.dSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
-    o.dchi = ar.take<char>(rs * nq * nz); o.dS = ar.take<double>(nq * nz);
+    o.dchi = ar.take<char>(sweep ? 0 : rs * nq * nz); o.dS = ar.take<double>(sweep ? 0 : nq * nz);
+    const size_t TQ = sweep ? (size_t)nz * col_pitch((int)nq) : 0;
+    o.v32 = ar.take<float>(sweep ? N : 0);
+    o.chiT = ar.take<float>(TQ); o.S32T = ar.take<float>(TQ); o.dSkT = ar.take<float>(TQ);
+    o.dchiT = ar.take<float>(TQ); o.dS32T = ar.take<float>(TQ); o.dJ32T = ar.take<float>(TQ);
     o.ddSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
     const size_t pr = per_ray ? rs * 2 * nmu * nq * nz : 0;
     o.H = ar.take<char>(pr); o.dH = ar.take<char>(pr); o.HI = ar.take<char>(pr);
     o.LX = ar.take<char>(pr); o.LE = ar.take<char>(pr);
-    o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(nq * nz);
+    o.part = ar.take<char>(b->formal_kind == FORMAL_SWEEP ? sweep_scratch_bytes((int)nq, (int)nz) : 0);
+    o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(sweep ? 0 : nq * nz);
     o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
     o.Rup = ar.take<double>(nt * nz); o.Rdn = ar.take<double>(nt * nz);
     o.dRup = ar.take<double>(nt * nz); o.dRdn = ar.take<double>(nt * nz);
@@ -105,9 +113,20 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     w.istar = ar.ptr<int>(o.istar);
     w.chi = ar.ptr<void>(o.chi); w.S = ar.ptr<double>(o.S); w.dSk = ar.ptr<void>(o.dSk);
     w.dchi = ar.ptr<void>(o.dchi); w.dS = ar.ptr<double>(o.dS); w.ddSk = ar.ptr<void>(o.ddSk);
+    const bool sweep = (b->formal_kind == FORMAL_SWEEP);
+    w.v32 = sweep ? ar.ptr<float>(o.v32) : nullptr;
+    w.chiT = sweep ? ar.ptr<float>(o.chiT) : nullptr;
+    w.S32T = sweep ? ar.ptr<float>(o.S32T) : nullptr;
+    w.dSkT = sweep ? ar.ptr<float>(o.dSkT) : nullptr;
+    w.dchiT = sweep ? ar.ptr<float>(o.dchiT) : nullptr;
+    w.dS32T = sweep ? ar.ptr<float>(o.dS32T) : nullptr;
+    w.dJ32T = sweep ? ar.ptr<float>(o.dJ32T) : nullptr;
+    if (sweep) w.dchi = nullptr;
     w.H = ar.ptr<void>(o.H); w.dH = ar.ptr<void>(o.dH); w.HI = ar.ptr<void>(o.HI);
     w.LX = ar.ptr<void>(o.LX); w.LE = ar.ptr<void>(o.LE);
+    w.part = ar.ptr<void>(o.part);
     w.J = ar.ptr<double>(o.J); w.dJ = ar.ptr<double>(o.dJ);
+    if (sweep) { w.dS = nullptr; w.dJ = nullptr; }   // the mixed tangent path is FP32 throughout
     w.Lchi = ar.ptr<double>(o.Lchi); w.Leta = ar.ptr<double>(o.Leta);
     w.zeta = nullptr;
     w.Rup = ar.ptr<double>(o.Rup); w.Rdn = ar.ptr<double>(o.Rdn);
@@ -122,6 +141,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   }
   JFNK_CUDA(cudaMemcpy(b->d_cols, b->h_cols.data(), nc * sizeof(ColDesc), cudaMemcpyHostToDevice));
   JFNK_CUDA(cudaMemset(b->d_state, 0, nc * sizeof(SolverState)));
+  if (b->formal_kind == FORMAL_SWEEP) return sweep_prepare(b);
   return fused_prepare(b);
 }
 

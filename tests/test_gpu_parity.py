@@ -217,6 +217,27 @@ def test_limited_hybrid_solve(ctx, precision):
     np.testing.assert_allclose(n, ref.n, rtol=1e-5 if precision == 0 else 1e-3)
 
 
+@pytest.mark.parametrize("n_mu", [3, 5])
+@pytest.mark.parametrize("start", ["lte", "hybrid"])
+def test_sweep_variants_are_bit_identical(ctx, n_mu, start):
+    """The two mixed-mode formal kernels (thread per frequency; warp per
+    frequency pair) give bit-identical solves, so the autotuner's choice
+    changes the speed only."""
+    wl = W.config4(n_columns=3, nz_min=60, nz_max=90, nu_scale=0.1)
+    atom = B.Atom(ctx, wl.atom)
+    atms = [B.Atmosphere(ctx, atom, c, n_mu=n_mu) for c in wl.columns]
+    init = dict(rh92_warmup=10, rh92_switch=0.1) if start == "hybrid" else {}
+    outs = []
+    for v in (B.JFNK_FORMAL_SWEEP_THREAD, B.JFNK_FORMAL_SWEEP_WARP):
+        opts = B.default_options(precision=B.JFNK_MIXED, formal_variant=v, **init)
+        ns, st = B.batch_solve(ctx, atms, opts, raise_on_fail=False)
+        assert all(s["formal_kernel"] == v for s in st)
+        outs.append((ns, st))
+    for na, nb, sa, sb in zip(outs[0][0], outs[1][0], outs[0][1], outs[1][1]):
+        assert sa["status"] == sb["status"] and sa["F_calls"] == sb["F_calls"]
+        np.testing.assert_array_equal(na, nb)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_equals_single(ctx, precision):
     """Each column's result in a batch is bit-identical to its result alone."""
