@@ -187,6 +187,7 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   const int nfull = b->ncols;
   ColDesc* dfull = b->d_cols;
   const int fz = b->max_nz, fq = b->max_nq, ft = b->max_nt, fN = b->max_N, fm = b->max_nmu;
+  const int fvariant = b->sweep_variant, fthreads = b->formal_threads;
   std::vector<int> view(nfull);
   for (int c = 0; c < nfull; ++c) view[c] = c;
   cudaGraphExec_t cur = b->graph;
@@ -223,6 +224,13 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
       b->d_cols = b->d_view;
       b->ncols = (int)running.size();
       b->max_nz = mz; b->max_nq = mq; b->max_nt = mt; b->max_N = mN; b->max_nmu = mm;
+      // a few columns: one thread per frequency leaves most SMs idle, and the
+      // warp-per-frequency-pair sweep (same results) finishes each tick sooner
+      if (b->formal_kind == FORMAL_SWEEP && b->sweep_variant == 1 &&
+          (long)b->ncols * b->max_nq < 256L * b->n_sm && sweep_warp_size(b->max_nz) > 0) {
+        b->sweep_variant = 2;
+        b->formal_threads = sweep_warp_size(b->max_nz);
+      }
       if (b->graph_view) { cudaGraphExecDestroy(b->graph_view); b->graph_view = nullptr; }
       if ((rc = capture_ticks(b, s, profile, &b->graph_view))) break;
       cur = b->graph_view;
@@ -233,6 +241,8 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   b->d_cols = dfull;
   b->ncols = nfull;
   b->max_nz = fz; b->max_nq = fq; b->max_nt = ft; b->max_N = fN; b->max_nmu = fm;
+  b->sweep_variant = fvariant;
+  b->formal_threads = fthreads;
   return rc;
 }
 

@@ -48,6 +48,7 @@ enum Phase : int {
 // Immutable tables of one column (device pointers), built at atmosphere creation.
 struct ColTables {
   int nz, nq, nl, nt, nmu, nwin;  // nwin = sum over transitions of window points
+  int max_overlap;                // most transitions active at one frequency
   const double* nu;       // [nq]
   const double* c2;       // [nq] 2 h nu^3 / c^2
   const double* rw;       // [nq] 4 pi / (h nu)
@@ -66,6 +67,10 @@ struct ColTables {
   const float* V32T;      // [nz][nwin] the same, depth-major
   const float* G32T;      // [nz][nwin]
   const float* W32;       // [nwin] omega_t(nu_q) 4 pi/(h nu_q) 2 h nu_q^3/c^2 in float
+  const float* Wr32;      // [nwin] omega_t(nu_q) 4 pi/(h nu_q) in float
+  const float* c2f;       // [nq] 2 h nu^3/c^2 in float
+  const int* qmeta;       // [kQMetaT][nq] transitions active at nu_q, packed as
+                          // window point << 8 | lo << 4 | up; -1 past the last
   const double* dz;       // [nz-1] |z_k - z_{k+1}|
   const double* mu;       // [nmu]
   const double* wmu;      // [nmu]
@@ -157,6 +162,9 @@ struct ColWork {
   double* nprev;    // [N]
   SolverState* st;
 };
+
+// Transitions per frequency held in ColTables::qmeta (more go through q_off/q_t).
+constexpr int kQMetaT = 8;
 
 // Row pitch of the depth-major float arrays: frequencies rounded up to 32.
 __host__ __device__ inline int col_pitch(int nq) { return (nq + 31) & ~31; }

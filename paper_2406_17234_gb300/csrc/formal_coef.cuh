@@ -60,4 +60,37 @@ __device__ __forceinline__ void pl_coef_f(float x, float r, float& e, float& w, 
   }
 }
 
+// Every operation of a ray step is an explicitly rounded intrinsic: the
+// compiler may not contract or reorder any of them, so the two kernel
+// variants below (which see the same values in different registers, lanes
+// and orders of issue) produce bit-identical results.
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fma3(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Tangent of the opacity and source function at (nu, k) in FP32 (Eqs. chi,
+// eta differentiated; n and J^dagger fixed): per active transition
+//   dchi += V (dn_lo - g dn_up),  deta += g V dn_up   (eta normalised by 2 h nu^3/c^2)
+// and dS = (deta - S dchi)/chi. Shared by the opacity kernel and the sweeps
+// that form it on the fly, so that both give the same bits.
+struct TanAcc {
+  float dchi = 0.f, deta = 0.f;
+};
+__device__ __forceinline__ void tan_acc(TanAcc& t, float V, float g, float vlo, float vup) {
+  t.dchi = fma3(V, sub(vlo, mul(g, vup)), t.dchi);
+  t.deta = fma3(mul(g, V), vup, t.deta);
+}
+// Hardware reciprocal (1 ulp): a single instruction without a slow-path
+// branch, so that loops around it stay one basic block the compiler can
+// software-pipeline. Its arguments (opacity sums) are positive normal numbers.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float tan_dS(const TanAcc& t, float S, float chi) {
+  return mul(sub(t.deta, mul(S, t.dchi)), rcp_approx(chi));
+}
+
 }  // namespace jfnk

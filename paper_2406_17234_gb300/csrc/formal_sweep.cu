@@ -33,15 +33,6 @@ size_t sweep_scratch_bytes(int nq, int nz) {
   return sizeof(float) * (size_t)kSweepParts * nz * sweep_pitch(nq);
 }
 
-// Every operation of a ray step is an explicitly rounded intrinsic: the
-// compiler may not contract or reorder any of them, so the two kernel
-// variants below (which see the same values in different registers, lanes
-// and orders of issue) produce bit-identical results.
-__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float fma3(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-
 // App. A.1 coefficients of a step of optical depth x (r = 1/x): e = exp(-x),
 // w = (1 - e)/x, a = 1 - w, bq = (w - e)/x; below x = 0.1 each comes from its
 // Taylor series (truncated after x^5, below 3e-10 relative).
@@ -166,13 +157,13 @@ __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float*
 // Base evaluations read chi and S per frequency row ([q][k], S in FP64), form
 // S^u - S^k in FP64, and leave depth-major float copies of chi, S and the
 // rounded differences for the tangent evaluations of the same Newton step;
-// those then read and write depth-major float arrays only (one 128-byte line
-// per warp and depth) and run entirely in FP32.
+// those then read depth-major float arrays only (one 128-byte line per warp
+// and depth) and run entirely in FP32.
 template <int MU, bool TAN, bool UP>
 __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const float* __restrict__ s_dz,
                                              const float* __restrict__ s_idz) {
   const ColTables& T = cd.t;
-  const int nz = T.nz, nq = T.nq, nmu = T.nmu;
+  const int nz = T.nz, nq = T.nq, nmu = T.nmu, nl = T.nl;
   const size_t pitch = (size_t)col_pitch(nq);
   const size_t pstride = (size_t)nz * pitch;
   const size_t row = (size_t)q * nz;
@@ -194,13 +185,19 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     hw[m] = on ? (float)(0.5 * T.wmu[m]) : 0.f;
     two_mu[m] = on ? (float)(2.0 * T.mu[m]) : 0.f;
   }
+  // tangent opacity of depth kk, left by the opacity kernel
+  auto tan_in = [&](int kk, float& dc, float& dS) {
+    const size_t o = (size_t)kk * pitch;
+    dc = dchiT[o];
+    dS = dS32T[o];
+  };
 
   // boundary depth: I = 0 at the top, I = B at the bottom (Sect. 2.1)
   const int k0 = UP ? nz - 1 : 0;
   double Sp = S64[k0];
   float cp = TAN ? chiT[k0 * pitch] : chi[k0];
-  float dSp = TAN ? dS32T[k0 * pitch] : 0.f;
-  float dcp = TAN ? dchiT[k0 * pitch] : 0.f;
+  float dSp = 0.f, dcp = 0.f;
+  if (TAN) tan_in(k0, dcp, dSp);
   float Su = __double2float_rn(Sp);
   if (!TAN && !UP) {
     chiT[0] = cp;
@@ -249,17 +246,15 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   };
   emit(k0, Sp, dSp);
 
-  // the next depth's inputs are loaded one step ahead
+  // the next depth's inputs are prepared one step ahead
   int kn = UP ? nz - 2 : 1;
   float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f;
   double S_n = 0.0;
   auto load = [&](int kk) {
     if (TAN) {
-      const size_t o = (size_t)kk * pitch;
-      c_n = chiT[o];
-      dc_n = dchiT[o];
-      dS_n = dS32T[o];
+      c_n = chiT[(size_t)kk * pitch];
       dSl_n = dSkT[(size_t)(UP ? kk : kk - 1) * pitch];
+      tan_in(kk, dc_n, dS_n);
     } else {
       c_n = chi[kk];
       S_n = S64[kk];
@@ -277,7 +272,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     }
     StepIn in;
     in.csum = add(c0, cp);
-    in.rs = __frcp_rn(in.csum);
+    in.rs = rcp_approx(in.csum);
     in.dzk = s_dz[kd];
     in.idzk = s_idz[kd];
     if (TAN) {
@@ -295,7 +290,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
         dSkT[(size_t)kd * pitch] = -in.dSin;   // S^{k} - S^{k-1}
       }
       in.Su = Su;
-      in.rc0 = __frcp_rn(c0);
+      in.rc0 = rcp_approx(c0);
       in.dcs = in.ddSin = 0.f;
     }
 #pragma unroll
@@ -386,12 +381,17 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   const float two_mu = on ? (float)(2.0 * T.mu[m]) : 0.f;
   float* hp = wp + (size_t)(qi * 2 + hemi) * kWarpParts * nz;   // this hemisphere's sums [v][k]
   const bool writer = !TAN && !up && m == 0 && valid;           // depth-major copies
+  auto tan_in = [&](int kk, float& dc, float& dS) {
+    const size_t o = (size_t)kk * pitch;
+    dc = dchiT[o];
+    dS = dS32T[o];
+  };
 
   const int k0 = up ? nz - 1 : 0;
   double Sp = S64[k0];
   float cp = TAN ? chiT[k0 * pitch] : chi[k0];
-  float dSp = TAN ? dS32T[k0 * pitch] : 0.f;
-  float dcp = TAN ? dchiT[k0 * pitch] : 0.f;
+  float dSp = 0.f, dcp = 0.f;
+  if (TAN) tan_in(k0, dcp, dSp);
   float Su = __double2float_rn(Sp);
   if (writer) {
     chiT[0] = cp;
@@ -430,10 +430,8 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
     StepIn in;
     float c0, dc0 = 0.f, dS0 = 0.f;
     if (TAN) {
-      const size_t o = (size_t)k * pitch;
-      c0 = chiT[o];
-      dc0 = dchiT[o];
-      dS0 = dS32T[o];
+      c0 = chiT[(size_t)k * pitch];
+      tan_in(k, dc0, dS0);
       const float dSl = dSkT[(size_t)kd * pitch];
       in.dSin = up ? dSl : -dSl;
       in.S0 = in.Su = in.rc0 = 0.f;
@@ -457,11 +455,11 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
       in.dSin = __shfl_sync(0xffffffffu, dSin, leader);
       in.S0 = __shfl_sync(0xffffffffu, S0, leader);
       in.Su = Su;
-      in.rc0 = __frcp_rn(c0);
+      in.rc0 = rcp_approx(c0);
       in.dcs = in.ddSin = 0.f;
     }
     in.csum = add(c0, cp);
-    in.rs = __frcp_rn(in.csum);
+    in.rs = rcp_approx(in.csum);
     in.dzk = s_dz[kd];
     in.idzk = s_idz[kd];
     if (on) {
@@ -587,13 +585,13 @@ int sweep_autotune(Batch* b, cudaStream_t s) {
   float best = 1e30f;
   int bv = 1, bs = 128;
   const std::pair<int, int> cands[] = {{1, 32}, {1, 64}, {1, 128}, {1, 256}, {2, 1}, {2, 2}, {2, 4}, {2, 8}};
+  int rc = JFNK_OK;
   for (const auto& c : cands) {
     if (c.first == 2 && !warp_variant_fits(b->max_nz, c.second)) continue;
-    int rc = launch_sweep_cfg(*b, s, c.first, c.second);   // warm-up
-    if (rc) return rc;
+    if ((rc = launch_sweep_cfg(*b, s, c.first, c.second))) break;   // warm-up
     JFNK_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r)
-      if ((rc = launch_sweep_cfg(*b, s, c.first, c.second))) return rc;
+    for (int r = 0; r < 3 && !rc; ++r) rc = launch_sweep_cfg(*b, s, c.first, c.second);
+    if (rc) break;
     JFNK_CUDA(cudaEventRecord(e1, s));
     JFNK_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -602,6 +600,7 @@ int sweep_autotune(Batch* b, cudaStream_t s) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (rc) return rc;
   b->sweep_variant = bv;
   b->formal_threads = bs;
   return JFNK_OK;

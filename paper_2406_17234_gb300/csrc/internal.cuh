@@ -104,6 +104,8 @@ struct Batch {
   int formal_threads = 0;             // fused: threads per block; sweep: threads (variant 1) or warps (2)
   int sweep_variant = 0;              // sweep kernel: 1 thread per frequency, 2 warp per frequency pair
   int tuned_variant = 0, tuned_size = 0;   // autotuner's choice (a forced variant may replace it for a solve)
+  int max_overlap = 0;                // most transitions active at one frequency over the batch
+  int n_sm = 1;                       // multiprocessors of the batch's device
   bool tuned = false;                 // autotuner has run on this batch
   int graph_kernels = 0;              // kernel nodes in the captured tick graph
   long replays = 0;                   // graph replays of the last solve
@@ -138,6 +140,8 @@ int launch_formal_sweep(const Batch& b, cudaStream_t s);
 // Warps per block of the warp variant whose shared memory fits depth nz (0: none).
 int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);
+// Opacity kernel of the mixed mode (tangent columns skipped when the sweeps form it).
+int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent);
 // Sets every column's forced evaluation mode (explicit API calls) or -1.
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.

@@ -12,7 +12,7 @@
 // range.
 #include <cooperative_groups.h>
 
-#include "internal.cuh"
+#include "formal_coef.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -39,39 +39,29 @@ __device__ __forceinline__ const double* tangent_dir(const ColDesc& cd) {
 // a1: opacity and source function per (nu, k), shared by every ray
 // ---------------------------------------------------------------------------
 template <typename real>
-__global__ void k_opacity(const ColDesc* __restrict__ cols) {
+__device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i);
+
+// Grid-stride over the (nu, k) points of a column: a launch has a few blocks
+// per column, so that columns in another evaluation kind cost little.
+template <typename real>
+__global__ void k_opacity(const ColDesc* __restrict__ cols, int skip_tangent) {
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode(cd);
-  if (mode == EV_SKIP) return;
+  if (mode == EV_SKIP || (skip_tangent && mode == EV_TANGENT)) return;
+  const int n = cd.t.nq * cd.t.nz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    opacity_point<real>(cd, mode, i);
+}
+
+template <typename real>
+__device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i) {
   const ColTables& T = cd.t;
-  const int nz = T.nz, nl = T.nl, nq = T.nq;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq * nz) return;
+  const int nz = T.nz, nl = T.nl;
   if (mode == EV_TANGENT) {
     // chi and S at the base point are those of the Newton step's base
     // evaluation (n and J^dagger are unchanged): only their tangents are new,
     // in the working precision.
-    if (cd.mixed) {
-      // mixed mode: threads run over (k, q) with q fastest, on float tables,
-      // the float direction and the depth-major base-point arrays
-      const int k = i / nq, q = i - k * nq;
-      const float* v = cd.w.v32 + k * nl;
-      const float* V32 = T.V32T + (size_t)k * T.nwin;
-      const float* G32 = T.G32T + (size_t)k * T.nwin;
-      float dchi = 0.f, deta = 0.f;
-      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-        const int t = T.q_t[s];
-        const int p = T.t_base[t] + q - T.t_q0[t];
-        const float V = V32[p], g = G32[p];
-        const float vlo = v[T.t_lo[t]], vup = v[T.t_up[t]];
-        dchi += V * (vlo - g * vup);
-        deta += g * V * vup;               // normalised by 2 h nu^3 / c^2
-      }
-      const size_t o = (size_t)k * col_pitch(nq) + q;
-      cd.w.dchiT[o] = dchi;
-      cd.w.dS32T[o] = (deta - cd.w.S32T[o] * dchi) / cd.w.chiT[o];
-      return;
-    }
+    if (cd.mixed) return;   // k_opacity_tan32
     const int q = i / nz, k = i - q * nz;
     const double* v = tangent_dir(cd) + k * nl;
     real dchi = 0, deta = 0;
@@ -104,6 +94,100 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols) {
   }
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
   cd.w.S[i] = eta / (chi * c2);
+}
+
+// Mixed mode, tangent evaluations: dchi and dS in FP32 (tan_acc), one thread
+// per (k, nu) with nu fastest, so that every warp reads and writes coalesced
+// rows of the depth-major arrays and line tables; the transitions active at
+// nu come from the packed qmeta table (one dependent load, then the data).
+__global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
+  const ColTables& T = cd.t;
+  const int nq = T.nq, nz = T.nz, nl = T.nl, nwin = T.nwin;
+  const size_t pitch = (size_t)col_pitch(nq);
+  const float* __restrict__ V32T = T.V32T;
+  const float* __restrict__ G32T = T.G32T;
+  const float* __restrict__ v32 = cd.w.v32;
+  const int* __restrict__ qmeta = T.qmeta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq * nz; i += gridDim.x * blockDim.x) {
+    const int k = i / nq, q = i - k * nq;
+    const float* V32 = V32T + (size_t)k * nwin;
+    const float* G32 = G32T + (size_t)k * nwin;
+    const float* v = v32 + k * nl;
+    TanAcc ta;
+#pragma unroll
+    for (int j = 0; j < kQMetaT; ++j) {
+      const int m = __ldg(qmeta + (size_t)j * nq + q);
+      if (m < 0) break;
+      const int p = m >> 8;
+      tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + ((m >> 4) & 15)), __ldg(v + (m & 15)));
+    }
+    if (T.max_overlap > kQMetaT)
+      for (int s = T.q_off[q] + kQMetaT; s < T.q_off[q + 1]; ++s) {
+        const int t = T.q_t[s];
+        const int p = T.t_base[t] + q - T.t_q0[t];
+        tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + T.t_lo[t]), __ldg(v + T.t_up[t]));
+      }
+    const size_t o = (size_t)k * pitch + q;
+    cd.w.dchiT[o] = ta.dchi;
+    cd.w.dS32T[o] = tan_dS(ta, __ldg(cd.w.S32T + o), __ldg(cd.w.chiT + o));
+  }
+}
+
+// Mixed mode, tangent evaluations: the tangent rate integrals (Eqs. Rij/Rji
+// differentiated: only J moves) in FP32 from the depth-major dJ. One warp per
+// (transition, depth): lanes stride over the transition's frequency window
+// (coalesced rows of the depth-major tables) and a fixed xor-butterfly adds
+// the lanes, so the sums are bit-reproducible.
+constexpr int kRateTanWarps = 8;
+constexpr int kRateTanDepths = 4;   // depths per warp (independent sums in flight)
+__global__ void __launch_bounds__(32 * kRateTanWarps) k_rates_tan32(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.z];
+  if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
+  const ColTables& T = cd.t;
+  const int t = blockIdx.y;
+  // warp w of the block takes depths k0 + w + d * kRateTanWarps, d < kRateTanDepths
+  const int k0 = blockIdx.x * kRateTanWarps * kRateTanDepths + (threadIdx.x >> 5);
+  if (t >= T.nt || k0 >= T.nz) return;   // whole warps
+  const int lane = threadIdx.x & 31;
+  const int nz = T.nz, nwin = T.nwin;
+  const size_t pitch = (size_t)col_pitch(T.nq);
+  const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
+  const float* __restrict__ V32 = T.V32T + base - q0;
+  const float* __restrict__ G32 = T.G32T + base - q0;
+  const float* __restrict__ W32 = T.W32 + base - q0;
+  const float* __restrict__ dJ = cd.w.dJ32T;
+  float a0[kRateTanDepths], a1[kRateTanDepths];
+#pragma unroll
+  for (int d = 0; d < kRateTanDepths; ++d) a0[d] = a1[d] = 0.f;
+  for (int q = q0 + lane; q <= q1; q += 32) {
+    const float W = __ldg(W32 + q);
+#pragma unroll
+    for (int d = 0; d < kRateTanDepths; ++d) {
+      const int k = k0 + d * kRateTanWarps;
+      if (k < nz) {
+        const float WV = W * __ldg(V32 + (size_t)k * nwin + q);
+        const float x = __ldg(dJ + (size_t)k * pitch + q);
+        a0[d] = fmaf(WV, x, a0[d]);
+        a1[d] = fmaf(WV * __ldg(G32 + (size_t)k * nwin + q), x, a1[d]);
+      }
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < kRateTanDepths; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0[d] += __shfl_xor_sync(0xffffffffu, a0[d], o);
+      a1[d] += __shfl_xor_sync(0xffffffffu, a1[d], o);
+    }
+    const int k = k0 + d * kRateTanWarps;
+    if (lane == 0 && k < nz) {
+      const size_t i = (size_t)t * nz + k;
+      cd.w.dRup[i] = (double)a0[d];
+      cd.w.dRdn[i] = (double)a1[d];
+    }
+  }
 }
 
 // Mixed mode: float copy of the tangent direction of every column in a
@@ -352,8 +436,10 @@ __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __rest
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
   const int t = blockIdx.y;
-  // uniform over the cluster: every block takes the same branch
-  const bool active = (mode != EV_SKIP) && t < nt && (int)blockIdx.x * 32 < nz;
+  // uniform over the cluster: every block takes the same branch (mixed-mode
+  // tangents are integrated by k_rates_tan32)
+  const bool active = (mode != EV_SKIP) && !(mode == EV_TANGENT && cd.mixed) && t < nt &&
+                      (int)blockIdx.x * 32 < nz;
   __shared__ double red[kRateWarps][kRateAcc][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool tan = (mode == EV_TANGENT);
@@ -370,20 +456,47 @@ __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __rest
     const double* n = cd.w.n + k * nl;
     double acc[kRateAcc];
     for (int j = 0; j < nacc; ++j) acc[j] = 0.0;
+    float af[kRhFixed] = {0.f, 0.f, 0.f, 0.f};   // mixed-mode RH92 fixed sums
     const double n_lo = n[lo], n_up = n[upl];
     const double* Jd = rh ? jdag_ptr(cd) : nullptr;
-    if (tan && cd.mixed) {
-      // mixed mode: the tangent rate integrals in FP32 (float tables and dJ)
-      float a0 = 0.f, a1 = 0.f;
+    if (rh && cd.mixed) {
+      // mixed mode, RH92 sums: Jeff = J - Psi* eta cancels in thick layers
+      // and is formed in FP64; the products of the sums are FP32, the sums
+      // over transitions s accumulate in shared memory (lane-private slots
+      // aliasing ``red``, which is written only after this loop)
+      float* fs = reinterpret_cast<float*>(&red[0][0][0]) + (size_t)wid * kMaxT * 32 + lane;
+      for (int j = 0; j < nt; ++j) fs[j * 32] = 0.f;
+      const float nlo_f = (float)n_lo, nup_f = (float)n_up;
       for (int q = qa + wid; q <= qb; q += kRateWarps) {
         const size_t p = (size_t)(base + q - q0);
-        const float WV = T.W32[p] * T.V32[p * nz + k];
-        const float dJ = cd.w.dJ32T[(size_t)k * col_pitch(T.nq) + q];
-        a0 = fmaf(WV, dJ, a0);
-        a1 = fmaf(WV * T.G32[p * nz + k], dJ, a1);
+        const double W = T.t_w[p] * T.rw[q];
+        const double V = T.V[p * nz + k], g = T.G[p * nz + k];
+        const size_t o = (size_t)q * nz + k;
+        const double J = cd.w.J[o];
+        const double c2 = T.c2[q];
+        acc[0] += W * V * J;
+        acc[1] += W * g * V * (c2 + J);
+        const double Le = cd.w.Leta[o];
+        const double eta_bg = T.eta_c[o] + T.chi_sca[k] * Jd[o];
+        double eta_l = 0.0;
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
+        }
+        const float Jf = (float)(J - Le * (eta_bg + eta_l));
+        const float Wf = T.Wr32[p], Vf = T.V32[p * nz + k], gf = T.G32[p * nz + k], c2f = T.c2f[q];
+        af[0] = fmaf(Wf * Vf, Jf, af[0]);
+        af[1] = fmaf(Wf * gf * Vf, Jf, af[1]);
+        af[2] = fmaf(Wf * c2f, gf * Vf, af[2]);
+        const float wcp = Wf * (Vf * (nlo_f - gf * nup_f)) * (float)Le;
+        af[3] = fmaf(wcp, (float)eta_bg, af[3]);
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          fs[ts * 32] = fmaf(wcp * c2f, T.G32[ps] * T.V32[ps], fs[ts * 32]);
+        }
       }
-      acc[0] = a0;
-      acc[1] = a1;
     } else
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
       const size_t p = (size_t)(base + q - q0);
@@ -438,7 +551,22 @@ __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __rest
         }
       }
     }
-    for (int j = 0; j < nacc; ++j) red[wid][j][lane] = acc[j];
+    if (rh && cd.mixed) {
+      float tsv[kMaxT];
+      const float* fs = reinterpret_cast<const float*>(&red[0][0][0]) + (size_t)wid * kMaxT * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < kMaxT; ++j) tsv[j] = (j < nt) ? fs[j * 32] : 0.f;
+      __syncthreads();   // the float slots alias red
+      red[wid][0][lane] = acc[0];
+      red[wid][1][lane] = acc[1];
+#pragma unroll
+      for (int j = 0; j < kRhFixed; ++j) red[wid][2 + j][lane] = (double)af[j];
+#pragma unroll
+      for (int j = 0; j < kMaxT; ++j)
+        if (j < nt) red[wid][2 + kRhFixed + j][lane] = (double)tsv[j];
+    } else {
+      for (int j = 0; j < nacc; ++j) red[wid][j][lane] = acc[j];
+    }
     __syncthreads();
     if (wid == 0)
       for (int j = 0; j < nacc; ++j) {
@@ -634,6 +762,22 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Blocks per column of the grid-stride opacity kernel: all the points of a
+// column when the batch is small, about 32 blocks per SM in total otherwise.
+static dim3 opacity_grid(const Batch& b, int tb) {
+  const long need = ((long)b.max_nq * b.max_nz + tb - 1) / tb;
+  const long share = (32L * b.n_sm + b.ncols - 1) / b.ncols;
+  return dim3((unsigned)std::max(1L, std::min(need, share)), b.ncols);
+}
+
+int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
+  const int tb = 256;
+  k_opacity<float><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 1);   // base and RH92 columns
+  if (!skip_tangent) k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
 int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   const int nc = b.ncols;
   if (nc == 0) return JFNK_OK;
@@ -644,21 +788,21 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   if (b.formal_kind == FORMAL_SWEEP) {
     // (float tangent direction,) opacity, then the per-frequency sweeps
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
-    k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
+    int rc0 = launch_opacity_mixed(b, s, 0);
+    if (rc0) return rc0;
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     int rc = launch_formal_sweep(b, s);
     if (rc) return rc;
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   } else if (b.formal_kind == FORMAL_FUSED) {
     // opacity, then the fused formal solution with in-block ray sums
-    if (b.mixed) k_opacity<float><<<g_qk, tb, 0, s>>>(b.d_cols);
-    else k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+    k_opacity<double><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 0);
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     int rc = launch_formal_fused(b, s);
     if (rc) return rc;
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   } else {
-    k_opacity<double><<<g_qk, tb, 0, s>>>(b.d_cols);
+    k_opacity<double><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 0);
     k_source_diff<double><<<g_qk, tb, 0, s>>>(b.d_cols);
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     k_formal<double><<<g_ray, 64, 0, s>>>(b.d_cols);
@@ -668,6 +812,10 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   {
     int rc = launch_rates(b, s);
     if (rc) return rc;
+    if (b.mixed)
+      k_rates_tan32<<<dim3((b.max_nz + kRateTanWarps * kRateTanDepths - 1) / (kRateTanWarps * kRateTanDepths),
+                           b.max_nt, nc),
+                      32 * kRateTanWarps, 0, s>>>(b.d_cols);
   }
   k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());

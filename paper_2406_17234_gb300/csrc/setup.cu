@@ -417,7 +417,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
          o_vt = ar.take<double>(nz);
   size_t o_tr = ar.take<TransDev>(nt), o_cd = ar.take<CollDev>(nt);
   size_t o_V32 = ar.take<float>((size_t)nwin * nz), o_G32 = ar.take<float>((size_t)nwin * nz),
-         o_W32 = ar.take<float>(nwin);
+         o_W32 = ar.take<float>(nwin), o_Wr32 = ar.take<float>(nwin), o_c2f = ar.take<float>(nq);
+  size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
   size_t o_V32T = ar.take<float>((size_t)nwin * nz), o_G32T = ar.take<float>((size_t)nwin * nz);
   int rc = ar.allocate();
   if (rc) return rc;
@@ -430,12 +431,14 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   for (int k = 0; k + 1 < nz; ++k) dzv[k] = std::fabs(d->z[k] - d->z[k + 1]);
   gauss_legendre_01(nmu, mu.data(), wmu.data());
   std::vector<int> winT(nwin);
-  std::vector<float> w32(nwin);
+  std::vector<float> w32(nwin), wr32(nwin), c2f(nq);
+  for (int q = 0; q < nq; ++q) c2f[q] = (float)c2[q];
   for (int t = 0; t < nt; ++t)
     for (int p = 0; p <= A.t_q1[t] - A.t_q0[t]; ++p) {
       const int q = A.t_q0[t] + p;
       winT[A.t_base[t] + p] = t;
       w32[A.t_base[t] + p] = (float)(A.t_w[A.t_base[t] + p] * rw[q] * c2[q]);
+      wr32[A.t_base[t] + p] = (float)(A.t_w[A.t_base[t] + p] * rw[q]);
     }
   std::vector<TransDev> tr(nt);
   std::vector<CollDev> cd(nt);
@@ -474,6 +477,15 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(up(o_winT, winT.data(), nwin * 4));
   JFNK_CUDA(up(o_tw, A.t_w.data(), nwin * 8));
   JFNK_CUDA(up(o_W32, w32.data(), nwin * 4));
+  JFNK_CUDA(up(o_Wr32, wr32.data(), nwin * 4));
+  JFNK_CUDA(up(o_c2f, c2f.data(), nq * 4));
+  std::vector<int> qmeta((size_t)kQMetaT * nq, -1);
+  for (int q = 0; q < nq; ++q)
+    for (int s = A.q_off[q], j = 0; s < A.q_off[q + 1] && j < kQMetaT; ++s, ++j) {
+      const int t = A.q_t[s];
+      qmeta[(size_t)j * nq + q] = ((A.t_base[t] + q - A.t_q0[t]) << 8) | (A.t_lo[t] << 4) | A.t_up[t];
+    }
+  JFNK_CUDA(up(o_qmeta, qmeta.data(), qmeta.size() * 4));
   JFNK_CUDA(up(o_dz, dzv.data(), (nz - 1) * 8));
   JFNK_CUDA(up(o_mu, mu.data(), nmu * 8));
   JFNK_CUDA(up(o_wmu, wmu.data(), nmu * 8));
@@ -511,6 +523,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(cudaStreamSynchronize(s));
   ColTables& tb_ = M->tables;
   tb_.nz = nz; tb_.nq = nq; tb_.nl = nl; tb_.nt = nt; tb_.nmu = nmu; tb_.nwin = nwin;
+  tb_.max_overlap = 0;
+  for (int q = 0; q < nq; ++q) tb_.max_overlap = std::max(tb_.max_overlap, A.q_off[q + 1] - A.q_off[q]);
   tb_.nu = ar.ptr<double>(o_nu); tb_.c2 = ar.ptr<double>(o_c2); tb_.rw = ar.ptr<double>(o_rw);
   tb_.q_off = ar.ptr<int>(o_qoff); tb_.q_t = ar.ptr<int>(o_qt);
   tb_.t_lo = ar.ptr<int>(o_tlo); tb_.t_up = ar.ptr<int>(o_tup); tb_.t_q0 = ar.ptr<int>(o_tq0);
@@ -518,6 +532,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   tb_.V = ar.ptr<double>(o_V); tb_.G = ar.ptr<double>(o_G); tb_.dz = ar.ptr<double>(o_dz);
   tb_.V32 = ar.ptr<float>(o_V32); tb_.G32 = ar.ptr<float>(o_G32); tb_.W32 = ar.ptr<float>(o_W32);
   tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);
+  tb_.Wr32 = ar.ptr<float>(o_Wr32); tb_.c2f = ar.ptr<float>(o_c2f);
+  tb_.qmeta = ar.ptr<int>(o_qmeta);
   tb_.mu = ar.ptr<double>(o_mu); tb_.wmu = ar.ptr<double>(o_wmu);
   tb_.chi_c = ar.ptr<double>(o_chic); tb_.eta_c = ar.ptr<double>(o_etac);
   tb_.chi_sca = ar.ptr<double>(o_sca); tb_.Bn = ar.ptr<double>(o_B); tb_.C = ar.ptr<double>(o_C);

@@ -8,7 +8,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "internal.cuh"
+#include "formal_coef.cuh"
 
 namespace jfnk {
 
@@ -39,8 +39,18 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   DeviceArena& ar = b->arena;
   ar.reset();
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
-  int mnz = 0, mnmu = 0;
-  for (auto* c : cols) { mnz = std::max(mnz, c->nz); mnmu = std::max(mnmu, c->nmu); }
+  int mnz = 0, mnmu = 0, mov = 0;
+  for (auto* c : cols) {
+    mnz = std::max(mnz, c->nz);
+    mnmu = std::max(mnmu, c->nmu);
+    mov = std::max(mov, c->tables.max_overlap);
+  }
+  b->max_overlap = mov;
+  {
+    int dev = 0;
+    JFNK_CUDA(cudaGetDevice(&dev));
+    JFNK_CUDA(cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
   b->formal_qb = mixed ? 0 : fused_default_qb(mnz, mnmu, false);
   b->formal_kind = mixed ? FORMAL_SWEEP : (b->formal_qb > 0 ? FORMAL_FUSED : FORMAL_UNFUSED);
   const bool per_ray = (b->formal_kind == FORMAL_UNFUSED);   // unfused kernels need per-ray buffers
