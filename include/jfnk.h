@@ -288,6 +288,63 @@ int jfnk_batch_destroy(jfnk_batch* b);
 int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const double* n,
                          const double* J_dagger, double* F, double* J_new, void* stream);
 
+/* ---- serving: continuous batching of column solves ------------------------ */
+/* A server solves independent columns (Algorithm 2 per column) as they
+ * arrive. It holds max_slots columns on the device at once; every step
+ * advances all of them by one captured tick graph (8 F-class evaluations
+ * each) and, between steps, retires finished columns and admits queued ones
+ * in arrival order. A queued column is admitted when a slot is free AND its
+ * own work buffers (jfnk_server_bytes) fit in the server's device memory pool,
+ * which is carved by a first-fit allocator: large and small columns share the
+ * pool as memory frees up. Populations, Krylov bases, opacities and
+ * intensities stay resident on the device for the whole solve. A column's
+ * result does not depend on the other columns in flight. */
+typedef struct jfnk_server jfnk_server;
+
+typedef struct {
+  int max_slots;        /* columns in flight at once (>= 1)                        */
+  int max_depth;        /* slot shape: the largest n_depth a request may have      */
+  int max_freq;         /* largest union frequency grid                            */
+  int max_levels;       /* largest level count (<= JFNK_MAX_LEVELS)                */
+  int max_trans;        /* largest transition count (<= 32)                        */
+  int max_mu;           /* largest angle count per hemisphere (<= JFNK_MAX_MU)     */
+  size_t mem_bytes;     /* device memory pool for work buffers; 0: half the free memory */
+  jfnk_options opts;    /* default options of a request (init must be LTE)         */
+} jfnk_server_desc;
+
+typedef struct {
+  long long id;         /* the id given to jfnk_server_submit                      */
+  int status;           /* JFNK_OK when converged                                  */
+  jfnk_stats stats;
+  double t_submit;      /* jfnk_server_clock at submission, admission and retirement */
+  double t_admit;
+  double t_done;
+} jfnk_result;
+
+/* Creates a server on ctx (its own stream). Errors: JFNK_E_INVALID for a bad
+ * shape or options, JFNK_E_NOMEM when the pool cannot be allocated. */
+int jfnk_server_create(jfnk_ctx* ctx, const jfnk_server_desc* d, jfnk_server** out);
+/* Device bytes of the work buffers of column ``a`` in this server. */
+int jfnk_server_bytes(jfnk_server* sv, const jfnk_atmos* a, size_t* bytes);
+/* Enqueues a solve of column ``a`` from LTE populations. ``a`` (and its atom)
+ * must stay alive until the result has been polled. n_out (host, nz*nl
+ * doubles, nullable) receives the populations before the result is reported.
+ * opts (nullable: the server's) sets this column's tolerances, limits and
+ * hybrid start; its precision must be the server's and its krylov_max at most
+ * the server's. JFNK_E_INVALID when ``a`` exceeds the slot shape or the pool,
+ * or for such options. May be called from another thread than
+ * jfnk_server_step. */
+int jfnk_server_submit(jfnk_server* sv, const jfnk_atmos* a, long long id, double* n_out,
+                       const jfnk_options* opts);
+/* Admits, runs one tick graph over the columns in flight, retires the finished
+ * ones. n_active / n_queued (nullable): columns in flight / waiting after it. */
+int jfnk_server_step(jfnk_server* sv, int* n_active, int* n_queued);
+/* Moves up to ``max`` finished results to ``out``; *n gets their number. */
+int jfnk_server_poll(jfnk_server* sv, jfnk_result* out, int max, int* n);
+/* Seconds since the server was created (steady clock). */
+double jfnk_server_clock(jfnk_server* sv);
+int jfnk_server_destroy(jfnk_server* sv);
+
 /* ---- measurement ----------------------------------------------------------- */
 /* Throughput probe of one arithmetic pipe on the context's device, for roofline
  * denominators: kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add,

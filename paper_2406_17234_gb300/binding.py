@@ -83,6 +83,17 @@ class jfnk_stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class jfnk_server_desc(C.Structure):
+    _fields_ = [("max_slots", C.c_int), ("max_depth", C.c_int), ("max_freq", C.c_int),
+                ("max_levels", C.c_int), ("max_trans", C.c_int), ("max_mu", C.c_int),
+                ("mem_bytes", C.c_size_t), ("opts", jfnk_options)]
+
+
+class jfnk_result(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int), ("stats", jfnk_stats),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 # name -> (restype, argtypes)
 _SIGNATURES = {
     "jfnk_last_error": (C.c_char_p, []),
@@ -116,6 +127,14 @@ _SIGNATURES = {
     "jfnk_batch_destroy": (C.c_int, [C.c_void_p]),
     "jfnk_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
+    "jfnk_server_create": (C.c_int, [C.c_void_p, C.POINTER(jfnk_server_desc), C.POINTER(C.c_void_p)]),
+    "jfnk_server_bytes": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "jfnk_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
+                                     C.POINTER(jfnk_options)]),
+    "jfnk_server_step": (C.c_int, [C.c_void_p, _ip, _ip]),
+    "jfnk_server_poll": (C.c_int, [C.c_void_p, C.POINTER(jfnk_result), C.c_int, _ip]),
+    "jfnk_server_clock": (C.c_double, [C.c_void_p]),
+    "jfnk_server_destroy": (C.c_int, [C.c_void_p]),
     "jfnk_batch_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p),
                                    C.POINTER(jfnk_options), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.POINTER(jfnk_stats), C.c_int,
@@ -216,8 +235,10 @@ class Atom:
         return nu
 
     def __del__(self):
+        # a context finalized first (garbage cycles are finalized in any
+        # order) has already gone: its handle must not be touched any more
         try:
-            if self.h:
+            if self.h and self.ctx.h:
                 self.ctx.lib.jfnk_destroy_atom(self.h)
         except Exception:
             pass
@@ -259,7 +280,7 @@ class Atmosphere:
 
     def __del__(self):
         try:
-            if self.h:
+            if self.h and self.ctx.h:
                 self.ctx.lib.jfnk_destroy_atmosphere(self.h)
         except Exception:
             pass
@@ -382,9 +403,78 @@ class BatchPlan:
         return self.ns, [s.as_dict() for s in self.stats]
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             self.ctx.lib.jfnk_batch_destroy(self.h)
-            self.h = None
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (jfnk_server_*): columns are submitted
+    as they arrive, admitted into free slots when their work buffers fit in the
+    server's device pool, and advanced together one captured tick graph per
+    step. Results carry submission, admission and completion times on the
+    server clock."""
+
+    def __init__(self, ctx: Context, max_slots: int, max_depth: int, max_freq: int, max_levels: int = 6,
+                 max_trans: int = 16, max_mu: int = 5, mem_bytes: int = 0,
+                 opts: Optional[jfnk_options] = None):
+        self.ctx = ctx
+        d = jfnk_server_desc(max_slots=max_slots, max_depth=max_depth, max_freq=max_freq,
+                             max_levels=max_levels, max_trans=max_trans, max_mu=max_mu,
+                             mem_bytes=mem_bytes)
+        d.opts = opts or default_options(precision=JFNK_MIXED)
+        self.h = None
+        h = C.c_void_p()
+        check(ctx.lib.jfnk_server_create(ctx.h, C.byref(d), C.byref(h)), "jfnk_server_create")
+        self.h = h
+        self._pending = {}   # id -> (atmosphere, populations buffer)
+        self._res = (jfnk_result * 256)()
+
+    def bytes(self, atm: "Atmosphere") -> int:
+        v = C.c_size_t()
+        check(self.ctx.lib.jfnk_server_bytes(self.h, atm.h, C.byref(v)), "jfnk_server_bytes")
+        return v.value
+
+    def submit(self, atm: "Atmosphere", rid: int, opts: Optional[jfnk_options] = None) -> None:
+        n = np.zeros((atm.n_depth, atm.n_levels))
+        check(self.ctx.lib.jfnk_server_submit(self.h, atm.h, rid, n.ctypes.data,
+                                              C.byref(opts) if opts is not None else None),
+              "jfnk_server_submit")
+        self._pending[rid] = (atm, n)
+
+    def step(self):
+        a, q = C.c_int(), C.c_int()
+        check(self.ctx.lib.jfnk_server_step(self.h, C.byref(a), C.byref(q)), "jfnk_server_step")
+        return a.value, q.value
+
+    def poll(self):
+        """Finished requests as dicts (id, status, stats, times, n)."""
+        out = []
+        while True:
+            k = C.c_int()
+            check(self.ctx.lib.jfnk_server_poll(self.h, self._res, len(self._res), C.byref(k)),
+                  "jfnk_server_poll")
+            for i in range(k.value):
+                r = self._res[i]
+                _, n = self._pending.pop(r.id)
+                out.append(dict(id=r.id, status=r.status, stats=r.stats.as_dict(), t_submit=r.t_submit,
+                                t_admit=r.t_admit, t_done=r.t_done, n=n))
+            if k.value < len(self._res):
+                return out
+
+    def clock(self) -> float:
+        return self.ctx.lib.jfnk_server_clock(self.h)
+
+    def close(self):
+        if self.h and self.ctx.h:
+            self.ctx.lib.jfnk_server_destroy(self.h)
+        self.h = None
 
     def __del__(self):
         try:

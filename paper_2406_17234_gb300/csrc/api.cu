@@ -84,7 +84,7 @@ static int explicit_eval(jfnk_ctx* ctx, const jfnk_atmos* a, Batch* b, int mode,
   return launch_evaluation(*b, s);
 }
 
-static void options_to_device(const jfnk_options* o, SolverOpts* so) {
+void options_to_device(const jfnk_options* o, SolverOpts* so) {
   so->ftol = o->ftol;
   so->fdrop = o->fdrop;
   so->rtol = o->rtol;
@@ -97,7 +97,7 @@ static void options_to_device(const jfnk_options* o, SolverOpts* so) {
   so->max_ticks = o->max_ticks;
 }
 
-static int validate_options(const jfnk_options* o) {
+int validate_options(const jfnk_options* o) {
   if (!o) return fail(JFNK_E_INVALID, "options are NULL");
   if (!(o->rtol > 0.0 && o->rtol < 1.0)) return fail(JFNK_E_INVALID, "rtol must be in (0, 1)");
   if (!(o->ftol >= 0.0) || !(o->fdrop >= 0.0)) return fail(JFNK_E_INVALID, "ftol, fdrop must be >= 0");
@@ -122,11 +122,10 @@ __global__ void k_init_state(SolverState* st, int n, int phase) {
   st[c] = s;
 }
 
-constexpr int kTicksPerGraph = 8;
 
 // Captures kTicksPerGraph ticks (evaluation + Krylov step) of the batch's
 // current launch view into an executable graph.
-static int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out) {
+int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out) {
   if (profile && b->tick_ev.empty()) {
     b->tick_ev.resize(2 * kTicksPerGraph);
     for (auto& e : b->tick_ev) JFNK_CUDA(cudaEventCreate(&e));
@@ -450,6 +449,7 @@ int jfnk_destroy_ctx(jfnk_ctx* c) {
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   delete c;
+  cudaGetLastError();   // a teardown failure must not surface in a later call
   return JFNK_OK;
 }
 
@@ -505,6 +505,7 @@ int jfnk_destroy_atmosphere(jfnk_atmos* a) {
   cudaSetDevice(a->ctx->device);
   delete single_work(a);
   delete a;
+  cudaGetLastError();   // a teardown failure must not surface in a later call
   return JFNK_OK;
 }
 
@@ -680,6 +681,7 @@ int jfnk_batch_destroy(jfnk_batch* b) {
   if (!b) return JFNK_OK;
   cudaSetDevice(b->ctx->device);
   delete b;
+  cudaGetLastError();   // a teardown failure must not surface in a later call
   return JFNK_OK;
 }
 

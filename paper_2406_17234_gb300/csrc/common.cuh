@@ -174,6 +174,7 @@ struct ColDesc {
   ColWork w;
   int forced_mode;   // >= 0: evaluation mode for explicit API calls; < 0: from st->phase
   int mixed;         // 1: FP32 formal solution (buffers are float)
+  const SolverOpts* opts;   // this column's solver options (null: the batch's)
 };
 
 // The lagged mean intensity J^dagger and the newly computed J live in two

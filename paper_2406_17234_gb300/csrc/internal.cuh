@@ -119,6 +119,12 @@ struct Batch {
   ~Batch();
 };
 
+// Work buffers of one column: bytes of its block (256-byte aligned parts), and
+// the descriptor of a column whose block starts at ``base``.
+struct ColLayout;
+size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout* out);
+void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, SolverState* st, ColDesc* d);
+
 // Allocates work buffers for columns ``tabs`` (precision: mixed or FP64).
 int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed, int kmax);
 // Launch sequence of one F-class evaluation for every column of the batch.
@@ -142,6 +148,12 @@ int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);
 // Opacity kernel of the mixed mode (tangent columns skipped when the sweeps form it).
 int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent);
+// Solver options: checks, device copy (api.cu).
+int validate_options(const jfnk_options* o);
+void options_to_device(const jfnk_options* o, SolverOpts* so);
+// Captures kTicksPerGraph ticks (evaluation + Krylov step) of the batch's launch view.
+constexpr int kTicksPerGraph = 8;
+int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out);
 // Sets every column's forced evaluation mode (explicit API calls) or -1.
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.

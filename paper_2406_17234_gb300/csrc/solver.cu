@@ -30,6 +30,90 @@ void DeviceArena::release() {
   bytes = 0;
 }
 
+// Offsets of one column's work buffers, relative to the start of its block.
+struct ColLayout {
+  size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH,
+      LX, LE, part, J, dJ, Lchi, Leta, Rup, Rdn, dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x,
+      w, nprev;
+};
+
+size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout* out) {
+  DeviceArena ar;   // used as a cursor only
+  ColLayout o{};
+  const size_t rs = mixed ? sizeof(float) : sizeof(double);
+  const size_t nz = M.nz, nq = M.nq, nl = M.nl, nt = M.nt, nmu = M.nmu, N = nz * nl;
+  const bool per_ray = (kind == FORMAL_UNFUSED);   // unfused kernels need per-ray buffers
+  const bool sweep = (kind == FORMAL_SWEEP);
+  o.n = ar.take<double>(N); o.v = ar.take<double>(N);
+  o.Jdag = ar.take<double>(nq * nz); o.Jnew = ar.take<double>(nq * nz);
+  o.istar = ar.take<int>(nz);
+  o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<double>(nq * nz);
+  o.dSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
+  o.dchi = ar.take<char>(sweep ? 0 : rs * nq * nz); o.dS = ar.take<double>(sweep ? 0 : nq * nz);
+  const size_t TQ = sweep ? (size_t)nz * col_pitch((int)nq) : 0;
+  o.v32 = ar.take<float>(sweep ? N : 0);
+  o.chiT = ar.take<float>(TQ); o.S32T = ar.take<float>(TQ); o.dSkT = ar.take<float>(TQ);
+  o.dchiT = ar.take<float>(TQ); o.dS32T = ar.take<float>(TQ); o.dJ32T = ar.take<float>(TQ);
+  o.ddSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
+  const size_t pr = per_ray ? rs * 2 * nmu * nq * nz : 0;
+  o.H = ar.take<char>(pr); o.dH = ar.take<char>(pr); o.HI = ar.take<char>(pr);
+  o.LX = ar.take<char>(pr); o.LE = ar.take<char>(pr);
+  o.part = ar.take<char>(sweep ? sweep_scratch_bytes((int)nq, (int)nz) : 0);
+  o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(sweep ? 0 : nq * nz);
+  o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
+  o.Rup = ar.take<double>(nt * nz); o.Rdn = ar.take<double>(nt * nz);
+  o.dRup = ar.take<double>(nt * nz); o.dRdn = ar.take<double>(nt * nz);
+  o.Apart = ar.take<double>(nt * nz * nl);
+  o.rh = ar.take<double>(nt * nz * kRhStride);
+  o.F = ar.take<double>(N); o.dF = ar.take<double>(N);
+  o.P = ar.take<double>(nz * nl * nl); o.piv = ar.take<int>(nz * nl);
+  o.Iem = ar.take<double>(nq * nmu);
+  o.Vb = ar.take<double>((size_t)(kmax + 1) * N); o.Hh = ar.take<double>((size_t)(kmax + 1) * kmax);
+  o.cs = ar.take<double>(kmax); o.sn = ar.take<double>(kmax); o.gv = ar.take<double>(kmax + 1);
+  o.x = ar.take<double>(N); o.w = ar.take<double>(N); o.nprev = ar.take<double>(N);
+  if (out) *out = o;
+  return ar.cursor;
+}
+
+void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, SolverState* st, ColDesc* d) {
+  ColLayout o;
+  column_bytes(M, kind, mixed, kmax, &o);
+  auto P = [&](size_t off) { return static_cast<void*>(base + off); };
+  const bool sweep = (kind == FORMAL_SWEEP);
+  d->t = M.tables;
+  d->forced_mode = -1;
+  d->mixed = mixed;
+  d->opts = nullptr;
+  ColWork& w = d->w;
+  w = ColWork{};
+  w.n = (double*)P(o.n); w.v = (double*)P(o.v);
+  w.Jdag = (double*)P(o.Jdag); w.Jnew = (double*)P(o.Jnew);
+  w.istar = (int*)P(o.istar);
+  w.chi = P(o.chi); w.S = (double*)P(o.S); w.dSk = P(o.dSk);
+  w.dchi = sweep ? nullptr : P(o.dchi); w.ddSk = P(o.ddSk);
+  // the mixed tangent path is FP32 throughout: no FP64 tangent buffers
+  w.dS = sweep ? nullptr : (double*)P(o.dS);
+  if (sweep) {
+    w.v32 = (float*)P(o.v32);
+    w.chiT = (float*)P(o.chiT); w.S32T = (float*)P(o.S32T); w.dSkT = (float*)P(o.dSkT);
+    w.dchiT = (float*)P(o.dchiT); w.dS32T = (float*)P(o.dS32T); w.dJ32T = (float*)P(o.dJ32T);
+  }
+  w.H = P(o.H); w.dH = P(o.dH); w.HI = P(o.HI); w.LX = P(o.LX); w.LE = P(o.LE);
+  w.part = P(o.part);
+  w.J = (double*)P(o.J); w.dJ = sweep ? nullptr : (double*)P(o.dJ);
+  w.Lchi = (double*)P(o.Lchi); w.Leta = (double*)P(o.Leta);
+  w.zeta = nullptr;
+  w.Rup = (double*)P(o.Rup); w.Rdn = (double*)P(o.Rdn);
+  w.dRup = (double*)P(o.dRup); w.dRdn = (double*)P(o.dRdn);
+  w.Apart = (double*)P(o.Apart); w.rh = (double*)P(o.rh);
+  w.F = (double*)P(o.F); w.dF = (double*)P(o.dF);
+  w.P = (double*)P(o.P); w.piv = (int*)P(o.piv); w.Iem = (double*)P(o.Iem);
+  w.Vb = (double*)P(o.Vb); w.Hh = (double*)P(o.Hh);
+  w.cs = (double*)P(o.cs); w.sn = (double*)P(o.sn); w.gv = (double*)P(o.gv);
+  w.x = (double*)P(o.x); w.w = (double*)P(o.w); w.nprev = (double*)P(o.nprev);
+  w.st = st;
+}
+
 int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed, int kmax) {
   const int nc = (int)cols.size();
   b->ncols = nc;
@@ -38,12 +122,14 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   b->max_nz = b->max_nq = b->max_nt = b->max_N = b->max_nmu = 0;
   DeviceArena& ar = b->arena;
   ar.reset();
-  const size_t rs = mixed ? sizeof(float) : sizeof(double);
-  int mnz = 0, mnmu = 0, mov = 0;
+  int mov = 0;
   for (auto* c : cols) {
-    mnz = std::max(mnz, c->nz);
-    mnmu = std::max(mnmu, c->nmu);
     mov = std::max(mov, c->tables.max_overlap);
+    b->max_nz = std::max(b->max_nz, c->nz);
+    b->max_nq = std::max(b->max_nq, c->nq);
+    b->max_nt = std::max(b->max_nt, c->nt);
+    b->max_N = std::max(b->max_N, c->nz * c->nl);
+    b->max_nmu = std::max(b->max_nmu, c->nmu);
   }
   b->max_overlap = mov;
   {
@@ -51,53 +137,11 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     JFNK_CUDA(cudaGetDevice(&dev));
     JFNK_CUDA(cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev));
   }
-  b->formal_qb = mixed ? 0 : fused_default_qb(mnz, mnmu, false);
+  b->formal_qb = mixed ? 0 : fused_default_qb(b->max_nz, b->max_nmu, false);
   b->formal_kind = mixed ? FORMAL_SWEEP : (b->formal_qb > 0 ? FORMAL_FUSED : FORMAL_UNFUSED);
-  const bool per_ray = (b->formal_kind == FORMAL_UNFUSED);   // unfused kernels need per-ray buffers
-  struct Offs {
-    size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH, LX, LE, part, J, dJ,
-        Lchi, Leta, Rup, Rdn,
-        dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x, w, nprev;
-  };
-  std::vector<Offs> off(nc);
-  for (int c = 0; c < nc; ++c) {
-    const AtmosData& M = *cols[c];
-    const size_t nz = M.nz, nq = M.nq, nl = M.nl, nt = M.nt, nmu = M.nmu, N = nz * nl;
-    b->max_nz = std::max(b->max_nz, (int)nz);
-    b->max_nq = std::max(b->max_nq, (int)nq);
-    b->max_nt = std::max(b->max_nt, (int)nt);
-    b->max_N = std::max(b->max_N, (int)N);
-    b->max_nmu = std::max(b->max_nmu, (int)nmu);
-    Offs& o = off[c];
-    o.n = ar.take<double>(N); o.v = ar.take<double>(N);
-    o.Jdag = ar.take<double>(nq * nz); o.Jnew = ar.take<double>(nq * nz);
-    o.istar = ar.take<int>(nz);
-    o.chi = ar.take<char>(rs * nq * nz); o.S = ar.take<double>(nq * nz);
-    const bool sweep = (b->formal_kind == FORMAL_SWEEP);
-    o.dSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
-    o.dchi = ar.take<char>(sweep ? 0 : rs * nq * nz); o.dS = ar.take<double>(sweep ? 0 : nq * nz);
-    const size_t TQ = sweep ? (size_t)nz * col_pitch((int)nq) : 0;
-    o.v32 = ar.take<float>(sweep ? N : 0);
-    o.chiT = ar.take<float>(TQ); o.S32T = ar.take<float>(TQ); o.dSkT = ar.take<float>(TQ);
-    o.dchiT = ar.take<float>(TQ); o.dS32T = ar.take<float>(TQ); o.dJ32T = ar.take<float>(TQ);
-    o.ddSk = ar.take<char>(per_ray ? rs * nq * nz : 0);
-    const size_t pr = per_ray ? rs * 2 * nmu * nq * nz : 0;
-    o.H = ar.take<char>(pr); o.dH = ar.take<char>(pr); o.HI = ar.take<char>(pr);
-    o.LX = ar.take<char>(pr); o.LE = ar.take<char>(pr);
-    o.part = ar.take<char>(b->formal_kind == FORMAL_SWEEP ? sweep_scratch_bytes((int)nq, (int)nz) : 0);
-    o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(sweep ? 0 : nq * nz);
-    o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
-    o.Rup = ar.take<double>(nt * nz); o.Rdn = ar.take<double>(nt * nz);
-    o.dRup = ar.take<double>(nt * nz); o.dRdn = ar.take<double>(nt * nz);
-    o.Apart = ar.take<double>(nt * nz * nl);
-    o.rh = ar.take<double>(nt * nz * kRhStride);
-    o.F = ar.take<double>(N); o.dF = ar.take<double>(N);
-    o.P = ar.take<double>(nz * nl * nl); o.piv = ar.take<int>(nz * nl);
-    o.Iem = ar.take<double>(nq * nmu);
-    o.Vb = ar.take<double>((kmax + 1) * N); o.Hh = ar.take<double>((kmax + 1) * kmax);
-    o.cs = ar.take<double>(kmax); o.sn = ar.take<double>(kmax); o.gv = ar.take<double>(kmax + 1);
-    o.x = ar.take<double>(N); o.w = ar.take<double>(N); o.nprev = ar.take<double>(N);
-  }
+  std::vector<size_t> off(nc);
+  for (int c = 0; c < nc; ++c)
+    off[c] = ar.take<char>(column_bytes(*cols[c], b->formal_kind, mixed, kmax, nullptr));
   size_t o_cols = ar.take<ColDesc>(nc);
   size_t o_state = ar.take<SolverState>(nc);
   size_t o_status = ar.take<int>(nc);
@@ -111,44 +155,8 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   b->d_status = ar.ptr<int>(o_status);
   b->d_opts = ar.ptr<SolverOpts>(o_opts);
   b->d_view = ar.ptr<ColDesc>(o_view);
-  for (int c = 0; c < nc; ++c) {
-    const Offs& o = off[c];
-    ColDesc& d = b->h_cols[c];
-    d.t = cols[c]->tables;
-    d.forced_mode = -1;
-    d.mixed = mixed;
-    ColWork& w = d.w;
-    w.n = ar.ptr<double>(o.n); w.v = ar.ptr<double>(o.v);
-    w.Jdag = ar.ptr<double>(o.Jdag); w.Jnew = ar.ptr<double>(o.Jnew);
-    w.istar = ar.ptr<int>(o.istar);
-    w.chi = ar.ptr<void>(o.chi); w.S = ar.ptr<double>(o.S); w.dSk = ar.ptr<void>(o.dSk);
-    w.dchi = ar.ptr<void>(o.dchi); w.dS = ar.ptr<double>(o.dS); w.ddSk = ar.ptr<void>(o.ddSk);
-    const bool sweep = (b->formal_kind == FORMAL_SWEEP);
-    w.v32 = sweep ? ar.ptr<float>(o.v32) : nullptr;
-    w.chiT = sweep ? ar.ptr<float>(o.chiT) : nullptr;
-    w.S32T = sweep ? ar.ptr<float>(o.S32T) : nullptr;
-    w.dSkT = sweep ? ar.ptr<float>(o.dSkT) : nullptr;
-    w.dchiT = sweep ? ar.ptr<float>(o.dchiT) : nullptr;
-    w.dS32T = sweep ? ar.ptr<float>(o.dS32T) : nullptr;
-    w.dJ32T = sweep ? ar.ptr<float>(o.dJ32T) : nullptr;
-    if (sweep) w.dchi = nullptr;
-    w.H = ar.ptr<void>(o.H); w.dH = ar.ptr<void>(o.dH); w.HI = ar.ptr<void>(o.HI);
-    w.LX = ar.ptr<void>(o.LX); w.LE = ar.ptr<void>(o.LE);
-    w.part = ar.ptr<void>(o.part);
-    w.J = ar.ptr<double>(o.J); w.dJ = ar.ptr<double>(o.dJ);
-    if (sweep) { w.dS = nullptr; w.dJ = nullptr; }   // the mixed tangent path is FP32 throughout
-    w.Lchi = ar.ptr<double>(o.Lchi); w.Leta = ar.ptr<double>(o.Leta);
-    w.zeta = nullptr;
-    w.Rup = ar.ptr<double>(o.Rup); w.Rdn = ar.ptr<double>(o.Rdn);
-    w.dRup = ar.ptr<double>(o.dRup); w.dRdn = ar.ptr<double>(o.dRdn);
-    w.Apart = ar.ptr<double>(o.Apart); w.rh = ar.ptr<double>(o.rh);
-    w.F = ar.ptr<double>(o.F); w.dF = ar.ptr<double>(o.dF);
-    w.P = ar.ptr<double>(o.P); w.piv = ar.ptr<int>(o.piv); w.Iem = ar.ptr<double>(o.Iem);
-    w.Vb = ar.ptr<double>(o.Vb); w.Hh = ar.ptr<double>(o.Hh);
-    w.cs = ar.ptr<double>(o.cs); w.sn = ar.ptr<double>(o.sn); w.gv = ar.ptr<double>(o.gv);
-    w.x = ar.ptr<double>(o.x); w.w = ar.ptr<double>(o.w); w.nprev = ar.ptr<double>(o.nprev);
-    w.st = b->d_state + c;
-  }
+  for (int c = 0; c < nc; ++c)
+    column_bind(ar.base + off[c], *cols[c], b->formal_kind, mixed, kmax, b->d_state + c, &b->h_cols[c]);
   JFNK_CUDA(cudaMemcpy(b->d_cols, b->h_cols.data(), nc * sizeof(ColDesc), cudaMemcpyHostToDevice));
   JFNK_CUDA(cudaMemset(b->d_state, 0, nc * sizeof(SolverState)));
   if (b->formal_kind == FORMAL_SWEEP) return sweep_prepare(b);
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
                                                 const SolverOpts* __restrict__ opts,
                                                 int* status_out) {
   const ColDesc& cd = cols[blockIdx.x];
-  const SolverOpts o = *opts;
+  const SolverOpts o = cd.opts ? *cd.opts : *opts;
   SolverState* st = cd.w.st;
   __shared__ double sh[32];
   __shared__ double s_h[kMaxKrylov + 1];
