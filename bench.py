@@ -42,8 +42,12 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="ca", choices=["ca", "two-level", "h", "batch"])
+    p.add_argument("--workload", default="ca", choices=["ca", "two-level", "h", "batch", "serve"])
     p.add_argument("--columns", type=int, default=4096, help="batch workload: number of columns")
+    p.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
+    p.add_argument("--rate", type=float, default=2000.0, help="serve workload: Poisson arrival rate [1/s]")
+    p.add_argument("--slots", type=int, default=512, help="serve workload: columns in flight")
+    p.add_argument("--producers", type=int, default=4, help="serve workload: threads building requests")
     p.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -418,6 +422,110 @@ def run_batch(args, rank, ws, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def serve_options(atom):
+    """Start options per atom kind of the serving stream: the H I-like columns
+    need a longer RH92 warm-up (Sect. 3.5 hybrid) than the others."""
+    from paper_2406_17234_gb300 import binding as B
+    if atom.name.startswith("H"):
+        return B.default_options(precision=B.JFNK_MIXED, rh92_warmup=60, rh92_switch=0.03)
+    return B.default_options(precision=B.JFNK_MIXED, rh92_warmup=10, rh92_switch=0.1)
+
+
+def run_serve(args, rank, ws, local, dist):
+    """Serving stream (continuous batching): requests arrive on a seeded Poisson
+    schedule; a producer thread builds each request's atom and atmosphere
+    tables at its arrival time and submits it; the main thread steps the
+    server and retires results. Latency = completion - scheduled arrival, so a
+    request that waits (for the producer, a slot or memory) pays for it."""
+    import threading
+    import torch
+    from paper_2406_17234_gb300 import binding as B
+    wl = W.config5(n_requests=args.requests, rate=args.rate, seed=20240624 + rank)
+    torch.cuda.set_device(local)
+    ctx = B.Context(local)
+    # slot shape: the stream's largest column (frequency counts from the atoms)
+    max_nq = max(sum(l.n_nu for l in a.lines) + sum(c.n_nu for c in a.conts) for a in wl.atoms)
+    sv = B.Server(ctx, max_slots=args.slots, max_depth=max(c.n_depth for c in wl.columns), max_freq=max_nq,
+                  max_levels=max(a.n_levels for a in wl.atoms),
+                  max_trans=max(len(a.lines) + len(a.conts) for a in wl.atoms), max_mu=wl.n_mu,
+                  opts=serve_options(wl.atoms[1]))
+    n = len(wl.columns)
+    live = {}                     # id -> (atom, atmosphere) until retired
+    lock = threading.Lock()
+    window = threading.Semaphore(4 * args.slots)   # requests built but not retired
+    err = []
+    t_start = sv.clock()
+    arrivals = t_start + np.asarray(wl.arrivals)
+
+    def producer(first):
+        try:
+            for r in range(first, n, args.producers):
+                window.acquire()
+                wait = arrivals[r] - sv.clock()
+                if wait > 0:
+                    time.sleep(wait)
+                atom = B.Atom(ctx, wl.atoms[r])
+                atm = B.Atmosphere(ctx, atom, wl.columns[r], n_mu=wl.n_mu)
+                with lock:
+                    live[r] = (atom, atm)
+                sv.submit(atm, r, serve_options(wl.atoms[r]))
+        except Exception as e:   # surfaced by the main thread
+            err.append(e)
+
+    ths = [threading.Thread(target=producer, args=(i,), daemon=True) for i in range(args.producers)]
+    clk = clocks_start() if rank == 0 else None
+    for th in ths:
+        th.start()
+    done = []
+    while len(done) < n and not err:
+        active, queued = sv.step()
+        res = sv.poll()
+        for r in res:
+            with lock:
+                live.pop(r["id"], None)
+            window.release()
+        done += res
+        if active == 0 and not res:
+            time.sleep(2e-4)
+    for th in ths:
+        th.join()
+    clocks = clocks_stop(clk, local) if rank == 0 else None
+    if err:
+        raise err[0]
+    t_end = max(r["t_done"] for r in done)
+    conv = [r for r in done if r["status"] == 0]
+    lat = np.array([r["t_done"] - arrivals[r["id"]] for r in done])
+    pts = float(sum(r["stats"]["ray_points"] for r in done))
+    wall = t_end - t_start
+    sv.close()
+    if dist is not None:
+        t = torch.tensor([wall, len(conv), pts], dtype=torch.float64, device="cuda")
+        tmax = t.clone(); dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone(); dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        wall, nconv, pts = float(tmax[0]), float(tsum[1]), float(tsum[2])
+    else:
+        nconv = float(len(conv))
+    if rank != 0:
+        return
+    line = {"metric": "converged NLTE columns/s", "value": nconv / wall, "unit": "columns/s", "n_gpus": ws,
+            "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 formal solution / f64 rates, Krylov, Newton", "data": "synthetic",
+            "config": {"workload": f"serving: {n} column solves, Poisson arrivals at {args.rate:g}/s, atoms "
+                                   "20 % two-level / 40 % Ca II-like / 40 % H I-like, depths 48-300, "
+                                   "500-2000 frequencies, mixed precision, continuous batching",
+                       "slots": args.slots, "requests": n,
+                       "l2": "inputs of the in-flight columns exceed L2 (work buffers of hundreds of columns)"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
+            "queueing_ms": {  # where the latency goes: building the request, waiting for a slot, solving
+                "submit_after_arrival_p50": float(np.median([r["t_submit"] - arrivals[r["id"]] for r in done]) * 1e3),
+                "admit_after_submit_p50": float(np.median([r["t_admit"] - r["t_submit"] for r in done]) * 1e3),
+                "solve_p50": float(np.median([r["t_done"] - r["t_admit"] for r in done]) * 1e3)},
+            "producer_threads": args.producers,
+            "converged_fraction": len(conv) / n, "ray_points_per_s": pts / wall,
+            "offered_rate": args.rate, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, ws, local, dist = dist_setup()
@@ -425,6 +533,8 @@ def main():
         run_reference(args, rank, ws, dist)
     elif args.workload == "batch":
         run_batch(args, rank, ws, local, dist)
+    elif args.workload == "serve":
+        run_serve(args, rank, ws, local, dist)
     else:
         run_ours(args, rank, ws, local, dist)
     if dist is not None:
