@@ -168,6 +168,52 @@ def cpu_baseline(wl, budget_s=20.0):
                       f"of the same column at LTE, {dt:.1f} s, numpy FP64/complex128 single thread"}
 
 
+# Algorithmic work per ray-point (value / JVP evaluation): FP32-pipe
+# instructions and MUFU operations (exp and reciprocal), after the unit count
+# of the path (Delta tau, exp, 1/Delta tau, w a b, I update, J accumulation;
+# the tangent adds the differentiated recurrence).
+ALG_OPS = {"value": (10, 2), "jvp": (26, 2)}
+FORMAL_KERNELS = {0: "k_formal<double> + k_ray_sum (per-ray buffers)", 1: "k_formal_fused<double>",
+                  2: "k_formal_sweep (thread per frequency)", 3: "k_formal_sweep_warp (warp per frequency pair)"}
+
+
+def alu_roofline(B, ctx, fp64, n_value, n_jvp, pts_per_launch, kern_ms, launches, clocks, kernel, device):
+    """Roofline of the formal-solution kernel against the ALU peak derived from
+    unit counts and the SM clock sampled during the run: per SM and clock 128
+    FP32 lanes and 16 MUFU operations (the mixed path is bound by the slower of
+    the two); FP64 at the nominal 1.25 TFLOP/s dense rate, with exp and the
+    reciprocal as software sequences whose FP64-pipe cost is measured
+    (jfnk_probe_alu). Achieved = ray-points per launch / mean launch time
+    (in-graph CUDA events around the formal kernels of every tick)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    clk = mhz * 1e6
+    w_v, w_j = n_value / max(1, n_value + n_jvp), n_jvp / max(1, n_value + n_jvp)
+    if fp64:
+        fma = B.probe_alu(ctx, 0)                 # FP64 flop/s measured (FMA = 2)
+        c_exp = fma / B.probe_alu(ctx, 2)         # exp in FP64-pipe flops
+        fp_rate = 1.25e12 / 2                     # nominal FP64 FMA instructions/s
+        t = {m: (ops + mufu * c_exp / 2) / fp_rate for m, (ops, mufu) in ALG_OPS.items()}
+        src = "nominal FP64 1.25 TFLOP/s dense (FMA instr/s = half); exp/rcp cost from jfnk_probe_alu"
+    else:
+        fp_rate, mufu_rate = sms * 128 * clk, sms * 16 * clk
+        t = {m: max(ops / fp_rate, mufu / mufu_rate) for m, (ops, mufu) in ALG_OPS.items()}
+        src = f"{sms} SMs x (128 FP32 lanes, 16 MUFU) x {mhz:.0f} MHz sampled SM clock"
+    peak = 1.0 / (w_v * t["value"] + w_j * t["jvp"])          # ray-points/s
+    avg_s = kern_ms * 1e-3 / max(1, launches)
+    achieved = pts_per_launch / avg_s if avg_s > 0 else 0.0
+    key = "formal_fp64" if fp64 else "formal_fp32"
+    traffic_pp = measured_traffic(key)
+    return {"bound": "alu", "kernel": FORMAL_KERNELS.get(kernel, str(kernel)),
+            "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G ray-points/s",
+            "frac": achieved / peak,
+            "traffic": None if traffic_pp is None else traffic_pp * pts_per_launch,
+            "ops_per_ray_point": {"value": ALG_OPS["value"], "jvp": ALG_OPS["jvp"],
+                                  "mix": {"value": w_v, "jvp": w_j}},
+            "avg_launch_us": avg_s * 1e6, "launches": launches, "peak_source": src}
+
+
 def run_reference(args, rank, ws, dist):
     if rank != 0:
         return
@@ -293,29 +339,15 @@ def run_ours(args, rank, ws, local, dist):
     lat = np.array(times)
     cols_per_s = ws * args.steps / (total_ms * 1e-3)
     s0 = stats[-1]
-    # roofline of the formal-solution kernel (dominant): algorithmic work per launch / event time
+    # roofline of the formal-solution kernel (dominant)
     launches = sum(s["formal_launches"] for s in stats)
     kern_ms = sum(s["formal_ms"] for s in stats)
     fp64 = precision == B.JFNK_FP64
-    fma_peak = B.probe_alu(ctx, 0 if fp64 else 1)
-    exp_rate = B.probe_alu(ctx, 2 if fp64 else 3)
-    exp_cost = fma_peak / exp_rate          # exp in FMA-pipe flop equivalents (measured)
     n_jvp = sum(s["jvp_calls"] for s in stats)
     n_all = sum(s["F_calls"] for s in stats)
-    n_base = n_all - n_jvp
-    flops_pt = (n_base * (9 + 13) + n_jvp * (9 + 12)) / max(1, n_all) + exp_cost
-    per_launch_pts = atm.ray_points
-    achieved = per_launch_pts * flops_pt / (kern_ms / max(1, launches) * 1e-3)
-    key = "formal_fp64" if fp64 else "formal_fp32"
-    traffic_pp = measured_traffic(key)
-    roofline = {"bound": "alu", "kernel": f"k_formal<{'double' if fp64 else 'float'}>",
-                "achieved": achieved / 1e9, "peak": fma_peak / 1e9, "unit": "GFLOP/s",
-                "frac": achieved / fma_peak,
-                "traffic": None if traffic_pp is None else traffic_pp * per_launch_pts,
-                "flops_per_ray_point": flops_pt, "exp_cost_flops": exp_cost,
-                "avg_launch_us": 1e3 * kern_ms / max(1, launches), "launches": launches,
-                "share_of_step": kern_ms / total_ms,
-                "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA throughput (jfnk_probe_alu) on this GPU"}
+    roofline = alu_roofline(B, ctx, fp64, n_all - n_jvp, n_jvp, atm.ray_points, kern_ms, launches,
+                            clocks, s0["formal_kernel"], local)
+    roofline["share_of_step"] = kern_ms / total_ms
     gpu_launches = int(sum(s["kernel_launches"] for s in stats))
     line = {"metric": METRIC, "value": value, "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -401,6 +433,11 @@ def run_batch(args, rank, ws, local, dist):
     st0 = allstats[-1]
     launches = sum(s["formal_launches"] for s in st0[:1]) * args.steps
     kern_ms = sum(st[0]["formal_ms"] for st in allstats)
+    n_jvp = sum(s["jvp_calls"] for st in allstats for s in st)
+    n_all = sum(s["F_calls"] for st in allstats for s in st)
+    roofline = alu_roofline(B, ctx, False, n_all - n_jvp, n_jvp, pts / max(1, launches), kern_ms, launches,
+                            clocks, st0[0]["formal_kernel"], local)
+    roofline["share_of_step"] = kern_ms / total_ms
     nz = [a.n_depth for a in atms]
     line = {"metric": METRIC, "value": pts / (total_ms * 1e-3), "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -418,7 +455,9 @@ def run_batch(args, rank, ws, local, dist):
             "formal_kernel": {"avg_launch_ms": kern_ms / max(1, launches), "launches": launches,
                               "share_of_step": kern_ms / total_ms, "qb": st0[0]["formal_qb"],
                               "threads": st0[0]["formal_threads"]},
-            "max_ticks": max(s["F_calls"] for s in st0), "setup_s": setup_s, "clocks": clocks}
+            "max_ticks": max(s["F_calls"] for s in st0), "setup_s": setup_s,
+            "roofline": roofline, "gpu_launches": int(st0[0]["kernel_launches"]) * args.steps,
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
