@@ -84,6 +84,26 @@ def dist_setup():
     return rank, ws, local, dist
 
 
+def reduce_ranks(dist, values, device="cuda"):
+    """Whole-job aggregates over the ranks of a weak-scaling run: the maximum
+    (times: the slowest rank sets the job's time) and the sum (work done) of
+    each value. Returns (max list, sum list); a single process returns its own."""
+    if dist is None:
+        return list(values), list(values)
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return tmax.tolist(), tsum.tolist()
+
+
+def rank_seed(base, rank):
+    """Seed of a rank's share of a sharded workload (distinct columns per rank)."""
+    return base + rank
+
+
 def clocks_start():
     try:
         return subprocess.Popen(
@@ -325,16 +345,8 @@ def run_ours(args, rank, ws, local, dist):
         e2e_times.append(time.perf_counter() - t0)
         B.check(rc, "jfnk_solve (host)")
         e2e_pts += st2.ray_points
-    if dist is not None:
-        t = torch.tensor([total_ms, pts, sum(e2e_times), e2e_pts], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, pts = float(tmax[0]), float(tsum[1])
-        e2e_s, e2e_pts_all = float(tmax[2]), float(tsum[3])
-    else:
-        e2e_s, e2e_pts_all = sum(e2e_times), e2e_pts
+    mx, sm = reduce_ranks(dist, [total_ms, pts, sum(e2e_times), e2e_pts], dev)
+    total_ms, pts, e2e_s, e2e_pts_all = mx[0], sm[1], mx[2], sm[3]
     if rank != 0:
         return
     value = pts / (total_ms * 1e-3)
@@ -378,7 +390,7 @@ def run_batch(args, rank, ws, local, dist):
     against the plain FP64 path that solves one column per launch sequence."""
     import torch
     from paper_2406_17234_gb300 import binding as B
-    wl = W.config4(n_columns=args.columns, seed=20240624 + rank)
+    wl = W.config4(n_columns=args.columns, seed=rank_seed(20240624, rank))
     torch.cuda.set_device(local)
     ctx = B.Context(local)
     atom = B.Atom(ctx, wl.atom)
@@ -427,11 +439,8 @@ def run_batch(args, rank, ws, local, dist):
         _, _, s1 = B.solve(a, B.default_options(**start), raise_on_fail=False)
         fp64_t.append(time.perf_counter() - ta)
     fp64_cols_s = nsample / sum(fp64_t)
-    if dist is not None:
-        t = torch.tensor([total_ms, pts, conv], dtype=torch.float64, device="cuda")
-        tmax = t.clone(); dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone(); dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms, pts, conv = float(tmax[0]), float(tsum[1]), float(tsum[2])
+    mx, sm = reduce_ranks(dist, [total_ms, pts, conv])
+    total_ms, pts, conv = mx[0], sm[1], sm[2]
     if rank != 0:
         return
     st0 = allstats[-1]
@@ -483,7 +492,7 @@ def run_serve(args, rank, ws, local, dist):
     import threading
     import torch
     from paper_2406_17234_gb300 import binding as B
-    wl = W.config5(n_requests=args.requests, rate=args.rate, seed=20240624 + rank)
+    wl = W.config5(n_requests=args.requests, rate=args.rate, seed=rank_seed(20240624, rank))
     torch.cuda.set_device(local)
     ctx = B.Context(local)
     # slot shape: the stream's largest column (frequency counts from the atoms)
@@ -541,13 +550,8 @@ def run_serve(args, rank, ws, local, dist):
     pts = float(sum(r["stats"]["ray_points"] for r in done))
     wall = t_end - t_start
     sv.close()
-    if dist is not None:
-        t = torch.tensor([wall, len(conv), pts], dtype=torch.float64, device="cuda")
-        tmax = t.clone(); dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone(); dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        wall, nconv, pts = float(tmax[0]), float(tsum[1]), float(tsum[2])
-    else:
-        nconv = float(len(conv))
+    mx, sm = reduce_ranks(dist, [wall, len(conv), pts])
+    wall, nconv, pts = mx[0], sm[1], sm[2]
     if rank != 0:
         return
     line = {"metric": "converged NLTE columns/s", "value": nconv / wall, "unit": "columns/s", "n_gpus": ws,
