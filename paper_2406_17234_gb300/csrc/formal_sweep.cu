@@ -55,6 +55,9 @@ struct StepIn {
   float rs;      // 1/(chi^k + chi^u)
   float dzk;     // |z_k - z_u|
   float idzk;    // 1/|z_k - z_u|
+  float tz;      // |dz| (chi^k + chi^u):   dtau = tz / (2 mu)
+  float rz;      // 1/(|dz| (chi^k + chi^u)): 1/dtau = rz 2 mu
+  float dtz;     // |dz| (dchi^k + dchi^u): ddtau = dtz / (2 mu)
   float dSin;    // S^u - S^k (formed in FP64)
   float S0, Su;  // S^k, S^u
   float rc0;     // 1/chi^k
@@ -81,20 +84,21 @@ template <bool TAN>
 __device__ __forceinline__ RayOut ray_step(const StepIn& in, float inv2mu, float two_mu, float hw, float& D,
                                            float& I, float& M, float& dD) {
   RayOut o;
-  const float h = mul(in.dzk, inv2mu);
-  const float dtau = mul(h, in.csum);
-  const float rdt = mul(in.rs, mul(in.idzk, two_mu));
+  // the depth's factors are formed once per depth (StepIn), one multiply per angle here
+  const float dtau = mul(in.tz, inv2mu);
+  const float rdt = mul(in.rz, two_mu);
   float e, w, a, bq;
   pl_coef_rn(dtau, rdt, e, w, a, bq);
   const float Du = D;
   float Dn = fma3(Du, e, mul(w, in.dSin));
   if (TAN) {
-    const float ddtau = mul(h, in.dcs);
+    const float ddtau = mul(in.dtz, inv2mu);
     const float dDn = fma3(dD, e, fma3(-ddtau, fma3(e, Du, mul(bq, in.dSin)), mul(w, in.ddSin)));
     dD = dDn;
     o.xd = mul(hw, dDn);
     o.xD = o.xI = o.xx = o.xe = 0.f;
   } else {
+    const float h = mul(in.dzk, inv2mu);
     const float In = fma3(I, e, fma3(a, in.S0, mul(mul(bq, dtau), in.Su)));
     const float lx = -fma3(mul(in.S0, in.rc0), a, mul(h, fma3(in.dSin, bq, mul(e, Du))));
     o.xI = mul(hw, In);
@@ -275,10 +279,14 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     in.rs = rcp_approx(in.csum);
     in.dzk = s_dz[kd];
     in.idzk = s_idz[kd];
+    in.tz = mul(in.dzk, in.csum);
+    in.rz = mul(in.rs, in.idzk);
+    in.dtz = 0.f;
     if (TAN) {
       in.dSin = UP ? dSl : -dSl;
       in.S0 = in.Su = in.rc0 = 0.f;
       in.dcs = add(dc0, dcp);
+      in.dtz = mul(in.dzk, in.dcs);
       in.ddSin = sub(dSp, dS0);
     } else {
       in.dSin = __double2float_rn(__dsub_rn(Sp, Sk64));
@@ -424,25 +432,44 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
     }
   };
   store(k0);
+  // the next depth's inputs are loaded one step ahead (latency off the chain)
+  float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f;
+  double S_n = 0.0;
+  auto load = [&](int s) {
+    const int k = up ? nz - 1 - s : s;
+    const int kd = up ? k : k - 1;
+    if (TAN) {
+      c_n = chiT[(size_t)k * pitch];
+      tan_in(k, dc_n, dS_n);
+      dSl_n = dSkT[(size_t)kd * pitch];
+    } else {
+      c_n = chi[k];
+      if (m == 0) S_n = S64[k];
+    }
+  };
+  if (nz > 1) load(1);
   for (int s = 1; s < nz; ++s) {
     const int k = up ? nz - 1 - s : s;
     const int kd = up ? k : k - 1;
     StepIn in;
-    float c0, dc0 = 0.f, dS0 = 0.f;
+    const float c0 = c_n;
+    float dc0 = 0.f, dS0 = 0.f;
+    const float dSl = dSl_n;
+    const double Sk64 = S_n;
     if (TAN) {
-      c0 = chiT[(size_t)k * pitch];
-      tan_in(k, dc0, dS0);
-      const float dSl = dSkT[(size_t)kd * pitch];
+      dc0 = dc_n;
+      dS0 = dS_n;
+    }
+    if (s + 1 < nz) load(s + 1);
+    if (TAN) {
       in.dSin = up ? dSl : -dSl;
       in.S0 = in.Su = in.rc0 = 0.f;
       in.dcs = add(dc0, dcp);
       in.ddSin = sub(dSp, dS0);
     } else {
-      c0 = chi[k];
       // the FP64 difference is formed once per hemisphere (angle lane 0)
       float dSin = 0.f, S0 = 0.f;
       if (m == 0) {
-        const double Sk64 = S64[k];
         dSin = __double2float_rn(__dsub_rn(Sp, Sk64));
         S0 = __double2float_rn(Sk64);
         Sp = Sk64;
@@ -462,6 +489,9 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
     in.rs = rcp_approx(in.csum);
     in.dzk = s_dz[kd];
     in.idzk = s_idz[kd];
+    in.tz = mul(in.dzk, in.csum);
+    in.rz = mul(in.rs, in.idzk);
+    in.dtz = TAN ? mul(in.dzk, in.dcs) : 0.f;
     if (on) {
       r = ray_step<TAN>(in, inv2mu, two_mu, hw, D, I, M, dD);
     } else {
