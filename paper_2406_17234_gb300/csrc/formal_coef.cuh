@@ -22,24 +22,31 @@ __device__ __forceinline__ int eval_mode_f(const ColDesc& cd) {
 // a = 1 - w and bq = (w - e)/x, each from its own Taylor series below
 // x = 0.1 (where 1 - e, 1 - w and w - e cancel); r = 1/x is supplied by the
 // caller (shared between the rays of a layer).
+// FP64 Taylor coefficients: w = sum_{n>=0} (-x)^n/(n+1)!,
+// a/x = sum_{n>=0} (-x)^n/(n+2)!, bq = sum_{n>=0} (-x)^n (n+1)/(n+2)!.
+__device__ __forceinline__ void pl_series64(double x, double& w, double& a, double& bq) {
+  // terms up to n = 5: below x = 1e-3 the first omitted one is < 3e-23 relative
+  constexpr double f[8] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040};
+  double pw = 0.0, pa = 0.0, pb = 0.0;
+#pragma unroll
+  for (int m = 5; m >= 0; --m) {
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    pw = fma(pw, x, sg * f[m + 1]);
+    pa = fma(pa, x, sg * f[m + 2]);
+    pb = fma(pb, x, sg * (m + 1) * f[m + 2]);
+  }
+  w = pw;
+  a = pa * x;
+  bq = pb;
+}
+
+// In FP64 the direct forms of w, a and bq lose about 1e-16/x^2 relative
+// (1 - e, 1 - w and w - e cancel): 2e-10 at x = 1e-3, so the series takes
+// over below x = 1e-3 only.
 __device__ __forceinline__ void pl_coef_f(double x, double r, double& e, double& w, double& a, double& bq) {
   e = exp(-x);
-  if (x < 0.1) {
-    double pw = 0.0, pa = 0.0, pb = 0.0;
-    double inv_fact[17];
-    inv_fact[0] = 1.0;
-#pragma unroll
-    for (int m = 1; m < 17; ++m) inv_fact[m] = inv_fact[m - 1] / m;
-#pragma unroll
-    for (int m = 13; m >= 0; --m) {
-      const double sg = (m & 1) ? -1.0 : 1.0;
-      pw = pw * x + sg * inv_fact[m + 1];
-      pa = pa * x + sg * inv_fact[m + 2];
-      pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
-    }
-    w = pw;
-    a = pa * x;
-    bq = pb;
+  if (x < 1e-3) {
+    pl_series64(x, w, a, bq);
   } else {
     w = (1.0 - e) * r;
     a = 1.0 - w;

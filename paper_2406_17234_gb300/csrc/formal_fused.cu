@@ -90,6 +90,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     if (tan) {
       s_dchi[i] = dchi_g[o];
       s_ddS[i] = (k < nz - 1) ? (real)(dS64[o + 1] - dS64[o]) : (real)0;
+    } else {
+      s_dchi[i] = (real)1 / chi_g[o];   // base evaluations: 1/chi^k, shared by the 2 n_mu rays
     }
   }
   for (int ql = threadIdx.x; ql < nqb; ql += blockDim.x) {
@@ -145,8 +147,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
       } else if (der) {
         const real S0 = s_S[ql * nz + k], Su = s_S[ql * nz + ku];
         P1[si] = a * S0 + bq * dtau * Su;
-        P2[si] = hw * (-(S0 / c0) * a - h * dSin * bq);
-        LE[si] = hw * (a / c0);
+        const real rc0 = s_dchi[ql * nz + k];   // 1/chi^k (base evaluations)
+        P2[si] = hw * (-(S0 * rc0) * a - h * dSin * bq);
+        LE[si] = hw * (a * rc0);
       }
     }
   }

@@ -220,27 +220,13 @@ __global__ void k_source_diff(const ColDesc* __restrict__ cols) {
 
 // Piecewise-linear coefficients (App. A.1) in the form the difference
 // recurrence needs: e = exp(-x), w = (1 - e)/x, a = 1 - w and bq = b/x with
-// b = w - e. Below x = 0.1 every one of them comes from its own Taylor series,
-// since 1 - e, 1 - w and w - e all cancel there (a = 1 - w loses all FP32
-// digits at x ~ 1e-6).
+// b = w - e. Below a threshold every one of them comes from its own Taylor
+// series, since 1 - e, 1 - w and w - e all cancel there (a = 1 - w loses all
+// FP32 digits at x ~ 1e-6): x = 0.1 in FP32, x = 1e-3 in FP64.
 __device__ __forceinline__ void pl_coef(double x, double& e, double& w, double& a, double& bq) {
   e = exp(-x);
-  if (x < 0.1) {
-    // w = sum_{n>=0} (-x)^n/(n+1)!, a = sum_{n>=1} (-1)^{n+1} x^n/(n+1)!,
-    // bq = sum_{n>=1} (-1)^{n+1} n x^{n-1}/(n+1)!
-    double pw = 0.0, pa = 0.0, pb = 0.0;
-    double inv_fact[17];
-    inv_fact[0] = 1.0;
-    for (int m = 1; m < 17; ++m) inv_fact[m] = inv_fact[m - 1] / m;
-    for (int m = 13; m >= 0; --m) {
-      const double sg = (m & 1) ? -1.0 : 1.0;
-      pw = pw * x + sg * inv_fact[m + 1];
-      pa = pa * x + sg * inv_fact[m + 2];
-      pb = pb * x + sg * (m + 1) * inv_fact[m + 2];
-    }
-    w = pw;
-    a = pa * x;
-    bq = pb;
+  if (x < 1e-3) {
+    pl_series64(x, w, a, bq);   // see formal_coef.cuh
   } else {
     const double r = 1.0 / x;
     w = (1.0 - e) * r;
