@@ -23,7 +23,7 @@ namespace jfnk {
 
 constexpr int kFusedThreads = 256;
 constexpr int kFusedSlots = 5;   // E, X(D), P1(dD coef | I), P2(dD | LX), LE
-constexpr int kFusedStage = 6;   // chi, S, dS, dchi, ddS, 1/(chi^k + chi^{k+1}) per (q, k)
+constexpr int kFusedStage = 7;   // chi, S, dS, dchi, ddS, two layer factors per (q, k)
 
 __host__ __device__ inline size_t round16(size_t bytes) { return (bytes + 15) / 16 * 16; }
 
@@ -62,10 +62,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
   real* s_dS = s_S + Qb * nz;
   real* s_dchi = s_dS + Qb * nz;
   real* s_ddS = s_dchi + Qb * nz;
-  real* s_rs = s_ddS + Qb * nz;   // 1/(chi^k + chi^{k+1}) of layer k
-  real* s_Bb = s_rs + Qb * nz;
-  real* s_idz = s_Bb + Qb;        // 1/|z_k - z_{k+1}|
-  real* s_dz = s_idz + nz;        // |z_k - z_{k+1}|
+  real* s_rs = s_ddS + Qb * nz;   // layer k: 1/(|dz| (chi^k + chi^{k+1}))
+  real* s_tz = s_rs + Qb * nz;    // layer k: |dz| (chi^k + chi^{k+1})
+  real* s_Bb = s_tz + Qb * nz;
+  real* s_dz = s_Bb + Qb + nz;    // |z_k - z_{k+1}| (one spare row of nz before it)
   real* s_mu = s_dz + nz;         // per angle: 1/(2 mu), 1/2 w_mu, 2 mu
   real* slot = reinterpret_cast<real*>(smem_raw + round16(sizeof(real) * ((size_t)kFusedStage * Qb * nz + Qb + 2 * nz + 4 * kMaxMu)));
   const size_t plane = (size_t)nz * R;
@@ -84,11 +84,16 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     const int ql = i / nz, k = i - ql * nz;
     const size_t o = (size_t)(qb0 + ql) * nz + k;
     s_chi[i] = chi_g[o];
-    if (k < nz - 1) s_rs[i] = (real)1 / (chi_g[o] + chi_g[o + 1]);   // shared by the 2 n_mu rays of the layer
+    if (k < nz - 1) {   // layer factors shared by the 2 n_mu rays of the layer
+      const real t = (real)T.dz[k] * (chi_g[o] + chi_g[o + 1]);
+      s_tz[i] = t;
+      s_rs[i] = (real)1 / t;
+    }
     s_S[i] = (real)S64[o];
     s_dS[i] = (k < nz - 1) ? (real)(S64[o + 1] - S64[o]) : (real)0;   // formed in FP64
     if (tan) {
-      s_dchi[i] = dchi_g[o];
+      // layer k: |dz| (dchi^k + dchi^{k+1}), so that ddtau = this / (2 mu)
+      s_dchi[i] = (k < nz - 1) ? (real)T.dz[k] * (dchi_g[o] + dchi_g[o + 1]) : (real)0;
       s_ddS[i] = (k < nz - 1) ? (real)(dS64[o + 1] - dS64[o]) : (real)0;
     } else {
       s_dchi[i] = (real)1 / chi_g[o];   // base evaluations: 1/chi^k, shared by the 2 n_mu rays
@@ -99,7 +104,6 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     s_Bb[ql] = (real)(T.Bn[(size_t)q * nz + nz - 1] / T.c2[q]);
   }
   for (int k = threadIdx.x; k < nz - 1; k += blockDim.x) {
-    s_idz[k] = (real)(1.0 / T.dz[k]);
     s_dz[k] = (real)T.dz[k];
   }
   for (int m = threadIdx.x; m < nmu; m += blockDim.x) {
@@ -123,16 +127,18 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
     const real two_mu = s_mu[3 * m + 2];
     const real* ch = s_chi + ql * nz;
     const real* rs = s_rs + ql * nz;
+    const real* tz = s_tz + ql * nz;
     const real* dSq = s_dS + ql * nz;
     const int kbeg = up ? 0 : 1, kend = up ? nz - 1 : nz;   // steps into depth k
     for (int k = kbeg + kl; k < kend; k += klanes) {
       const int ku = up ? k + 1 : k - 1;
       const int kd = up ? k : k - 1;
-      const real c0 = ch[k], cu = ch[ku];
+      const real c0 = ch[k];
       const real h = s_dz[kd] * inv2mu;
-      const real dtau = h * (c0 + cu);
-      // 1/dtau = (2 mu / dz) / (chi^k + chi^u): the layer reciprocal is shared
-      const real rdt = rs[kd] * (s_idz[kd] * two_mu);
+      // dtau = |dz| (chi^k + chi^u) / (2 mu), 1/dtau = 2 mu / (|dz| (chi^k + chi^u)):
+      // the layer's factors are staged once for its 2 n_mu rays
+      const real dtau = tz[kd] * inv2mu;
+      const real rdt = rs[kd] * two_mu;
       real e, w, a, bq;
       pl_coef_f(dtau, rdt, e, w, a, bq);
       const real dSin = up ? dSq[k] : -dSq[k - 1];
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
       E[si] = e;
       X[si] = w * dSin;
       if (tan) {
-        const real ddtau = h * (s_dchi[ql * nz + k] + s_dchi[ql * nz + ku]);
+        const real ddtau = s_dchi[ql * nz + kd] * inv2mu;
         const real ddSin = up ? s_ddS[ql * nz + k] : -s_ddS[ql * nz + k - 1];
         P1[si] = -ddtau * e;
         P2[si] = -ddtau * bq * dSin + w * ddSin;
