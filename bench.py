@@ -398,9 +398,9 @@ def run_batch(args, rank, ws, local, dist):
     atms = [B.Atmosphere(ctx, atom, c, n_mu=wl.n_mu) for c in wl.columns]
     setup_s = time.perf_counter() - t0
     plan = B.BatchPlan(ctx, atms, precision=B.JFNK_MIXED)
-    # hybrid start (Sect. 3.5): at most 10 per-depth limited RH92 iterations,
+    # hybrid start (Sect. 5): at most 5 per-depth limited RH92 iterations,
     # fewer once the population change is below 0.1, then Algorithm 2
-    start = dict(rh92_warmup=10, rh92_switch=0.1)
+    start = dict(rh92_warmup=5, rh92_switch=0.1)
     opts = B.default_options(precision=B.JFNK_MIXED, profile=1, **start)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -459,7 +459,7 @@ def run_batch(args, rank, ws, local, dist):
             "config": {"workload": f"batched 1.5D: {len(atms)} Ca II-like columns, depths "
                                    f"{min(nz)}-{max(nz)}, {atms[0].n_nu} frequencies, 5 mu, T noise 5 %, "
                                    "mixed precision, one batched solve per step",
-                       "columns": len(atms), "init": "LTE, then <= 10 limited RH92 iterations (switch below 0.1 change), then JFNK",
+                       "columns": len(atms), "init": "LTE, then <= 5 limited RH92 iterations (switch below 0.1 change), then JFNK",
                        "l2": "flushed by a 256 MiB device write before every timed step"},
             "columns_per_s": conv / (total_ms * 1e-3),
             "converged_fraction": conv / (len(atms) * args.steps * ws),
