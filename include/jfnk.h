@@ -155,6 +155,8 @@ typedef struct {
   int profile;          /* 1: time the formal-solution kernel of every active tick */
   int formal_variant;   /* mixed mode: 0 autotuned, JFNK_FORMAL_SWEEP_THREAD or
                            JFNK_FORMAL_SWEEP_WARP forced (identical results)      */
+  int precond;          /* 1: block-Jacobi, first solution of Sect. 2.5.2 (default);
+                           0: none (GMRES on J x = -F)                            */
 } jfnk_options;
 
 typedef struct {

@@ -95,6 +95,7 @@ void options_to_device(const jfnk_options* o, SolverOpts* so) {
   so->clamp = o->clamp;
   so->rh92_warmup = o->rh92_warmup;
   so->max_ticks = o->max_ticks;
+  so->precond = o->precond;
 }
 
 int validate_options(const jfnk_options* o) {
@@ -104,8 +105,9 @@ int validate_options(const jfnk_options* o) {
   if (o->krylov_max < 1 || o->krylov_max > kMaxKrylov) return fail(JFNK_E_INVALID, "krylov_max must be in [1, 64]");
   if (o->maxiter < 1 || o->max_restarts < 0 || o->max_ticks < 1) return fail(JFNK_E_INVALID, "iteration limits must be positive");
   if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return fail(JFNK_E_INVALID, "unknown precision");
-  if (o->init != JFNK_INIT_LTE && o->init != JFNK_INIT_USER)
-    return fail(JFNK_E_INVALID, "init must be JFNK_INIT_LTE or JFNK_INIT_USER");
+  if (o->init != JFNK_INIT_LTE && o->init != JFNK_INIT_USER && o->init != JFNK_INIT_ZERO_RADIATION)
+    return fail(JFNK_E_INVALID, "init must be JFNK_INIT_LTE, JFNK_INIT_USER or JFNK_INIT_ZERO_RADIATION");
+  if (o->precond != 0 && o->precond != 1) return fail(JFNK_E_INVALID, "precond must be 0 or 1");
   if (o->rh92_warmup < 0) return fail(JFNK_E_INVALID, "rh92_warmup must be >= 0");
   if (o->formal_variant != 0 && o->formal_variant != JFNK_FORMAL_SWEEP_THREAD &&
       o->formal_variant != JFNK_FORMAL_SWEEP_WARP)
@@ -284,7 +286,7 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
     if (o->init == JFNK_INIT_USER) {
       if (!n_in || !n_in[c]) return fail(JFNK_E_INVALID, "JFNK_INIT_USER needs n_inout");
       if ((rc = copy_in(cd.w.n, n_in[c], N * 8, where, s))) return rc;
-    } else {
+    } else {   // LTE, also the conservation rows of the zero-radiation guess
       JFNK_CUDA(cudaMemcpyAsync(cd.w.n, M.tables.nstar, N * 8, cudaMemcpyDeviceToDevice, s));
     }
     if (J_in && J_in[c]) {
@@ -293,6 +295,7 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
       JFNK_CUDA(cudaMemcpyAsync(cd.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
+  if (o->init == JFNK_INIT_ZERO_RADIATION && (rc = launch_zero_radiation(*b, s))) return rc;
   if (b->formal_kind == FORMAL_SWEEP && o->formal_variant != 0) {
     // a forced sweep variant (results are the same as with the tuned one)
     const int v = o->formal_variant == JFNK_FORMAL_SWEEP_WARP ? 2 : 1;
@@ -417,6 +420,7 @@ void jfnk_default_options(jfnk_options* o) {
   o->max_ticks = 20000;
   o->profile = 0;
   o->formal_variant = 0;
+  o->precond = 1;
 }
 
 int jfnk_init(int device, jfnk_ctx** out) {

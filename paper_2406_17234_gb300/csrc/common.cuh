@@ -86,6 +86,7 @@ struct ColTables {
 struct SolverOpts {
   double ftol, fdrop, rtol, rh92_switch;
   int maxiter, krylov_max, max_restarts, clamp, rh92_warmup, max_ticks;
+  int precond;   // 1: apply P^{-1} (block Jacobi); 0: no preconditioning
 };
 
 // Per-column solver state (device memory, written by the Krylov kernel only).

@@ -158,6 +158,9 @@ int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out);
 int batch_set_forced_mode(Batch* b, int mode, cudaStream_t s);
 // Conservation rows from the current populations.
 int launch_istar(const Batch& b, cudaStream_t s);
+// Zero-radiation initial guess (rate equations with I = 0) in every column's n;
+// reads n = LTE populations for the conservation rows.
+int launch_zero_radiation(const Batch& b, cudaStream_t s);
 // RH92 per-depth update from an EV_RH92 evaluation (explicit API path).
 int launch_rh92_update(const Batch& b, cudaStream_t s);
 

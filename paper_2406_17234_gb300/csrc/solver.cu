@@ -277,10 +277,15 @@ __device__ double rh92_depth(const ColDesc& cd, int k, bool clamp) {
 // Krylov / Newton step: one CTA per column
 // ---------------------------------------------------------------------------
 __device__ void apply_pinv(const ColDesc& cd, const double* in, double sign_in, const double* in2,
-                           double sign_in2, double* out) {
+                           double sign_in2, double* out, bool precond = true) {
   // out = P^{-1} (sign_in in + sign_in2 in2): w.P holds the explicit block
   // inverses after a solver base evaluation; one thread per (depth, row)
   const int nz = cd.t.nz, nl = cd.t.nl;
+  if (!precond) {   // no preconditioning: out = sign_in in + sign_in2 in2
+    for (int idx = threadIdx.x; idx < nz * nl; idx += blockDim.x)
+      out[idx] = sign_in * in[idx] + (in2 ? sign_in2 * in2[idx] : 0.0);
+    return;
+  }
   for (int idx = threadIdx.x; idx < nz * nl; idx += blockDim.x) {
     const int k = idx / nl, i = idx - k * nl;
     const double* Pi = cd.w.P + ((size_t)k * nl + i) * nl;
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       return;
     }
     // r0 = -P^{-1} F (x0 = 0)
-    apply_pinv(cd, cd.w.F, -1.0, nullptr, 0.0, w);
+    apply_pinv(cd, cd.w.F, -1.0, nullptr, 0.0, w, o.precond != 0);
     for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = 0.0;
     __syncthreads();
     double ss = 0.0;
@@ -390,7 +395,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
     // a Jacobian-vector product J u is in dF (u = V_j or u = x)
     if (threadIdx.x == 0) { st->F_calls++; st->jvp_calls++; st->ticks++; }
     if (phase == PH_RESTART) {
-      apply_pinv(cd, cd.w.F, -1.0, cd.w.dF, -1.0, w);   // r = P^{-1}(-F - J x)
+      apply_pinv(cd, cd.w.F, -1.0, cd.w.dF, -1.0, w, o.precond != 0);   // r = P^{-1}(-F - J x)
       __syncthreads();
       double ss = 0.0;
       for (int i = threadIdx.x; i < N; i += blockDim.x) ss += w[i] * w[i];
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       }
     } else {
       const int j = st->j;
-      apply_pinv(cd, cd.w.dF, 1.0, nullptr, 0.0, w);
+      apply_pinv(cd, cd.w.dF, 1.0, nullptr, 0.0, w, o.precond != 0);
       __syncthreads();
       // classical Gram-Schmidt, twice (CGS2)
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -553,6 +558,51 @@ __global__ void k_rh92_apply(const ColDesc* __restrict__ cols) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= cd.t.nz) return;
   rh92_depth(cd, k, false);   // the plain update: jfnk_rh92_update applies no limiting
+}
+
+// Zero-radiation initial guess (Sect. 2.2.1): the rate equations with I = 0,
+// i.e. collisions plus spontaneous radiative rates R_ji = sum_nu W g V
+// 2 h nu^3/c^2 (the J = 0 limit of Eqs. Rij/Rji), with the conservation row on
+// the most populated LTE level; one thread per depth. Expects n = LTE.
+__global__ void k_zero_radiation(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const ColTables& T = cd.t;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= T.nz) return;
+  const int nl = T.nl, nt = T.nt, nz = T.nz;
+  double M[kMaxL * kMaxL], rhs[kMaxL];
+  for (int i = 0; i < nl * nl; ++i) M[i] = 0.0;
+  const double* C = T.C + (size_t)k * nl * nl;
+  for (int t = 0; t < nt; ++t) {
+    const int lo = T.t_lo[t], up = T.t_up[t], q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
+    double rdn = 0.0;
+    for (int q = q0; q <= q1; ++q) {
+      const size_t p = (size_t)(base + q - q0);
+      rdn += T.t_w[p] * T.rw[q] * T.G[p * nz + k] * T.V[p * nz + k] * T.c2[q];
+    }
+    const double ur = C[lo * nl + up], dr = C[up * nl + lo] + rdn;
+    // d n_lo/dt = -n_lo ur + n_up dr, d n_up/dt = +n_lo ur - n_up dr
+    M[lo * nl + lo] += ur;
+    M[lo * nl + up] -= dr;
+    M[up * nl + lo] -= ur;
+    M[up * nl + up] += dr;
+  }
+  double* n = cd.w.n + (size_t)k * nl;
+  int is = 0;
+  for (int l = 1; l < nl; ++l)
+    if (n[l] > n[is]) is = l;
+  for (int l = 0; l < nl; ++l) rhs[l] = 0.0;
+  for (int j = 0; j < nl; ++j) M[is * nl + j] = 1.0;
+  rhs[is] = T.ntot[k];
+  if (!small_solve(M, rhs, nl)) return;   // singular: the LTE start stays
+  for (int l = 0; l < nl; ++l) n[l] = rhs[l];
+}
+
+int launch_zero_radiation(const Batch& b, cudaStream_t s) {
+  dim3 g((b.max_nz + 63) / 64, b.ncols);
+  k_zero_radiation<<<g, 64, 0, s>>>(b.d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
 }
 
 int launch_rh92_update(const Batch& b, cudaStream_t s) {
