@@ -137,6 +137,21 @@ typedef enum {
   JFNK_FORMAL_SWEEP_WARP = 3     /* mixed: warp per frequency pair, lane per ray   */
 } jfnk_formal_kernel;
 
+/* Jacobian-vector products inside GMRES (Sect. 2.4, Fig. 2). The default is
+ * the exact tangent of every step, the eps -> 0 limit of the complex step
+ * (Eq. complex); the difference schemes evaluate F at n +- eps u with J^dagger
+ * and the conservation rows of the base point: forward with eps_1 = b
+ * sum|n|/(N ||u||) + b (b = 1e-6) or eps_2 = eps_mach^(1/2) sqrt(1 + ||n||)/||u||,
+ * central with eps_mach^(1/3) sqrt(1 + ||n||)/||u||. The difference schemes
+ * run in JFNK_FP64 only (a difference of FP32 residuals at these steps would
+ * be rounding noise); other precisions return JFNK_E_INVALID. */
+typedef enum {
+  JFNK_JVP_TANGENT = 0,
+  JFNK_JVP_FORWARD_EPS1 = 1,
+  JFNK_JVP_FORWARD_EPS2 = 2,
+  JFNK_JVP_CENTRAL = 3
+} jfnk_jvp_scheme;
+
 /* Solver options (Algorithm 2; defaults from jfnk_default_options). */
 typedef struct {
   double ftol;          /* 1/2 ||(n - n_prev)/(n + n_prev)||_inf threshold (1e-4)  */
@@ -157,6 +172,8 @@ typedef struct {
                            JFNK_FORMAL_SWEEP_WARP forced (identical results)      */
   int precond;          /* 1: block-Jacobi, first solution of Sect. 2.5.2 (default);
                            0: none (GMRES on J x = -F)                            */
+  int jvp;              /* Jacobian-vector products: JFNK_JVP_TANGENT (default) or a
+                           finite difference of Fig. 2 (jfnk_jvp_scheme)          */
 } jfnk_options;
 
 typedef struct {

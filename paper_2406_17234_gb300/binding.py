@@ -32,6 +32,10 @@ JFNK_MIXED = 1
 JFNK_INIT_LTE = 0
 JFNK_INIT_USER = 1
 JFNK_INIT_ZERO_RADIATION = 2
+JFNK_JVP_TANGENT = 0
+JFNK_JVP_FORWARD_EPS1 = 1
+JFNK_JVP_FORWARD_EPS2 = 2
+JFNK_JVP_CENTRAL = 3
 JFNK_FORMAL_PER_RAY = 0
 JFNK_FORMAL_FUSED = 1
 JFNK_FORMAL_SWEEP_THREAD = 2
@@ -70,7 +74,7 @@ class jfnk_options(C.Structure):
                 ("maxiter", C.c_int), ("krylov_max", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("init", C.c_int), ("clamp", C.c_int),
                 ("rh92_warmup", C.c_int), ("rh92_switch", C.c_double), ("max_ticks", C.c_int),
-                ("profile", C.c_int), ("formal_variant", C.c_int), ("precond", C.c_int)]
+                ("profile", C.c_int), ("formal_variant", C.c_int), ("precond", C.c_int), ("jvp", C.c_int)]
 
 
 class jfnk_stats(C.Structure):

@@ -96,6 +96,7 @@ void options_to_device(const jfnk_options* o, SolverOpts* so) {
   so->rh92_warmup = o->rh92_warmup;
   so->max_ticks = o->max_ticks;
   so->precond = o->precond;
+  so->jvp = o->jvp;
 }
 
 int validate_options(const jfnk_options* o) {
@@ -108,6 +109,9 @@ int validate_options(const jfnk_options* o) {
   if (o->init != JFNK_INIT_LTE && o->init != JFNK_INIT_USER && o->init != JFNK_INIT_ZERO_RADIATION)
     return fail(JFNK_E_INVALID, "init must be JFNK_INIT_LTE, JFNK_INIT_USER or JFNK_INIT_ZERO_RADIATION");
   if (o->precond != 0 && o->precond != 1) return fail(JFNK_E_INVALID, "precond must be 0 or 1");
+  if (o->jvp < JFNK_JVP_TANGENT || o->jvp > JFNK_JVP_CENTRAL) return fail(JFNK_E_INVALID, "unknown jvp scheme");
+  if (o->jvp != JFNK_JVP_TANGENT && o->precision != JFNK_FP64)
+    return fail(JFNK_E_INVALID, "difference JVPs need precision JFNK_FP64");
   if (o->rh92_warmup < 0) return fail(JFNK_E_INVALID, "rh92_warmup must be >= 0");
   if (o->formal_variant != 0 && o->formal_variant != JFNK_FORMAL_SWEEP_THREAD &&
       o->formal_variant != JFNK_FORMAL_SWEEP_WARP)
@@ -421,6 +425,7 @@ void jfnk_default_options(jfnk_options* o) {
   o->profile = 0;
   o->formal_variant = 0;
   o->precond = 1;
+  o->jvp = JFNK_JVP_TANGENT;
 }
 
 int jfnk_init(int device, jfnk_ctx** out) {

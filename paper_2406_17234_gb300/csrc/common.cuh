@@ -34,6 +34,8 @@ enum EvalMode : int {
   EV_BASE = 1,      // F(n), new J, preconditioner coefficients
   EV_TANGENT = 2,   // J_F(n) v (tangent of every step)
   EV_RH92 = 3,      // F(n), new J, Lambda_eta (RH92 update afterwards)
+  EV_FD = 4,        // F(n + s eps u) for a finite-difference JVP: J^dagger and the
+                    // conservation rows of the base point, F into dF, no new J or P
 };
 
 // Solver phases of the per-column state machine (one evaluation per tick).
@@ -87,6 +89,7 @@ struct SolverOpts {
   double ftol, fdrop, rtol, rh92_switch;
   int maxiter, krylov_max, max_restarts, clamp, rh92_warmup, max_ticks;
   int precond;   // 1: apply P^{-1} (block Jacobi); 0: no preconditioning
+  int jvp;       // 0 exact tangent; 1 forward eps_1; 2 forward eps_2; 3 central eps_2
 };
 
 // Per-column solver state (device memory, written by the Krylov kernel only).
@@ -106,6 +109,9 @@ struct SolverState {
   double F0norm;
   double Fnorm;
   double err;
+  int fd_scheme;       // JVPs: 0 exact tangent, 1/2 forward difference, 3 central difference
+  int fd_side;         // central difference: +1 before F(n + eps u), -1 before F(n - eps u)
+  double fd_eps;       // difference step of the current JVP
 };
 
 // Work buffers of one column (device pointers). ``real`` buffers hold float in
@@ -161,6 +167,8 @@ struct ColWork {
   double* x;        // [N]
   double* w;        // [N]
   double* nprev;    // [N]
+  double* np;       // [N] populations of a finite-difference evaluation (n + s eps u)
+  double* fdp;      // [N] F(n + eps u) of a central difference
   SolverState* st;
 };
 
@@ -186,6 +194,12 @@ __device__ __forceinline__ const double* jdag_ptr(const ColDesc& cd) {
 }
 __device__ __forceinline__ double* jnew_ptr(const ColDesc& cd) {
   return (cd.forced_mode < 0 && cd.w.st->jsel) ? cd.w.Jdag : cd.w.Jnew;
+}
+
+// Populations an evaluation of kind ``mode`` reads (perturbed ones for a
+// finite-difference JVP).
+__device__ __forceinline__ const double* eval_pops(const ColDesc& cd, int mode) {
+  return mode == EV_FD ? cd.w.np : cd.w.n;
 }
 
 // RH92 per-transition sums: [0] sum W V Jeff, [1] sum W g V Jeff, [2] sum W U,

@@ -12,7 +12,7 @@ __device__ __forceinline__ int eval_mode_f(const ColDesc& cd) {
   switch (cd.w.st->phase) {
     case PH_BASE: return EV_BASE;
     case PH_JVP:
-    case PH_RESTART: return EV_TANGENT;
+    case PH_RESTART: return cd.w.st->fd_scheme ? EV_FD : EV_TANGENT;
     case PH_RH92: return EV_RH92;
     default: return EV_SKIP;
   }

@@ -132,11 +132,12 @@ __device__ __forceinline__ float butterfly8(float v) {
 
 // Output of one depth from the two hemisphere sums (base: D, |D|, I, Lchi, Leta).
 __device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, double Sk64, double c2, float fD, float fa,
-                                           float fI, float fx, float fe) {
+                                           float fI, float fx, float fe, bool fd) {
   // the representation with the smaller rounding error (intensities are >= 0)
   double J = __dmul_rn(__dadd_rn(Sk64, (double)fD), c2);
   if (fabsf(fI) < fa) J = __dmul_rn((double)fI, c2);
   cd.w.J[o] = J;
+  if (fd) return;   // finite-difference evaluation: J feeds its rates only
   jnew_ptr(cd)[o] = J;
   cd.w.Lchi[o] = __dmul_rn((double)fx, c2);
   cd.w.Leta[o] = (double)fe;
@@ -180,6 +181,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   const float* __restrict__ dS32T = cd.w.dS32T + q;
   float* __restrict__ part = reinterpret_cast<float*>(cd.w.part) + q;
   const double c2 = T.c2[q];
+  const bool fdm = !TAN && eval_mode_f(cd) == EV_FD;
 
   float inv2mu[MU], hw[MU], two_mu[MU];
 #pragma unroll
@@ -245,7 +247,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       pp[4 * pstride] = te;
     } else {
       write_base(cd, row + k, Sk64, c2, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
-                 add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]));
+                 add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]), fdm);
     }
   };
   emit(k0, Sp, dSp);
@@ -383,6 +385,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   const float* __restrict__ dchiT = cd.w.dchiT + qq;
   const float* __restrict__ dS32T = cd.w.dS32T + qq;
   const double c2 = T.c2[qq];
+  const bool fdm = !TAN && eval_mode_f(cd) == EV_FD;
   const bool on = m < nmu;
   const float inv2mu = on ? (float)(0.5 / T.mu[m]) : 0.f;
   const float hw = on ? (float)(0.5 * T.wmu[m]) : 0.f;
@@ -516,7 +519,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
     } else {
       write_base(cd, row + k, S64[k], c2, add(upp[k], dn[k]), add(upp[nz + k], dn[nz + k]),
                  add(upp[2 * nz + k], dn[2 * nz + k]), add(upp[3 * nz + k], dn[3 * nz + k]),
-                 add(upp[4 * nz + k], dn[4 * nz + k]));
+                 add(upp[4 * nz + k], dn[4 * nz + k]), fdm);
     }
   }
 }

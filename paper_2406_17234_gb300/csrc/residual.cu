@@ -23,7 +23,7 @@ __device__ __forceinline__ int eval_mode(const ColDesc& cd) {
   switch (cd.w.st->phase) {
     case PH_BASE: return EV_BASE;
     case PH_JVP:
-    case PH_RESTART: return EV_TANGENT;
+    case PH_RESTART: return cd.w.st->fd_scheme ? EV_FD : EV_TANGENT;
     case PH_RH92: return EV_RH92;
     default: return EV_SKIP;
   }
@@ -81,7 +81,7 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
   }
   const int q = i / nz, k = i - q * nz;
   const double c2 = T.c2[q];
-  const double* n = cd.w.n + k * nl;
+  const double* n = eval_pops(cd, mode) + k * nl;
   double chi = T.chi_c[i] + T.chi_sca[k];
   double eta = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
   for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
@@ -372,7 +372,7 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
     sa += fabs(h);
   }
   double J = (cd.w.S[o] + s) * c2;
-  if (mode != EV_TANGENT) {
+  if (mode == EV_BASE || mode == EV_RH92) {
     // take the representation with the smaller rounding error: sum |w D| vs sum |w I|
     const real* HI = reinterpret_cast<const real*>(cd.w.HI) + i;
     double si = 0.0;
@@ -385,7 +385,7 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
     double ds = 0.0;
     for (int r = 0; r < nr; ++r) ds += (double)dH[r * plane];
     cd.w.dJ[o] = (cd.w.dS[o] + ds) * c2;
-  } else {
+  } else if (mode != EV_FD) {
     jnew_ptr(cd)[o] = J;
     const real* LX = reinterpret_cast<const real*>(cd.w.LX) + i;
     const real* LE = reinterpret_cast<const real*>(cd.w.LE) + i;
@@ -625,11 +625,12 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
   __shared__ double s_up[kAsmWarps][kMaxT], s_dn[kAsmWarps][kMaxT], s_kap[kAsmWarps][kMaxT];
   __shared__ double s_P[kAsmWarps][kMaxL * kMaxL];
   __shared__ int s_piv[kAsmWarps][kMaxL];
-  const double* n = cd.w.n + k * nl;
+  const bool fd = (mode == EV_FD);
+  const double* n = eval_pops(cd, mode) + k * nl;
   const double* C = T.C + (size_t)k * nl * nl;
   const bool tan = (mode == EV_TANGENT);
   int is;
-  if (!tan) {
+  if (!tan && !fd) {
     // conservation row at the most populated level (lowest index on ties)
     is = 0;
     for (int l = 1; l < nl; ++l)
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
         f = T.ntot[k] - sv;
       }
     }
-    (tan ? cd.w.dF : cd.w.F)[k * nl + lane] = f;
+    (tan || fd ? cd.w.dF : cd.w.F)[k * nl + lane] = f;
   }
   if (mode != EV_BASE) return;
   // P^k = Gamma^k + A^kk (Sect. 2.5.1), conservation row -1

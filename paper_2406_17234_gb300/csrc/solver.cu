@@ -34,7 +34,7 @@ void DeviceArena::release() {
 struct ColLayout {
   size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH,
       LX, LE, part, J, dJ, Lchi, Leta, Rup, Rdn, dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x,
-      w, nprev;
+      w, nprev, np, fdp;
 };
 
 size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout* out) {
@@ -71,6 +71,7 @@ size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout
   o.Vb = ar.take<double>((size_t)(kmax + 1) * N); o.Hh = ar.take<double>((size_t)(kmax + 1) * kmax);
   o.cs = ar.take<double>(kmax); o.sn = ar.take<double>(kmax); o.gv = ar.take<double>(kmax + 1);
   o.x = ar.take<double>(N); o.w = ar.take<double>(N); o.nprev = ar.take<double>(N);
+  o.np = ar.take<double>(N); o.fdp = ar.take<double>(N);
   if (out) *out = o;
   return ar.cursor;
 }
@@ -111,6 +112,7 @@ void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, 
   w.Vb = (double*)P(o.Vb); w.Hh = (double*)P(o.Hh);
   w.cs = (double*)P(o.cs); w.sn = (double*)P(o.sn); w.gv = (double*)P(o.gv);
   w.x = (double*)P(o.x); w.w = (double*)P(o.w); w.nprev = (double*)P(o.nprev);
+  w.np = (double*)P(o.np); w.fdp = (double*)P(o.fdp);
   w.st = st;
 }
 
@@ -301,6 +303,42 @@ __device__ void apply_pinv(const ColDesc& cd, const double* in, double sign_in, 
   }
 }
 
+// Finite-difference JVPs (Sect. 2.4, Fig. 2): the step for direction u and
+// the populations n + side eps u of the next evaluation. Called by every
+// thread of the column's block.
+__device__ void fd_prepare(const ColDesc& cd, SolverState* st, int scheme, const double* u, int side,
+                           double* sh) {
+  const int N = cd.t.nz * cd.t.nl;
+  const double* n = cd.w.n;
+  double su = 0.0, sn = 0.0, sa = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    su += u[i] * u[i];
+    sn += n[i] * n[i];
+    sa += fabs(n[i]);
+  }
+  su = block_sum(su, sh);
+  sn = block_sum(sn, sh);
+  sa = block_sum(sa, sh);
+  const double un = sqrt(su);
+  double eps = 1.0;
+  if (un > 0.0) {
+    if (scheme == 1) {
+      const double b = 1e-6;
+      eps = b * sa / ((double)N * un) + b;                 // eps_1
+    } else {
+      // eps_2: eps_mach^(1/r) sqrt(1 + ||n||)/||u||, r = 2 (forward) or 3 (central)
+      const double root = scheme == 3 ? 6.0554544523933395e-06    // 2^(-52/3)
+                                      : 1.4901161193847656e-08;   // 2^(-26)
+      eps = root * sqrt(1.0 + sqrt(sn)) / un;
+    }
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) cd.w.np[i] = n[i] + side * eps * u[i];
+  if (threadIdx.x == 0) {
+    st->fd_eps = eps;
+    st->fd_side = side;
+  }
+}
+
 constexpr int kKrylovThreads = 512;
 
 __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __restrict__ cols,
@@ -359,6 +397,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       st->F_calls++;
       st->ticks++;
       st->Fnorm = fm;
+      st->fd_scheme = o.jvp;   // the kind of this Newton step's JVP evaluations
       int nx = NX_START_GMRES;
       if (!(fm < INFINITY)) { st->status = JFNK_E_NAN; nx = NX_DONE; }
       else if (st->newton_iter == 0) st->F0norm = fm;
@@ -392,7 +431,32 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
     }
     start_beta = beta;
   } else {
-    // a Jacobian-vector product J u is in dF (u = V_j or u = x)
+    // a Jacobian-vector product J u is in dF (u = V_j or u = x); with a
+    // difference scheme dF holds F(n + side eps u) and the quotient is formed here
+    const int scheme = st->fd_scheme;
+    if (scheme) {
+      const int side = st->fd_side;
+      const double eps = st->fd_eps;
+      const double* u = (phase == PH_RESTART) ? x : Vb + (size_t)st->j * N;
+      __syncthreads();   // every thread has read the state before it changes
+      if (scheme == 3 && side > 0) {
+        // central difference, first half: keep F(n + eps u), evaluate F(n - eps u) next
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+          cd.w.fdp[i] = cd.w.dF[i];
+          cd.w.np[i] = cd.w.n[i] - eps * u[i];
+        }
+        if (threadIdx.x == 0) {
+          st->fd_side = -1;
+          st->F_calls++;
+          st->ticks++;
+          status_out[blockIdx.x] = st->status;
+        }
+        return;
+      }
+      for (int i = threadIdx.x; i < N; i += blockDim.x)
+        cd.w.dF[i] = scheme == 3 ? (cd.w.fdp[i] - cd.w.dF[i]) / (2.0 * eps) : (cd.w.dF[i] - cd.w.F[i]) / eps;
+      __syncthreads();
+    }
     if (threadIdx.x == 0) { st->F_calls++; st->jvp_calls++; st->ticks++; }
     if (phase == PH_RESTART) {
       apply_pinv(cd, cd.w.F, -1.0, cd.w.dF, -1.0, w, o.precond != 0);   // r = P^{-1}(-F - J x)
@@ -489,6 +553,10 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
         const double hn = s_val;
         double* vn = Vb + (size_t)(j + 1) * N;
         for (int e = threadIdx.x; e < N; e += blockDim.x) vn[e] = w[e] / hn;
+        if (o.jvp) {
+          __syncthreads();
+          fd_prepare(cd, st, o.jvp, vn, +1, sh);
+        }
         if (threadIdx.x == 0) { st->j = j + 1; st->phase = PH_JVP; status_out[blockIdx.x] = st->status; }
         return;
       }
@@ -500,6 +568,7 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       }
       __syncthreads();
       if (next == 100) {
+        if (o.jvp) fd_prepare(cd, st, o.jvp, x, +1, sh);   // the restart residual needs J x
         if (threadIdx.x == 0) { st->phase = PH_RESTART; status_out[blockIdx.x] = st->status; }
         return;
       }
@@ -509,6 +578,10 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
   if (next == NX_START_GMRES) {
     const double beta = start_beta;
     for (int e = threadIdx.x; e < N; e += blockDim.x) Vb[e] = w[e] / beta;
+    if (o.jvp) {
+      __syncthreads();
+      fd_prepare(cd, st, o.jvp, Vb, +1, sh);
+    }
     if (threadIdx.x == 0) {
       for (int i = 0; i <= kmax; ++i) cd.w.gv[i] = 0.0;
       cd.w.gv[0] = beta;

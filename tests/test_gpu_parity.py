@@ -340,3 +340,33 @@ def test_unpreconditioned_solve_reaches_the_oracle_solution(ctx):
     n1, _, s1 = B.solve(atm, B.default_options(rtol=1e-6, ftol=1e-10))
     assert s0["status"] == 0 and s0["jvp_calls"] > s1["jvp_calls"]
     np.testing.assert_allclose(n0, ref.n, rtol=1e-5)
+
+
+@pytest.mark.parametrize("scheme,ojvp,ochoice,per_jvp", [
+    ("JFNK_JVP_FORWARD_EPS1", "forward", "eps1", 1),
+    ("JFNK_JVP_FORWARD_EPS2", "forward", "eps2", 1),
+    ("JFNK_JVP_CENTRAL", "central", "eps2", 2),
+])
+def test_difference_jvps_reach_the_oracle_solution(ctx, scheme, ojvp, ochoice, per_jvp):
+    """Finite-difference JVPs (Sect. 2.4, Fig. 2) inside the on-device GMRES:
+    the same fixed point as the oracle's iteration with the same scheme and
+    step, and one (forward) or two (central) residual evaluations per JVP."""
+    wl = W.config1(n_depth=41, n_nu=21)
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    tight = dict(rtol=1e-6, ftol=1e-10)
+    ref = jfnk(m, m.nstar, jvp=ojvp, fd_choice=ochoice, **tight)
+    n_fd, _, s = B.solve(atm, B.default_options(jvp=getattr(B, scheme), **tight))
+    _, _, st = B.solve(atm, B.default_options(**tight))
+    assert ref.converged and s["status"] == 0
+    np.testing.assert_allclose(n_fd, ref.n, rtol=1e-5)
+    # base evaluations are counted the same way in both runs
+    assert (s["F_calls"] - per_jvp * s["jvp_calls"] - s["newton_iters"]
+            == st["F_calls"] - st["jvp_calls"] - st["newton_iters"])
+    assert abs(s["newton_iters"] - ref.newton_iters) <= 2
+
+
+def test_difference_jvps_are_fp64_only(ctx):
+    wl = W.config1(n_depth=21, n_nu=11)
+    atom, atm, m = _pair(ctx, wl, n_mu=2)
+    with pytest.raises(RuntimeError):
+        B.solve(atm, B.default_options(jvp=B.JFNK_JVP_CENTRAL, precision=B.JFNK_MIXED))
