@@ -145,10 +145,18 @@ def clocks_stop(proc, device):
             "samples": len(sm)}
 
 
-def source_hash():
+# the sources each formal kernel is compiled from (its translation unit and the
+# ray-step coefficient header): a change to any of them voids its ncu traffic
+KERNEL_SOURCES = {
+    "formal_fp64": ("formal_fused.cu", "formal_coef.cuh"),
+    "formal_fp32": ("formal_sweep.cu", "formal_coef.cuh"),
+}
+
+
+def source_hash(kernel_key):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_17234_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES[kernel_key]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -162,7 +170,7 @@ def measured_traffic(kernel_key):
     except Exception:
         return None
     e = d.get(kernel_key)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel_key):
         return None
     return e.get("bytes_per_ray_point")
 
