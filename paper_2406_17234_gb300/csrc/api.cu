@@ -441,6 +441,7 @@ int jfnk_init(int device, jfnk_ctx** out) {
   cudaError_t e = cudaGetDeviceProperties(&p, device);
   if (e != cudaSuccess) { delete c; return fail(JFNK_E_CUDA, cudaGetErrorString(e)); }
   c->n_sm = p.multiProcessorCount;
+  if (int rc = prepare_kernels()) { delete c; return rc; }
   e = cudaStreamCreateWithFlags(&c->setup_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);

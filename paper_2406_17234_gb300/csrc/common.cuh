@@ -64,6 +64,9 @@ struct ColTables {
   const double* t_w;      // [nwin] trapezoid weight omega_t(nu_q)
   const double* V;        // [nwin][nz]
   const double* G;        // [nwin][nz]
+  const double* WV;       // [nwin][nz] W V with W = omega_t(nu_q) 4 pi/(h nu_q): rate-integral weights
+  const double* WgV;      // [nwin][nz] W g V
+  const double* Rsp;      // [nt][nz] sum_q W g V 2 h nu^3/c^2: the spontaneous part of R_ji
   const float* V32;       // [nwin][nz] float copies (mixed-mode tangent evaluations)
   const float* G32;       // [nwin][nz]
   const float* V32T;      // [nz][nwin] the same, depth-major
@@ -167,6 +170,8 @@ struct ColWork {
   double* x;        // [N]
   double* w;        // [N]
   double* nprev;    // [N]
+  double* eta;      // [nq][nz] emissivity of an RH92 evaluation, for Jeff = J - Psi* eta
+  float* etab32;    // [nq][nz] its background part eta_c + chi_sca J^dagger (mixed mode)
   double* np;       // [N] populations of a finite-difference evaluation (n + s eps u)
   double* fdp;      // [N] F(n + eps u) of a central difference
   SolverState* st;

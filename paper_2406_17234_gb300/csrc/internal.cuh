@@ -146,6 +146,8 @@ int launch_formal_sweep(const Batch& b, cudaStream_t s);
 // Warps per block of the warp variant whose shared memory fits depth nz (0: none).
 int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);
+// Kernel attributes of the current device, set once per context (residual.cu).
+int prepare_kernels();
 // Opacity kernel of the mixed mode (tangent columns skipped when the sweeps form it).
 int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent);
 // Solver options: checks, device copy (api.cu).

@@ -83,7 +83,8 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
   const double c2 = T.c2[q];
   const double* n = eval_pops(cd, mode) + k * nl;
   double chi = T.chi_c[i] + T.chi_sca[k];
-  double eta = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
+  const double eta_bg = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
+  double eta = eta_bg;
   for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
     const int t = T.q_t[s];
     const int lo = T.t_lo[t], up = T.t_up[t];
@@ -94,6 +95,10 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
   }
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
   cd.w.S[i] = eta / (chi * c2);
+  if (mode == EV_RH92) {   // for the RH92 rate sums
+    cd.w.eta[i] = eta;
+    if (cd.mixed) cd.w.etab32[i] = (float)eta_bg;
+  }
 }
 
 // Mixed mode, tangent evaluations: dchi and dS in FP32 (tan_acc), one thread
@@ -405,194 +410,258 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
 // and in RH92 mode the sums of the preconditioned rate equations.
 // ---------------------------------------------------------------------------
 constexpr int kRateWarps = 4;
-constexpr int kRateSplit = 4;   // blocks of a cluster sharing one (transition, depth tile)
-constexpr int kRateAcc = 2 + (kRhFixed + kMaxT > kMaxL ? kRhFixed + kMaxT : kMaxL);
+constexpr int kRateSplit = 4;            // blocks of a cluster sharing one (transition, depth tile)
+constexpr int kRateClustersPerSM = 32;   // clusters of the column loop per multiprocessor
 
-// One cluster of kRateSplit blocks per (32-depth tile, transition, column):
-// lanes map to depths (every table and J access is coalesced), the blocks of
-// the cluster split the frequency window into contiguous chunks and their
-// warps stride through the chunk; partial sums are reduced through shared
-// memory inside a block and through distributed shared memory across the
-// cluster, in a fixed order (bit-reproducible, no atomics).
-__global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __restrict__ cols) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const ColDesc& cd = cols[blockIdx.z / kRateSplit];
+// Per-lane partial sums in dynamic shared memory: racc doubles
+// [warp][slot][lane], then (mixed mode) fslots floats [warp][slot][lane].
+struct RateSmem {
+  double* red;
+  float* fsl;
+  int racc, fslots;
+  __device__ double& d(int w, int j, int lane) const { return red[((size_t)w * racc + j) * 32 + lane]; }
+  __device__ float& f(int w, int j, int lane) const { return fsl[((size_t)w * fslots + j) * 32 + lane]; }
+};
+
+// The evaluation kind this cluster integrates for column cd, EV_SKIP when it
+// has nothing to do there. Uniform over the cluster: its blocks differ only
+// in their frequency chunk.
+__device__ __forceinline__ int rate_mode(const ColDesc& cd, int t, int tile) {
   const int mode = eval_mode(cd);
+  if (mode == EV_SKIP || (mode == EV_TANGENT && cd.mixed) || t >= cd.t.nt || tile * 32 >= cd.t.nz)
+    return EV_SKIP;
+  return mode;
+}
+
+// One (32-depth tile, transition t, column): lanes map to depths (every table
+// and J access is coalesced), the kRateSplit blocks of the cluster split the
+// frequency window into contiguous chunks and their warps stride through the
+// chunk; partial sums are reduced through shared memory inside a block and
+// through distributed shared memory across the cluster, in a fixed order
+// (bit-reproducible, no atomics).
+//
+// R_ij = sum W V J and R_ji = Rsp + sum W g V J (Eqs. Rij, Rji) take one FP64
+// product per term from the WV, WgV tables. Mixed mode forms the
+// preconditioner sums (base) and the RH92 sums in FP32; Jeff = J - Psi* eta
+// stays FP64 because it cancels in optically thick layers.
+__device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const int tile, const int rank,
+                           const RateSmem& sm, cg::cluster_group& cluster) {
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
-  const int t = blockIdx.y;
-  // uniform over the cluster: every block takes the same branch (mixed-mode
-  // tangents are integrated by k_rates_tan32)
-  const bool active = (mode != EV_SKIP) && !(mode == EV_TANGENT && cd.mixed) && t < nt &&
-                      (int)blockIdx.x * 32 < nz;
-  __shared__ double red[kRateWarps][kRateAcc][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool tan = (mode == EV_TANGENT);
   const bool base_mode = (mode == EV_BASE);
   const bool rh = (mode == EV_RH92);
+  const bool mix = cd.mixed != 0;
   const int nacc = tan ? 2 : (base_mode ? 2 + nl : (rh ? 2 + kRhFixed + nt : 2));
-  if (active) {
-    const int k = min((int)blockIdx.x * 32 + lane, nz - 1);
-    const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
-    const int nw = q1 - q0 + 1;
-    const int qa = q0 + (int)(((long)nw * rank) / kRateSplit);
-    const int qb = q0 + (int)(((long)nw * (rank + 1)) / kRateSplit) - 1;
-    const int lo = T.t_lo[t], upl = T.t_up[t];
-    const double* n = cd.w.n + k * nl;
-    double acc[kRateAcc];
-    for (int j = 0; j < nacc; ++j) acc[j] = 0.0;
-    float af[kRhFixed] = {0.f, 0.f, 0.f, 0.f};   // mixed-mode RH92 fixed sums
-    const double n_lo = n[lo], n_up = n[upl];
-    const double* Jd = rh ? jdag_ptr(cd) : nullptr;
-    if (rh && cd.mixed) {
-      // mixed mode, RH92 sums: Jeff = J - Psi* eta cancels in thick layers
-      // and is formed in FP64; the products of the sums are FP32, the sums
-      // over transitions s accumulate in shared memory (lane-private slots
-      // aliasing ``red``, which is written only after this loop)
-      float* fs = reinterpret_cast<float*>(&red[0][0][0]) + (size_t)wid * kMaxT * 32 + lane;
-      for (int j = 0; j < nt; ++j) fs[j * 32] = 0.f;
-      const float nlo_f = (float)n_lo, nup_f = (float)n_up;
-      for (int q = qa + wid; q <= qb; q += kRateWarps) {
-        const size_t p = (size_t)(base + q - q0);
-        const double W = T.t_w[p] * T.rw[q];
-        const double V = T.V[p * nz + k], g = T.G[p * nz + k];
-        const size_t o = (size_t)q * nz + k;
-        const double J = cd.w.J[o];
-        const double c2 = T.c2[q];
-        acc[0] += W * V * J;
-        acc[1] += W * g * V * (c2 + J);
-        const double Le = cd.w.Leta[o];
-        const double eta_bg = T.eta_c[o] + T.chi_sca[k] * Jd[o];
-        double eta_l = 0.0;
-        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-          const int ts = T.q_t[s];
-          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-          eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
-        }
-        const float Jf = (float)(J - Le * (eta_bg + eta_l));
-        const float Wf = T.Wr32[p], Vf = T.V32[p * nz + k], gf = T.G32[p * nz + k], c2f = T.c2f[q];
-        af[0] = fmaf(Wf * Vf, Jf, af[0]);
-        af[1] = fmaf(Wf * gf * Vf, Jf, af[1]);
-        af[2] = fmaf(Wf * c2f, gf * Vf, af[2]);
-        const float wcp = Wf * (Vf * (nlo_f - gf * nup_f)) * (float)Le;
-        af[3] = fmaf(wcp, (float)eta_bg, af[3]);
-        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-          const int ts = T.q_t[s];
-          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-          fs[ts * 32] = fmaf(wcp * c2f, T.G32[ps] * T.V32[ps], fs[ts * 32]);
-        }
-      }
-    } else
+  const int k = min(tile * 32 + lane, nz - 1);
+  const int q0 = T.t_q0[t], q1 = T.t_q1[t], wbase = T.t_base[t];
+  const int nw = q1 - q0 + 1;
+  const int qa = q0 + (int)(((long)nw * rank) / kRateSplit);
+  const int qb = q0 + (int)(((long)nw * (rank + 1)) / kRateSplit) - 1;
+  const double* n = eval_pops(cd, mode) + k * nl;
+  const double n_lo = n[T.t_lo[t]], n_up = n[T.t_up[t]];
+  // slots indexed by level or transition accumulate in place (lane-private)
+  for (int j = 2; j < nacc; ++j) sm.d(wid, j, lane) = 0.0;
+  if (mix) for (int j = 0; j < sm.fslots; ++j) sm.f(wid, j, lane) = 0.f;
+  const double* __restrict__ J = tan ? cd.w.dJ : cd.w.J;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a5 = 0.0;
+  float f0 = 0.f, f1 = 0.f, f3 = 0.f;
+  if (!base_mode && !rh) {
+    // tangent (FP64 mode) or a difference evaluation: the two rate sums only
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
-      const size_t p = (size_t)(base + q - q0);
-      const double W = T.t_w[p] * T.rw[q];
-      const double V = T.V[p * nz + k], g = T.G[p * nz + k];
-      const size_t o = (size_t)q * nz + k;
-      if (tan) {
-        const double WV = W * V;
-        const double dJ = cd.w.dJ[o];
-        acc[0] += WV * dJ;
-        acc[1] += WV * g * dJ;
-        continue;
-      }
-      const double J = cd.w.J[o];
-      const double c2 = T.c2[q];
-      acc[0] += W * V * J;
-      acc[1] += W * g * V * (c2 + J);
-      const double chi_t = V * (n_lo - g * n_up);
-      if (base_mode) {
-        double zeta[kMaxL];
-        for (int j = 0; j < nl; ++j) zeta[j] = 0.0;
-        const double Lx = cd.w.Lchi[o], Le = cd.w.Leta[o];
-        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-          const int ts = T.q_t[s];
-          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-          const double Vs = T.V[ps], gs = T.G[ps];
-          zeta[T.t_lo[ts]] += Vs * Lx;                          // beta_j (Sect. 2.5.1, read from Eq. chi)
-          zeta[T.t_up[ts]] += -gs * Vs * Lx + c2 * gs * Vs * Le;  // and gamma_j (Eq. der_eta_n)
-        }
-        const double Wc = W * chi_t;
-        for (int j = 0; j < nl; ++j) acc[2 + j] += Wc * zeta[j];
-      } else if (rh) {
-        // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
-        const double Le = cd.w.Leta[o];
-        const double eta_bg = T.eta_c[o] + T.chi_sca[k] * Jd[o];
-        double eta_l = 0.0;
-        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-          const int ts = T.q_t[s];
-          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-          eta_l += c2 * T.G[ps] * T.V[ps] * n[T.t_up[ts]];
-        }
-        const double Jeff = J - Le * (eta_bg + eta_l);
-        acc[2] += W * V * Jeff;
-        acc[3] += W * g * V * Jeff;
-        acc[4] += W * c2 * g * V;
-        const double wcp = W * chi_t * Le;
-        acc[5] += wcp * eta_bg;
-        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-          const int ts = T.q_t[s];
-          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-          acc[2 + kRhFixed + ts] += wcp * c2 * T.G[ps] * T.V[ps];
-        }
+      const size_t pk = (size_t)(wbase + q - q0) * nz + k;
+      const double Jq = J[(size_t)q * nz + k];
+      a0 = fma(T.WV[pk], Jq, a0);
+      a1 = fma(T.WgV[pk], Jq, a1);
+    }
+  } else if (base_mode && mix) {
+    // preconditioner sums A^kk_{t,j} = sum W chi_t (beta_j Lchi + gamma_j Leta) in FP32
+    const float nlo_f = (float)n_lo, nup_f = (float)n_up;
+    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+      const int p = wbase + q - q0;
+      const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
+      const double Jq = J[o];
+      a0 = fma(T.WV[pk], Jq, a0);
+      a1 = fma(T.WgV[pk], Jq, a1);
+      const float Vf = T.V32[pk], gf = T.G32[pk];
+      const float Wc = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
+      const float Lx = (float)cd.w.Lchi[o], Le = (float)cd.w.Leta[o];
+      const float cLx = Wc * Lx, cU = Wc * (T.c2f[q] * Le - Lx);
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        const float Vs = T.V32[ps];
+        float& zl = sm.f(wid, T.t_lo[ts], lane);
+        zl = fmaf(cLx, Vs, zl);                     // beta_j (Sect. 2.5.1, read from Eq. chi)
+        float& zu = sm.f(wid, T.t_up[ts], lane);
+        zu = fmaf(cU, T.G32[ps] * Vs, zu);          // and gamma_j (Eq. der_eta_n)
       }
     }
-    if (rh && cd.mixed) {
-      float tsv[kMaxT];
-      const float* fs = reinterpret_cast<const float*>(&red[0][0][0]) + (size_t)wid * kMaxT * 32 + lane;
-#pragma unroll
-      for (int j = 0; j < kMaxT; ++j) tsv[j] = (j < nt) ? fs[j * 32] : 0.f;
-      __syncthreads();   // the float slots alias red
-      red[wid][0][lane] = acc[0];
-      red[wid][1][lane] = acc[1];
-#pragma unroll
-      for (int j = 0; j < kRhFixed; ++j) red[wid][2 + j][lane] = (double)af[j];
-#pragma unroll
-      for (int j = 0; j < kMaxT; ++j)
-        if (j < nt) red[wid][2 + kRhFixed + j][lane] = (double)tsv[j];
-    } else {
-      for (int j = 0; j < nacc; ++j) red[wid][j][lane] = acc[j];
-    }
-    __syncthreads();
-    if (wid == 0)
-      for (int j = 0; j < nacc; ++j) {
-        double v = red[0][j][lane];
-        for (int w = 1; w < kRateWarps; ++w) v += red[w][j][lane];
-        red[0][j][lane] = v;
+  } else if (base_mode) {
+    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+      const size_t pk = (size_t)(wbase + q - q0) * nz + k, o = (size_t)q * nz + k;
+      const double Jq = J[o];
+      const double wv = T.WV[pk], wgv = T.WgV[pk];
+      a0 = fma(wv, Jq, a0);
+      a1 = fma(wgv, Jq, a1);
+      const double Wc = wv * n_lo - wgv * n_up;     // W chi_t
+      const double Lx = cd.w.Lchi[o], Le = cd.w.Leta[o], c2 = T.c2[q];
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        const double Vs = T.V[ps], gs = T.G[ps];
+        sm.d(wid, 2 + T.t_lo[ts], lane) += Wc * (Vs * Lx);
+        sm.d(wid, 2 + T.t_up[ts], lane) += Wc * (-gs * Vs * Lx + c2 * gs * Vs * Le);
       }
+    }
+  } else if (mix) {
+    // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
+    const float nlo_f = (float)n_lo, nup_f = (float)n_up;
+    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+      const int p = wbase + q - q0;
+      const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
+      const double Jq = J[o];
+      a0 = fma(T.WV[pk], Jq, a0);
+      a1 = fma(T.WgV[pk], Jq, a1);
+      const double Le = cd.w.Leta[o];
+      const float Jf = (float)fma(-Le, cd.w.eta[o], Jq);
+      const float Wf = T.Wr32[p], Vf = T.V32[pk], gf = T.G32[pk], c2f = T.c2f[q];
+      const float WVf = Wf * Vf;
+      f0 = fmaf(WVf, Jf, f0);
+      f1 = fmaf(WVf * gf, Jf, f1);
+      const float wcp = Wf * (Vf * (nlo_f - gf * nup_f)) * (float)Le;
+      f3 = fmaf(wcp, cd.w.etab32[o], f3);
+      const float wcu = wcp * c2f;
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        float& z = sm.f(wid, ts, lane);
+        z = fmaf(wcu, T.G32[ps] * T.V32[ps], z);
+      }
+    }
+  } else {
+    const double* Jd = jdag_ptr(cd);
+    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+      const size_t pk = (size_t)(wbase + q - q0) * nz + k, o = (size_t)q * nz + k;
+      const double Jq = J[o];
+      const double wv = T.WV[pk], wgv = T.WgV[pk];
+      a0 = fma(wv, Jq, a0);
+      a1 = fma(wgv, Jq, a1);
+      const double Le = cd.w.Leta[o];
+      const double Jeff = fma(-Le, cd.w.eta[o], Jq);
+      a2 = fma(wv, Jeff, a2);
+      a3 = fma(wgv, Jeff, a3);
+      const double wcp = (wv * n_lo - wgv * n_up) * Le;
+      a5 = fma(wcp, T.eta_c[o] + T.chi_sca[k] * Jd[o], a5);
+      const double wcu = wcp * T.c2[q];
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+        sm.d(wid, 2 + kRhFixed + ts, lane) += wcu * (T.G[ps] * T.V[ps]);
+      }
+    }
   }
+  sm.d(wid, 0, lane) = a0;
+  sm.d(wid, 1, lane) = a1;
+  if (rh) {
+    // slot 2 + 2 (sum W U, U = 2 h nu^3/c^2 g V) is the spontaneous table, added below
+    sm.d(wid, 2, lane) = mix ? (double)f0 : a2;
+    sm.d(wid, 3, lane) = mix ? (double)f1 : a3;
+    sm.d(wid, 5, lane) = mix ? (double)f3 : a5;
+    if (mix)
+      for (int j = 0; j < nt; ++j) sm.d(wid, 2 + kRhFixed + j, lane) = (double)sm.f(wid, j, lane);
+  } else if (base_mode && mix) {
+    for (int j = 0; j < nl; ++j) sm.d(wid, 2 + j, lane) = (double)sm.f(wid, j, lane);
+  }
+  __syncthreads();
+  if (wid == 0)
+    for (int j = 0; j < nacc; ++j) {
+      double v = sm.d(0, j, lane);
+      for (int w = 1; w < kRateWarps; ++w) v += sm.d(w, j, lane);
+      sm.d(0, j, lane) = v;
+    }
   cluster.sync();
-  if (active && rank == 0 && wid == 0) {
-    const int kw = (int)blockIdx.x * 32 + lane;
+  if (rank == 0 && wid == 0) {
+    const int kw = tile * 32 + lane;
     if (kw < nz) {
-      double acc[kRateAcc];
-      for (int j = 0; j < nacc; ++j) acc[j] = red[0][j][lane];
+      double acc[2 + kRhFixed + kMaxT > 2 + kMaxL ? 2 + kRhFixed + kMaxT : 2 + kMaxL];
+      for (int j = 0; j < nacc; ++j) acc[j] = sm.d(0, j, lane);
       for (int r = 1; r < kRateSplit; ++r) {
-        const double* peer = cluster.map_shared_rank(&red[0][0][0], r);
-        for (int j = 0; j < nacc; ++j) acc[j] += peer[j * 32 + lane];
+        const double* peer = cluster.map_shared_rank(sm.red, r);
+        for (int j = 0; j < nacc; ++j) acc[j] += peer[(size_t)j * 32 + lane];
       }
       const size_t i = (size_t)t * nz + kw;
       if (tan) {
         cd.w.dRup[i] = acc[0];
         cd.w.dRdn[i] = acc[1];
       } else {
+        const double rsp = T.Rsp[i];
         cd.w.Rup[i] = acc[0];
-        cd.w.Rdn[i] = acc[1];
+        cd.w.Rdn[i] = acc[1] + rsp;
         if (base_mode)
           for (int j = 0; j < nl; ++j) cd.w.Apart[i * nl + j] = acc[2 + j];
-        if (rh)
+        if (rh) {
+          acc[4] = rsp;
           for (int j = 0; j < kRhFixed + nt; ++j) cd.w.rh[i * kRhStride + j] = acc[2 + j];
+        }
       }
     }
   }
   cluster.sync();   // peers keep their shared memory until rank 0 has read it
 }
 
+// A persistent-style loop over the batch's columns: each cluster owns one
+// (depth tile, transition) and walks the columns 32 at a time, lane l testing
+// column c0 + l * step, so that columns in another evaluation kind cost one
+// load each instead of a cluster launch.
+__global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __restrict__ cols, int ncols,
+                                                           int racc, int fslots) {
+  extern __shared__ __align__(16) unsigned char rate_smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  RateSmem sm;
+  sm.red = reinterpret_cast<double*>(rate_smem);
+  sm.fsl = reinterpret_cast<float*>(sm.red + (size_t)kRateWarps * racc * 32);
+  sm.racc = racc;
+  sm.fslots = fslots;
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.y, tile = blockIdx.x;
+  const int step = gridDim.z / kRateSplit;
+  for (int c0 = blockIdx.z / kRateSplit; c0 < ncols; c0 += 32 * step) {
+    const int cl = c0 + lane * step;
+    const int ml = cl < ncols ? rate_mode(cols[cl], t, tile) : EV_SKIP;
+    unsigned act = __ballot_sync(0xffffffffu, ml != EV_SKIP);   // the same in every warp of the cluster
+    while (act) {
+      const int l = __ffs(act) - 1;
+      act &= act - 1;
+      const int mode = __shfl_sync(0xffffffffu, ml, l);
+      rates_tile(cols[c0 + l * step], mode, t, tile, rank, sm, cluster);
+    }
+  }
+}
+
+// Kernel attributes, set once per device when a context is created (outside
+// any stream capture): the rate kernel's largest dynamic shared memory.
+int prepare_kernels() {
+  const int max_smem = (int)((size_t)kRateWarps * 32 * ((2 + kRhFixed + kMaxT) * sizeof(double) +
+                                                       std::max(kMaxT, kMaxL) * sizeof(float)));
+  JFNK_CUDA(cudaFuncSetAttribute(k_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+  return JFNK_OK;
+}
+
 static int launch_rates(const Batch& b, cudaStream_t s) {
+  const int tiles = (b.max_nz + 31) / 32;
+  const int racc = 2 + std::max(kRhFixed + b.max_nt, kMaxL);
+  const int fslots = b.mixed ? std::max(b.max_nt, kMaxL) : 0;
+  const size_t smem = (size_t)kRateWarps * 32 * (racc * sizeof(double) + fslots * sizeof(float));
+  const long want = (long)kRateClustersPerSM * std::max(b.n_sm, 1);
+  const long per = (long)tiles * std::max(b.max_nt, 1);
+  const int cz = (int)std::max(1L, std::min<long>(b.ncols, (want + per - 1) / per));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((b.max_nz + 31) / 32, b.max_nt, b.ncols * kRateSplit);
+  cfg.gridDim = dim3(tiles, b.max_nt, cz * kRateSplit);
   cfg.blockDim = dim3(32 * kRateWarps);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -601,7 +670,7 @@ static int launch_rates(const Batch& b, cudaStream_t s) {
   attr[0].val.clusterDim.z = kRateSplit;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_rates, (const ColDesc*)b.d_cols));
+  JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_rates, (const ColDesc*)b.d_cols, b.ncols, racc, fslots));
   return JFNK_OK;
 }
 

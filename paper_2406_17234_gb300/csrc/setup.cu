@@ -330,6 +330,36 @@ __global__ void k_normalise_lines(int nt, const TransDev* tr, const int* t_q0, c
     for (int p = 0; p < nw; ++p) Vt[(size_t)p * nz + k] /= s;
 }
 
+// Rate-integral weights per (window point, depth): W V and W g V with
+// W = omega_t(nu_q) 4 pi/(h nu_q) (Eqs. Rij, Rji), so that the rate integrals
+// take one product per term.
+__global__ void k_rate_weights(int nwin, int nz, const int* winT, const int* t_q0, const int* t_base,
+                               const double* t_w, const double* rw, const double* V, const double* G,
+                               double* WV, double* WgV) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nwin * nz) return;
+  const int p = (int)(i / nz);
+  const int t = winT[p];
+  const double W = t_w[p] * rw[t_q0[t] + p - t_base[t]];
+  const double wv = W * V[i];
+  WV[i] = wv;
+  WgV[i] = wv * G[i];
+}
+
+// The population-independent part of R_ji (Eq. Rji): sum over the window of
+// W g V 2 h nu^3/c^2, in window order.
+__global__ void k_spontaneous(int nt, int nz, const int* t_q0, const int* t_q1, const int* t_base,
+                              const double* c2, const double* WgV, double* Rsp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nt * nz) return;
+  const int t = i / nz, k = i % nz;
+  const int nw = t_q1[t] - t_q0[t] + 1;
+  const double* w = WgV + (size_t)t_base[t] * nz + k;
+  double s = 0.0;
+  for (int p = 0; p < nw; ++p) s += w[(size_t)p * nz] * c2[t_q0[t] + p];
+  Rsp[i] = s;
+}
+
 struct CollDev {
   int kind, lo, up;
   double nu0, f, upsilon, eps, q0;
@@ -420,6 +450,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
          o_W32 = ar.take<float>(nwin), o_Wr32 = ar.take<float>(nwin), o_c2f = ar.take<float>(nq);
   size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
   size_t o_V32T = ar.take<float>((size_t)nwin * nz), o_G32T = ar.take<float>((size_t)nwin * nz);
+  size_t o_WV = ar.take<double>((size_t)nwin * nz), o_WgV = ar.take<double>((size_t)nwin * nz),
+         o_Rsp = ar.take<double>((size_t)nt * nz);
   int rc = ar.allocate();
   if (rc) return rc;
   // host-side staging
@@ -514,6 +546,13 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   k_normalise_lines<<<(nt * nz + tb - 1) / tb, tb, 0, s>>>(
       nt, ar.ptr<TransDev>(o_tr), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tq1), ar.ptr<int>(o_tbase),
       ar.ptr<double>(o_tw), nz, ar.ptr<double>(o_V));
+  k_rate_weights<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
+      nwin, nz, ar.ptr<int>(o_winT), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tbase), ar.ptr<double>(o_tw),
+      ar.ptr<double>(o_rw), ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<double>(o_WV),
+      ar.ptr<double>(o_WgV));
+  k_spontaneous<<<(nt * nz + tb - 1) / tb, tb, 0, s>>>(nt, nz, ar.ptr<int>(o_tq0), ar.ptr<int>(o_tq1),
+                                                        ar.ptr<int>(o_tbase), ar.ptr<double>(o_c2),
+                                                        ar.ptr<double>(o_WgV), ar.ptr<double>(o_Rsp));
   k_collisions<<<(nz + tb - 1) / tb, tb, 0, s>>>(nt, ar.ptr<CollDev>(o_cd), at, nz, T, ne,
                                                   ar.ptr<double>(o_C));
   k_float_copy<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
@@ -530,6 +569,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   tb_.t_lo = ar.ptr<int>(o_tlo); tb_.t_up = ar.ptr<int>(o_tup); tb_.t_q0 = ar.ptr<int>(o_tq0);
   tb_.t_q1 = ar.ptr<int>(o_tq1); tb_.t_base = ar.ptr<int>(o_tbase); tb_.t_w = ar.ptr<double>(o_tw);
   tb_.V = ar.ptr<double>(o_V); tb_.G = ar.ptr<double>(o_G); tb_.dz = ar.ptr<double>(o_dz);
+  tb_.WV = ar.ptr<double>(o_WV); tb_.WgV = ar.ptr<double>(o_WgV); tb_.Rsp = ar.ptr<double>(o_Rsp);
   tb_.V32 = ar.ptr<float>(o_V32); tb_.G32 = ar.ptr<float>(o_G32); tb_.W32 = ar.ptr<float>(o_W32);
   tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);
   tb_.Wr32 = ar.ptr<float>(o_Wr32); tb_.c2f = ar.ptr<float>(o_c2f);
