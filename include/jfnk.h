@@ -372,6 +372,13 @@ int jfnk_server_destroy(jfnk_server* sv);
  * an exp as 1 operation). */
 int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s);
 
+/* Accuracy check of the FP64 quotient the mixed-mode opacity kernel forms by
+ * Newton-Raphson from an FP32 reciprocal (S = eta / chi, Eq. chi-eta): writes
+ * q[i] = a[i] / b[i] computed that way for n host values, b[i] > 0 with a
+ * normal float rounding. Host arrays, caller-owned; JFNK_E_INVALID for n < 0
+ * or NULL pointers. */
+int jfnk_check_quotient(jfnk_ctx* ctx, const double* a, const double* b, double* q, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,8 @@ struct ColTables {
   const double* t_w;      // [nwin] trapezoid weight omega_t(nu_q)
   const double* V;        // [nwin][nz]
   const double* G;        // [nwin][nz]
+  const double* gV;       // [nwin][nz] g V
+  const double* rc2;      // [nq] c^2 / (2 h nu^3)
   const double* WV;       // [nwin][nz] W V with W = omega_t(nu_q) 4 pi/(h nu_q): rate-integral weights
   const double* WgV;      // [nwin][nz] W g V
   const double* Rsp;      // [nt][nz] sum_q W g V 2 h nu^3/c^2: the spontaneous part of R_ji
@@ -147,8 +149,10 @@ struct ColWork {
   float* dJ32T;     // tangent of J (normalised)
   double* J;        // [nq][nz]
   double* dJ;
-  double* Lchi;
+  double* Lchi;     // [nq][nz] Lambda diagonals dJ/dchi, dJ/deta (FP64 mode)
   double* Leta;
+  float* Lchi32;    // [nq][nz] the same in float (mixed mode, where they are FP32 sums)
+  float* Leta32;
   double* zeta;     // [nq][nz][nl] beta_j Lchi + gamma_j Leta (preconditioner)
   double* Rup;      // [nt][nz]
   double* Rdn;

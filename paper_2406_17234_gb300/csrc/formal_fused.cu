@@ -244,11 +244,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_formal_fused(const ColDesc* _
       }
       // the representation with the smaller rounding error (intensities are >= 0)
       if ((sI < (real)0 ? -sI : sI) < sa) J = (double)sI * c2;
-      jnew_ptr(cd)[o] = J;
+      jnew_ptr(cd)[o] = J;   // base and RH92 rates read J here
       cd.w.Lchi[o] = (double)sx * c2;
       cd.w.Leta[o] = (double)se;
+    } else {
+      Jout[o] = J;           // finite-difference evaluation
     }
-    Jout[o] = J;
   }
 }
 

@@ -131,16 +131,20 @@ __device__ __forceinline__ float butterfly8(float v) {
 }
 
 // Output of one depth from the two hemisphere sums (base: D, |D|, I, Lchi, Leta).
-__device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, double Sk64, double c2, float fD, float fa,
-                                           float fI, float fx, float fe, bool fd) {
+// Base and RH92 evaluations write J once, into J_new (the rates read it there);
+// the Lambda diagonals are FP32 sums and stay float.
+__device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, double Sk64, double c2, float c2f,
+                                           float fD, float fa, float fI, float fx, float fe, bool fd) {
   // the representation with the smaller rounding error (intensities are >= 0)
   double J = __dmul_rn(__dadd_rn(Sk64, (double)fD), c2);
   if (fabsf(fI) < fa) J = __dmul_rn((double)fI, c2);
-  cd.w.J[o] = J;
-  if (fd) return;   // finite-difference evaluation: J feeds its rates only
+  if (fd) {   // finite-difference evaluation: J feeds its rates only
+    cd.w.J[o] = J;
+    return;
+  }
   jnew_ptr(cd)[o] = J;
-  cd.w.Lchi[o] = __dmul_rn((double)fx, c2);
-  cd.w.Leta[o] = (double)fe;
+  cd.w.Lchi32[o] = mul(fx, c2f);
+  cd.w.Leta32[o] = fe;
 }
 // Tangent output: dJ (normalised by 2 h nu^3/c^2) in float, depth-major, read
 // by the FP32 tangent rate integrals; o indexes the depth-major arrays.
@@ -181,6 +185,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   const float* __restrict__ dS32T = cd.w.dS32T + q;
   float* __restrict__ part = reinterpret_cast<float*>(cd.w.part) + q;
   const double c2 = T.c2[q];
+  const float c2f = T.c2f[q];
   const bool fdm = !TAN && eval_mode_f(cd) == EV_FD;
 
   float inv2mu[MU], hw[MU], two_mu[MU];
@@ -246,7 +251,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       pp[3 * pstride] = tx;
       pp[4 * pstride] = te;
     } else {
-      write_base(cd, row + k, Sk64, c2, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
+      write_base(cd, row + k, Sk64, c2, c2f, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
                  add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]), fdm);
     }
   };
@@ -385,6 +390,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   const float* __restrict__ dchiT = cd.w.dchiT + qq;
   const float* __restrict__ dS32T = cd.w.dS32T + qq;
   const double c2 = T.c2[qq];
+  const float c2f = T.c2f[qq];
   const bool fdm = !TAN && eval_mode_f(cd) == EV_FD;
   const bool on = m < nmu;
   const float inv2mu = on ? (float)(0.5 / T.mu[m]) : 0.f;
@@ -517,7 +523,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
       const size_t o = (size_t)k * pitch + q;
       write_tan(cd, o, cd.w.dS32T[o], add(upp[k], dn[k]));
     } else {
-      write_base(cd, row + k, S64[k], c2, add(upp[k], dn[k]), add(upp[nz + k], dn[nz + k]),
+      write_base(cd, row + k, S64[k], c2, c2f, add(upp[k], dn[k]), add(upp[nz + k], dn[nz + k]),
                  add(upp[2 * nz + k], dn[2 * nz + k]), add(upp[3 * nz + k], dn[3 * nz + k]),
                  add(upp[4 * nz + k], dn[4 * nz + k]), fdm);
     }

@@ -1,6 +1,6 @@
 // Arithmetic-pipe throughput probe (roofline denominators for ALU-bound
 // kernels): every thread runs independent dependent chains of one operation.
-#include "internal.cuh"
+#include "formal_coef.cuh"
 
 namespace jfnk {
 
@@ -50,9 +50,34 @@ __global__ void k_probe_exp32(float* out) {
   if (s == 12345.678f) out[0] = s;
 }
 
+__global__ void k_check_quotient(const double* a, const double* b, double* q, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = div_nr(a[i], b[i], (float)b[i]);
+}
+
 }  // namespace jfnk
 
 using namespace jfnk;
+
+extern "C" int jfnk_check_quotient(jfnk_ctx* ctx, const double* a, const double* b, double* q, int n) {
+  if (!ctx || n < 0 || (n > 0 && (!a || !b || !q))) return fail(JFNK_E_INVALID, "bad quotient-check arguments");
+  if (n == 0) return JFNK_OK;
+  JFNK_CUDA(cudaSetDevice(ctx->device));
+  double* d = nullptr;
+  JFNK_CUDA(cudaMalloc(&d, sizeof(double) * 3 * (size_t)n));
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(d, a, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, b, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    k_check_quotient<<<(n + 255) / 256, 256, 0, s>>>(d, d + n, d + 2 * (size_t)n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(q, d + 2 * (size_t)n, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(JFNK_E_CUDA, cudaGetErrorString(e));
+  return JFNK_OK;
+}
 
 extern "C" int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s) {
   if (!ctx || !ops_per_s || kind < 0 || kind > 3) return fail(JFNK_E_INVALID, "bad probe arguments");

@@ -80,10 +80,34 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
     return;
   }
   const int q = i / nz, k = i - q * nz;
-  const double c2 = T.c2[q];
   const double* n = eval_pops(cd, mode) + k * nl;
-  double chi = T.chi_c[i] + T.chi_sca[k];
   const double eta_bg = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
+  if (sizeof(real) == sizeof(float)) {
+    // mixed mode: chi is stored in float and S in FP64; on GB300 the FP64
+    // pipe bounds this loop, so each term takes the fewest FP64 operations
+    // (g V tabulated, 2 h nu^3/c^2 factored out of the line emissivity, the
+    // quotient by Newton-Raphson)
+    double chi = T.chi_c[i] + T.chi_sca[k];
+    double el = 0.0;   // sum over lines of g V n_up = eta_lines / (2 h nu^3/c^2)
+    for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+      const int t = T.q_t[s];
+      const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+      const double nup = n[T.t_up[t]], gv = T.gV[p];
+      chi = fma(T.V[p], n[T.t_lo[t]], chi);
+      chi = fma(-gv, nup, chi);
+      el = fma(gv, nup, el);
+    }
+    const float chif = (float)chi;
+    reinterpret_cast<float*>(cd.w.chi)[i] = chif;
+    cd.w.S[i] = div_nr(fma(eta_bg, T.rc2[q], el), chi, chif);
+    if (mode == EV_RH92) {   // for the RH92 rate sums
+      cd.w.eta[i] = fma(el, T.c2[q], eta_bg);
+      cd.w.etab32[i] = (float)eta_bg;
+    }
+    return;
+  }
+  const double c2 = T.c2[q];
+  double chi = T.chi_c[i] + T.chi_sca[k];
   double eta = eta_bg;
   for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
     const int t = T.q_t[s];
@@ -95,10 +119,7 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
   }
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
   cd.w.S[i] = eta / (chi * c2);
-  if (mode == EV_RH92) {   // for the RH92 rate sums
-    cd.w.eta[i] = eta;
-    if (cd.mixed) cd.w.etab32[i] = (float)eta_bg;
-  }
+  if (mode == EV_RH92) cd.w.eta[i] = eta;   // for the RH92 rate sums
 }
 
 // Mixed mode, tangent evaluations: dchi and dS in FP32 (tan_acc), one thread
@@ -384,7 +405,7 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
     for (int r = 0; r < nr; ++r) si += (double)HI[r * plane];
     if (fabs(si) < sa) J = si * c2;   // intensities are non-negative: sum |w I| = sum w I
   }
-  cd.w.J[o] = J;
+  if (mode == EV_FD) cd.w.J[o] = J;   // base and RH92 rates read J_new
   if (mode == EV_TANGENT) {
     const real* dH = reinterpret_cast<const real*>(cd.w.dH) + i;
     double ds = 0.0;
@@ -464,7 +485,8 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
   // slots indexed by level or transition accumulate in place (lane-private)
   for (int j = 2; j < nacc; ++j) sm.d(wid, j, lane) = 0.0;
   if (mix) for (int j = 0; j < sm.fslots; ++j) sm.f(wid, j, lane) = 0.f;
-  const double* __restrict__ J = tan ? cd.w.dJ : cd.w.J;
+  // base and RH92 evaluations leave J in J_new, difference evaluations in J
+  const double* __restrict__ J = tan ? cd.w.dJ : (mode == EV_FD ? cd.w.J : jnew_ptr(cd));
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a5 = 0.0;
   float f0 = 0.f, f1 = 0.f, f3 = 0.f;
   if (!base_mode && !rh) {
@@ -486,7 +508,7 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       a1 = fma(T.WgV[pk], Jq, a1);
       const float Vf = T.V32[pk], gf = T.G32[pk];
       const float Wc = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
-      const float Lx = (float)cd.w.Lchi[o], Le = (float)cd.w.Leta[o];
+      const float Lx = cd.w.Lchi32[o], Le = cd.w.Leta32[o];
       const float cLx = Wc * Lx, cU = Wc * (T.c2f[q] * Le - Lx);
       for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
         const int ts = T.q_t[s];
@@ -524,13 +546,13 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       const double Jq = J[o];
       a0 = fma(T.WV[pk], Jq, a0);
       a1 = fma(T.WgV[pk], Jq, a1);
-      const double Le = cd.w.Leta[o];
-      const float Jf = (float)fma(-Le, cd.w.eta[o], Jq);
+      const float Le = cd.w.Leta32[o];
+      const float Jf = (float)fma(-(double)Le, cd.w.eta[o], Jq);
       const float Wf = T.Wr32[p], Vf = T.V32[pk], gf = T.G32[pk], c2f = T.c2f[q];
       const float WVf = Wf * Vf;
       f0 = fmaf(WVf, Jf, f0);
       f1 = fmaf(WVf * gf, Jf, f1);
-      const float wcp = Wf * (Vf * (nlo_f - gf * nup_f)) * (float)Le;
+      const float wcp = Wf * (Vf * (nlo_f - gf * nup_f)) * Le;
       f3 = fmaf(wcp, cd.w.etab32[o], f3);
       const float wcu = wcp * c2f;
       for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {

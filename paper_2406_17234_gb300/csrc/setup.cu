@@ -330,18 +330,20 @@ __global__ void k_normalise_lines(int nt, const TransDev* tr, const int* t_q0, c
     for (int p = 0; p < nw; ++p) Vt[(size_t)p * nz + k] /= s;
 }
 
-// Rate-integral weights per (window point, depth): W V and W g V with
-// W = omega_t(nu_q) 4 pi/(h nu_q) (Eqs. Rij, Rji), so that the rate integrals
-// take one product per term.
+// Products of the window tables per (window point, depth): g V (stimulated
+// emission and emissivity, Eqs. chi, eta) and the rate-integral weights W V and
+// W g V with W = omega_t(nu_q) 4 pi/(h nu_q) (Eqs. Rij, Rji), so that each term
+// of those sums takes one product.
 __global__ void k_rate_weights(int nwin, int nz, const int* winT, const int* t_q0, const int* t_base,
                                const double* t_w, const double* rw, const double* V, const double* G,
-                               double* WV, double* WgV) {
+                               double* gV, double* WV, double* WgV) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)nwin * nz) return;
   const int p = (int)(i / nz);
   const int t = winT[p];
   const double W = t_w[p] * rw[t_q0[t] + p - t_base[t]];
   const double wv = W * V[i];
+  gV[i] = G[i] * V[i];
   WV[i] = wv;
   WgV[i] = wv * G[i];
 }
@@ -451,13 +453,15 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
   size_t o_V32T = ar.take<float>((size_t)nwin * nz), o_G32T = ar.take<float>((size_t)nwin * nz);
   size_t o_WV = ar.take<double>((size_t)nwin * nz), o_WgV = ar.take<double>((size_t)nwin * nz),
-         o_Rsp = ar.take<double>((size_t)nt * nz);
+         o_Rsp = ar.take<double>((size_t)nt * nz), o_gV = ar.take<double>((size_t)nwin * nz),
+         o_rc2 = ar.take<double>(nq);
   int rc = ar.allocate();
   if (rc) return rc;
   // host-side staging
-  std::vector<double> c2(nq), rw(nq), dzv(nz - 1), mu(nmu), wmu(nmu);
+  std::vector<double> c2(nq), rc2(nq), rw(nq), dzv(nz - 1), mu(nmu), wmu(nmu);
   for (int q = 0; q < nq; ++q) {
     c2[q] = 2.0 * kH * A.nu[q] * A.nu[q] * A.nu[q] / (kC * kC);
+    rc2[q] = 1.0 / c2[q];
     rw[q] = 4.0 * kPi / (kH * A.nu[q]);
   }
   for (int k = 0; k + 1 < nz; ++k) dzv[k] = std::fabs(d->z[k] - d->z[k + 1]);
@@ -499,6 +503,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(up(o_nu, A.nu.data(), nq * 8));
   JFNK_CUDA(up(o_c2, c2.data(), nq * 8));
   JFNK_CUDA(up(o_rw, rw.data(), nq * 8));
+  JFNK_CUDA(up(o_rc2, rc2.data(), nq * 8));
   JFNK_CUDA(up(o_qoff, A.q_off.data(), (nq + 1) * 4));
   JFNK_CUDA(up(o_qt, A.q_t.data(), A.q_t.size() * 4));
   JFNK_CUDA(up(o_tlo, A.t_lo.data(), nt * 4));
@@ -548,8 +553,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
       ar.ptr<double>(o_tw), nz, ar.ptr<double>(o_V));
   k_rate_weights<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
       nwin, nz, ar.ptr<int>(o_winT), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tbase), ar.ptr<double>(o_tw),
-      ar.ptr<double>(o_rw), ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<double>(o_WV),
-      ar.ptr<double>(o_WgV));
+      ar.ptr<double>(o_rw), ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<double>(o_gV),
+      ar.ptr<double>(o_WV), ar.ptr<double>(o_WgV));
   k_spontaneous<<<(nt * nz + tb - 1) / tb, tb, 0, s>>>(nt, nz, ar.ptr<int>(o_tq0), ar.ptr<int>(o_tq1),
                                                         ar.ptr<int>(o_tbase), ar.ptr<double>(o_c2),
                                                         ar.ptr<double>(o_WgV), ar.ptr<double>(o_Rsp));
@@ -569,6 +574,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   tb_.t_lo = ar.ptr<int>(o_tlo); tb_.t_up = ar.ptr<int>(o_tup); tb_.t_q0 = ar.ptr<int>(o_tq0);
   tb_.t_q1 = ar.ptr<int>(o_tq1); tb_.t_base = ar.ptr<int>(o_tbase); tb_.t_w = ar.ptr<double>(o_tw);
   tb_.V = ar.ptr<double>(o_V); tb_.G = ar.ptr<double>(o_G); tb_.dz = ar.ptr<double>(o_dz);
+  tb_.gV = ar.ptr<double>(o_gV); tb_.rc2 = ar.ptr<double>(o_rc2);
   tb_.WV = ar.ptr<double>(o_WV); tb_.WgV = ar.ptr<double>(o_WgV); tb_.Rsp = ar.ptr<double>(o_Rsp);
   tb_.V32 = ar.ptr<float>(o_V32); tb_.G32 = ar.ptr<float>(o_G32); tb_.W32 = ar.ptr<float>(o_W32);
   tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);

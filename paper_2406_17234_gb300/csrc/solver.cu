@@ -33,7 +33,7 @@ void DeviceArena::release() {
 // Offsets of one column's work buffers, relative to the start of its block.
 struct ColLayout {
   size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH,
-      LX, LE, part, J, dJ, Lchi, Leta, Rup, Rdn, dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x,
+      LX, LE, part, J, dJ, Lchi, Leta, Lchi32, Leta32, Rup, Rdn, dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x,
       w, nprev, np, fdp, eta, etab32;
 };
 
@@ -60,7 +60,8 @@ size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout
   o.LX = ar.take<char>(pr); o.LE = ar.take<char>(pr);
   o.part = ar.take<char>(sweep ? sweep_scratch_bytes((int)nq, (int)nz) : 0);
   o.J = ar.take<double>(nq * nz); o.dJ = ar.take<double>(sweep ? 0 : nq * nz);
-  o.Lchi = ar.take<double>(nq * nz); o.Leta = ar.take<double>(nq * nz);
+  o.Lchi = ar.take<double>(sweep ? 0 : nq * nz); o.Leta = ar.take<double>(sweep ? 0 : nq * nz);
+  o.Lchi32 = ar.take<float>(sweep ? nq * nz : 0); o.Leta32 = ar.take<float>(sweep ? nq * nz : 0);
   o.Rup = ar.take<double>(nt * nz); o.Rdn = ar.take<double>(nt * nz);
   o.dRup = ar.take<double>(nt * nz); o.dRdn = ar.take<double>(nt * nz);
   o.Apart = ar.take<double>(nt * nz * nl);
@@ -103,7 +104,8 @@ void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, 
   w.H = P(o.H); w.dH = P(o.dH); w.HI = P(o.HI); w.LX = P(o.LX); w.LE = P(o.LE);
   w.part = P(o.part);
   w.J = (double*)P(o.J); w.dJ = sweep ? nullptr : (double*)P(o.dJ);
-  w.Lchi = (double*)P(o.Lchi); w.Leta = (double*)P(o.Leta);
+  w.Lchi = sweep ? nullptr : (double*)P(o.Lchi); w.Leta = sweep ? nullptr : (double*)P(o.Leta);
+  w.Lchi32 = sweep ? (float*)P(o.Lchi32) : nullptr; w.Leta32 = sweep ? (float*)P(o.Leta32) : nullptr;
   w.zeta = nullptr;
   w.Rup = (double*)P(o.Rup); w.Rdn = (double*)P(o.Rdn);
   w.dRup = (double*)P(o.dRup); w.dRdn = (double*)P(o.dRdn);

@@ -370,3 +370,17 @@ def test_difference_jvps_are_fp64_only(ctx):
     atom, atm, m = _pair(ctx, wl, n_mu=2)
     with pytest.raises(RuntimeError):
         B.solve(atm, B.default_options(jvp=B.JFNK_JVP_CENTRAL, precision=B.JFNK_MIXED))
+
+
+def test_newton_raphson_quotient_within_one_ulp(ctx):
+    """The FP64 quotient of the mixed-mode opacity kernel (S = eta / chi by a
+    Newton-Raphson reciprocal and a residual correction) against the
+    correctly rounded IEEE quotient, over the opacity sums' range."""
+    rng = np.random.default_rng(29)
+    a = 10.0 ** rng.uniform(-30, 30, 100_000)
+    b = 10.0 ** rng.uniform(-30, 30, 100_000)
+    a[:10] = 0.0
+    q = B.check_quotient(ctx, a, b)
+    exact = a / b
+    ulps = np.abs(q - exact) / np.spacing(np.maximum(np.abs(exact), np.finfo(float).tiny))
+    assert ulps.max() <= 1.0
