@@ -22,7 +22,21 @@ Batch::~Batch() {
   if (graph_view) cudaGraphExecDestroy(graph_view);
   if (h_status) cudaFreeHost(h_status);
   for (cudaEvent_t e : tick_ev) cudaEventDestroy(e);
+  if (fork_ev) cudaEventDestroy(fork_ev);
+  if (join_ev) cudaEventDestroy(join_ev);
+  if (side) cudaStreamDestroy(side);
 }
+
+int ensure_side_stream(Batch* b) {
+  if (b->side) return JFNK_OK;
+  JFNK_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+  JFNK_CUDA(cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming));
+  JFNK_CUDA(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+  return JFNK_OK;
+}
+
+// Events per tick of a profiled graph: one pair per formal kernel launch.
+static int tick_events(const Batch& b) { return b.formal_kind == FORMAL_SWEEP ? 4 : 2; }
 
 // Work buffers and the tick graph of one column, cached in its handle.
 struct SingleWork {
@@ -132,16 +146,23 @@ __global__ void k_init_state(SolverState* st, int n, int phase) {
 // Captures kTicksPerGraph ticks (evaluation + Krylov step) of the batch's
 // current launch view into an executable graph.
 int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out) {
-  if (profile && b->tick_ev.empty()) {
-    b->tick_ev.resize(2 * kTicksPerGraph);
+  const int ne = tick_events(*b);
+  if (profile && (int)b->tick_ev.size() < ne * kTicksPerGraph) {
+    for (cudaEvent_t e : b->tick_ev) cudaEventDestroy(e);
+    b->tick_ev.assign(ne * kTicksPerGraph, nullptr);
     for (auto& e : b->tick_ev) JFNK_CUDA(cudaEventCreate(&e));
+  }
+  if (b->formal_kind == FORMAL_SWEEP) {
+    int rs = ensure_side_stream(b);
+    if (rs) return rs;
   }
   cudaGraph_t g;
   JFNK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int rc = JFNK_OK;
   for (int t = 0; t < kTicksPerGraph && !rc; ++t) {
-    rc = profile ? launch_evaluation(*b, s, b->tick_ev[2 * t], b->tick_ev[2 * t + 1])
-                 : launch_evaluation(*b, s);
+    cudaEvent_t* ev = profile ? &b->tick_ev[(size_t)ne * t] : nullptr;
+    rc = launch_evaluation(*b, s, ev ? ev[0] : nullptr, ev ? ev[1] : nullptr, b->side,
+                           ev && ne == 4 ? ev[2] : nullptr, ev && ne == 4 ? ev[3] : nullptr);
     if (!rc) rc = launch_krylov_step(*b, s);   // P^k was factorised by the assembly
   }
   cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -203,12 +224,16 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
     b->replays++;
     if (cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(JFNK_E_CUDA, "status poll failed"); break; }
-    if (profile)
+    if (profile) {
+      // the formal kernels' own durations (summed when the two sweeps overlap)
+      const int ne = tick_events(*b);
       for (int t = 0; t < b->graph_ticks; ++t) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, b->tick_ev[2 * t], b->tick_ev[2 * t + 1]);
-        b->tick_ms.push_back(ms);
+        float ms = 0.f, ms2 = 0.f;
+        cudaEventElapsedTime(&ms, b->tick_ev[(size_t)ne * t], b->tick_ev[(size_t)ne * t + 1]);
+        if (ne == 4) cudaEventElapsedTime(&ms2, b->tick_ev[(size_t)ne * t + 2], b->tick_ev[(size_t)ne * t + 3]);
+        b->tick_ms.push_back(ms + ms2);
       }
+    }
     std::vector<int> running;
     for (int c = 0; c < b->ncols; ++c)
       if (b->h_status[c] == 1) running.push_back(view[c]);

@@ -530,11 +530,11 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   }
 }
 
-__global__ void __launch_bounds__(256) k_formal_sweep_warp(const ColDesc* __restrict__ cols) {
+__global__ void __launch_bounds__(256) k_formal_sweep_warp(const ColDesc* __restrict__ cols, int which) {
   extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|, per warp [2][2][parts][nz]
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode_f(cd);
-  if (mode == EV_SKIP) return;
+  if (mode == EV_SKIP || (which == 1 && mode == EV_TANGENT) || (which == 2 && mode != EV_TANGENT)) return;
   const ColTables& T = cd.t;
   const int nz = T.nz, nq = T.nq;
   const int warps = blockDim.x >> 5;
@@ -562,26 +562,27 @@ static int sweep_mu_class(int nmu) {
 }
 
 template <int MU>
-static void launch_mu(const Batch& b, cudaStream_t s, int threads) {
+static void launch_mu(const Batch& b, cudaStream_t s, int threads, int which) {
   dim3 g((b.max_nq + threads - 1) / threads, b.ncols);
   const size_t bytes = sizeof(float) * 2 * (size_t)b.max_nz;
-  k_formal_sweep<MU, true><<<g, threads, bytes, s>>>(b.d_cols);
-  k_formal_sweep<MU, false><<<g, threads, bytes, s>>>(b.d_cols);
+  if (which != 1) k_formal_sweep<MU, true><<<g, threads, bytes, s>>>(b.d_cols);
+  if (which != 2) k_formal_sweep<MU, false><<<g, threads, bytes, s>>>(b.d_cols);
 }
 
-// variant 1: ``size`` threads per block; variant 2: ``size`` warps per block
-static int launch_sweep_cfg(const Batch& b, cudaStream_t s, int variant, int size) {
+// variant 1: ``size`` threads per block; variant 2: ``size`` warps per block;
+// which: 0 every column, 1 base-type evaluations, 2 tangent ones
+static int launch_sweep_cfg(const Batch& b, cudaStream_t s, int variant, int size, int which = 0) {
   if (variant == 2) {
     const int fpb = 2 * size;   // frequencies per block
     dim3 g((b.max_nq + fpb - 1) / fpb, b.ncols);
-    k_formal_sweep_warp<<<g, 32 * size, warp_variant_smem(b.max_nz, size), s>>>(b.d_cols);
+    k_formal_sweep_warp<<<g, 32 * size, warp_variant_smem(b.max_nz, size), s>>>(b.d_cols, which);
   } else {
     switch (sweep_mu_class(b.max_nmu)) {
-      case 2: launch_mu<2>(b, s, size); break;
-      case 3: launch_mu<3>(b, s, size); break;
-      case 4: launch_mu<4>(b, s, size); break;
-      case 5: launch_mu<5>(b, s, size); break;
-      default: launch_mu<8>(b, s, size); break;
+      case 2: launch_mu<2>(b, s, size, which); break;
+      case 3: launch_mu<3>(b, s, size, which); break;
+      case 4: launch_mu<4>(b, s, size, which); break;
+      case 5: launch_mu<5>(b, s, size, which); break;
+      default: launch_mu<8>(b, s, size, which); break;
     }
   }
   JFNK_CUDA(cudaGetLastError());
@@ -603,8 +604,9 @@ int sweep_prepare(Batch* b) {
   return JFNK_OK;
 }
 
-int launch_formal_sweep(const Batch& b, cudaStream_t s) {
-  return launch_sweep_cfg(b, s, b.sweep_variant == 2 ? 2 : 1, b.formal_threads > 0 ? b.formal_threads : 128);
+int launch_formal_sweep(const Batch& b, cudaStream_t s, int which) {
+  return launch_sweep_cfg(b, s, b.sweep_variant == 2 ? 2 : 1, b.formal_threads > 0 ? b.formal_threads : 128,
+                          which);
 }
 
 int sweep_warp_size(int nz) {

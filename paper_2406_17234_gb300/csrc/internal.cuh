@@ -109,7 +109,11 @@ struct Batch {
   bool tuned = false;                 // autotuner has run on this batch
   int graph_kernels = 0;              // kernel nodes in the captured tick graph
   long replays = 0;                   // graph replays of the last solve
-  std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel of each tick
+  std::vector<cudaEvent_t> tick_ev;   // event pairs around the formal kernel(s) of each tick
+  // mixed mode: the tangent kernels of a tick run on a side stream, beside the
+  // base kernels of the other columns, and join before the assembly
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve
   int* h_status = nullptr;            // pinned host mirror of d_status
   // launch view over the columns still running (straggler compaction)
@@ -128,9 +132,13 @@ void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, 
 // Allocates work buffers for columns ``tabs`` (precision: mixed or FP64).
 int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed, int kmax);
 // Launch sequence of one F-class evaluation for every column of the batch.
-// ev0/ev1 (optional) are recorded around the formal-solution kernel.
-int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                      cudaEvent_t ev1 = nullptr);
+// ev0/ev1 (optional) are recorded around the formal-solution kernel. With a
+// side stream (mixed mode) the tangent kernels go there, forked from and joined
+// back into s, and ev2/ev3 bracket the tangent sweep (ev0/ev1 the base one).
+int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                      cudaStream_t side = nullptr, cudaEvent_t ev2 = nullptr, cudaEvent_t ev3 = nullptr);
+// Creates the side stream and the fork/join events of a mixed-mode batch.
+int ensure_side_stream(Batch* b);
 // Launch of the Krylov/Newton state machine step.
 int launch_krylov_step(const Batch& b, cudaStream_t s);
 // Fused formal solution + ray sums (formal_fused.cu).
@@ -142,7 +150,8 @@ int fused_autotune(Batch* b, cudaStream_t s);
 // Per-frequency sweep kernel of the mixed mode (formal_sweep.cu).
 size_t sweep_scratch_bytes(int nq, int nz);
 int sweep_prepare(Batch* b);
-int launch_formal_sweep(const Batch& b, cudaStream_t s);
+// which: 0 every column, 1 base-type evaluations only, 2 tangent ones only
+int launch_formal_sweep(const Batch& b, cudaStream_t s, int which = 0);
 // Warps per block of the warp variant whose shared memory fits depth nz (0: none).
 int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);

@@ -431,8 +431,8 @@ __global__ void k_ray_sum(const ColDesc* __restrict__ cols) {
 // and in RH92 mode the sums of the preconditioned rate equations.
 // ---------------------------------------------------------------------------
 constexpr int kRateWarps = 4;
-constexpr int kRateSplit = 4;            // blocks of a cluster sharing one (transition, depth tile)
-constexpr int kRateClustersPerSM = 32;   // clusters of the column loop per multiprocessor
+constexpr int kRateSplit = 4;            // most blocks of a cluster sharing one (transition, depth tile)
+constexpr int kRateBlocksPerSM = 128;    // blocks of the column loop per multiprocessor
 
 // Per-lane partial sums in dynamic shared memory: racc doubles
 // [warp][slot][lane], then (mixed mode) fslots floats [warp][slot][lane].
@@ -455,7 +455,7 @@ __device__ __forceinline__ int rate_mode(const ColDesc& cd, int t, int tile) {
 }
 
 // One (32-depth tile, transition t, column): lanes map to depths (every table
-// and J access is coalesced), the kRateSplit blocks of the cluster split the
+// and J access is coalesced), the ``split`` blocks of the cluster split the
 // frequency window into contiguous chunks and their warps stride through the
 // chunk; partial sums are reduced through shared memory inside a block and
 // through distributed shared memory across the cluster, in a fixed order
@@ -478,8 +478,9 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
   const int k = min(tile * 32 + lane, nz - 1);
   const int q0 = T.t_q0[t], q1 = T.t_q1[t], wbase = T.t_base[t];
   const int nw = q1 - q0 + 1;
-  const int qa = q0 + (int)(((long)nw * rank) / kRateSplit);
-  const int qb = q0 + (int)(((long)nw * (rank + 1)) / kRateSplit) - 1;
+  const int split = (int)cluster.num_blocks();
+  const int qa = q0 + (int)(((long)nw * rank) / split);
+  const int qb = q0 + (int)(((long)nw * (rank + 1)) / split) - 1;
   const double* n = eval_pops(cd, mode) + k * nl;
   const double n_lo = n[T.t_lo[t]], n_up = n[T.t_up[t]];
   // slots indexed by level or transition accumulate in place (lane-private)
@@ -609,7 +610,7 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
     if (kw < nz) {
       double acc[2 + kRhFixed + kMaxT > 2 + kMaxL ? 2 + kRhFixed + kMaxT : 2 + kMaxL];
       for (int j = 0; j < nacc; ++j) acc[j] = sm.d(0, j, lane);
-      for (int r = 1; r < kRateSplit; ++r) {
+      for (int r = 1; r < split; ++r) {
         const double* peer = cluster.map_shared_rank(sm.red, r);
         for (int j = 0; j < nacc; ++j) acc[j] += peer[(size_t)j * 32 + lane];
       }
@@ -649,8 +650,9 @@ __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __rest
   sm.fslots = fslots;
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.y, tile = blockIdx.x;
-  const int step = gridDim.z / kRateSplit;
-  for (int c0 = blockIdx.z / kRateSplit; c0 < ncols; c0 += 32 * step) {
+  const int split = (int)cluster.num_blocks();
+  const int step = gridDim.z / split;
+  for (int c0 = blockIdx.z / split; c0 < ncols; c0 += 32 * step) {
     const int cl = c0 + lane * step;
     const int ml = cl < ncols ? rate_mode(cols[cl], t, tile) : EV_SKIP;
     unsigned act = __ballot_sync(0xffffffffu, ml != EV_SKIP);   // the same in every warp of the cluster
@@ -677,11 +679,15 @@ static int launch_rates(const Batch& b, cudaStream_t s) {
   const int racc = 2 + std::max(kRhFixed + b.max_nt, kMaxL);
   const int fslots = b.mixed ? std::max(b.max_nt, kMaxL) : 0;
   const size_t smem = (size_t)kRateWarps * 32 * (racc * sizeof(double) + fslots * sizeof(float));
-  const long want = (long)kRateClustersPerSM * std::max(b.n_sm, 1);
+  const long sms = std::max(b.n_sm, 1);
   const long per = (long)tiles * std::max(b.max_nt, 1);
+  // a frequency window is split over a cluster only when the (tile,
+  // transition, column) units alone leave the multiprocessors short of blocks
+  const int split = (long)b.ncols * per >= 32 * sms ? 1 : kRateSplit;
+  const long want = kRateBlocksPerSM * sms / split;
   const int cz = (int)std::max(1L, std::min<long>(b.ncols, (want + per - 1) / per));
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(tiles, b.max_nt, cz * kRateSplit);
+  cfg.gridDim = dim3(tiles, b.max_nt, cz * split);
   cfg.blockDim = dim3(32 * kRateWarps);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -689,7 +695,7 @@ static int launch_rates(const Batch& b, cudaStream_t s) {
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 1;
   attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = kRateSplit;
+  attr[0].val.clusterDim.z = split;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_rates, (const ColDesc*)b.d_cols, b.ncols, racc, fslots));
@@ -856,13 +862,45 @@ int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
   return JFNK_OK;
 }
 
-int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+static void launch_rates_tan32(const Batch& b, cudaStream_t s) {
+  k_rates_tan32<<<dim3((b.max_nz + kRateTanWarps * kRateTanDepths - 1) / (kRateTanWarps * kRateTanDepths),
+                       b.max_nt, b.ncols),
+                  32 * kRateTanWarps, 0, s>>>(b.d_cols);
+}
+
+int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t side,
+                      cudaEvent_t ev2, cudaEvent_t ev3) {
   const int nc = b.ncols;
   if (nc == 0) return JFNK_OK;
   const int tb = 256;
   dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
   dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
   dim3 g_asm((b.max_nz + kAsmWarps - 1) / kAsmWarps, nc);
+  if (b.formal_kind == FORMAL_SWEEP && side) {
+    // Two independent chains over disjoint columns (a column is in one
+    // evaluation kind per tick): tangent evaluations (FP32, issue-bound) on the
+    // side stream, base and RH92 ones (FP64-heavy) on s; joined before the
+    // assembly, which reads both.
+    JFNK_CUDA(cudaEventRecord(b.fork_ev, s));
+    JFNK_CUDA(cudaStreamWaitEvent(side, b.fork_ev, 0));
+    k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, side>>>(b.d_cols);
+    k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, side>>>(b.d_cols);
+    if (ev2) JFNK_CUDA(cudaEventRecordWithFlags(ev2, side, cudaEventRecordExternal));
+    int rc = launch_formal_sweep(b, side, 2);
+    if (rc) return rc;
+    if (ev3) JFNK_CUDA(cudaEventRecordWithFlags(ev3, side, cudaEventRecordExternal));
+    launch_rates_tan32(b, side);
+    JFNK_CUDA(cudaEventRecord(b.join_ev, side));
+    k_opacity<float><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 1);
+    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+    if ((rc = launch_formal_sweep(b, s, 1))) return rc;
+    if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+    if ((rc = launch_rates(b, s))) return rc;
+    JFNK_CUDA(cudaStreamWaitEvent(s, b.join_ev, 0));
+    k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
+    JFNK_CUDA(cudaGetLastError());
+    return JFNK_OK;
+  }
   if (b.formal_kind == FORMAL_SWEEP) {
     // (float tangent direction,) opacity, then the per-frequency sweeps
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
@@ -890,10 +928,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   {
     int rc = launch_rates(b, s);
     if (rc) return rc;
-    if (b.mixed)
-      k_rates_tan32<<<dim3((b.max_nz + kRateTanWarps * kRateTanDepths - 1) / (kRateTanWarps * kRateTanDepths),
-                           b.max_nt, nc),
-                      32 * kRateTanWarps, 0, s>>>(b.d_cols);
+    if (b.mixed) launch_rates_tan32(b, s);
   }
   k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());
