@@ -135,9 +135,10 @@ __device__ __forceinline__ float butterfly8(float v) {
 // the Lambda diagonals are FP32 sums and stay float.
 __device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, double Sk64, double c2, float c2f,
                                            float fD, float fa, float fI, float fx, float fe, bool fd) {
-  // the representation with the smaller rounding error (intensities are >= 0)
-  double J = __dmul_rn(__dadd_rn(Sk64, (double)fD), c2);
-  if (fabsf(fI) < fa) J = __dmul_rn((double)fI, c2);
+  // the representation with the smaller rounding error (intensities are >= 0),
+  // J = (S + sum D) c2 or (sum I) c2, with one conversion and one FP64 sum
+  const bool useI = fabsf(fI) < fa;
+  const double J = __dmul_rn(__dadd_rn(useI ? 0.0 : Sk64, (double)(useI ? fI : fD)), c2);
   if (fd) {   // finite-difference evaluation: J feeds its rates only
     cd.w.J[o] = J;
     return;
@@ -259,13 +260,21 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
 
   // the next depth's inputs are prepared one step ahead
   int kn = UP ? nz - 2 : 1;
-  float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f;
+  float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f, Sf_n = 0.f;
   double S_n = 0.0;
   auto load = [&](int kk) {
     if (TAN) {
       c_n = chiT[(size_t)kk * pitch];
       dSl_n = dSkT[(size_t)(UP ? kk : kk - 1) * pitch];
       tan_in(kk, dc_n, dS_n);
+    } else if (UP) {
+      // the outward sweep of a base evaluation reads the float copies its own
+      // inward sweep left (coalesced; the same values, no FP64 difference)
+      // and S in FP64 for J only
+      c_n = chiT[(size_t)kk * pitch];
+      Sf_n = S32T[(size_t)kk * pitch];
+      dSl_n = dSkT[(size_t)kk * pitch];
+      S_n = S64[kk];
     } else {
       c_n = chi[kk];
       S_n = S64[kk];
@@ -275,7 +284,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   for (int s = 1; s < nz; ++s) {
     const int k = kn;
     const int kd = UP ? k : k - 1;   // layer between k and its upstream neighbour
-    const float c0 = c_n, dc0 = dc_n, dS0 = dS_n, dSl = dSl_n;
+    const float c0 = c_n, dc0 = dc_n, dS0 = dS_n, dSl = dSl_n, Sf = Sf_n;
     const double Sk64 = S_n;
     if (s + 1 < nz) {
       kn = UP ? k - 1 : k + 1;
@@ -296,8 +305,8 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       in.dtz = mul(in.dzk, in.dcs);
       in.ddSin = sub(dSp, dS0);
     } else {
-      in.dSin = __double2float_rn(__dsub_rn(Sp, Sk64));
-      in.S0 = __double2float_rn(Sk64);
+      in.dSin = UP ? dSl : __double2float_rn(__dsub_rn(Sp, Sk64));
+      in.S0 = UP ? Sf : __double2float_rn(Sk64);
       if (!UP) {
         // depth-major copies for the tangent evaluations
         chiT[(size_t)k * pitch] = c0;
