@@ -142,15 +142,9 @@ __global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict
     const float* G32 = G32T + (size_t)k * nwin;
     const float* v = v32 + k * nl;
     TanAcc ta;
-    // every packed entry first (independent loads, up to the column's largest
-    // overlap), then the table values of the active ones: two dependent
-    // round trips per point instead of two per transition
-    int mq[kQMetaT];
-#pragma unroll
-    for (int j = 0; j < kQMetaT; ++j) mq[j] = j < T.max_overlap ? __ldg(qmeta + (size_t)j * nq + q) : -1;
 #pragma unroll
     for (int j = 0; j < kQMetaT; ++j) {
-      const int m = mq[j];
+      const int m = __ldg(qmeta + (size_t)j * nq + q);
       if (m < 0) break;
       const int p = m >> 8;
       tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + ((m >> 4) & 15)), __ldg(v + (m & 15)));
@@ -193,7 +187,6 @@ __global__ void __launch_bounds__(32 * kRateTanWarps) k_rates_tan32(const ColDes
   float a0[kRateTanDepths], a1[kRateTanDepths];
 #pragma unroll
   for (int d = 0; d < kRateTanDepths; ++d) a0[d] = a1[d] = 0.f;
-#pragma unroll 2
   for (int q = q0 + lane; q <= q1; q += 32) {
     const float W = __ldg(W32 + q);
 #pragma unroll
