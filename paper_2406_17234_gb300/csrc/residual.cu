@@ -92,11 +92,10 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
     for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
       const int t = T.q_t[s];
       const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
-      const double nup = n[T.t_up[t]], gv = T.gV[p];
       chi = fma(T.V[p], n[T.t_lo[t]], chi);
-      chi = fma(-gv, nup, chi);
-      el = fma(gv, nup, el);
+      el = fma(T.gV[p], n[T.t_up[t]], el);
     }
+    chi -= el;   // stimulated emission: the same sum of g V n_up
     const float chif = (float)chi;
     reinterpret_cast<float*>(cd.w.chi)[i] = chif;
     cd.w.S[i] = div_nr(fma(eta_bg, T.rc2[q], el), chi, chif);
@@ -721,7 +720,6 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
   if (k >= nz) return;
   __shared__ double s_up[kAsmWarps][kMaxT], s_dn[kAsmWarps][kMaxT], s_kap[kAsmWarps][kMaxT];
   __shared__ double s_P[kAsmWarps][kMaxL * kMaxL];
-  __shared__ int s_piv[kAsmWarps][kMaxL];
   const bool fd = (mode == EV_FD);
   const double* n = eval_pops(cd, mode) + k * nl;
   const double* C = T.C + (size_t)k * nl * nl;
@@ -790,57 +788,51 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
     for (int e = lane; e < nl * nl; e += 32) P[e] = s_P[wid][e];
     return;
   }
-  if (lane == 0) {
-    // LU with partial pivoting, in shared memory
-    double* A = s_P[wid];
-    for (int c = 0; c < nl; ++c) {
-      int pr = c;
-      double best = fabs(A[c * nl + c]);
-      for (int r = c + 1; r < nl; ++r) {
-        const double vv = fabs(A[r * nl + c]);
-        if (vv > best) { best = vv; pr = r; }
-      }
-      s_piv[wid][c] = pr;
-      if (pr != c)
-        for (int j = 0; j < nl; ++j) {
-          const double tmp = A[c * nl + j];
-          A[c * nl + j] = A[pr * nl + j];
-          A[pr * nl + j] = tmp;
-        }
-      const double d = A[c * nl + c];
-      for (int r = c + 1; r < nl; ++r) {
-        const double f = A[r * nl + c] / d;
-        A[r * nl + c] = f;
-        for (int j = c + 1; j < nl; ++j) A[r * nl + j] -= f * A[c * nl + j];
-      }
-    }
+  // explicit inverse of P^k, so that the Krylov step applies P^{-1} as a fully
+  // parallel small mat-vec: Gauss-Jordan elimination with partial pivoting on
+  // [P | I], lane j owning column j (2 nl <= 32 lanes); every lane finds the
+  // same pivot from the same shared data, one reciprocal per column
+  __shared__ double s_aug[kAsmWarps][kMaxL * 2 * kMaxL];
+  double* G = s_aug[wid];
+  const int w2 = 2 * nl;
+  for (int e = lane; e < nl * w2; e += 32) {
+    const int r = e / w2, j = e - r * w2;
+    G[e] = j < nl ? s_P[wid][r * nl + j] : (j - nl == r ? 1.0 : 0.0);
   }
   __syncwarp();
-  // explicit inverse of P^k: lane j solves P x = e_j with the factors, so that
-  // the Krylov step applies P^{-1} as a fully parallel small mat-vec
-  __shared__ double s_inv[kAsmWarps][kMaxL * kMaxL];
-  if (lane < nl) {
-    const double* A = s_P[wid];
-    double x[kMaxL];
-    for (int r = 0; r < nl; ++r) x[r] = (r == lane) ? 1.0 : 0.0;
-    for (int c = 0; c < nl; ++c) {
-      const int p = s_piv[wid][c];
-      if (p != c) { const double t = x[c]; x[c] = x[p]; x[p] = t; }
+  const bool own = lane < w2;
+  for (int c = 0; c < nl; ++c) {
+    int pr = c;
+    double best = fabs(G[c * w2 + c]);
+    for (int r = c + 1; r < nl; ++r) {
+      const double vv = fabs(G[r * w2 + c]);
+      if (vv > best) { best = vv; pr = r; }
     }
-    for (int r = 1; r < nl; ++r) {
-      double acc = x[r];
-      for (int c = 0; c < r; ++c) acc -= A[r * nl + c] * x[c];
-      x[r] = acc;
+    __syncwarp();   // every lane has read column c before rows move
+    if (own && pr != c) {
+      const double tmp = G[c * w2 + lane];
+      G[c * w2 + lane] = G[pr * w2 + lane];
+      G[pr * w2 + lane] = tmp;
     }
-    for (int r = nl - 1; r >= 0; --r) {
-      double acc = x[r];
-      for (int c = r + 1; c < nl; ++c) acc -= A[r * nl + c] * x[c];
-      x[r] = acc / A[r * nl + r];
+    __syncwarp();
+    const double rd = 1.0 / G[c * w2 + c];
+    double f[kMaxL];
+#pragma unroll
+    for (int r = 0; r < kMaxL; ++r) f[r] = r < nl ? G[r * w2 + c] : 0.0;
+    __syncwarp();   // the pivot row and column are read before they change
+    if (own) {
+      const double pc = G[c * w2 + lane] * rd;
+      G[c * w2 + lane] = pc;
+#pragma unroll
+      for (int r = 0; r < kMaxL; ++r)
+        if (r < nl && r != c) G[r * w2 + lane] = fma(-f[r], pc, G[r * w2 + lane]);
     }
-    for (int r = 0; r < nl; ++r) s_inv[wid][r * nl + lane] = x[r];
+    __syncwarp();
   }
-  __syncwarp();
-  for (int e = lane; e < nl * nl; e += 32) P[e] = s_inv[wid][e];
+  for (int e = lane; e < nl * nl; e += 32) {
+    const int r = e / nl, j = e - r * nl;
+    P[e] = G[r * w2 + nl + j];
+  }
 }
 
 // ---------------------------------------------------------------------------
