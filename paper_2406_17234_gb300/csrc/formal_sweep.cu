@@ -344,10 +344,9 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
 }
 
 // One kernel per evaluation kind (its own register allocation): blocks of
-// columns in the other kind return at once. The base kind carries five sums
-// per angle; its register budget is capped so that more warps hide latency.
+// columns in the other kind return at once.
 template <int MU, bool TAN>
-__global__ void __launch_bounds__(256, TAN ? 1 : 3) k_formal_sweep(const ColDesc* __restrict__ cols) {
+__global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict__ cols) {
   extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode_f(cd);
