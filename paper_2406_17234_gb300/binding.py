@@ -125,7 +125,7 @@ _SIGNATURES = {
     "jfnk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(jfnk_options), C.c_void_p,
                              C.c_void_p, C.POINTER(jfnk_stats), C.c_int, C.c_void_p]),
     "jfnk_probe_alu": (C.c_int, [C.c_void_p, C.c_int, _dp]),
-    "jfnk_check_quotient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "jfnk_check_arith": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "jfnk_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.c_int, C.c_int,
                                     C.POINTER(C.c_void_p)]),
     "jfnk_batch_run": (C.c_int, [C.c_void_p, C.POINTER(jfnk_options), C.POINTER(C.c_void_p),
@@ -369,12 +369,16 @@ def probe_alu(ctx: Context, kind: int) -> float:
     return v.value
 
 
-def check_quotient(ctx: Context, a, b):
-    """The library's FP64 Newton-Raphson quotient a / b (its accuracy test)."""
+ARITH_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "acc": 4}
+
+
+def check_arith(ctx: Context, op: str, a, b):
+    """The library's float-pair arithmetic on a, b (its accuracy test)."""
     a, b = _f64(a).ravel(), _f64(b).ravel()
-    q = np.zeros_like(a)
-    check(ctx.lib.jfnk_check_quotient(ctx.h, _ptr(a), _ptr(b), _ptr(q), a.size), "jfnk_check_quotient")
-    return q
+    out = np.zeros_like(a)
+    check(ctx.lib.jfnk_check_arith(ctx.h, ARITH_OPS[op], _ptr(a), _ptr(b), _ptr(out), a.size),
+          "jfnk_check_arith")
+    return out
 
 
 def batch_solve(ctx: Context, atms: Sequence[Atmosphere], opts: Optional[jfnk_options] = None,

@@ -95,6 +95,7 @@ static int explicit_eval(jfnk_ctx* ctx, const jfnk_atmos* a, Batch* b, int mode,
     JFNK_CUDA(cudaMemcpyAsync(c.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
   }
   if ((rc = batch_set_forced_mode(b, mode, s))) return rc;
+  if (b->mixed && (rc = launch_j_pairs(b->d_cols, 1, QZ, s, true))) return rc;
   return launch_evaluation(*b, s);
 }
 
@@ -324,6 +325,7 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
       JFNK_CUDA(cudaMemcpyAsync(cd.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, s));
     }
   }
+  if (b->mixed && (rc = launch_j_pairs(b->d_cols, b->ncols, (size_t)b->max_nq * b->max_nz, s, true))) return rc;
   if (o->init == JFNK_INIT_ZERO_RADIATION && (rc = launch_zero_radiation(*b, s))) return rc;
   if (b->formal_kind == FORMAL_SWEEP && o->formal_variant != 0) {
     // a forced sweep variant (results are the same as with the tuned one)
@@ -366,13 +368,15 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
   JFNK_CUDA(cudaMemcpyAsync(st.data(), b->d_state, sizeof(SolverState) * b->ncols, cudaMemcpyDeviceToHost, s));
   JFNK_CUDA(cudaStreamSynchronize(s));
   int rc;
+  if (b->mixed && J_out && (rc = launch_j_pairs(b->d_cols, b->ncols, (size_t)b->max_nq * b->max_nz, s, false)))
+    return rc;
   for (int c = 0; c < b->ncols; ++c) {
     const ColDesc& cd = b->h_cols[c];
     const AtmosData& M = cols[c]->d;
     const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
     if (n_out && n_out[c] && (rc = copy_out(n_out[c], cd.w.n, N * 8, where, s))) return rc;
     // after the last base evaluation the new J sits in the buffer opposite to J^dagger
-    const double* Jfinal = st[c].jsel ? cd.w.Jdag : cd.w.Jnew;
+    const double* Jfinal = st[c].jsel ? cd.w.Jdag : cd.w.Jnew;   // FP64 again in mixed mode
     if (J_out && J_out[c] && (rc = copy_out(J_out[c], Jfinal, QZ * 8, where, s))) return rc;
   }
   JFNK_CUDA(cudaStreamSynchronize(s));
@@ -593,6 +597,7 @@ int jfnk_residual(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const doubl
     const ColDesc& c = b->h_cols[0];
     const AtmosData& M = a->d;
     if ((r = copy_out(F, c.w.F, (size_t)M.nz * M.nl * 8, where, s))) return r;
+    if (J_new && b->mixed && (r = launch_j_pairs(b->d_cols, 1, (size_t)M.nq * M.nz, s, false))) return r;
     if (J_new && (r = copy_out(J_new, c.w.Jnew, (size_t)M.nq * M.nz * 8, where, s))) return r;
     if (I_emergent && (r = copy_out(I_emergent, c.w.Iem, (size_t)M.nq * M.nmu * 8, where, s))) return r;
     return 0;
@@ -652,6 +657,7 @@ int jfnk_rh92_update(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const do
     const ColDesc& c = b->h_cols[0];
     const AtmosData& M = a->d;
     if ((r = copy_out(n_out, c.w.n, (size_t)M.nz * M.nl * 8, where, s))) return r;
+    if (J_new && b->mixed && (r = launch_j_pairs(b->d_cols, 1, (size_t)M.nq * M.nz, s, false))) return r;
     if (J_new && (r = copy_out(J_new, c.w.Jnew, (size_t)M.nq * M.nz * 8, where, s))) return r;
     return 0;
   });

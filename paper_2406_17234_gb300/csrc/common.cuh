@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "jfnk.h"
 
 namespace jfnk {
@@ -65,6 +66,16 @@ struct ColTables {
   const double* V;        // [nwin][nz]
   const double* G;        // [nwin][nz]
   const double* gV;       // [nwin][nz] g V
+  // float pairs (hi + lo, about 48 bits) of the tables the mixed mode's
+  // base evaluations need beyond FP32, for arithmetic on the FP32 pipe
+  const float2* V2;       // [nwin][nz] V
+  const float2* gV2;      // [nwin][nz] g V
+  const float2* W2;       // [nwin] W = omega_t(nu_q) 4 pi/(h nu_q)
+  const float2* chibg2;   // [nq][nz] chi_c + chi_sca
+  const float2* etac2;    // [nq][nz] eta_c
+  const float2* chisca2;  // [nz] chi_sca
+  const float2* c2p;      // [nq] 2 h nu^3/c^2
+  const float2* rc2p;     // [nq] c^2/(2 h nu^3)
   const double* rc2;      // [nq] c^2 / (2 h nu^3)
   const double* WV;       // [nwin][nz] W V with W = omega_t(nu_q) 4 pi/(h nu_q): rate-integral weights
   const double* WgV;      // [nwin][nz] W g V
@@ -175,6 +186,7 @@ struct ColWork {
   double* w;        // [N]
   double* nprev;    // [N]
   double* eta;      // [nq][nz] emissivity of an RH92 evaluation, for Jeff = J - Psi* eta
+  float2* n2;       // [N] populations as float pairs (mixed-mode base evaluations)
   float* etab32;    // [nq][nz] its background part eta_c + chi_sca J^dagger (mixed mode)
   double* np;       // [N] populations of a finite-difference evaluation (n + s eps u)
   double* fdp;      // [N] F(n + eps u) of a central difference
@@ -194,6 +206,13 @@ struct ColDesc {
   int mixed;         // 1: FP32 formal solution (buffers are float)
   const SolverOpts* opts;   // this column's solver options (null: the batch's)
 };
+
+// Mixed mode: S, J^dagger, J_new and the RH92 emissivity hold float pairs
+// (hi, lo) in the bytes of their FP64 arrays.
+__host__ __device__ __forceinline__ float2* as_pairs(double* p) { return reinterpret_cast<float2*>(p); }
+__host__ __device__ __forceinline__ const float2* as_pairs(const double* p) {
+  return reinterpret_cast<const float2*>(p);
+}
 
 // The lagged mean intensity J^dagger and the newly computed J live in two
 // buffers whose roles swap after every Newton update (no copy); explicit

@@ -96,18 +96,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// a / b in FP64 by Newton-Raphson from the FP32 reciprocal of b (the
-// classical reciprocal iteration r <- r + r (1 - b r), which squares the
-// relative error: 2^-23 -> 2^-46), then one correction of the quotient from its
-// residual, q <- q + r (a - b q) (Markstein's final step): within an ulp or so
-// of a / b, five FP64 operations instead of a full division. For b > 0 whose
-// float rounding bf is normal (the opacity sums here: 1e-30 < b < 1e30).
-__device__ __forceinline__ double div_nr(double a, double b, float bf) {
-  double r = (double)rcp_approx(bf);
-  r = fma(r, fma(-b, r, 1.0), r);
-  const double q = a * r;
-  return fma(r, fma(-b, q, a), q);
-}
 __device__ __forceinline__ float tan_dS(const TanAcc& t, float S, float chi) {
   return mul(sub(t.deta, mul(S, t.dchi)), rcp_approx(chi));
 }

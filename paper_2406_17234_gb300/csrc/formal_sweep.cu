@@ -131,19 +131,16 @@ __device__ __forceinline__ float butterfly8(float v) {
 }
 
 // Output of one depth from the two hemisphere sums (base: D, |D|, I, Lchi, Leta).
-// Base and RH92 evaluations write J once, into J_new (the rates read it there);
-// the Lambda diagonals are FP32 sums and stay float.
-__device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, double Sk64, double c2, float c2f,
-                                           float fD, float fa, float fI, float fx, float fe, bool fd) {
-  // the representation with the smaller rounding error (intensities are >= 0),
-  // J = (S + sum D) c2 or (sum I) c2, with one conversion and one FP64 sum
-  const bool useI = fabsf(fI) < fa;
-  const double J = __dmul_rn(__dadd_rn(useI ? 0.0 : Sk64, (double)(useI ? fI : fD)), c2);
-  if (fd) {   // finite-difference evaluation: J feeds its rates only
-    cd.w.J[o] = J;
-    return;
-  }
-  jnew_ptr(cd)[o] = J;
+// J = (S + sum D) c2, or (sum I) c2 where that representation carries the
+// smaller rounding error (intensities are >= 0), is formed in pair arithmetic
+// and written once, into J_new (the rates read it there); the Lambda
+// diagonals are FP32 sums and stay float. The sweeps serve the mixed mode
+// only, whose Jacobian-vector products are exact tangents (no difference
+// evaluations).
+__device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, df Sk, df c2, float c2f, float fD, float fa,
+                                           float fI, float fx, float fe) {
+  const df J = fabsf(fI) < fa ? df_mul_f(c2, fI) : df_mul(df_add_f(Sk, fD), c2);
+  df_store(as_pairs(jnew_ptr(cd)), o, J);
   cd.w.Lchi32[o] = mul(fx, c2f);
   cd.w.Leta32[o] = fe;
 }
@@ -178,7 +175,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   const size_t pstride = (size_t)nz * pitch;
   const size_t row = (size_t)q * nz;
   const float* __restrict__ chi = reinterpret_cast<const float*>(cd.w.chi) + row;
-  const double* __restrict__ S64 = cd.w.S + row;
+  const float2* __restrict__ S2 = as_pairs(cd.w.S) + row;   // S as float pairs
   float* __restrict__ chiT = cd.w.chiT + q;
   float* __restrict__ S32T = cd.w.S32T + q;
   float* __restrict__ dSkT = cd.w.dSkT + q;
@@ -187,7 +184,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   float* __restrict__ part = reinterpret_cast<float*>(cd.w.part) + q;
   const double c2 = T.c2[q];
   const float c2f = T.c2f[q];
-  const bool fdm = !TAN && eval_mode_f(cd) == EV_FD;
+  const df c2p = df_load(T.c2p, q);
 
   float inv2mu[MU], hw[MU], two_mu[MU];
 #pragma unroll
@@ -206,17 +203,17 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
 
   // boundary depth: I = 0 at the top, I = B at the bottom (Sect. 2.1)
   const int k0 = UP ? nz - 1 : 0;
-  double Sp = S64[k0];
+  df Sp = df_load(S2, k0);
   float cp = TAN ? chiT[k0 * pitch] : chi[k0];
   float dSp = 0.f, dcp = 0.f;
   if (TAN) tan_in(k0, dcp, dSp);
-  float Su = __double2float_rn(Sp);
+  float Su = Sp.hi;
   if (!TAN && !UP) {
     chiT[0] = cp;
     S32T[0] = Su;
   }
   const double Ib64 = UP ? T.Bn[row + nz - 1] / c2 : 0.0;
-  const float D0 = __double2float_rn(__dsub_rn(Ib64, Sp));
+  const float D0 = df_to_float(df_sub(df_from_double(Ib64), Sp));
   const float I0 = __double2float_rn(Ib64);
   const float dD0 = -dSp;
   float D[MU], I[MU], M[MU], dD[MU];
@@ -236,7 +233,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       xd[m] = mul(hw[m], dD0);
     }
   }
-  auto emit = [&](int k, double Sk64, float dS) {
+  auto emit = [&](int k, df Sk, float dS) {
     float* pp = part + (size_t)k * pitch;
     if (TAN) {
       const float td = tree8(xd);
@@ -252,8 +249,8 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       pp[3 * pstride] = tx;
       pp[4 * pstride] = te;
     } else {
-      write_base(cd, row + k, Sk64, c2, c2f, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
-                 add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]), fdm);
+      write_base(cd, row + k, Sk, c2p, c2f, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
+                 add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]));
     }
   };
   emit(k0, Sp, dSp);
@@ -261,7 +258,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   // the next depth's inputs are prepared one step ahead
   int kn = UP ? nz - 2 : 1;
   float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f, Sf_n = 0.f;
-  double S_n = 0.0;
+  df S_n = df_make(0.f, 0.f);
   auto load = [&](int kk) {
     if (TAN) {
       c_n = chiT[(size_t)kk * pitch];
@@ -269,15 +266,15 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       tan_in(kk, dc_n, dS_n);
     } else if (UP) {
       // the outward sweep of a base evaluation reads the float copies its own
-      // inward sweep left (coalesced; the same values, no FP64 difference)
-      // and S in FP64 for J only
+      // inward sweep left (coalesced; the same values, no pair difference)
+      // and the S pair for J only
       c_n = chiT[(size_t)kk * pitch];
       Sf_n = S32T[(size_t)kk * pitch];
       dSl_n = dSkT[(size_t)kk * pitch];
-      S_n = S64[kk];
+      S_n = df_load(S2, kk);
     } else {
       c_n = chi[kk];
-      S_n = S64[kk];
+      S_n = df_load(S2, kk);
     }
   };
   if (nz > 1) load(kn);
@@ -285,7 +282,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     const int k = kn;
     const int kd = UP ? k : k - 1;   // layer between k and its upstream neighbour
     const float c0 = c_n, dc0 = dc_n, dS0 = dS_n, dSl = dSl_n, Sf = Sf_n;
-    const double Sk64 = S_n;
+    const df Sk = S_n;
     if (s + 1 < nz) {
       kn = UP ? k - 1 : k + 1;
       load(kn);
@@ -305,8 +302,9 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       in.dtz = mul(in.dzk, in.dcs);
       in.ddSin = sub(dSp, dS0);
     } else {
-      in.dSin = UP ? dSl : __double2float_rn(__dsub_rn(Sp, Sk64));
-      in.S0 = UP ? Sf : __double2float_rn(Sk64);
+      // S^u - S^k formed from the pairs, then rounded
+      in.dSin = UP ? dSl : df_to_float(df_sub(Sp, Sk));
+      in.S0 = UP ? Sf : Sk.hi;
       if (!UP) {
         // depth-major copies for the tangent evaluations
         chiT[(size_t)k * pitch] = c0;
@@ -329,8 +327,8 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
         xd[m] = r.xd;
       }
     }
-    emit(k, Sk64, dS0);
-    Sp = Sk64;
+    emit(k, Sk, dS0);
+    Sp = Sk;
     Su = in.S0;
     cp = c0;
     dSp = dS0;
@@ -392,7 +390,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   const size_t row = (size_t)qq * nz;
   const size_t pitch = (size_t)col_pitch(nq);
   const float* __restrict__ chi = reinterpret_cast<const float*>(cd.w.chi) + row;
-  const double* __restrict__ S64 = cd.w.S + row;
+  const float2* __restrict__ S2 = as_pairs(cd.w.S) + row;   // S as float pairs
   float* __restrict__ chiT = cd.w.chiT + qq;
   float* __restrict__ S32T = cd.w.S32T + qq;
   float* __restrict__ dSkT = cd.w.dSkT + qq;
@@ -400,7 +398,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   const float* __restrict__ dS32T = cd.w.dS32T + qq;
   const double c2 = T.c2[qq];
   const float c2f = T.c2f[qq];
-  const bool fdm = !TAN && eval_mode_f(cd) == EV_FD;
+  const df c2p = df_load(T.c2p, qq);
   const bool on = m < nmu;
   const float inv2mu = on ? (float)(0.5 / T.mu[m]) : 0.f;
   const float hw = on ? (float)(0.5 * T.wmu[m]) : 0.f;
@@ -414,17 +412,17 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   };
 
   const int k0 = up ? nz - 1 : 0;
-  double Sp = S64[k0];
+  df Sp = df_load(S2, k0);
   float cp = TAN ? chiT[k0 * pitch] : chi[k0];
   float dSp = 0.f, dcp = 0.f;
   if (TAN) tan_in(k0, dcp, dSp);
-  float Su = __double2float_rn(Sp);
+  float Su = Sp.hi;
   if (writer) {
     chiT[0] = cp;
     S32T[0] = Su;
   }
   const double Ib64 = up ? T.Bn[row + nz - 1] / c2 : 0.0;
-  const float D0 = __double2float_rn(__dsub_rn(Ib64, Sp));
+  const float D0 = df_to_float(df_sub(df_from_double(Ib64), Sp));
   const float I0 = __double2float_rn(Ib64);
   const float dD0 = -dSp;
   float D = D0, I = I0, M = fabsf(D0), dD = dD0;
@@ -452,7 +450,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   store(k0);
   // the next depth's inputs are loaded one step ahead (latency off the chain)
   float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f;
-  double S_n = 0.0;
+  df S_n = df_make(0.f, 0.f);
   auto load = [&](int s) {
     const int k = up ? nz - 1 - s : s;
     const int kd = up ? k : k - 1;
@@ -462,7 +460,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
       dSl_n = dSkT[(size_t)kd * pitch];
     } else {
       c_n = chi[k];
-      if (m == 0) S_n = S64[k];
+      if (m == 0) S_n = df_load(S2, k);
     }
   };
   if (nz > 1) load(1);
@@ -473,7 +471,7 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
     const float c0 = c_n;
     float dc0 = 0.f, dS0 = 0.f;
     const float dSl = dSl_n;
-    const double Sk64 = S_n;
+    const df Sk = S_n;
     if (TAN) {
       dc0 = dc_n;
       dS0 = dS_n;
@@ -485,12 +483,12 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
       in.dcs = add(dc0, dcp);
       in.ddSin = sub(dSp, dS0);
     } else {
-      // the FP64 difference is formed once per hemisphere (angle lane 0)
+      // the pair difference is formed once per hemisphere (angle lane 0)
       float dSin = 0.f, S0 = 0.f;
       if (m == 0) {
-        dSin = __double2float_rn(__dsub_rn(Sp, Sk64));
-        S0 = __double2float_rn(Sk64);
-        Sp = Sk64;
+        dSin = df_to_float(df_sub(Sp, Sk));
+        S0 = Sk.hi;
+        Sp = Sk;
         if (writer) {
           chiT[(size_t)k * pitch] = c0;
           S32T[(size_t)k * pitch] = S0;
@@ -532,9 +530,9 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
       const size_t o = (size_t)k * pitch + q;
       write_tan(cd, o, cd.w.dS32T[o], add(upp[k], dn[k]));
     } else {
-      write_base(cd, row + k, S64[k], c2, c2f, add(upp[k], dn[k]), add(upp[nz + k], dn[nz + k]),
+      write_base(cd, row + k, df_load(S2, k), c2p, c2f, add(upp[k], dn[k]), add(upp[nz + k], dn[nz + k]),
                  add(upp[2 * nz + k], dn[2 * nz + k]), add(upp[3 * nz + k], dn[3 * nz + k]),
-                 add(upp[4 * nz + k], dn[4 * nz + k]), fdm);
+                 add(upp[4 * nz + k], dn[4 * nz + k]));
     }
   }
 }

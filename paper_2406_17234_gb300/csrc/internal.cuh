@@ -155,6 +155,10 @@ int launch_formal_sweep(const Batch& b, cudaStream_t s, int which = 0);
 // Warps per block of the warp variant whose shared memory fits depth nz (0: none).
 int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);
+// Mixed mode: converts the J^dagger of columns d_cols[0, ncols) (FP64, as
+// filled by the host or the tables) to float pairs in place (to_pairs), or
+// their J_new back to FP64; FP64 columns are left alone.
+int launch_j_pairs(const ColDesc* d_cols, int ncols, size_t max_qz, cudaStream_t s, bool to_pairs);
 // Kernel attributes of the current device, set once per context (residual.cu).
 int prepare_kernels();
 // Opacity kernel of the mixed mode (tangent columns skipped when the sweeps form it).

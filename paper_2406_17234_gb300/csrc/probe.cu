@@ -50,17 +50,28 @@ __global__ void k_probe_exp32(float* out) {
   if (s == 12345.678f) out[0] = s;
 }
 
-__global__ void k_check_quotient(const double* a, const double* b, double* q, int n) {
+__global__ void k_check_arith(int op, const double* a, const double* b, double* out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) q[i] = div_nr(a[i], b[i], (float)b[i]);
+  if (i >= n) return;
+  const df x = df_from_double(a[i]), y = df_from_double(b[i]);
+  df r;
+  switch (op) {
+    case 0: r = df_add(x, y); break;
+    case 1: r = df_sub(x, y); break;
+    case 2: r = df_mul(x, y); break;
+    case 3: r = df_div(x, y); break;
+    default: r = df_acc(x, y); break;
+  }
+  out[i] = df_to_double(r);
 }
 
 }  // namespace jfnk
 
 using namespace jfnk;
 
-extern "C" int jfnk_check_quotient(jfnk_ctx* ctx, const double* a, const double* b, double* q, int n) {
-  if (!ctx || n < 0 || (n > 0 && (!a || !b || !q))) return fail(JFNK_E_INVALID, "bad quotient-check arguments");
+extern "C" int jfnk_check_arith(jfnk_ctx* ctx, int op, const double* a, const double* b, double* q, int n) {
+  if (!ctx || op < 0 || op > 4 || n < 0 || (n > 0 && (!a || !b || !q)))
+    return fail(JFNK_E_INVALID, "bad arithmetic-check arguments");
   if (n == 0) return JFNK_OK;
   JFNK_CUDA(cudaSetDevice(ctx->device));
   double* d = nullptr;
@@ -69,7 +80,7 @@ extern "C" int jfnk_check_quotient(jfnk_ctx* ctx, const double* a, const double*
   cudaError_t e = cudaMemcpyAsync(d, a, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, b, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    k_check_quotient<<<(n + 255) / 256, 256, 0, s>>>(d, d + n, d + 2 * (size_t)n, n);
+    k_check_arith<<<(n + 255) / 256, 256, 0, s>>>(op, d, d + n, d + 2 * (size_t)n, n);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(q, d + 2 * (size_t)n, sizeof(double) * n, cudaMemcpyDeviceToHost, s);

@@ -80,31 +80,34 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
     return;
   }
   const int q = i / nz, k = i - q * nz;
-  const double* n = eval_pops(cd, mode) + k * nl;
-  const double eta_bg = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
   if (sizeof(real) == sizeof(float)) {
-    // mixed mode: chi is stored in float and S in FP64; on GB300 the FP64
-    // pipe bounds this loop, so each term takes the fewest FP64 operations
-    // (g V tabulated, 2 h nu^3/c^2 factored out of the line emissivity, the
-    // quotient by Newton-Raphson)
-    double chi = T.chi_c[i] + T.chi_sca[k];
-    double el = 0.0;   // sum over lines of g V n_up = eta_lines / (2 h nu^3/c^2)
+    // mixed mode: chi is stored in float, S (and the RH92 emissivity) as
+    // float pairs; every sum runs in pair arithmetic on the FP32 pipe (GB300's
+    // FP64 pipe is 1/64 of it): chi = chi_c + chi_sca + sum V n_lo - sum g V
+    // n_up, eta / (2 h nu^3/c^2) = (eta_c + chi_sca J^dagger) c^2/(2 h nu^3)
+    // + sum g V n_up (Eqs. chi, eta)
+    const float2* n2 = cd.w.n2 + k * nl;
+    const df jd = df_load(as_pairs(jdag_ptr(cd)), i);
+    const df eta_bg = df_add(df_load(T.etac2, i), df_mul(df_load(T.chisca2, k), jd));
+    df chl = df_make(0.f, 0.f), el = df_make(0.f, 0.f);
     for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
       const int t = T.q_t[s];
       const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
-      chi = fma(T.V[p], n[T.t_lo[t]], chi);
-      el = fma(T.gV[p], n[T.t_up[t]], el);
+      chl = df_add(chl, df_mul(df_load(T.V2, p), df_load(n2, T.t_lo[t])));
+      el = df_add(el, df_mul(df_load(T.gV2, p), df_load(n2, T.t_up[t])));
     }
-    chi -= el;   // stimulated emission: the same sum of g V n_up
-    const float chif = (float)chi;
-    reinterpret_cast<float*>(cd.w.chi)[i] = chif;
-    cd.w.S[i] = div_nr(fma(eta_bg, T.rc2[q], el), chi, chif);
+    const df chi = df_sub(df_add(df_load(T.chibg2, i), chl), el);
+    const df etan = df_add(df_mul(eta_bg, df_load(T.rc2p, q)), el);
+    reinterpret_cast<float*>(cd.w.chi)[i] = chi.hi;
+    df_store(as_pairs(cd.w.S), i, df_div(etan, chi));
     if (mode == EV_RH92) {   // for the RH92 rate sums
-      cd.w.eta[i] = fma(el, T.c2[q], eta_bg);
-      cd.w.etab32[i] = (float)eta_bg;
+      df_store(as_pairs(cd.w.eta), i, df_add(eta_bg, df_mul(el, df_load(T.c2p, q))));
+      cd.w.etab32[i] = eta_bg.hi;
     }
     return;
   }
+  const double* n = eval_pops(cd, mode) + k * nl;
+  const double eta_bg = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
   const double c2 = T.c2[q];
   double chi = T.chi_c[i] + T.chi_sca[k];
   double eta = eta_bg;
@@ -224,6 +227,49 @@ __global__ void k_dir32(const ColDesc* __restrict__ cols) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   cd.w.v32[i] = (float)tangent_dir(cd)[i];
+}
+
+// Mixed mode: J^dagger as float pairs in the bytes of its FP64 array (after
+// the host or the tables filled it in FP64), and J_new back to FP64 for the
+// caller; in place, element by element.
+__global__ void k_jdag_to_pairs(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const size_t n = (size_t)cd.t.nq * cd.t.nz;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!cd.mixed || i >= n) return;
+  double* J = const_cast<double*>(jdag_ptr(cd));
+  const double x = J[i];
+  df_store(as_pairs(J), i, df_from_double(x));
+}
+__global__ void k_jnew_to_double(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const size_t n = (size_t)cd.t.nq * cd.t.nz;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!cd.mixed || i >= n) return;
+  double* J = jnew_ptr(cd);
+  const float2 p = as_pairs(J)[i];
+  J[i] = (double)p.x + (double)p.y;
+}
+int launch_j_pairs(const ColDesc* d_cols, int ncols, size_t max_qz, cudaStream_t s, bool to_pairs) {
+  if (ncols <= 0 || max_qz == 0) return JFNK_OK;
+  const dim3 g((unsigned)((max_qz + 255) / 256), ncols);
+  if (to_pairs) k_jdag_to_pairs<<<g, 256, 0, s>>>(d_cols);
+  else k_jnew_to_double<<<g, 256, 0, s>>>(d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+// Mixed mode, base and RH92 evaluations: the populations as float pairs for
+// the pair arithmetic of the opacity kernel.
+__global__ void k_pop_pairs(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (!cd.mixed) return;
+  const int mode = eval_mode(cd);
+  if (mode != EV_BASE && mode != EV_RH92) return;
+  const int N = cd.t.nz * cd.t.nl;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  df_store(cd.w.n2, i, df_from_double(cd.w.n[i]));
 }
 
 // Differences of the source function (and of its tangent) between adjacent
@@ -488,6 +534,9 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
   // base and RH92 evaluations leave J in J_new, difference evaluations in J
   const double* __restrict__ J = tan ? cd.w.dJ : (mode == EV_FD ? cd.w.J : jnew_ptr(cd));
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a5 = 0.0;
+  // mixed mode: J, S and eta are float pairs; the rate sums accumulate in pairs
+  const float2* __restrict__ J2 = mix ? as_pairs(jnew_ptr(cd)) : nullptr;
+  df s0 = df_make(0.f, 0.f), s1 = df_make(0.f, 0.f);
   float f0 = 0.f, f1 = 0.f, f3 = 0.f;
   if (!base_mode && !rh) {
     // tangent (FP64 mode) or a difference evaluation: the two rate sums only
@@ -498,14 +547,15 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       a1 = fma(T.WgV[pk], Jq, a1);
     }
   } else if (base_mode && mix) {
-    // preconditioner sums A^kk_{t,j} = sum W chi_t (beta_j Lchi + gamma_j Leta) in FP32
+    // rate sums in pair arithmetic, preconditioner sums
+    // A^kk_{t,j} = sum W chi_t (beta_j Lchi + gamma_j Leta) in FP32
     const float nlo_f = (float)n_lo, nup_f = (float)n_up;
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
-      const double Jq = J[o];
-      a0 = fma(T.WV[pk], Jq, a0);
-      a1 = fma(T.WgV[pk], Jq, a1);
+      const df Jq = df_load(J2, o), w = df_load(T.W2, p);
+      s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
+      s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
       const float Vf = T.V32[pk], gf = T.G32[pk];
       const float Wc = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
       const float Lx = cd.w.Lchi32[o], Le = cd.w.Leta32[o];
@@ -543,11 +593,12 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
-      const double Jq = J[o];
-      a0 = fma(T.WV[pk], Jq, a0);
-      a1 = fma(T.WgV[pk], Jq, a1);
+      const df Jq = df_load(J2, o), w = df_load(T.W2, p);
+      s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
+      s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
       const float Le = cd.w.Leta32[o];
-      const float Jf = (float)fma(-(double)Le, cd.w.eta[o], Jq);
+      // Jeff = J - Psi* eta cancels in optically thick layers: formed from the pairs
+      const float Jf = df_to_float(df_sub(Jq, df_mul_f(df_load(as_pairs(cd.w.eta), o), Le)));
       const float Wf = T.Wr32[p], Vf = T.V32[pk], gf = T.G32[pk], c2f = T.c2f[q];
       const float WVf = Wf * Vf;
       f0 = fmaf(WVf, Jf, f0);
@@ -584,8 +635,9 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       }
     }
   }
-  sm.d(wid, 0, lane) = a0;
-  sm.d(wid, 1, lane) = a1;
+  const bool pairs = mix && (base_mode || rh);
+  sm.d(wid, 0, lane) = pairs ? df_to_double(s0) : a0;
+  sm.d(wid, 1, lane) = pairs ? df_to_double(s1) : a1;
   if (rh) {
     // slot 2 + 2 (sum W U, U = 2 h nu^3/c^2 g V) is the spontaneous table, added below
     sm.d(wid, 2, lane) = mix ? (double)f0 : a2;
@@ -848,6 +900,7 @@ static dim3 opacity_grid(const Batch& b, int tb) {
 
 int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
   const int tb = 256;
+  k_pop_pairs<<<dim3((b.max_N + tb - 1) / tb, b.ncols), tb, 0, s>>>(b.d_cols);
   k_opacity<float><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 1);   // base and RH92 columns
   if (!skip_tangent) k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());
@@ -883,6 +936,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     if (ev3) JFNK_CUDA(cudaEventRecordWithFlags(ev3, side, cudaEventRecordExternal));
     launch_rates_tan32(b, side);
     JFNK_CUDA(cudaEventRecord(b.join_ev, side));
+    k_pop_pairs<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
     k_opacity<float><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 1);
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     if ((rc = launch_formal_sweep(b, s, 1))) return rc;

@@ -128,6 +128,10 @@ int admit(jfnk_server* sv, int i, ServerReq& r) {
   JFNK_CUDA(cudaMemcpyAsync(sv->d_sopts + i, &r.o, sizeof(SolverOpts), cudaMemcpyHostToDevice, sv->stream));
   JFNK_CUDA(cudaMemcpyAsync(d.w.n, M.tables.nstar, N * 8, cudaMemcpyDeviceToDevice, sv->stream));
   JFNK_CUDA(cudaMemcpyAsync(d.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, sv->stream));
+  if (sv->mixed) {
+    int rc = launch_j_pairs(b.d_cols + i, 1, QZ, sv->stream, true);
+    if (rc) return rc;
+  }
   sv->h_status[i] = 1;
   JFNK_CUDA(cudaMemcpyAsync(b.d_status + i, sv->h_status + i, sizeof(int), cudaMemcpyHostToDevice, sv->stream));
   // the staged copies read host values that change with the next admission

@@ -362,6 +362,23 @@ __global__ void k_spontaneous(int nt, int nz, const int* t_q0, const int* t_q1, 
   Rsp[i] = s;
 }
 
+// Float-pair copies of FP64 tables (the mixed mode's base evaluations).
+__global__ void k_pairs(const double* src, float2* dst, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const df p = df_from_double(src[i]);
+    dst[i] = make_float2(p.hi, p.lo);
+  }
+}
+// chi_c + chi_sca per (nu, depth), summed in FP64, as pairs
+__global__ void k_chibg_pairs(int nq, int nz, const double* chi_c, const double* chi_sca, float2* dst) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (size_t)nq * nz) {
+    const df p = df_from_double(chi_c[i] + chi_sca[i % nz]);
+    dst[i] = make_float2(p.hi, p.lo);
+  }
+}
+
 struct CollDev {
   int kind, lo, up;
   double nu0, f, upsilon, eps, q0;
@@ -455,6 +472,10 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   size_t o_WV = ar.take<double>((size_t)nwin * nz), o_WgV = ar.take<double>((size_t)nwin * nz),
          o_Rsp = ar.take<double>((size_t)nt * nz), o_gV = ar.take<double>((size_t)nwin * nz),
          o_rc2 = ar.take<double>(nq);
+  size_t o_V2 = ar.take<float2>((size_t)nwin * nz), o_gV2 = ar.take<float2>((size_t)nwin * nz),
+         o_W2 = ar.take<float2>(nwin), o_chibg2 = ar.take<float2>((size_t)nq * nz),
+         o_etac2 = ar.take<float2>((size_t)nq * nz), o_chisca2 = ar.take<float2>(nz),
+         o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
   int rc = ar.allocate();
   if (rc) return rc;
   // host-side staging
@@ -468,6 +489,12 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   gauss_legendre_01(nmu, mu.data(), wmu.data());
   std::vector<int> winT(nwin);
   std::vector<float> w32(nwin), wr32(nwin), c2f(nq);
+  std::vector<float2> w2(nwin), c2p(nq), rc2p(nq);
+  for (int q = 0; q < nq; ++q) {
+    const df a = df_from_double(c2[q]), b = df_from_double(rc2[q]);
+    c2p[q] = make_float2(a.hi, a.lo);
+    rc2p[q] = make_float2(b.hi, b.lo);
+  }
   for (int q = 0; q < nq; ++q) c2f[q] = (float)c2[q];
   for (int t = 0; t < nt; ++t)
     for (int p = 0; p <= A.t_q1[t] - A.t_q0[t]; ++p) {
@@ -475,6 +502,8 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
       winT[A.t_base[t] + p] = t;
       w32[A.t_base[t] + p] = (float)(A.t_w[A.t_base[t] + p] * rw[q] * c2[q]);
       wr32[A.t_base[t] + p] = (float)(A.t_w[A.t_base[t] + p] * rw[q]);
+      const df wp = df_from_double(A.t_w[A.t_base[t] + p] * rw[q]);
+      w2[A.t_base[t] + p] = make_float2(wp.hi, wp.lo);
     }
   std::vector<TransDev> tr(nt);
   std::vector<CollDev> cd(nt);
@@ -516,6 +545,9 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(up(o_W32, w32.data(), nwin * 4));
   JFNK_CUDA(up(o_Wr32, wr32.data(), nwin * 4));
   JFNK_CUDA(up(o_c2f, c2f.data(), nq * 4));
+  JFNK_CUDA(up(o_W2, w2.data(), nwin * sizeof(float2)));
+  JFNK_CUDA(up(o_c2p, c2p.data(), nq * sizeof(float2)));
+  JFNK_CUDA(up(o_rc2p, rc2p.data(), nq * sizeof(float2)));
   std::vector<int> qmeta((size_t)kQMetaT * nq, -1);
   for (int q = 0; q < nq; ++q)
     for (int s = A.q_off[q], j = 0; s < A.q_off[q + 1] && j < kQMetaT; ++s, ++j) {
@@ -558,6 +590,15 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   k_spontaneous<<<(nt * nz + tb - 1) / tb, tb, 0, s>>>(nt, nz, ar.ptr<int>(o_tq0), ar.ptr<int>(o_tq1),
                                                         ar.ptr<int>(o_tbase), ar.ptr<double>(o_c2),
                                                         ar.ptr<double>(o_WgV), ar.ptr<double>(o_Rsp));
+  {
+    const size_t nwz = (size_t)nwin * nz, nqz = (size_t)nq * nz;
+    k_pairs<<<(int)((nwz + tb - 1) / tb), tb, 0, s>>>(ar.ptr<double>(o_V), ar.ptr<float2>(o_V2), nwz);
+    k_pairs<<<(int)((nwz + tb - 1) / tb), tb, 0, s>>>(ar.ptr<double>(o_gV), ar.ptr<float2>(o_gV2), nwz);
+    k_pairs<<<(int)((nqz + tb - 1) / tb), tb, 0, s>>>(ar.ptr<double>(o_etac), ar.ptr<float2>(o_etac2), nqz);
+    k_pairs<<<(nz + tb - 1) / tb, tb, 0, s>>>(ar.ptr<double>(o_sca), ar.ptr<float2>(o_chisca2), (size_t)nz);
+    k_chibg_pairs<<<(int)((nqz + tb - 1) / tb), tb, 0, s>>>(nq, nz, ar.ptr<double>(o_chic), ar.ptr<double>(o_sca),
+                                                            ar.ptr<float2>(o_chibg2));
+  }
   k_collisions<<<(nz + tb - 1) / tb, tb, 0, s>>>(nt, ar.ptr<CollDev>(o_cd), at, nz, T, ne,
                                                   ar.ptr<double>(o_C));
   k_float_copy<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
@@ -575,6 +616,9 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   tb_.t_q1 = ar.ptr<int>(o_tq1); tb_.t_base = ar.ptr<int>(o_tbase); tb_.t_w = ar.ptr<double>(o_tw);
   tb_.V = ar.ptr<double>(o_V); tb_.G = ar.ptr<double>(o_G); tb_.dz = ar.ptr<double>(o_dz);
   tb_.gV = ar.ptr<double>(o_gV); tb_.rc2 = ar.ptr<double>(o_rc2);
+  tb_.V2 = ar.ptr<float2>(o_V2); tb_.gV2 = ar.ptr<float2>(o_gV2); tb_.W2 = ar.ptr<float2>(o_W2);
+  tb_.chibg2 = ar.ptr<float2>(o_chibg2); tb_.etac2 = ar.ptr<float2>(o_etac2);
+  tb_.chisca2 = ar.ptr<float2>(o_chisca2); tb_.c2p = ar.ptr<float2>(o_c2p); tb_.rc2p = ar.ptr<float2>(o_rc2p);
   tb_.WV = ar.ptr<double>(o_WV); tb_.WgV = ar.ptr<double>(o_WgV); tb_.Rsp = ar.ptr<double>(o_Rsp);
   tb_.V32 = ar.ptr<float>(o_V32); tb_.G32 = ar.ptr<float>(o_G32); tb_.W32 = ar.ptr<float>(o_W32);
   tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);

@@ -34,7 +34,7 @@ void DeviceArena::release() {
 struct ColLayout {
   size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH,
       LX, LE, part, J, dJ, Lchi, Leta, Lchi32, Leta32, Rup, Rdn, dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x,
-      w, nprev, np, fdp, eta, etab32;
+      w, nprev, np, fdp, eta, etab32, n2;
 };
 
 size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout* out) {
@@ -74,6 +74,7 @@ size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout
   o.x = ar.take<double>(N); o.w = ar.take<double>(N); o.nprev = ar.take<double>(N);
   o.np = ar.take<double>(N); o.fdp = ar.take<double>(N);
   o.eta = ar.take<double>(nq * nz); o.etab32 = ar.take<float>(mixed ? nq * nz : 0);
+  o.n2 = ar.take<float2>(mixed ? N : 0);
   if (out) *out = o;
   return ar.cursor;
 }
@@ -117,6 +118,7 @@ void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, 
   w.x = (double*)P(o.x); w.w = (double*)P(o.w); w.nprev = (double*)P(o.nprev);
   w.np = (double*)P(o.np); w.fdp = (double*)P(o.fdp);
   w.eta = (double*)P(o.eta); w.etab32 = mixed ? (float*)P(o.etab32) : nullptr;
+  w.n2 = mixed ? (float2*)P(o.n2) : nullptr;
   w.st = st;
 }
 
