@@ -90,11 +90,23 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
     const df jd = df_load(as_pairs(jdag_ptr(cd)), i);
     const df eta_bg = df_add(df_load(T.etac2, i), df_mul(df_load(T.chisca2, k), jd));
     df chl = df_make(0.f, 0.f), el = df_make(0.f, 0.f);
-    for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-      const int t = T.q_t[s];
-      const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
-      chl = df_add(chl, df_mul(df_load(T.V2, p), df_load(n2, T.t_lo[t])));
-      el = df_add(el, df_mul(df_load(T.gV2, p), df_load(n2, T.t_up[t])));
+    if (T.max_overlap <= kQMetaT) {
+      // the packed table gives window point and levels in one load
+#pragma unroll
+      for (int j = 0; j < kQMetaT; ++j) {
+        const int m = __ldg(T.qmeta + (size_t)j * T.nq + q);
+        if (m < 0) break;
+        const size_t p = (size_t)(m >> 8) * nz + k;
+        chl = df_add(chl, df_mul(df_load(T.V2, p), df_load(n2, (m >> 4) & 15)));
+        el = df_add(el, df_mul(df_load(T.gV2, p), df_load(n2, m & 15)));
+      }
+    } else {
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int t = T.q_t[s];
+        const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+        chl = df_add(chl, df_mul(df_load(T.V2, p), df_load(n2, T.t_lo[t])));
+        el = df_add(el, df_mul(df_load(T.gV2, p), df_load(n2, T.t_up[t])));
+      }
     }
     const df chi = df_sub(df_add(df_load(T.chibg2, i), chl), el);
     const df etan = df_add(df_mul(eta_bg, df_load(T.rc2p, q)), el);
