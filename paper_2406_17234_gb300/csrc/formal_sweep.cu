@@ -166,10 +166,9 @@ __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float*
 // rounded differences for the tangent evaluations of the same Newton step;
 // those then read depth-major float arrays only (one 128-byte line per warp
 // and depth) and run entirely in FP32.
-template <int MU, bool TAN, bool UP, bool FUSE>
+template <int MU, bool TAN, bool UP>
 __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const float* __restrict__ s_dz,
                                              const float* __restrict__ s_idz) {
-  constexpr bool fuse = TAN && FUSE;
   const ColTables& T = cd.t;
   const int nz = T.nz, nq = T.nq, nmu = T.nmu, nl = T.nl;
   const size_t pitch = (size_t)col_pitch(nq);
@@ -195,33 +194,11 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     hw[m] = on ? (float)(0.5 * T.wmu[m]) : 0.f;
     two_mu[m] = on ? (float)(2.0 * T.mu[m]) : 0.f;
   }
-  // tangent opacity of depth kk: left by the opacity kernel, or (fuse) formed
-  // here from the tangent direction with the opacity kernel's arithmetic
-  // (tan_acc over the packed transition list of q, then tan_dS), so that the
-  // values are the same bits and are never stored
-  int mq[kQMetaT];
-#pragma unroll
-  for (int j = 0; j < kQMetaT; ++j) mq[j] = (fuse && j < T.max_overlap) ? __ldg(T.qmeta + (size_t)j * nq + q) : -1;
+  // tangent opacity of depth kk, left by the opacity kernel
   auto tan_in = [&](int kk, float& dc, float& dS) {
     const size_t o = (size_t)kk * pitch;
-    if (fuse) {
-      const float* __restrict__ V = T.V32T + (size_t)kk * T.nwin;
-      const float* __restrict__ G = T.G32T + (size_t)kk * T.nwin;
-      const float* __restrict__ v = cd.w.v32 + kk * nl;
-      TanAcc ta;
-#pragma unroll
-      for (int j = 0; j < kQMetaT; ++j) {
-        const int m = mq[j];
-        if (m < 0) break;
-        const int p = m >> 8;
-        tan_acc(ta, __ldg(V + p), __ldg(G + p), __ldg(v + ((m >> 4) & 15)), __ldg(v + (m & 15)));
-      }
-      dc = ta.dchi;
-      dS = tan_dS(ta, S32T[o], chiT[o]);
-    } else {
-      dc = dchiT[o];
-      dS = dS32T[o];
-    }
+    dc = dchiT[o];
+    dS = dS32T[o];
   };
 
   // boundary depth: I = 0 at the top, I = B at the bottom (Sect. 2.1)
@@ -286,7 +263,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     if (TAN) {
       c_n = chiT[(size_t)kk * pitch];
       dSl_n = dSkT[(size_t)(UP ? kk : kk - 1) * pitch];
-      if (!fuse) tan_in(kk, dc_n, dS_n);   // a fused opacity tangent is formed at its depth
+      tan_in(kk, dc_n, dS_n);
     } else if (UP) {
       // the outward sweep of a base evaluation reads the float copies its own
       // inward sweep left (coalesced; the same values, no pair difference)
@@ -304,14 +281,12 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   for (int s = 1; s < nz; ++s) {
     const int k = kn;
     const int kd = UP ? k : k - 1;   // layer between k and its upstream neighbour
-    const float c0 = c_n, dSl = dSl_n, Sf = Sf_n;
-    float dc0 = dc_n, dS0 = dS_n;
+    const float c0 = c_n, dc0 = dc_n, dS0 = dS_n, dSl = dSl_n, Sf = Sf_n;
     const df Sk = S_n;
     if (s + 1 < nz) {
       kn = UP ? k - 1 : k + 1;
       load(kn);
     }
-    if (TAN && fuse) tan_in(k, dc0, dS0);
     StepIn in;
     in.csum = add(c0, cp);
     in.rs = rcp_approx(in.csum);
@@ -367,11 +342,9 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
 }
 
 // One kernel per evaluation kind (its own register allocation): blocks of
-// columns in the other kind return at once. FUSE: tangent evaluations form
-// the opacity tangent themselves (no k_opacity_tan32 launch); its register
-// budget is held to the non-fused kernel's neighbourhood (no spills).
-template <int MU, bool TAN, bool FUSE = false>
-__global__ void __launch_bounds__(256, FUSE ? 3 : 1) k_formal_sweep(const ColDesc* __restrict__ cols) {
+// columns in the other kind return at once.
+template <int MU, bool TAN>
+__global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict__ cols) {
   extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode_f(cd);
@@ -385,8 +358,8 @@ __global__ void __launch_bounds__(256, FUSE ? 3 : 1) k_formal_sweep(const ColDes
   __syncthreads();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
-  sweep_thread<MU, TAN, false, FUSE>(cd, q, s_dz, s_idz);
-  sweep_thread<MU, TAN, true, FUSE>(cd, q, s_dz, s_idz);
+  sweep_thread<MU, TAN, false>(cd, q, s_dz, s_idz);
+  sweep_thread<MU, TAN, true>(cd, q, s_dz, s_idz);
 }
 
 // ---------------------------------------------------------------------------
@@ -599,12 +572,7 @@ template <int MU>
 static void launch_mu(const Batch& b, cudaStream_t s, int threads, int which) {
   dim3 g((b.max_nq + threads - 1) / threads, b.ncols);
   const size_t bytes = sizeof(float) * 2 * (size_t)b.max_nz;
-  if (which != 1) {
-    if (sweep_fuses_tangent_opacity(1, b.max_overlap))   // variant 1 forms the opacity tangent
-      k_formal_sweep<MU, true, true><<<g, threads, bytes, s>>>(b.d_cols);
-    else
-      k_formal_sweep<MU, true><<<g, threads, bytes, s>>>(b.d_cols);
-  }
+  if (which != 1) k_formal_sweep<MU, true><<<g, threads, bytes, s>>>(b.d_cols);
   if (which != 2) k_formal_sweep<MU, false><<<g, threads, bytes, s>>>(b.d_cols);
 }
 
@@ -668,15 +636,9 @@ int sweep_autotune(Batch* b, cudaStream_t s) {
   int rc = JFNK_OK;
   for (const auto& c : cands) {
     if (c.first == 2 && !warp_variant_fits(b->max_nz, c.second)) continue;
-    // the warp variant needs the opacity tangent kernel that variant 1 folds in
-    const bool opac = c.first == 2 || !sweep_fuses_tangent_opacity(1, b->max_overlap);
-    if (opac) launch_opacity_tan32(*b, s);
     if ((rc = launch_sweep_cfg(*b, s, c.first, c.second))) break;   // warm-up
     JFNK_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3 && !rc; ++r) {
-      if (opac) launch_opacity_tan32(*b, s);
-      rc = launch_sweep_cfg(*b, s, c.first, c.second);
-    }
+    for (int r = 0; r < 3 && !rc; ++r) rc = launch_sweep_cfg(*b, s, c.first, c.second);
     if (rc) break;
     JFNK_CUDA(cudaEventRecord(e1, s));
     JFNK_CUDA(cudaEventSynchronize(e1));

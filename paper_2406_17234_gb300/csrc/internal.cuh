@@ -161,13 +161,6 @@ int sweep_autotune(Batch* b, cudaStream_t s);
 int launch_j_pairs(const ColDesc* d_cols, int ncols, size_t max_qz, cudaStream_t s, bool to_pairs);
 // Kernel attributes of the current device, set once per context (residual.cu).
 int prepare_kernels();
-// Whether the tangent sweep of ``variant`` forms the opacity tangent itself
-// (thread variant, every frequency's transitions in the packed table).
-inline bool sweep_fuses_tangent_opacity(int variant, int max_overlap) {
-  return variant != 2 && max_overlap <= kQMetaT;
-}
-// The mixed mode's opacity tangent kernel alone (residual.cu).
-void launch_opacity_tan32(const Batch& b, cudaStream_t s);
 // Opacity kernel of the mixed mode (tangent columns skipped when the sweeps form it).
 int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent);
 // Solver options: checks, device copy (api.cu).

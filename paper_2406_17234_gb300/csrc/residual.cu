@@ -910,10 +910,6 @@ static dim3 opacity_grid(const Batch& b, int tb) {
   return dim3((unsigned)std::max(1L, std::min(need, share)), b.ncols);
 }
 
-void launch_opacity_tan32(const Batch& b, cudaStream_t s) {
-  k_opacity_tan32<<<opacity_grid(b, 256), 256, 0, s>>>(b.d_cols);
-}
-
 int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
   const int tb = 256;
   k_pop_pairs<<<dim3((b.max_N + tb - 1) / tb, b.ncols), tb, 0, s>>>(b.d_cols);
@@ -945,8 +941,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     JFNK_CUDA(cudaEventRecord(b.fork_ev, s));
     JFNK_CUDA(cudaStreamWaitEvent(side, b.fork_ev, 0));
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, side>>>(b.d_cols);
-    if (!sweep_fuses_tangent_opacity(b.sweep_variant, b.max_overlap))
-      k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, side>>>(b.d_cols);
+    k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, side>>>(b.d_cols);
     if (ev2) JFNK_CUDA(cudaEventRecordWithFlags(ev2, side, cudaEventRecordExternal));
     int rc = launch_formal_sweep(b, side, 2);
     if (rc) return rc;
@@ -967,7 +962,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   if (b.formal_kind == FORMAL_SWEEP) {
     // (float tangent direction,) opacity, then the per-frequency sweeps
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
-    int rc0 = launch_opacity_mixed(b, s, sweep_fuses_tangent_opacity(b.sweep_variant, b.max_overlap));
+    int rc0 = launch_opacity_mixed(b, s, 0);
     if (rc0) return rc0;
     if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
     int rc = launch_formal_sweep(b, s);
