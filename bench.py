@@ -145,6 +145,11 @@ def clocks_stop(proc, device):
             "samples": len(sm)}
 
 
+# the arithmetic of the mixed mode: FP32 formal solution and tangents, float
+# pairs (about 48 bits, FP32 pipe) for S, J and the base rate sums, FP64 for
+# the rate-equation assembly, the block inverses, GMRES and the Newton update
+MIXED_DTYPE = "f32 formal solution / f32-pair S, J, rate sums / f64 assembly, Krylov, Newton"
+
 # the sources each formal kernel is compiled from (its translation unit and the
 # ray-step coefficient header): a change to any of them voids its ncu traffic
 KERNEL_SOURCES = {
@@ -374,7 +379,7 @@ def run_ours(args, rank, ws, local, dist):
     line = {"metric": METRIC, "value": value, "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if fp64 else "f32 formal solution / f64 rates, Krylov, Newton",
+            "dtype": "f64" if fp64 else MIXED_DTYPE,
             "data": "synthetic",
             "config": workload_config(wl, (atm.n_nu, atm.n_depth, atm.n_mu), prec),
             "columns_per_s": cols_per_s,
@@ -463,7 +468,7 @@ def run_batch(args, rank, ws, local, dist):
     line = {"metric": METRIC, "value": pts / (total_ms * 1e-3), "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 formal solution / f64 rates, Krylov, Newton", "data": "synthetic",
+            "dtype": MIXED_DTYPE, "data": "synthetic",
             "config": {"workload": f"batched 1.5D: {len(atms)} Ca II-like columns, depths "
                                    f"{min(nz)}-{max(nz)}, {atms[0].n_nu} frequencies, 5 mu, T noise 5 %, "
                                    "mixed precision, one batched solve per step",
@@ -564,7 +569,7 @@ def run_serve(args, rank, ws, local, dist):
         return
     line = {"metric": "converged NLTE columns/s", "value": nconv / wall, "unit": "columns/s", "n_gpus": ws,
             "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 formal solution / f64 rates, Krylov, Newton", "data": "synthetic",
+            "vs_baseline": None, "dtype": MIXED_DTYPE, "data": "synthetic",
             "config": {"workload": f"serving: {n} column solves, Poisson arrivals at {args.rate:g}/s, atoms "
                                    "20 % two-level / 40 % Ca II-like / 40 % H I-like, depths 48-300, "
                                    "500-2000 frequencies, mixed precision, continuous batching",
