@@ -407,10 +407,12 @@ def run_batch(args, rank, ws, local, dist):
     torch.cuda.set_device(local)
     ctx = B.Context(local)
     atom = B.Atom(ctx, wl.atom)
+    free0, total_mem = torch.cuda.mem_get_info()
     t0 = time.perf_counter()
     atms = [B.Atmosphere(ctx, atom, c, n_mu=wl.n_mu) for c in wl.columns]
     setup_s = time.perf_counter() - t0
     plan = B.BatchPlan(ctx, atms, precision=B.JFNK_MIXED)
+    free1, _ = torch.cuda.mem_get_info()
     # hybrid start (Sect. 5): at most 5 per-depth limited RH92 iterations,
     # fewer once the population change is below 0.1, then Algorithm 2
     start = dict(rh92_warmup=5, rh92_switch=0.1)
@@ -482,6 +484,7 @@ def run_batch(args, rank, ws, local, dist):
                               "share_of_step": kern_ms / total_ms, "qb": st0[0]["formal_qb"],
                               "threads": st0[0]["formal_threads"]},
             "max_ticks": max(s["F_calls"] for s in st0), "setup_s": setup_s,
+            "device_memory_gb": {"tables_and_batch": (free0 - free1) / 1e9, "device_total": total_mem / 1e9},
             "roofline": roofline, "gpu_launches": int(st0[0]["kernel_launches"]) * args.steps,
             "clocks": clocks}
     print(json.dumps(line), flush=True)

@@ -393,3 +393,39 @@ def test_float_pair_arithmetic(ctx, op, bar):
     exact = {"add": x + y, "sub": x - y, "mul": x * y, "div": x / y, "acc": x + y}[op]
     scale = np.abs(exact) if op in ("mul", "div") else np.maximum(np.abs(x), np.abs(y))
     assert np.max(np.abs(out - exact) / scale) <= bar
+
+
+@pytest.mark.parametrize("case", ["two-level", "ca-small", "h-small"])
+def test_mixed_residual_matches_oracle(ctx, case):
+    """The mixed mode's residual (FP32 formal solution, float-pair S, J and
+    rate sums, FP64 assembly) against the FP64 oracle: J to the FP32 sweep's
+    accuracy and F within 1e-4 of the gross rates of each level (the FP32
+    rounding of the intensity differences, about 1e-6 relative, with a wide
+    margin); the conservation rows are FP64 and exact."""
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    rng = np.random.default_rng(11)
+    n = W.perturbed_populations(m.nstar, rng, 0.3)
+    Jd = m.B * np.exp(rng.normal(0, 0.2, m.B.shape))
+    F, J, _ = B.residual(atm, n, Jd, precision=B.JFNK_MIXED, want_J=True)
+    r = ora_residual(m, n, Jd)
+    gross = _gross(m, n, r.R_up, r.R_dn)
+    assert np.all(np.abs(F - r.F) <= 1e-4 * gross)
+    k = np.arange(m.nz)
+    np.testing.assert_allclose(F[k, r.istar], r.F[k, r.istar], rtol=1e-13)
+    np.testing.assert_allclose(J, r.J, rtol=1e-4, atol=1e-9 * np.max(np.abs(r.J)))
+
+
+@pytest.mark.parametrize("case", ["two-level", "ca-small"])
+def test_mixed_jvp_matches_complex_step(ctx, case):
+    """The mixed mode's FP32 tangent (Jacobian-vector product) against the
+    oracle's complex step, relative to the largest entry of each depth."""
+    wl = CASES[case]()
+    atom, atm, m = _pair(ctx, wl, n_mu=3)
+    rng = np.random.default_rng(12)
+    n = W.perturbed_populations(m.nstar, rng, 0.2)
+    v = rng.normal(size=n.shape) * n
+    g = B.jvp(atm, n, v, m.B, precision=B.JFNK_MIXED)
+    ref = jvp_complex(m, n, m.B, v)
+    scale = np.max(np.abs(ref), axis=1, keepdims=True) + 1e-300
+    assert np.max(np.abs(g - ref) / scale) < 1e-3
