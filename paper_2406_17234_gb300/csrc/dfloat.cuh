@@ -116,36 +116,6 @@ __device__ __forceinline__ df df_div(df a, df b) {
   return df_make(hi, h);
 }
 __device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
-
-// c - a b rounded to a float, for pairs c, a and a float b: the product's
-// leading part is exact (FMA) and its difference with c.hi is formed by
-// two-sum, so a cancellation between them leaves the small terms intact
-__device__ __forceinline__ float df_sub_mul_to_float(df c, df a, float b) {
-  float pe;
-  const float p = two_prod(a.hi, b, pe);
-  pe = __fmaf_rn(a.lo, b, pe);
-  float se;
-  const float s = two_sum(c.hi, -p, se);
-  return __fadd_rn(s, __fadd_rn(__fsub_rn(se, pe), c.lo));
-}
-
-// A compensated dot product over float pairs (Ogita, Rump and Oishi, 2005,
-// "Accurate sum and dot product", Dot2): the running sum s takes each leading
-// product by two-sum, and every rounding error (of the products and of the
-// sums) collects in c; the value is s + c.
-struct DotAcc {
-  float s = 0.f, c = 0.f;
-};
-__device__ __forceinline__ void dot_add(DotAcc& acc, df a, df b) {
-  float pe;
-  const float p = two_prod(a.hi, b.hi, pe);
-  pe = __fmaf_rn(a.hi, b.lo, pe);
-  pe = __fmaf_rn(a.lo, b.hi, pe);
-  float se;
-  acc.s = two_sum(acc.s, p, se);
-  acc.c = __fadd_rn(acc.c, __fadd_rn(se, pe));
-}
-__device__ __forceinline__ double dot_value(const DotAcc& a) { return (double)a.s + (double)a.c; }
 __device__ __forceinline__ df df_load(const float2* p, size_t i) {
   const float2 v = p[i];
   return df_make(v.x, v.y);

@@ -548,7 +548,7 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a5 = 0.0;
   // mixed mode: J, S and eta are float pairs; the rate sums accumulate in pairs
   const float2* __restrict__ J2 = mix ? as_pairs(jnew_ptr(cd)) : nullptr;
-  DotAcc s0, s1;
+  df s0 = df_make(0.f, 0.f), s1 = df_make(0.f, 0.f);
   float f0 = 0.f, f1 = 0.f, f3 = 0.f;
   if (!base_mode && !rh) {
     // tangent (FP64 mode) or a difference evaluation: the two rate sums only
@@ -566,31 +566,20 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
       const df Jq = df_load(J2, o), w = df_load(T.W2, p);
-      dot_add(s0, df_mul(w, df_load(T.V2, pk)), Jq);
-      dot_add(s1, df_mul(w, df_load(T.gV2, pk)), Jq);
+      s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
+      s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
       const float Vf = T.V32[pk], gf = T.G32[pk];
       const float Wc = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
       const float Lx = cd.w.Lchi32[o], Le = cd.w.Leta32[o];
       const float cLx = Wc * Lx, cU = Wc * (T.c2f[q] * Le - Lx);
-      auto zeta = [&](size_t ps, int lo, int up) {
+      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+        const int ts = T.q_t[s];
+        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
         const float Vs = T.V32[ps];
-        float& zl = sm.f(wid, lo, lane);
+        float& zl = sm.f(wid, T.t_lo[ts], lane);
         zl = fmaf(cLx, Vs, zl);                     // beta_j (Sect. 2.5.1, read from Eq. chi)
-        float& zu = sm.f(wid, up, lane);
+        float& zu = sm.f(wid, T.t_up[ts], lane);
         zu = fmaf(cU, T.G32[ps] * Vs, zu);          // and gamma_j (Eq. der_eta_n)
-      };
-      if (T.max_overlap <= kQMetaT) {
-        // the packed per-frequency table: window point and levels in one load
-        for (int j = 0; j < kQMetaT; ++j) {
-          const int m = __ldg(T.qmeta + (size_t)j * T.nq + q);
-          if (m < 0) break;
-          zeta((size_t)(m >> 8) * nz + k, (m >> 4) & 15, m & 15);
-        }
-      } else {
-        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-          const int ts = T.q_t[s];
-          zeta((size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k, T.t_lo[ts], T.t_up[ts]);
-        }
       }
     }
   } else if (base_mode) {
@@ -617,11 +606,11 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
       const df Jq = df_load(J2, o), w = df_load(T.W2, p);
-      dot_add(s0, df_mul(w, df_load(T.V2, pk)), Jq);
-      dot_add(s1, df_mul(w, df_load(T.gV2, pk)), Jq);
+      s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
+      s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
       const float Le = cd.w.Leta32[o];
       // Jeff = J - Psi* eta cancels in optically thick layers: formed from the pairs
-      const float Jf = df_sub_mul_to_float(Jq, df_load(as_pairs(cd.w.eta), o), Le);
+      const float Jf = df_to_float(df_sub(Jq, df_mul_f(df_load(as_pairs(cd.w.eta), o), Le)));
       const float Wf = T.Wr32[p], Vf = T.V32[pk], gf = T.G32[pk], c2f = T.c2f[q];
       const float WVf = Wf * Vf;
       f0 = fmaf(WVf, Jf, f0);
@@ -659,8 +648,8 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
     }
   }
   const bool pairs = mix && (base_mode || rh);
-  sm.d(wid, 0, lane) = pairs ? dot_value(s0) : a0;
-  sm.d(wid, 1, lane) = pairs ? dot_value(s1) : a1;
+  sm.d(wid, 0, lane) = pairs ? df_to_double(s0) : a0;
+  sm.d(wid, 1, lane) = pairs ? df_to_double(s1) : a1;
   if (rh) {
     // slot 2 + 2 (sum W U, U = 2 h nu^3/c^2 g V) is the spontaneous table, added below
     sm.d(wid, 2, lane) = mix ? (double)f0 : a2;
@@ -712,7 +701,7 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
 // (depth tile, transition) and walks the columns 32 at a time, lane l testing
 // column c0 + l * step, so that columns in another evaluation kind cost one
 // load each instead of a cluster launch.
-__global__ void __launch_bounds__(32 * kRateWarps, 4) k_rates(const ColDesc* __restrict__ cols, int ncols,
+__global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __restrict__ cols, int ncols,
                                                            int racc, int fslots) {
   extern __shared__ __align__(16) unsigned char rate_smem[];
   cg::cluster_group cluster = cg::this_cluster();
