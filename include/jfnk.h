@@ -53,6 +53,11 @@ extern "C" {
 #define JFNK_MAX_DEPTH  1024
 
 typedef enum { JFNK_MEM_HOST = 0, JFNK_MEM_DEVICE = 1 } jfnk_mem;
+/* JFNK_FP64: every step in FP64. JFNK_MIXED: formal solution, tangents and
+ * the preconditioner and RH92 sums in FP32; the source function, the mean
+ * intensity, the base opacity and rate sums in float pairs (hi + lo, about 48
+ * bits, on the FP32 pipe); rate-equation assembly, block inverses, GMRES and
+ * the Newton update in FP64. Arrays crossing the API are FP64 in both. */
 typedef enum { JFNK_FP64 = 0, JFNK_MIXED = 1 } jfnk_precision;
 typedef enum {
   JFNK_INIT_LTE = 0,             /* Saha-Boltzmann populations (Sect. 2.2.1)     */
