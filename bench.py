@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import math
 import os
 import subprocess
@@ -154,16 +155,23 @@ MIXED_DTYPE = "f32 formal solution / f32-pair S, J, rate sums / f64 assembly, Kr
 # ray-step coefficient header): a change to any of them voids its ncu traffic
 KERNEL_SOURCES = {
     "formal_fp64": ("formal_fused.cu", "formal_coef.cuh"),
-    "formal_fp32": ("formal_sweep.cu", "formal_coef.cuh"),
+    "formal_fp32": ("formal_sweep.cu", "formal_coef.cuh", "dfloat.cuh"),
 }
+
+
+def _code_only(text):
+    """Source text without comments and blank space (a comment edit leaves the kernel as it was)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
 
 
 def source_hash(kernel_key):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_17234_gb300", "csrc")
     for f in KERNEL_SOURCES[kernel_key]:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

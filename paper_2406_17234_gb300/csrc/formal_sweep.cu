@@ -58,11 +58,11 @@ struct StepIn {
   float tz;      // |dz| (chi^k + chi^u):   dtau = tz / (2 mu)
   float rz;      // 1/(|dz| (chi^k + chi^u)): 1/dtau = rz 2 mu
   float dtz;     // |dz| (dchi^k + dchi^u): ddtau = dtz / (2 mu)
-  float dSin;    // S^u - S^k (formed in FP64)
+  float dSin;    // S^u - S^k (formed from the S pairs, then rounded)
   float S0, Su;  // S^k, S^u
   float rc0;     // 1/chi^k
   float dcs;     // dchi^k + dchi^u
-  float ddSin;   // dS^u - dS^k (formed in FP64)
+  float ddSin;   // dS^u - dS^k
 };
 
 // Contributions of one ray to the sums of its depth, each already x 1/2 w_mu.
@@ -161,9 +161,10 @@ __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float*
 // ---------------------------------------------------------------------------
 // Variant 1: one thread per frequency, all angles of a hemisphere in registers.
 // ---------------------------------------------------------------------------
-// Base evaluations read chi and S per frequency row ([q][k], S in FP64), form
-// S^u - S^k in FP64, and leave depth-major float copies of chi, S and the
-// rounded differences for the tangent evaluations of the same Newton step;
+// Base evaluations read chi and S per frequency row ([q][k], S as a float
+// pair), form S^u - S^k in pair arithmetic, and leave depth-major float
+// copies of chi, S and the rounded differences for the tangent evaluations
+// of the same Newton step;
 // those then read depth-major float arrays only (one 128-byte line per warp
 // and depth) and run entirely in FP32.
 template <int MU, bool TAN, bool UP>

@@ -6,10 +6,10 @@
 // block-Jacobi preconditioner blocks (Sect. 2.5.2).
 //
 // Precision: ``real`` is double in the FP64 mode and float in the mixed mode
-// for chi, S, I and their tangents; every sum over rays and frequencies and
-// everything downstream of the rates is double. Intensities and source
-// functions are carried normalised by 2 h nu^3 / c^2 so that float keeps
-// range.
+// for chi, I and their tangents. The mixed mode's base evaluations keep S, J
+// and the opacity and rate sums in float pairs (dfloat.cuh); the assembly and
+// everything after it is double. Intensities and source functions are carried
+// normalised by 2 h nu^3 / c^2 so that float keeps range.
 #include <cooperative_groups.h>
 
 #include "formal_coef.cuh"
@@ -518,10 +518,11 @@ __device__ __forceinline__ int rate_mode(const ColDesc& cd, int t, int tile) {
 // through distributed shared memory across the cluster, in a fixed order
 // (bit-reproducible, no atomics).
 //
-// R_ij = sum W V J and R_ji = Rsp + sum W g V J (Eqs. Rij, Rji) take one FP64
-// product per term from the WV, WgV tables. Mixed mode forms the
-// preconditioner sums (base) and the RH92 sums in FP32; Jeff = J - Psi* eta
-// stays FP64 because it cancels in optically thick layers.
+// R_ij = sum W V J and R_ji = Rsp + sum W g V J (Eqs. Rij, Rji): in FP64 one
+// product per term from the WV, WgV tables; in mixed mode the same sums in
+// float pairs (W, V, g V, J pairs), the preconditioner sums (base) and the
+// RH92 sums in FP32, and Jeff = J - Psi* eta from the pairs because it cancels
+// in optically thick layers.
 __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const int tile, const int rank,
                            const RateSmem& sm, cg::cluster_group& cluster) {
   const ColTables& T = cd.t;
@@ -936,8 +937,8 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   if (b.formal_kind == FORMAL_SWEEP && side) {
     // Two independent chains over disjoint columns (a column is in one
     // evaluation kind per tick): tangent evaluations (FP32, issue-bound) on the
-    // side stream, base and RH92 ones (FP64-heavy) on s; joined before the
-    // assembly, which reads both.
+    // side stream, base and RH92 ones (float-pair sums, latency-bound) on s;
+    // joined before the assembly, which reads both.
     JFNK_CUDA(cudaEventRecord(b.fork_ev, s));
     JFNK_CUDA(cudaStreamWaitEvent(side, b.fork_ev, 0));
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, side>>>(b.d_cols);
