@@ -356,7 +356,10 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
   __shared__ double sh[32];
   __shared__ double s_h[kMaxKrylov + 1];
   __shared__ double s_y[kMaxKrylov];
+  __shared__ double s_cs[kMaxKrylov], s_sn[kMaxKrylov];   // Givens state of the step
+  __shared__ double s_H[(kMaxKrylov + 1) * kMaxKrylov];   // H and g for the least-squares solve
   __shared__ int s_next;      // decision broadcast
+  __shared__ int s_solve;
   __shared__ double s_val;
   const int phase = st->phase;
   if (phase == PH_DONE) return;
@@ -511,45 +514,66 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       double ss = 0.0;
       for (int i = threadIdx.x; i < N; i += blockDim.x) ss += w[i] * w[i];
       const double hnext = sqrt(block_sum(ss, sh));
+      // the Givens state staged in shared memory by every thread, so that the
+      // serial update below touches no global memory on its dependent chain
+      for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        s_cs[i] = cd.w.cs[i];
+        s_sn[i] = cd.w.sn[i];
+      }
+      __syncthreads();
       if (threadIdx.x == 0) {
         double* Hh = cd.w.Hh;
-        double* cs = cd.w.cs;
-        double* sn = cd.w.sn;
         double* gv = cd.w.gv;
-        for (int i = 0; i <= j; ++i) Hh[i * kmax + j] = s_h[i];
-        Hh[(j + 1) * kmax + j] = hnext;
+        s_h[j + 1] = hnext;
         for (int i = 0; i < j; ++i) {   // previous Givens rotations
-          double a = Hh[i * kmax + j], bb = Hh[(i + 1) * kmax + j];
-          Hh[i * kmax + j] = cs[i] * a + sn[i] * bb;
-          Hh[(i + 1) * kmax + j] = -sn[i] * a + cs[i] * bb;
+          const double a = s_h[i], bb = s_h[i + 1];
+          s_h[i] = s_cs[i] * a + s_sn[i] * bb;
+          s_h[i + 1] = -s_sn[i] * a + s_cs[i] * bb;
         }
-        double a = Hh[j * kmax + j], bb = Hh[(j + 1) * kmax + j];
-        double rr = hypot(a, bb);
-        cs[j] = rr == 0.0 ? 1.0 : a / rr;
-        sn[j] = rr == 0.0 ? 0.0 : bb / rr;
-        Hh[j * kmax + j] = rr;
-        Hh[(j + 1) * kmax + j] = 0.0;
-        gv[j + 1] = -sn[j] * gv[j];
-        gv[j] = cs[j] * gv[j];
-        const double resid = fabs(gv[j + 1]);
+        const double a = s_h[j], bb = s_h[j + 1];
+        const double rr = hypot(a, bb);
+        const double cj = rr == 0.0 ? 1.0 : a / rr, sj = rr == 0.0 ? 0.0 : bb / rr;
+        cd.w.cs[j] = cj;
+        cd.w.sn[j] = sj;
+        s_h[j] = rr;
+        s_h[j + 1] = 0.0;
+        for (int i = 0; i <= j + 1; ++i) Hh[i * kmax + j] = s_h[i];   // column j of the rotated H
+        const double gj = gv[j];
+        gv[j + 1] = -sj * gj;
+        gv[j] = cj * gj;
+        const double resid = fabs(sj * gj);
         const bool conv = resid < o.rtol * st->r0norm || !(hnext > 1e-300 * st->r0norm);
         const bool full = (j + 1 >= kmax);
-        int nx;
+        int nx, solve = 0;
         if (!(resid == resid) || !(rr == rr)) { st->status = JFNK_E_NAN; nx = NX_DONE; }
         else if (!conv && !full) nx = NX_NONE;       // continue Arnoldi
         else {
-          // y = H^{-1} g (upper triangular, j+1)
-          for (int r = j; r >= 0; --r) {
-            double s = gv[r];
-            for (int c = r + 1; c <= j; ++c) s -= Hh[r * kmax + c] * s_y[c];
-            s_y[r] = s / Hh[r * kmax + r];
-          }
+          solve = 1;                                  // y = H^{-1} g below
           nx = (conv || st->restarts >= o.max_restarts) ? NX_NEWTON : 100;   // 100: restart
         }
         s_next = nx;
+        s_solve = solve;
         s_val = hnext;
       }
       __syncthreads();
+      if (s_solve) {
+        // y = H^{-1} g (upper triangular, j+1): H and g gathered into shared
+        // memory by every thread, then one back substitution
+        const int m1 = j + 1;
+        for (int e = threadIdx.x; e < m1 * m1; e += blockDim.x) {
+          const int r = e / m1, c = e - r * m1;
+          s_H[r * kMaxKrylov + c] = c >= r ? cd.w.Hh[r * kmax + c] : 0.0;
+        }
+        for (int r = threadIdx.x; r < m1; r += blockDim.x) s_y[r] = cd.w.gv[r];
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int r = j; r >= 0; --r) {
+            double sv = s_y[r];
+            for (int c = r + 1; c <= j; ++c) sv -= s_H[r * kMaxKrylov + c] * s_y[c];
+            s_y[r] = sv / s_H[r * kMaxKrylov + r];
+          }
+        __syncthreads();
+      }
       next = s_next;
       if (next == NX_DONE) {
         if (threadIdx.x == 0) { st->phase = PH_DONE; status_out[blockIdx.x] = st->status; }
