@@ -150,43 +150,28 @@ __global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict
   const float* __restrict__ G32T = T.G32T;
   const float* __restrict__ v32 = cd.w.v32;
   const int* __restrict__ qmeta = T.qmeta;
-  // a thread takes two depths k, k+1 of one frequency: one transition list,
-  // two independent sums (twice the loads in flight per dependent step)
-  const int nz2 = (nz + 1) >> 1;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq * nz2; i += gridDim.x * blockDim.x) {
-    const int kp = i / nq, q = i - kp * nq;
-    const int k0 = 2 * kp, k1 = min(k0 + 1, nz - 1);   // k1 == k0 on an odd last row
-    const float* V0 = V32T + (size_t)k0 * nwin;
-    const float* V1 = V32T + (size_t)k1 * nwin;
-    const float* G0 = G32T + (size_t)k0 * nwin;
-    const float* G1 = G32T + (size_t)k1 * nwin;
-    const float* v0 = v32 + k0 * nl;
-    const float* v1 = v32 + k1 * nl;
-    TanAcc ta0, ta1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq * nz; i += gridDim.x * blockDim.x) {
+    const int k = i / nq, q = i - k * nq;
+    const float* V32 = V32T + (size_t)k * nwin;
+    const float* G32 = G32T + (size_t)k * nwin;
+    const float* v = v32 + k * nl;
+    TanAcc ta;
 #pragma unroll
     for (int j = 0; j < kQMetaT; ++j) {
       const int m = __ldg(qmeta + (size_t)j * nq + q);
       if (m < 0) break;
-      const int p = m >> 8, lo = (m >> 4) & 15, up = m & 15;
-      tan_acc(ta0, __ldg(V0 + p), __ldg(G0 + p), __ldg(v0 + lo), __ldg(v0 + up));
-      tan_acc(ta1, __ldg(V1 + p), __ldg(G1 + p), __ldg(v1 + lo), __ldg(v1 + up));
+      const int p = m >> 8;
+      tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + ((m >> 4) & 15)), __ldg(v + (m & 15)));
     }
     if (T.max_overlap > kQMetaT)
       for (int s = T.q_off[q] + kQMetaT; s < T.q_off[q + 1]; ++s) {
         const int t = T.q_t[s];
         const int p = T.t_base[t] + q - T.t_q0[t];
-        tan_acc(ta0, __ldg(V0 + p), __ldg(G0 + p), __ldg(v0 + T.t_lo[t]), __ldg(v0 + T.t_up[t]));
-        tan_acc(ta1, __ldg(V1 + p), __ldg(G1 + p), __ldg(v1 + T.t_lo[t]), __ldg(v1 + T.t_up[t]));
+        tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + T.t_lo[t]), __ldg(v + T.t_up[t]));
       }
-    const size_t o0 = (size_t)k0 * pitch + q, o1 = (size_t)k1 * pitch + q;
-    const float S0 = __ldg(cd.w.S32T + o0), c0 = __ldg(cd.w.chiT + o0);
-    const float S1 = __ldg(cd.w.S32T + o1), c1 = __ldg(cd.w.chiT + o1);
-    cd.w.dchiT[o0] = ta0.dchi;
-    cd.w.dS32T[o0] = tan_dS(ta0, S0, c0);
-    if (k1 != k0) {
-      cd.w.dchiT[o1] = ta1.dchi;
-      cd.w.dS32T[o1] = tan_dS(ta1, S1, c1);
-    }
+    const size_t o = (size_t)k * pitch + q;
+    cd.w.dchiT[o] = ta.dchi;
+    cd.w.dS32T[o] = tan_dS(ta, __ldg(cd.w.S32T + o), __ldg(cd.w.chiT + o));
   }
 }
 
@@ -196,7 +181,7 @@ __global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict
 // (coalesced rows of the depth-major tables) and a fixed xor-butterfly adds
 // the lanes, so the sums are bit-reproducible.
 constexpr int kRateTanWarps = 8;
-constexpr int kRateTanDepths = 8;   // depths per warp (independent sums in flight)
+constexpr int kRateTanDepths = 4;   // depths per warp (independent sums in flight)
 __global__ void __launch_bounds__(32 * kRateTanWarps) k_rates_tan32(const ColDesc* __restrict__ cols) {
   const ColDesc& cd = cols[blockIdx.z];
   if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
