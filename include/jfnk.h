@@ -377,13 +377,11 @@ int jfnk_server_destroy(jfnk_server* sv);
  * an exp as 1 operation). */
 int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s);
 
-/* Accuracy check of the library's own arithmetic: ops 0-4 the float-pair
- * arithmetic (hi + lo, about 48 bits, on the FP32 pipe) that the mixed mode's
- * base evaluations use for S, J, the opacity sums (Eqs. chi, eta) and the rate
- * sums (Eqs. Rij, Rji): each a[i], b[i] is rounded to a pair, combined (0 sum,
- * 1 difference, 2 product, 3 quotient, 4 same-sign accumulation) and returned
- * as hi + lo in FP64; op 5 the FP64 exp(-a[i]) of the formal solution's step
- * coefficients (App. A.1; b ignored).
+/* Accuracy check of the float-pair arithmetic (hi + lo, about 48 bits, on the
+ * FP32 pipe) that the mixed mode's base evaluations use for S, J, the opacity
+ * sums (Eqs. chi, eta) and the rate sums (Eqs. Rij, Rji): each a[i], b[i] is
+ * rounded to a pair, combined by op (0 sum, 1 difference, 2 product,
+ * 3 quotient, 4 same-sign accumulation) and returned as hi + lo in FP64.
  * Host arrays of n values, caller-owned; JFNK_E_INVALID for an unknown op,
  * n < 0 or NULL pointers. */
 int jfnk_check_arith(jfnk_ctx* ctx, int op, const double* a, const double* b, double* out, int n);

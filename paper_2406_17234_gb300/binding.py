@@ -369,7 +369,7 @@ def probe_alu(ctx: Context, kind: int) -> float:
     return v.value
 
 
-ARITH_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "acc": 4, "exp_neg": 5}
+ARITH_OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3, "acc": 4}
 
 
 def check_arith(ctx: Context, op: str, a, b):

@@ -43,49 +43,8 @@ __device__ __forceinline__ void pl_series64(double x, double& w, double& a, doub
 // In FP64 the direct forms of w, a and bq lose about 1e-16/x^2 relative
 // (1 - e, 1 - w and w - e cancel): 2e-10 at x = 1e-3, so the series takes
 // over below x = 1e-3 only.
-// exp(-x) in FP64 by the table-driven method of P. T. P. Tang (ACM Trans.
-// Math. Softw. 15, 1989): x 32/ln2 = k + f with k the nearest integer,
-// r = x - k ln2/32 (Cody-Waite: ln2/32 = L1 + L2 with L1 of 32 significant
-// bits, so that k L1 is exact), exp(-x) = 2^-m 2^(-j/32) exp(-r) for
-// k = 32 m + j, with 2^(-j/32) tabulated (the values below are those powers
-// correctly rounded) and exp(-r), |r| <= ln2/64, from its Taylor polynomial of
-// degree 6 (truncation below 4e-18): 11 FP64 operations, the power of two by
-// integer arithmetic on the exponent. Within about 2 ulp (tested against the
-// IEEE value); 0 above x = 700 (exp(-700) ~ 1e-304); NaN stays NaN.
-static __device__ const double kExpTab[32] = {
-    0x1.0000000000000p+0, 0x1.f50765b6e4540p-1, 0x1.ea4afa2a490dap-1, 0x1.dfc97337b9b5fp-1,
-    0x1.d5818dcfba487p-1, 0x1.cb720dcef9069p-1, 0x1.c199bdd85529cp-1, 0x1.b7f76f2fb5e47p-1,
-    0x1.ae89f995ad3adp-1, 0x1.a5503b23e255dp-1, 0x1.9c49182a3f090p-1, 0x1.93737b0cdc5e5p-1,
-    0x1.8ace5422aa0dbp-1, 0x1.82589994cce13p-1, 0x1.7a11473eb0187p-1, 0x1.71f75e8ec5f74p-1,
-    0x1.6a09e667f3bcdp-1, 0x1.6247eb03a5585p-1, 0x1.5ab07dd485429p-1, 0x1.5342b569d4f82p-1,
-    0x1.4bfdad5362a27p-1, 0x1.44e086061892dp-1, 0x1.3dea64c123422p-1, 0x1.371a7373aa9cbp-1,
-    0x1.306fe0a31b715p-1, 0x1.29e9df51fdee1p-1, 0x1.2387a6e756238p-1, 0x1.1d4873168b9aap-1,
-    0x1.172b83c7d517bp-1, 0x1.11301d0125b51p-1, 0x1.0b5586cf9890fp-1, 0x1.059b0d3158574p-1,
-};
-__device__ __forceinline__ double exp_neg(double x) {
-  if (!(x <= 700.0)) return x > 700.0 ? 0.0 : x;
-  const double kInvL = 0x1.71547652b82fep+5;    // 32/ln2
-  const double kShift = 0x1.8p+52;              // 1.5 2^52: the low word of x/L + shift is k
-  const double kL1 = 0x1.62e42ff000000p-6;      // ln2/32, leading 32 bits
-  const double kL2 = -0x1.718432a1b0e26p-40;    // ln2/32 - L1
-  const double t = fma(x, kInvL, kShift);
-  const int k = __double2loint(t);
-  const double kd = t - kShift;
-  double r = fma(-kd, kL1, x);
-  r = fma(-kd, kL2, r);
-  const double s = -r;
-  double p = fma(s, 1.0 / 720.0, 1.0 / 120.0);
-  p = fma(p, s, 1.0 / 24.0);
-  p = fma(p, s, 1.0 / 6.0);
-  p = fma(p, s, 0.5);
-  p = fma(p, s, 1.0);
-  p = fma(p, s, 1.0);
-  const double v = kExpTab[k & 31] * p;
-  return __hiloint2double(__double2hiint(v) - ((k >> 5) << 20), __double2loint(v));
-}
-
 __device__ __forceinline__ void pl_coef_f(double x, double r, double& e, double& w, double& a, double& bq) {
-  e = exp_neg(x);
+  e = exp(-x);
   if (x < 1e-3) {
     pl_series64(x, w, a, bq);
   } else {

@@ -60,7 +60,6 @@ __global__ void k_check_arith(int op, const double* a, const double* b, double* 
     case 1: r = df_sub(x, y); break;
     case 2: r = df_mul(x, y); break;
     case 3: r = df_div(x, y); break;
-    case 5: out[i] = exp_neg(a[i]); return;
     default: r = df_acc(x, y); break;
   }
   out[i] = df_to_double(r);
@@ -71,7 +70,7 @@ __global__ void k_check_arith(int op, const double* a, const double* b, double* 
 using namespace jfnk;
 
 extern "C" int jfnk_check_arith(jfnk_ctx* ctx, int op, const double* a, const double* b, double* q, int n) {
-  if (!ctx || op < 0 || op > 5 || n < 0 || (n > 0 && (!a || !b || !q)))
+  if (!ctx || op < 0 || op > 4 || n < 0 || (n > 0 && (!a || !b || !q)))
     return fail(JFNK_E_INVALID, "bad arithmetic-check arguments");
   if (n == 0) return JFNK_OK;
   JFNK_CUDA(cudaSetDevice(ctx->device));
