@@ -221,6 +221,10 @@ int jfnk_atom_frequencies(const jfnk_atom* a, double* nu);
  * synchronised before returning. */
 int jfnk_create_atmosphere(jfnk_ctx* ctx, const jfnk_atom* atom, const jfnk_atmos_desc* d,
                            jfnk_atmos** out);
+/* Returns the column's tables to the device's stream-ordered pool (on the
+ * context's internal stream: no device-wide synchronisation, so a serving loop
+ * can drop finished columns while others run). The caller must not destroy an
+ * atmosphere that a launched solve still uses, nor after its context. */
 int jfnk_destroy_atmosphere(jfnk_atmos* a);
 /* n_depth, n_nu, n_levels, n_transitions, and ray-points per evaluation. */
 int jfnk_atmos_info(const jfnk_atmos* a, int* n_depth, int* n_nu, int* n_levels,

@@ -471,6 +471,15 @@ int jfnk_init(int device, jfnk_ctx** out) {
   if (e != cudaSuccess) { delete c; return fail(JFNK_E_CUDA, cudaGetErrorString(e)); }
   c->n_sm = p.multiProcessorCount;
   if (int rc = prepare_kernels()) { delete c; return rc; }
+  {
+    // the stream-ordered pool keeps freed atmosphere tables for reuse
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   e = cudaStreamCreateWithFlags(&c->setup_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);

@@ -8,12 +8,17 @@
 
 namespace jfnk {
 
-// Bump allocator over one cudaMalloc: callers reserve typed blocks, then
-// allocate once; every block is 256-byte aligned.
+// Bump allocator over one device allocation: callers reserve typed blocks,
+// then allocate once; every block is 256-byte aligned. With a stream the
+// block comes from the device's stream-ordered pool (cudaMallocAsync /
+// cudaFreeAsync on that stream), so that releasing it does not wait for the
+// whole device, as cudaFree does: a serving loop creates and drops one
+// atmosphere per request while other columns run.
 struct DeviceArena {
   char* base = nullptr;
   size_t bytes = 0;
   size_t cursor = 0;
+  cudaStream_t stream = nullptr;
   void reset() { cursor = 0; }
   template <typename T>
   size_t take(size_t count) {

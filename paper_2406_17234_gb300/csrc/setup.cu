@@ -451,6 +451,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   // one device arena for every table
   DeviceArena& ar = M->arena;
   ar.reset();
+  ar.stream = ctx->setup_stream;   // stream-ordered pool: dropping an atmosphere does not stall the device
   size_t o_nu = ar.take<double>(nq), o_c2 = ar.take<double>(nq), o_rw = ar.take<double>(nq);
   size_t o_qoff = ar.take<int>(nq + 1), o_qt = ar.take<int>(A.q_t.size() + 1);
   size_t o_tlo = ar.take<int>(nt), o_tup = ar.take<int>(nt), o_tq0 = ar.take<int>(nt),

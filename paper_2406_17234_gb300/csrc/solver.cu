@@ -16,16 +16,19 @@ int DeviceArena::allocate() {
   release();
   bytes = cursor;
   if (bytes == 0) return JFNK_OK;
-  cudaError_t e = cudaMalloc(&base, bytes);
+  cudaError_t e = stream ? cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, stream) : cudaMalloc(&base, bytes);
   if (e != cudaSuccess) {
     base = nullptr;
-    return fail(JFNK_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return fail(JFNK_E_NOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
   }
   return JFNK_OK;
 }
 
 void DeviceArena::release() {
-  if (base) cudaFree(base);
+  if (base) {
+    if (stream) cudaFreeAsync(base, stream);
+    else cudaFree(base);
+  }
   base = nullptr;
   bytes = 0;
 }
