@@ -493,6 +493,7 @@ int jfnk_destroy_ctx(jfnk_ctx* c) {
   if (!c) return JFNK_OK;
   cudaSetDevice(c->device);
   if (c->setup_stream) cudaStreamDestroy(c->setup_stream);
+  if (c->stage) cudaFreeHost(c->stage);
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);

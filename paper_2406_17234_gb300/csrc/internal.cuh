@@ -66,6 +66,10 @@ struct jfnk_ctx {
   cudaStream_t stream = nullptr;      // stream of the evaluations and solves
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::mutex mu;
+  // pinned staging of an atmosphere's host-computed tables (one copy per
+  // atmosphere; reused under mu once the setup stream has drained)
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
 };
 
 struct jfnk_atom {

@@ -452,31 +452,34 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   DeviceArena& ar = M->arena;
   ar.reset();
   ar.stream = ctx->setup_stream;   // stream-ordered pool: dropping an atmosphere does not stall the device
-  size_t o_nu = ar.take<double>(nq), o_c2 = ar.take<double>(nq), o_rw = ar.take<double>(nq);
+  // host-computed tables first (one contiguous prefix, uploaded by one copy
+  // from pinned staging), then the tables the setup kernels compute
+  size_t o_nu = ar.take<double>(nq), o_c2 = ar.take<double>(nq), o_rw = ar.take<double>(nq),
+         o_rc2 = ar.take<double>(nq);
   size_t o_qoff = ar.take<int>(nq + 1), o_qt = ar.take<int>(A.q_t.size() + 1);
   size_t o_tlo = ar.take<int>(nt), o_tup = ar.take<int>(nt), o_tq0 = ar.take<int>(nt),
          o_tq1 = ar.take<int>(nt), o_tbase = ar.take<int>(nt), o_winT = ar.take<int>(nwin);
   size_t o_tw = ar.take<double>(nwin);
-  size_t o_V = ar.take<double>((size_t)nwin * nz), o_G = ar.take<double>((size_t)nwin * nz);
   size_t o_dz = ar.take<double>(nz - 1), o_mu = ar.take<double>(nmu), o_wmu = ar.take<double>(nmu);
-  size_t o_chic = ar.take<double>((size_t)nq * nz), o_etac = ar.take<double>((size_t)nq * nz);
-  size_t o_sca = ar.take<double>(nz), o_B = ar.take<double>((size_t)nq * nz);
-  size_t o_C = ar.take<double>((size_t)nz * nl * nl), o_ntot = ar.take<double>(nz),
-         o_nstar = ar.take<double>((size_t)nz * nl);
+  size_t o_ntot = ar.take<double>(nz);
   size_t o_T = ar.take<double>(nz), o_ne = ar.take<double>(nz), o_rho = ar.take<double>(nz),
          o_vt = ar.take<double>(nz);
   size_t o_tr = ar.take<TransDev>(nt), o_cd = ar.take<CollDev>(nt);
-  size_t o_V32 = ar.take<float>((size_t)nwin * nz), o_G32 = ar.take<float>((size_t)nwin * nz),
-         o_W32 = ar.take<float>(nwin), o_Wr32 = ar.take<float>(nwin), o_c2f = ar.take<float>(nq);
+  size_t o_W32 = ar.take<float>(nwin), o_Wr32 = ar.take<float>(nwin), o_c2f = ar.take<float>(nq);
   size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
+  size_t o_W2 = ar.take<float2>(nwin), o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
+  const size_t host_prefix = ar.cursor;
+  size_t o_V = ar.take<double>((size_t)nwin * nz), o_G = ar.take<double>((size_t)nwin * nz);
+  size_t o_chic = ar.take<double>((size_t)nq * nz), o_etac = ar.take<double>((size_t)nq * nz);
+  size_t o_sca = ar.take<double>(nz), o_B = ar.take<double>((size_t)nq * nz);
+  size_t o_C = ar.take<double>((size_t)nz * nl * nl), o_nstar = ar.take<double>((size_t)nz * nl);
+  size_t o_V32 = ar.take<float>((size_t)nwin * nz), o_G32 = ar.take<float>((size_t)nwin * nz);
   size_t o_V32T = ar.take<float>((size_t)nwin * nz), o_G32T = ar.take<float>((size_t)nwin * nz);
   size_t o_WV = ar.take<double>((size_t)nwin * nz), o_WgV = ar.take<double>((size_t)nwin * nz),
-         o_Rsp = ar.take<double>((size_t)nt * nz), o_gV = ar.take<double>((size_t)nwin * nz),
-         o_rc2 = ar.take<double>(nq);
+         o_Rsp = ar.take<double>((size_t)nt * nz), o_gV = ar.take<double>((size_t)nwin * nz);
   size_t o_V2 = ar.take<float2>((size_t)nwin * nz), o_gV2 = ar.take<float2>((size_t)nwin * nz),
-         o_W2 = ar.take<float2>(nwin), o_chibg2 = ar.take<float2>((size_t)nq * nz),
-         o_etac2 = ar.take<float2>((size_t)nq * nz), o_chisca2 = ar.take<float2>(nz),
-         o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
+         o_chibg2 = ar.take<float2>((size_t)nq * nz), o_etac2 = ar.take<float2>((size_t)nq * nz),
+         o_chisca2 = ar.take<float2>(nz);
   int rc = ar.allocate();
   if (rc) return rc;
   // host-side staging
@@ -527,8 +530,17 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   }
   std::vector<double> zeros(nz, 0.0);
   cudaStream_t s = ctx->setup_stream;
+  if (ctx->stage_bytes < host_prefix) {
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    JFNK_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&ctx->stage), host_prefix, cudaHostAllocDefault));
+    ctx->stage_bytes = host_prefix;
+  }
   auto up = [&](size_t off, const void* src, size_t bytes) {
-    return cudaMemcpyAsync(ar.base + off, src, bytes, cudaMemcpyHostToDevice, s);
+    if (off + bytes > host_prefix) return cudaErrorInvalidValue;   // only the host-computed prefix
+    std::memcpy(ctx->stage + off, src, bytes);   // copied below at once
+    return cudaSuccess;
   };
   JFNK_CUDA(up(o_nu, A.nu.data(), nq * 8));
   JFNK_CUDA(up(o_c2, c2.data(), nq * 8));
@@ -566,6 +578,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(up(o_vt, d->vturb ? d->vturb : zeros.data(), nz * 8));
   JFNK_CUDA(up(o_tr, tr.data(), nt * sizeof(TransDev)));
   JFNK_CUDA(up(o_cd, cd.data(), nt * sizeof(CollDev)));
+  JFNK_CUDA(cudaMemcpyAsync(ar.base, ctx->stage, host_prefix, cudaMemcpyHostToDevice, s));
   AtomDev at{};
   at.nl = nl; at.nt = nt; at.mass = A.mass;
   for (int l = 0; l < nl; ++l) { at.E[l] = A.E[l]; at.g[l] = A.g[l]; at.stage[l] = A.stage[l]; }
