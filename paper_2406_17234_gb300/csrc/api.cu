@@ -480,7 +480,12 @@ int jfnk_init(int device, jfnk_ctx** out) {
     }
     cudaGetLastError();
   }
-  e = cudaStreamCreateWithFlags(&c->setup_stream, cudaStreamNonBlocking);
+  // atmosphere set-up runs at the highest stream priority: its small kernels
+  // are scheduled ahead of queued blocks of running solves, so that a request
+  // being built does not wait behind a served batch's long launches
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  e = cudaStreamCreateWithPriority(&c->setup_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
