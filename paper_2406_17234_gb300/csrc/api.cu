@@ -485,7 +485,11 @@ int jfnk_init(int device, jfnk_ctx** out) {
   // being built does not wait behind a served batch's long launches
   int prio_low = 0, prio_high = 0;
   cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
-  e = cudaStreamCreateWithPriority(&c->setup_stream, cudaStreamNonBlocking, prio_high);
+  e = cudaSuccess;
+  for (int i = 0; i < jfnk_ctx::kSetupLanes && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithPriority(&c->setup_stream[i], cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->setup_done[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
@@ -497,8 +501,12 @@ int jfnk_init(int device, jfnk_ctx** out) {
 int jfnk_destroy_ctx(jfnk_ctx* c) {
   if (!c) return JFNK_OK;
   cudaSetDevice(c->device);
-  if (c->setup_stream) cudaStreamDestroy(c->setup_stream);
-  if (c->stage) cudaFreeHost(c->stage);
+  for (int i = 0; i < jfnk_ctx::kSetupLanes; ++i) {
+    if (c->setup_done[i]) cudaEventSynchronize(c->setup_done[i]);
+    if (c->setup_stream[i]) cudaStreamDestroy(c->setup_stream[i]);
+    if (c->setup_done[i]) cudaEventDestroy(c->setup_done[i]);
+    if (c->stage[i]) cudaFreeHost(c->stage[i]);
+  }
   if (c->stream) cudaStreamDestroy(c->stream);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -542,13 +550,27 @@ int jfnk_create_atmosphere(jfnk_ctx* ctx, const jfnk_atom* atom, const jfnk_atmo
   if (!ctx || !atom || !out) return fail(JFNK_E_INVALID, "context, atom and out are required");
   if (atom->ctx != ctx) return fail(JFNK_E_INVALID, "atom belongs to another context");
   *out = nullptr;
-  std::lock_guard<std::mutex> lk(ctx->mu);
+  // the set-up is enqueued under the context lock on the next set-up lane,
+  // whose previous set-up (and so its staging buffer) must be finished; the
+  // wait for this one happens outside the lock, so that several callers
+  // (the producer threads of a server) overlap their set-ups on the device
+  std::unique_lock<std::mutex> lk(ctx->mu);
   JFNK_CUDA(cudaSetDevice(ctx->device));
+  const int lane = ctx->next_lane;
+  ctx->next_lane = (lane + 1) % jfnk_ctx::kSetupLanes;
+  JFNK_CUDA(cudaEventSynchronize(ctx->setup_done[lane]));
   jfnk_atmos* a = new jfnk_atmos();
   a->ctx = ctx;
   a->atom = atom;
-  int rc = build_atmosphere(ctx, atom->d, d, &a->d);
-  if (rc) { delete a; return rc; }
+  int rc = build_atmosphere(ctx, lane, atom->d, d, &a->d);
+  if (rc) {
+    cudaStreamSynchronize(ctx->setup_stream[lane]);   // nothing left in flight on the lane
+    delete a;
+    return rc;
+  }
+  const cudaEvent_t done = ctx->setup_done[lane];
+  lk.unlock();
+  JFNK_CUDA(cudaEventSynchronize(done));   // the tables are ready for every stream
   a->work = new SingleWork();
   *out = a;
   return JFNK_OK;

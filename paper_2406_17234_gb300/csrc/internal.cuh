@@ -62,14 +62,18 @@ struct AtmosData {
 struct jfnk_ctx {
   int device = 0;
   int n_sm = 0;
-  cudaStream_t setup_stream = nullptr;
+  // atmosphere set-up lanes: a stream (highest priority), its pinned staging
+  // buffer and the event of its last set-up; callers take lanes in turn and
+  // wait for their own set-up outside the context lock
+  static constexpr int kSetupLanes = 4;
+  cudaStream_t setup_stream[kSetupLanes] = {};
+  cudaEvent_t setup_done[kSetupLanes] = {};
+  char* stage[kSetupLanes] = {};
+  size_t stage_bytes[kSetupLanes] = {};
+  int next_lane = 0;
   cudaStream_t stream = nullptr;      // stream of the evaluations and solves
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::mutex mu;
-  // pinned staging of an atmosphere's host-computed tables (one copy per
-  // atmosphere; reused under mu once the setup stream has drained)
-  char* stage = nullptr;
-  size_t stage_bytes = 0;
 };
 
 struct jfnk_atom {
@@ -87,7 +91,10 @@ struct jfnk_atmos {
 namespace jfnk {
 
 int build_atom(const jfnk_atom_desc* d, AtomData* A);
-int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d, AtmosData* M);
+// Enqueues the set-up of one column on set-up lane ``lane`` (its stream and
+// staging buffer, which must be idle) and records the lane's event; the
+// tables are ready once that event has completed.
+int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmos_desc* d, AtmosData* M);
 
 // Formal-solution kernels: per-ray buffers + ray-sum kernel (any size),
 // in-block fused kernel (FP64), per-frequency sweep kernel (mixed precision).

@@ -421,7 +421,7 @@ __global__ void k_collisions(int nt, const CollDev* cd, AtomDev at, int nz, cons
 // ---------------------------------------------------------------------------
 static bool g_voigt_ready[64] = {false};
 
-int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d, AtmosData* M) {
+int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmos_desc* d, AtmosData* M) {
   if (!d) return fail(JFNK_E_INVALID, "atmosphere descriptor is NULL");
   const int nz = d->n_depth;
   if (nz < 2 || nz > JFNK_MAX_DEPTH) return fail(JFNK_E_INVALID, "n_depth must be in [2, 1024]");
@@ -451,7 +451,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   // one device arena for every table
   DeviceArena& ar = M->arena;
   ar.reset();
-  ar.stream = ctx->setup_stream;   // stream-ordered pool: dropping an atmosphere does not stall the device
+  ar.stream = ctx->setup_stream[lane];   // stream-ordered pool: dropping an atmosphere does not stall the device
   // host-computed tables first (one contiguous prefix, uploaded by one copy
   // from pinned staging), then the tables the setup kernels compute
   size_t o_nu = ar.take<double>(nq), o_c2 = ar.take<double>(nq), o_rw = ar.take<double>(nq),
@@ -529,17 +529,18 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
     }
   }
   std::vector<double> zeros(nz, 0.0);
-  cudaStream_t s = ctx->setup_stream;
-  if (ctx->stage_bytes < host_prefix) {
-    if (ctx->stage) cudaFreeHost(ctx->stage);
-    ctx->stage = nullptr;
-    ctx->stage_bytes = 0;
-    JFNK_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&ctx->stage), host_prefix, cudaHostAllocDefault));
-    ctx->stage_bytes = host_prefix;
+  cudaStream_t s = ctx->setup_stream[lane];
+  char*& stage = ctx->stage[lane];
+  if (ctx->stage_bytes[lane] < host_prefix) {
+    if (stage) cudaFreeHost(stage);
+    stage = nullptr;
+    ctx->stage_bytes[lane] = 0;
+    JFNK_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&stage), host_prefix, cudaHostAllocDefault));
+    ctx->stage_bytes[lane] = host_prefix;
   }
   auto up = [&](size_t off, const void* src, size_t bytes) {
     if (off + bytes > host_prefix) return cudaErrorInvalidValue;   // only the host-computed prefix
-    std::memcpy(ctx->stage + off, src, bytes);   // copied below at once
+    std::memcpy(stage + off, src, bytes);   // copied below at once
     return cudaSuccess;
   };
   JFNK_CUDA(up(o_nu, A.nu.data(), nq * 8));
@@ -578,7 +579,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
   JFNK_CUDA(up(o_vt, d->vturb ? d->vturb : zeros.data(), nz * 8));
   JFNK_CUDA(up(o_tr, tr.data(), nt * sizeof(TransDev)));
   JFNK_CUDA(up(o_cd, cd.data(), nt * sizeof(CollDev)));
-  JFNK_CUDA(cudaMemcpyAsync(ar.base, ctx->stage, host_prefix, cudaMemcpyHostToDevice, s));
+  JFNK_CUDA(cudaMemcpyAsync(ar.base, stage, host_prefix, cudaMemcpyHostToDevice, s));
   AtomDev at{};
   at.nl = nl; at.nt = nt; at.mass = A.mass;
   for (int l = 0; l < nl; ++l) { at.E[l] = A.E[l]; at.g[l] = A.g[l]; at.stage[l] = A.stage[l]; }
@@ -619,7 +620,7 @@ int build_atmosphere(jfnk_ctx* ctx, const AtomData& A, const jfnk_atmos_desc* d,
       nwin, nz, ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<float>(o_V32), ar.ptr<float>(o_G32),
       ar.ptr<float>(o_V32T), ar.ptr<float>(o_G32T));
   JFNK_CUDA(cudaGetLastError());
-  JFNK_CUDA(cudaStreamSynchronize(s));
+  JFNK_CUDA(cudaEventRecord(ctx->setup_done[lane], s));
   ColTables& tb_ = M->tables;
   tb_.nz = nz; tb_.nq = nq; tb_.nl = nl; tb_.nt = nt; tb_.nmu = nmu; tb_.nwin = nwin;
   tb_.max_overlap = 0;
