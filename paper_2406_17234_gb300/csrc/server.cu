@@ -95,6 +95,12 @@ struct jfnk_server {
   std::vector<ServerReq> slot;
   std::vector<char> busy;
   int* h_status = nullptr;        // pinned mirror of the slot statuses
+  // pinned staging per slot for admissions and retirements: a step enqueues
+  // all its copies and synchronises once (a slot's staging is not rewritten
+  // before the step that used it has drained)
+  ColDesc* hp_cols = nullptr;
+  SolverState* hp_state = nullptr;
+  SolverOpts* hp_opts = nullptr;
 
   double clock() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -119,13 +125,18 @@ int admit(jfnk_server* sv, int i, ServerReq& r) {
   ColDesc& d = b.h_cols[i];
   column_bind(sv->pool.base + r.off, M, sv->kind, sv->mixed, sv->kmax, b.d_state + i, &d);
   d.opts = sv->d_sopts + i;
-  SolverState st{};
+  SolverState& st = sv->hp_state[i];
+  st = SolverState{};
   st.phase = r.rh92 ? PH_RH92 : PH_BASE;
   st.status = 1;
+  sv->hp_cols[i] = d;
+  sv->hp_opts[i] = r.o;
   const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
-  JFNK_CUDA(cudaMemcpyAsync(b.d_cols + i, &d, sizeof(ColDesc), cudaMemcpyHostToDevice, sv->stream));
-  JFNK_CUDA(cudaMemcpyAsync(b.d_state + i, &st, sizeof(st), cudaMemcpyHostToDevice, sv->stream));
-  JFNK_CUDA(cudaMemcpyAsync(sv->d_sopts + i, &r.o, sizeof(SolverOpts), cudaMemcpyHostToDevice, sv->stream));
+  JFNK_CUDA(cudaMemcpyAsync(b.d_cols + i, sv->hp_cols + i, sizeof(ColDesc), cudaMemcpyHostToDevice, sv->stream));
+  JFNK_CUDA(cudaMemcpyAsync(b.d_state + i, sv->hp_state + i, sizeof(SolverState), cudaMemcpyHostToDevice,
+                            sv->stream));
+  JFNK_CUDA(cudaMemcpyAsync(sv->d_sopts + i, sv->hp_opts + i, sizeof(SolverOpts), cudaMemcpyHostToDevice,
+                            sv->stream));
   JFNK_CUDA(cudaMemcpyAsync(d.w.n, M.tables.nstar, N * 8, cudaMemcpyDeviceToDevice, sv->stream));
   JFNK_CUDA(cudaMemcpyAsync(d.w.Jdag, M.tables.Bn, QZ * 8, cudaMemcpyDeviceToDevice, sv->stream));
   if (sv->mixed) {
@@ -134,24 +145,31 @@ int admit(jfnk_server* sv, int i, ServerReq& r) {
   }
   sv->h_status[i] = 1;
   JFNK_CUDA(cudaMemcpyAsync(b.d_status + i, sv->h_status + i, sizeof(int), cudaMemcpyHostToDevice, sv->stream));
-  // the staged copies read host values that change with the next admission
-  JFNK_CUDA(cudaStreamSynchronize(sv->stream));
   r.t_admit = sv->clock();
   sv->slot[i] = r;
   sv->busy[i] = 1;
   return JFNK_OK;
 }
 
+// Enqueues the copies out of a finished slot (state and populations).
+int retire_copy(jfnk_server* sv, int i) {
+  Batch& b = sv->b;
+  ServerReq& r = sv->slot[i];
+  const AtmosData& M = r.a->d;
+  JFNK_CUDA(cudaMemcpyAsync(sv->hp_state + i, b.d_state + i, sizeof(SolverState), cudaMemcpyDeviceToHost,
+                            sv->stream));
+  if (r.n_out)
+    JFNK_CUDA(cudaMemcpyAsync(r.n_out, b.h_cols[i].w.n, (size_t)M.nz * M.nl * 8, cudaMemcpyDeviceToHost,
+                              sv->stream));
+  return JFNK_OK;
+}
+
+// After the step's copies have drained: the slot's result, its pool block freed.
 int retire(jfnk_server* sv, int i) {
   Batch& b = sv->b;
   ServerReq& r = sv->slot[i];
   const AtmosData& M = r.a->d;
-  SolverState x;
-  JFNK_CUDA(cudaMemcpyAsync(&x, b.d_state + i, sizeof(x), cudaMemcpyDeviceToHost, sv->stream));
-  if (r.n_out)
-    JFNK_CUDA(cudaMemcpyAsync(r.n_out, b.h_cols[i].w.n, (size_t)M.nz * M.nl * 8, cudaMemcpyDeviceToHost,
-                              sv->stream));
-  JFNK_CUDA(cudaStreamSynchronize(sv->stream));
+  const SolverState& x = sv->hp_state[i];
   jfnk_result res{};
   res.id = r.id;
   res.status = x.status == 1 ? JFNK_E_TIMEOUT : x.status;
@@ -252,7 +270,10 @@ int jfnk_server_create(jfnk_ctx* ctx, const jfnk_server_desc* d, jfnk_server** o
   SolverOpts so;
   options_to_device(&d->opts, &so);
   if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost(&sv->h_status, sizeof(int) * S) != cudaSuccess)
+      cudaMallocHost(&sv->h_status, sizeof(int) * S) != cudaSuccess ||
+      cudaMallocHost(&sv->hp_cols, sizeof(ColDesc) * S) != cudaSuccess ||
+      cudaMallocHost(&sv->hp_state, sizeof(SolverState) * S) != cudaSuccess ||
+      cudaMallocHost(&sv->hp_opts, sizeof(SolverOpts) * S) != cudaSuccess)
     return bail(fail(JFNK_E_CUDA, "server stream or pinned status buffer"));
   for (int i = 0; i < S; ++i) sv->h_status[i] = 0;
   if (cudaMemcpy(b.d_cols, b.h_cols.data(), sizeof(ColDesc) * S, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -340,6 +361,14 @@ int jfnk_server_step(jfnk_server* sv, int* n_active, int* n_queued) {
     if (cudaGraphLaunch(sv->graph, sv->stream) != cudaSuccess) return fail(JFNK_E_CUDA, "cudaGraphLaunch failed");
     JFNK_CUDA(cudaMemcpyAsync(sv->h_status, sv->b.d_status, sizeof(int) * S, cudaMemcpyDeviceToHost, sv->stream));
     JFNK_CUDA(cudaStreamSynchronize(sv->stream));
+    // every finished slot's copies first, one synchronisation, then the results
+    bool any = false;
+    for (int i = 0; i < S; ++i)
+      if (sv->busy[i] && sv->h_status[i] != 1) {
+        if ((rc = retire_copy(sv, i))) return rc;
+        any = true;
+      }
+    if (any) JFNK_CUDA(cudaStreamSynchronize(sv->stream));
     for (int i = 0; i < S; ++i)
       if (sv->busy[i] && sv->h_status[i] != 1 && (rc = retire(sv, i))) return rc;
   }
@@ -373,6 +402,9 @@ int jfnk_server_destroy(jfnk_server* sv) {
   if (sv->stream) cudaStreamSynchronize(sv->stream);
   if (sv->graph) cudaGraphExecDestroy(sv->graph);
   if (sv->h_status) cudaFreeHost(sv->h_status);
+  if (sv->hp_cols) cudaFreeHost(sv->hp_cols);
+  if (sv->hp_state) cudaFreeHost(sv->hp_state);
+  if (sv->hp_opts) cudaFreeHost(sv->hp_opts);
   if (sv->stream) cudaStreamDestroy(sv->stream);
   delete sv;
   cudaGetLastError();   // a teardown failure must not surface in a later call
