@@ -121,16 +121,28 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
   const double* n = eval_pops(cd, mode) + k * nl;
   const double eta_bg = T.eta_c[i] + T.chi_sca[k] * jdag_ptr(cd)[i];
   const double c2 = T.c2[q];
-  double chi = T.chi_c[i] + T.chi_sca[k];
-  double eta = eta_bg;
-  for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-    const int t = T.q_t[s];
-    const int lo = T.t_lo[t], up = T.t_up[t];
-    const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
-    const double V = T.V[p], g = T.G[p];
-    chi += V * (n[lo] - g * n[up]);
-    eta += c2 * g * V * n[up];
+  // sum V n_lo and sum g V n_up (the latter serves chi and eta alike), two
+  // FP64 operations per transition; the packed table gives window point and
+  // levels in one load
+  double chl = 0.0, el = 0.0;
+  if (T.max_overlap <= kQMetaT) {
+    for (int j = 0; j < kQMetaT; ++j) {
+      const int m = __ldg(T.qmeta + (size_t)j * T.nq + q);
+      if (m < 0) break;
+      const size_t p = (size_t)(m >> 8) * nz + k;
+      chl = fma(T.V[p], n[(m >> 4) & 15], chl);
+      el = fma(T.gV[p], n[m & 15], el);
+    }
+  } else {
+    for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+      const int t = T.q_t[s];
+      const size_t p = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+      chl = fma(T.V[p], n[T.t_lo[t]], chl);
+      el = fma(T.gV[p], n[T.t_up[t]], el);
+    }
   }
+  const double chi = (T.chi_c[i] + T.chi_sca[k]) + (chl - el);
+  const double eta = fma(c2, el, eta_bg);
   reinterpret_cast<real*>(cd.w.chi)[i] = (real)chi;
   cd.w.S[i] = eta / (chi * c2);
   if (mode == EV_RH92) cd.w.eta[i] = eta;   // for the RH92 rate sums
