@@ -40,7 +40,8 @@ METRIC = "formal-solution ray-points/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 40 single-column solves, 10 batched solves or oracle steps)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="ca", choices=["ca", "two-level", "h", "batch", "serve"])
@@ -51,7 +52,13 @@ def parse():
     p.add_argument("--producers", type=int, default=4, help="serve workload: threads building requests")
     p.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    args = p.parse_args()
+    if args.steps is None:
+        # a single-column solve takes tens of ms: 40 of them give the clock
+        # sampler a timed region of about a second
+        single = args.impl == "ours" and args.workload in ("ca", "two-level", "h")
+        args.steps = 40 if single else 10
+    return args
 
 
 def workload(name):
@@ -111,7 +118,7 @@ def clocks_start():
             ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     except Exception:
         return None
