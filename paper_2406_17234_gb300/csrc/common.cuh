@@ -87,6 +87,8 @@ struct ColTables {
   const float* W32;       // [nwin] omega_t(nu_q) 4 pi/(h nu_q) 2 h nu_q^3/c^2 in float
   const float* Wr32;      // [nwin] omega_t(nu_q) 4 pi/(h nu_q) in float
   const float* c2f;       // [nq] 2 h nu^3/c^2 in float
+  const int* lvl_inc;     // [nl][nt + 1] transitions of each level in order, packed as
+                          // t << 1 | (1 if the level is the upper one), -1 after the last
   const int* qmeta;       // [kQMetaT][nq] transitions active at nu_q, packed as
                           // window point << 8 | lo << 4 | up; -1 past the last
   const double* dz;       // [nz-1] |z_k - z_{k+1}|

@@ -826,10 +826,15 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
   }
   __syncwarp();
   if (lane < nl) {
+    // the level's own transitions in index order (the same additions as a scan
+    // over every transition, without the FP64 instructions that add nothing)
     double f = 0.0;
-    for (int t = 0; t < nt; ++t) {
-      if (T.t_lo[t] == lane) f += s_kap[wid][t];
-      if (T.t_up[t] == lane) f -= s_kap[wid][t];
+    const int* inc = T.lvl_inc + lane * (nt + 1);
+    for (int e = 0; e < nt; ++e) {
+      const int m = inc[e];
+      if (m < 0) break;
+      const double kp = s_kap[wid][m >> 1];
+      f += (m & 1) ? -kp : kp;
     }
     if (lane == is) {
       double sv = 0.0;

@@ -468,6 +468,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   size_t o_W32 = ar.take<float>(nwin), o_Wr32 = ar.take<float>(nwin), o_c2f = ar.take<float>(nq);
   size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
   size_t o_W2 = ar.take<float2>(nwin), o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
+  size_t o_linc = ar.take<int>((size_t)nl * (nt + 1));
   const size_t host_prefix = ar.cursor;
   size_t o_V = ar.take<double>((size_t)nwin * nz), o_G = ar.take<double>((size_t)nwin * nz);
   size_t o_chic = ar.take<double>((size_t)nq * nz), o_etac = ar.take<double>((size_t)nq * nz);
@@ -569,6 +570,16 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
       qmeta[(size_t)j * nq + q] = ((A.t_base[t] + q - A.t_q0[t]) << 8) | (A.t_lo[t] << 4) | A.t_up[t];
     }
   JFNK_CUDA(up(o_qmeta, qmeta.data(), qmeta.size() * 4));
+  // per level, its transitions in index order (lower level: +, upper: -)
+  std::vector<int> linc((size_t)nl * (nt + 1), -1);
+  for (int l = 0; l < nl; ++l) {
+    int j = 0;
+    for (int t = 0; t < nt; ++t) {
+      if (A.t_lo[t] == l) linc[(size_t)l * (nt + 1) + j++] = t << 1;
+      else if (A.t_up[t] == l) linc[(size_t)l * (nt + 1) + j++] = (t << 1) | 1;
+    }
+  }
+  JFNK_CUDA(up(o_linc, linc.data(), linc.size() * 4));
   JFNK_CUDA(up(o_dz, dzv.data(), (nz - 1) * 8));
   JFNK_CUDA(up(o_mu, mu.data(), nmu * 8));
   JFNK_CUDA(up(o_wmu, wmu.data(), nmu * 8));
@@ -639,6 +650,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);
   tb_.Wr32 = ar.ptr<float>(o_Wr32); tb_.c2f = ar.ptr<float>(o_c2f);
   tb_.qmeta = ar.ptr<int>(o_qmeta);
+  tb_.lvl_inc = ar.ptr<int>(o_linc);
   tb_.mu = ar.ptr<double>(o_mu); tb_.wmu = ar.ptr<double>(o_wmu);
   tb_.chi_c = ar.ptr<double>(o_chic); tb_.eta_c = ar.ptr<double>(o_etac);
   tb_.chi_sca = ar.ptr<double>(o_sca); tb_.Bn = ar.ptr<double>(o_B); tb_.C = ar.ptr<double>(o_C);
