@@ -853,14 +853,16 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
   for (int e = lane; e < nl * nl; e += 32) {
     const int i = e / nl, j = e - i * nl;
     double pv = 0.0;
-    for (int t = 0; t < nt; ++t) {
+    const int* inc = T.lvl_inc + i * (nt + 1);   // the transitions of level i, in index order
+    for (int ee = 0; ee < nt; ++ee) {
+      const int m = inc[ee];
+      if (m < 0) break;
+      const int t = m >> 1;
       const int lo = T.t_lo[t], up = T.t_up[t];
-      const double sg = (lo == i) ? 1.0 : ((up == i) ? -1.0 : 0.0);
-      if (sg == 0.0) continue;
       double g = cd.w.Apart[((size_t)t * nz + k) * nl + j];
       if (j == lo) g += s_up[wid][t];
       if (j == up) g -= s_dn[wid][t];
-      pv += sg * g;
+      pv += (m & 1) ? -g : g;   // i is the lower level (+) or the upper one (-)
     }
     s_P[wid][e] = (i == is) ? -1.0 : pv;
   }
