@@ -62,7 +62,9 @@ def pop_change(n_new, n_prev) -> float:
 
 
 def zero_radiation_guess(m: Model) -> np.ndarray:
-    """Populations of the rate equations with I = 0 (spontaneous rates only) plus conservation."""
+    """Populations of the rate equations with I = 0 (spontaneous rates only) plus conservation
+    (Sect. 2.2.1). Pinned by the two-level closed form n_u/n_l = C_lu/(C_ul + A_ul) and by the
+    Saha-Boltzmann limit of a six-level atom when collisions dominate."""
     from .residual import rates_from_J
     R_up, R_dn = rates_from_J(m, np.zeros((m.nq, m.nz)))
     n = np.zeros((m.nz, m.nl))

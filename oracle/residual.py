@@ -24,7 +24,12 @@ eps_1 and eps_2 of the Fig. 2 caption.
 Pins (tests/test_oracle_residual.py): detailed balance at LTE populations with
 J = B (every net rate vanishes), collision-only detailed balance, linearity of
 the complex-step JVP, agreement with brute-force central differences, and the
-exactness of the block-Jacobi blocks against the dense Jacobian.
+exactness of the block-Jacobi blocks against the dense Jacobian. The
+background terms of the opacity and emissivity are pinned by three physical
+limits: Kirchhoff (isothermal LTE with J^dagger = B gives S = B_nu wherever
+only continua and background are active, and at every line centre), pure
+electron scattering (S = J^dagger for any J^dagger) and pure absorption (S
+independent of J^dagger, S = B_nu for continuum absorption alone).
 """
 from __future__ import annotations
 

@@ -27,6 +27,13 @@ limited per depth exactly like a Newton correction (Sect. 2.2.2, the same
 ``depth_clamp``): the paper states that limiting for the Newton step only, and
 applying it to the RH92 correction is this implementation's reading; it leaves
 every iteration that stays positive unchanged.
+
+Pins (tests/test_oracle_solvers.py): the fixed point is JFNK's solution on a
+column with background (which fixes the constant cross-coupling term), RH92
+and JFNK reach the same populations and emergent spectrum, and on the
+eps = 1e-4 slab RH92 ends orders of magnitude closer to the solution than the
+same loop with Psi* = 0 (plain Lambda iteration), which a dropped or
+mis-signed Psi* or cross-coupling term would reduce it to.
 """
 from __future__ import annotations
 

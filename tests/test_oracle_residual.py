@@ -6,7 +6,7 @@ import workloads as W
 from oracle import model as OM
 from oracle.dense import dense_jacobian
 from oracle.precond import block_jacobi
-from oracle.residual import assemble, jvp_complex, jvp_fd, rates_from_J, residual
+from oracle.residual import assemble, jvp_complex, jvp_fd, opacity_emissivity, rates_from_J, residual
 
 
 @pytest.fixture(scope="module")
@@ -145,3 +145,78 @@ def test_finite_differences_are_less_accurate_than_complex_step(small_ca):
     assert errs[("complex", None)] < 1e-10
     assert errs[("forward", "eps1")] > 1e3 * errs[("complex", None)]
     assert errs[("forward", "eps2")] > 1e3 * errs[("complex", None)]
+
+
+def _isothermal_column(nz=12, T=6000.0, thomson=True, kappa=1.0, ntot_scale=1.0):
+    """Isothermal column with the synthetic chromosphere's background law
+    (power-law UV rise, Thomson scattering) at constant temperature."""
+    base = W.chromosphere(nz, abundance=2.2e-6)
+    ones = np.ones(nz)
+    return W.replace(base, T=T * ones, ntot=ntot_scale * base.ntot, kappa=kappa, thomson=thomson)
+
+
+def _line_centre_indices(m):
+    out = []
+    for tr in m.trans:
+        if tr.kind == "bb":
+            q = int(np.argmin(np.abs(m.nu - tr.nu0)))
+            assert abs(m.nu[q] / tr.nu0 - 1.0) < 1e-15      # odd grids hold nu_0 itself
+            out.append(q)
+    return out
+
+
+def test_source_function_is_planck_in_thermodynamic_equilibrium():
+    """Kirchhoff (Eqs. chi, eta with the background of Sect. 2.1.1): on an
+    isothermal column at LTE populations with J^dagger = B_nu(T), the source
+    function equals B_nu at every frequency whose active transitions are
+    continua or background only, and at every line centre (the line's g_ij is
+    the Boltzmann ratio of its centre frequency). A dropped chi_sca in chi, a
+    wrong eta_c or a mis-signed stimulated-emission term breaks this."""
+    atom = W.ca_like_atom(0, 0.1)
+    col = _isothermal_column()
+    m = OM.build_model(atom, col, 2)
+    chi, eta = opacity_emissivity(m, m.nstar, m.B)
+    S = eta / chi
+    bb = np.array([tr.kind == "bb" for tr in m.trans])
+    no_line = ~m.active[bb].any(axis=0)
+    assert no_line.sum() > 10
+    np.testing.assert_allclose(S[no_line], m.B[no_line], rtol=1e-12)
+    qc = _line_centre_indices(m)
+    np.testing.assert_allclose(S[qc], m.B[qc], rtol=1e-12)
+    # and off line centre the lines pull S away from B_nu (the test would pass
+    # trivially if the line terms were missing)
+    in_line = m.active[bb].any(axis=0)
+    assert np.max(np.abs(S[in_line] / m.B[in_line] - 1.0)) > 1e-4
+
+
+def test_pure_scattering_limit_gives_source_function_equal_to_J_dagger():
+    """Pure electron scattering (no active atom, no continuum absorption):
+    S = J^dagger at every (nu, k) for any lagged mean intensity, through the
+    full residual evaluation (the scattering emissivity uses J^dagger, and
+    chi_sca enters both chi and eta)."""
+    atom = W.ca_like_atom(0, 0.1)
+    col = _isothermal_column(kappa=0.0, thomson=True, ntot_scale=0.0)
+    m = OM.build_model(atom, col, 2)
+    rng = np.random.default_rng(9)
+    Jd = m.B * np.exp(rng.normal(0.0, 1.0, m.B.shape))
+    n0 = np.zeros((m.nz, m.nl))
+    chi, eta = opacity_emissivity(m, n0, Jd)
+    np.testing.assert_allclose(eta / chi, Jd, rtol=1e-14)
+    r = residual(m, n0, Jd)
+    np.testing.assert_allclose(r.eta / r.chi, Jd, rtol=1e-14)
+
+
+def test_pure_absorption_limit_ignores_J_dagger():
+    """Without Thomson scattering the source function does not depend on
+    J^dagger, and continuum absorption alone (no active atom) gives S = B_nu."""
+    atom = W.ca_like_atom(0, 0.1)
+    m = OM.build_model(atom, _isothermal_column(thomson=False), 2)
+    rng = np.random.default_rng(10)
+    n = W.perturbed_populations(m.nstar, rng, 0.3)
+    c1, e1 = opacity_emissivity(m, n, m.B)
+    c2, e2 = opacity_emissivity(m, n, m.B * rng.uniform(0.1, 10.0, m.B.shape))
+    np.testing.assert_array_equal(c1, c2)
+    np.testing.assert_array_equal(e1, e2)
+    m0 = OM.build_model(atom, _isothermal_column(thomson=False, ntot_scale=0.0), 2)
+    chi, eta = opacity_emissivity(m0, np.zeros((m0.nz, m0.nl)), m0.B * 3.0)
+    np.testing.assert_allclose(eta / chi, m0.B, rtol=1e-14)

@@ -173,3 +173,75 @@ def test_zero_radiation_guess_solves_its_equations():
     n = zero_radiation_guess(m)
     assert np.all(n > 0)
     np.testing.assert_allclose(n.sum(axis=1), m.ntot, rtol=1e-12)
+
+
+def test_zero_radiation_guess_matches_the_two_level_closed_form():
+    """With I = 0 a two-level atom balances collisional excitation against
+    collisional de-excitation plus spontaneous emission:
+    n_u / n_l = C_lu / (C_ul + A_ul), with A_ul from the Einstein relation
+    A_ul = 8 pi^2 e^2 nu_0^2 / (m_e c^3) (g_l / g_u) f. The profile-weighted
+    spontaneous rate differs from A_ul only by the (nu/nu_0)^2 variation across
+    the Doppler core (< 1e-9)."""
+    wl = W.config1(n_depth=15, n_nu=21)
+    m = OM.build_model(wl.atom, wl.columns[0], 2)
+    ln = wl.atom.lines[0]
+    nu0 = m.trans[0].nu0
+    A_ul = 8.0 * np.pi ** 2 * OM.QE ** 2 * nu0 ** 2 / (OM.ME * OM.C ** 3) \
+        * (wl.atom.g[ln.i] / wl.atom.g[ln.j]) * ln.f
+    C_lu, C_ul = m.Cmat[:, 0, 1], m.Cmat[:, 1, 0]
+    n = zero_radiation_guess(m)
+    np.testing.assert_allclose(n[:, 1] / n[:, 0], C_lu / (C_ul + A_ul), rtol=1e-8)
+    np.testing.assert_allclose(n.sum(axis=1), m.ntot, rtol=1e-13)
+    # eps = 1e-4: C_ul is about 1e-4 A_ul, so the guess lies far below LTE
+    assert np.all(n[:, 1] / n[:, 0] < 1e-3 * m.nstar[:, 1] / m.nstar[:, 0])
+
+
+def test_zero_radiation_guess_tends_to_lte_when_collisions_dominate():
+    """Every row of the multi-level I = 0 rate equations (not only the one the
+    conservation row leaves in a two-level atom): with collisions scaled up by
+    1e12 the spontaneous rates are negligible and detailed balance of the
+    collision rates gives back the Saha-Boltzmann populations, the departure
+    shrinking like 1/scale (the ratio of spontaneous to collisional rates)."""
+    wl = W.config2(nu_scale=0.1, n_depth=12)
+    dev = []
+    for scale in (1e12, 1e14, 1e16):
+        m = OM.build_model(wl.atom, wl.columns[0], 2)
+        m.Cmat *= scale
+        dev.append(np.max(np.abs(zero_radiation_guess(m) / m.nstar - 1.0)))
+    assert 50 < dev[0] / dev[1] < 200 and 50 < dev[1] / dev[2] < 200
+    assert dev[2] < 1e-7
+
+
+def test_rh92_operator_splitting_beats_lambda_iteration():
+    """RH92 with its local operator Psi* against the same loop with Psi* = 0
+    (plain Lambda iteration, no cross-coupling) on the eps = 1e-4 slab: after
+    the same number of iterations RH92 is orders of magnitude closer to the
+    solution, while Lambda iteration stalls with small population changes far
+    from it (its classical false convergence). A dropped or mis-signed
+    Psi* / cross-coupling term turns RH92 into the latter."""
+    import oracle.rh92 as R
+    wl = W.config1(n_depth=61, n_nu=21)
+    m = OM.build_model(wl.atom, wl.columns[0], 3)
+    ref = jfnk(m, m.nstar, rtol=1e-8, ftol=1e-12)
+    assert ref.converged
+
+    def iterate(k, lambda_only):
+        n, Jd = m.nstar.copy(), OM.initial_J(m)
+        changes = []
+        for _ in range(k):
+            res = residual(m, n, Jd, want_lambda=True)
+            if lambda_only:
+                res.lam_eta = np.zeros_like(res.lam_eta)
+            n_new = R.rh92_update(m, n, res)
+            changes.append(0.5 * np.max(np.abs((n_new - n) / (n_new + n))))
+            n, Jd = n_new, res.J
+        return np.max(np.abs(n / ref.n - 1.0)), changes
+
+    e_rh, c_rh = iterate(160, False)
+    e_la, c_la = iterate(160, True)
+    assert e_rh < 0.05
+    assert e_la > 1.0
+    assert e_rh < 1e-2 * e_la
+    # Lambda iteration's last changes are already small although it is a
+    # factor of several away from the solution
+    assert c_la[-1] < 2e-3
