@@ -1,17 +1,23 @@
 """Benchmark: converged JFNK NLTE column solves on the GPU (one JSON line).
 
-Default workload: the six-level Ca II-like atom on the 82-depth synthetic
-chromosphere (about 1,000 frequencies, 5 mu per hemisphere), FP64, solved from
-LTE populations with the paper's stopping rule (Sect. 3.1). One step = one
-full solve: every F-class evaluation (opacity, formal solution, rates,
-assembly, preconditioner) and every Krylov/Newton update, on the device.
+Default workload (config 4): 4,096 independent Ca II-like columns of 64 to
+256 depths (about 1,000 frequencies, 5 mu per hemisphere), solved together in
+one persistent batch plan in the mixed precision mode, from LTE through a
+capped RH92 warm-up and Algorithm 2 to the paper's stopping rule (Sect. 3.1).
+One step = one batched solve of every column: every F-class evaluation
+(opacity, formal solution, rates, assembly, preconditioner) and every
+Krylov/Newton update, on the device.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload ca|two-level|h] [--precision fp64|mixed]
+                  [--workload batch|ca|two-level|h|serve] [--precision fp64|mixed]
 
 Metric: formal-solution ray-points/s (= F-class evaluations x N_nu x 2 N_mu x
-N_z per second); also converged columns/s and p50/p99 solve latency.
-N > 1 (torchrun): every rank solves its own column (weak scaling, no
+N_z per second, summed over columns); the line also carries converged
+columns/s, the FP64 one-column-per-launch path's columns/s on a sample of
+the same columns, and the error against the oracle on a sample. ``--workload
+ca`` is the FP64 single-column line (config 2), ``serve`` the continuous-
+batching stream (config 5, p50/p99 latency).
+N > 1 (torchrun): every rank solves its own columns (weak scaling, no
 collective on the data path); value = ray-points of all ranks / max time.
 ``--impl reference`` times the CPU oracle on the host cores instead.
 """
@@ -44,7 +50,7 @@ def parse():
                    help="timed steps (default: 40 single-column solves, 10 batched solves or oracle steps)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="ca", choices=["ca", "two-level", "h", "batch", "serve"])
+    p.add_argument("--workload", default="batch", choices=["batch", "ca", "two-level", "h", "serve"])
     p.add_argument("--columns", type=int, default=4096, help="batch workload: number of columns")
     p.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     p.add_argument("--rate", type=float, default=2000.0, help="serve workload: Poisson arrival rate [1/s]")
@@ -56,8 +62,8 @@ def parse():
     if args.steps is None:
         # a single-column solve takes tens of ms: 40 of them give the clock
         # sampler a timed region of about a second
-        single = args.impl == "ours" and args.workload in ("ca", "two-level", "h")
-        args.steps = 40 if single else 10
+        single = args.workload in ("ca", "two-level", "h")
+        args.steps = 40 if (single and args.impl == "ours") else 10
     return args
 
 
@@ -162,7 +168,8 @@ MIXED_DTYPE = "f32 formal solution / f32-pair S, J, rate sums / f64 assembly, Kr
 # ray-step coefficient header): a change to any of them voids its ncu traffic
 KERNEL_SOURCES = {
     "formal_fp64": ("formal_fused.cu", "formal_coef.cuh"),
-    "formal_fp32": ("formal_sweep.cu", "formal_coef.cuh", "dfloat.cuh"),
+    "formal_fp32_tan": ("formal_sweep.cu", "formal_coef.cuh", "dfloat.cuh"),
+    "formal_fp32_base": ("formal_sweep.cu", "formal_coef.cuh", "dfloat.cuh"),
 }
 
 
@@ -195,6 +202,21 @@ def measured_traffic(kernel_key):
     return e.get("bytes_per_ray_point")
 
 
+def host_cpu():
+    """CPU model and logical core count of this host (for the baseline's record)."""
+    fields = {}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields.setdefault(k.strip(), v.strip())
+    except Exception:
+        pass
+    model = fields.get("Model name") or fields.get("Vendor ID") or "unknown"
+    return model, os.cpu_count() or 1
+
+
 def cpu_baseline(wl, budget_s=20.0):
     """The oracle as it stands, on the host cores: a bounded sample of the same workload."""
     from oracle import model as OM
@@ -211,9 +233,64 @@ def cpu_baseline(wl, budget_s=20.0):
         jvp_complex(m, m.nstar, J0, v)
         evals += 1
     dt = time.perf_counter() - t0
+    model, ncpu = host_cpu()
     return {"value": evals * m.ray_points / dt, "unit": "ray-points/s", "cores": 1, "kind": "oracle",
+            "host_cores": ncpu, "cpu_model": model,
             "sample": f"{evals} oracle F-class evaluations (1 residual + {evals - 1} complex-step JVPs) "
-                      f"of the same column at LTE, {dt:.1f} s, numpy FP64/complex128 single thread"}
+                      f"of the same column at LTE, {dt:.1f} s, numpy FP64/complex128 single thread "
+                      f"(one column is one thread's work)"}
+
+
+def _oracle_column_solve(atom, col, n_mu, start):
+    """One column solved by the oracle with the batch's options (hybrid start,
+    paper stopping rule): populations, F-class evaluations, ray-points, seconds."""
+    from oracle import model as OM
+    from oracle.hybrid import hybrid
+    m = OM.build_model(atom, col, n_mu)
+    t0 = time.perf_counter()
+    r = hybrid(m, m.nstar, switch_tol=start["rh92_switch"], rh92_max=start["rh92_warmup"])
+    dt = time.perf_counter() - t0
+    return dict(n=r.n, converged=bool(r.converged), F_calls=int(r.F_calls),
+                ray_points=float(r.F_calls) * m.ray_points, seconds=dt)
+
+
+def _oracle_evals(atom, col, n_mu, k):
+    """k oracle F-class evaluations (1 residual + k - 1 complex-step JVPs) of one column at LTE."""
+    from oracle import model as OM
+    from oracle.residual import jvp_complex, residual
+    m = OM.build_model(atom, col, n_mu)
+    J0 = OM.initial_J(m)
+    rng = np.random.default_rng(0)
+    residual(m, m.nstar, J0)
+    for _ in range(k - 1):
+        jvp_complex(m, m.nstar, J0, rng.normal(size=m.nstar.shape) * m.nstar)
+    return k * m.ray_points
+
+
+def oracle_pool(workers):
+    """Process pool for the oracle: spawn-started (a child forked from a process
+    that holds a CUDA context can hang), one BLAS thread per worker."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    return ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
+def cpu_baseline_batch(wl, start, pool, futures, workers, t0):
+    """The oracle solving the first ``workers`` columns of the batch to
+    convergence, one column per host core (started before the GPU run; the
+    wall time counts from the pool's start)."""
+    res = [f.result() for f in futures]
+    wall = max(time.perf_counter() - t0, max(r["seconds"] for r in res))
+    model, ncpu = host_cpu()
+    pts = sum(r["ray_points"] for r in res)
+    conv = sum(r["converged"] for r in res)
+    return {"value": pts / wall, "unit": "ray-points/s", "cores": workers, "kind": "oracle",
+            "host_cores": ncpu, "cpu_model": model, "columns_per_s": conv / wall,
+            "sample": f"the first {len(res)} columns of the batch solved to the paper's stopping rule by the "
+                      f"oracle (hybrid start, complex-step JVPs, numpy FP64), one column per process, "
+                      f"{workers} processes in parallel, {wall:.1f} s wall; {conv} converged"}, res
 
 
 # Algorithmic work per ray-point (value / JVP evaluation): FP32-pipe
@@ -225,59 +302,102 @@ FORMAL_KERNELS = {0: "k_formal<double> + k_ray_sum (per-ray buffers)", 1: "k_for
                   2: "k_formal_sweep (thread per frequency)", 3: "k_formal_sweep_warp (warp per frequency pair)"}
 
 
-def alu_roofline(B, ctx, fp64, n_value, n_jvp, pts_per_launch, kern_ms, launches, clocks, kernel, device):
-    """Roofline of the formal-solution kernel against the ALU peak derived from
-    unit counts and the SM clock sampled during the run: per SM and clock 128
-    FP32 lanes and 16 MUFU operations (the mixed path is bound by the slower of
-    the two); FP64 at the nominal 1.25 TFLOP/s dense rate, with exp and the
-    reciprocal as software sequences whose FP64-pipe cost is measured
-    (jfnk_probe_alu). Achieved = ray-points per launch / mean launch time
-    (in-graph CUDA events around the formal kernels of every tick)."""
-    import torch
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    clk = mhz * 1e6
-    w_v, w_j = n_value / max(1, n_value + n_jvp), n_jvp / max(1, n_value + n_jvp)
+def measured_peaks(B, ctx):
+    """Pipe rates measured on this GPU by the library's probe kernels
+    (jfnk_probe_alu): FP32 and FP64 fused multiply-adds per second (lane
+    instructions) and MUFU exponentials per second."""
+    return {"fp32_fma_per_s": B.probe_alu(ctx, 1) / 2.0, "fp64_fma_per_s": B.probe_alu(ctx, 0) / 2.0,
+            "fp64_exp_per_s": B.probe_alu(ctx, 2), "mufu_per_s": B.probe_alu(ctx, 3)}
+
+
+def peak_rate(kind, fp64, peaks):
+    """Roofline ray-points/s of one evaluation kind ('value' or 'jvp') from the
+    algorithmic unit counts and the measured pipe rates: the mixed path is bound
+    by the slower of the FP32 lanes and the MUFU; in FP64 mode every operation
+    goes to the FP64 pipe, with exp and the reciprocal costed by the probe."""
+    ops, mufu = ALG_OPS[kind]
     if fp64:
-        fma = B.probe_alu(ctx, 0)                 # FP64 flop/s measured (FMA = 2)
-        c_exp = fma / B.probe_alu(ctx, 2)         # exp in FP64-pipe flops
-        fp_rate = 1.25e12 / 2                     # nominal FP64 FMA instructions/s
-        t = {m: (ops + mufu * c_exp / 2) / fp_rate for m, (ops, mufu) in ALG_OPS.items()}
-        src = "nominal FP64 1.25 TFLOP/s dense (FMA instr/s = half); exp/rcp cost from jfnk_probe_alu"
-    else:
-        fp_rate, mufu_rate = sms * 128 * clk, sms * 16 * clk
-        t = {m: max(ops / fp_rate, mufu / mufu_rate) for m, (ops, mufu) in ALG_OPS.items()}
-        src = f"{sms} SMs x (128 FP32 lanes, 16 MUFU) x {mhz:.0f} MHz sampled SM clock"
-    peak = 1.0 / (w_v * t["value"] + w_j * t["jvp"])          # ray-points/s
+        c_exp = peaks["fp64_fma_per_s"] / peaks["fp64_exp_per_s"]   # one exp in FMA-instruction time
+        return peaks["fp64_fma_per_s"] / (ops + mufu * c_exp)
+    return 1.0 / max(ops / peaks["fp32_fma_per_s"], mufu / peaks["mufu_per_s"])
+
+
+def kernel_roofline(name, kind, fp64, points, kern_ms, launches, peaks, traffic_key=None):
+    """One formal kernel: achieved = algorithmic ray-points of its launches /
+    their summed CUDA-event duration, against the roofline of its evaluation kind."""
+    peak = peak_rate(kind, fp64, peaks)
+    avg_s = kern_ms * 1e-3 / max(1, launches)
+    achieved = points / (kern_ms * 1e-3) if kern_ms > 0 else 0.0
+    tpp = measured_traffic(traffic_key) if traffic_key else None
+    return {"kernel": name, "kind": kind, "achieved": achieved / 1e9, "peak": peak / 1e9,
+            "frac": achieved / peak, "avg_launch_us": avg_s * 1e6, "launches": launches,
+            "ray_points_per_launch": points / max(1, launches),
+            "traffic": None if tpp is None else tpp * points / max(1, launches)}
+
+
+def peak_source(fp64, peaks):
+    if fp64:
+        return (f"measured FP64 FMA {peaks['fp64_fma_per_s'] * 2 / 1e12:.3f} TFLOP/s and FP64 exp "
+                f"{peaks['fp64_exp_per_s'] / 1e9:.1f} G/s (jfnk_probe_alu kinds 0, 2)")
+    return (f"measured FP32 FMA {peaks['fp32_fma_per_s'] * 2 / 1e12:.1f} TFLOP/s and MUFU exp "
+            f"{peaks['mufu_per_s'] / 1e12:.3f} T/s (jfnk_probe_alu kinds 1, 3) with unit counts "
+            f"value {ALG_OPS['value']}, jvp {ALG_OPS['jvp']} (FP32 ops, MUFU ops) per ray-point")
+
+
+def alu_roofline(B, ctx, fp64, n_value, n_jvp, pts_per_launch, kern_ms, launches, clocks, kernel, device):
+    """Roofline of the single-column formal-solution kernel (one launch per
+    tick, value and JVP evaluations mixed): achieved = ray-points per launch /
+    mean launch time (in-graph CUDA events around the formal kernel of every
+    tick), peak = the mix of the two kinds' rooflines at the measured rates."""
+    peaks = measured_peaks(B, ctx)
+    w_v, w_j = n_value / max(1, n_value + n_jvp), n_jvp / max(1, n_value + n_jvp)
+    peak = 1.0 / (w_v / peak_rate("value", fp64, peaks) + w_j / peak_rate("jvp", fp64, peaks))
     avg_s = kern_ms * 1e-3 / max(1, launches)
     achieved = pts_per_launch / avg_s if avg_s > 0 else 0.0
-    key = "formal_fp64" if fp64 else "formal_fp32"
-    traffic_pp = measured_traffic(key)
+    traffic_pp = measured_traffic("formal_fp64" if fp64 else "formal_fp32_tan")
     return {"bound": "alu", "kernel": FORMAL_KERNELS.get(kernel, str(kernel)),
             "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G ray-points/s",
             "frac": achieved / peak,
-            "traffic": None if traffic_pp is None else traffic_pp * pts_per_launch,
+            "traffic": None if traffic_pp is None or not fp64 else traffic_pp * pts_per_launch,
             "ops_per_ray_point": {"value": ALG_OPS["value"], "jvp": ALG_OPS["jvp"],
                                   "mix": {"value": w_v, "jvp": w_j}},
-            "avg_launch_us": avg_s * 1e6, "launches": launches, "peak_source": src}
+            "avg_launch_us": avg_s * 1e6, "launches": launches, "peak_source": peak_source(fp64, peaks),
+            "measured_peaks": peaks}
 
 
 def run_reference(args, rank, ws, dist):
+    """The oracle as it stands on the host cores (rank 0 only): each step is a
+    bounded sample of the workload's F-class evaluations. Batch workload: one
+    residual + one complex-step JVP of each of the batch's first P columns, one
+    column per process on P host cores; single-column workloads: one residual
+    + 3 JVPs of the column on one core."""
     if rank != 0:
         return
-    wl, prec = workload(args.workload)
-    from oracle import model as OM
-    from oracle.residual import jvp_complex, residual
-    m = OM.build_model(wl.atom, wl.columns[0], wl.n_mu)
-    J0 = OM.initial_J(m)
-    rng = np.random.default_rng(0)
+    model, ncpu = host_cpu()
+    if args.workload == "batch":
+        wl = W.config4(n_columns=args.columns, seed=rank_seed(20240624, 0))
+        workers = max(1, min(16, ncpu))
+        cols = wl.columns[:workers]
+        pool = oracle_pool(workers)
 
-    def step():
-        residual(m, m.nstar, J0)
-        for _ in range(3):
-            jvp_complex(m, m.nstar, J0, rng.normal(size=m.nstar.shape) * m.nstar)
-        return 4 * m.ray_points
+        def step():
+            return sum(f.result() for f in [pool.submit(_oracle_evals, wl.atom, c, wl.n_mu, 2) for c in cols])
 
+        cores, sample = workers, (f"per step: 1 residual + 1 complex-step JVP of each of the batch's first "
+                                  f"{workers} columns at LTE, one column per process on {workers} cores")
+        from oracle import model as OM
+        cfg = batch_config(wl.columns, OM.build_model(wl.atom, cols[0], wl.n_mu).nq, "FP64 oracle")
+    else:
+        wl, prec = workload(args.workload)
+        from oracle import model as OM
+        m = OM.build_model(wl.atom, wl.columns[0], wl.n_mu)
+        pool = None
+
+        def step():
+            return _oracle_evals(wl.atom, wl.columns[0], wl.n_mu, 4)
+
+        cores, sample = 1, "per step: 1 residual + 3 complex-step JVPs of the column at LTE"
+        cfg = workload_config(wl, (m.nq, m.nz, m.nmu), "fp64 oracle")
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
@@ -285,14 +405,15 @@ def run_reference(args, rank, ws, dist):
     for _ in range(args.steps):
         pts += step()
     dt = time.perf_counter() - t0
+    if pool is not None:
+        pool.shutdown()
     value = pts / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ray-points/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl, (m.nq, m.nz, m.nmu), "fp64 oracle"),
-            "cpu_baseline": {"value": value, "unit": "ray-points/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: 1 residual + 3 complex-step JVPs of the column at LTE"},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "ray-points/s", "cores": cores, "kind": "oracle",
+                             "host_cores": ncpu, "cpu_model": model, "sample": sample},
             "e2e": {"value": value, "unit": "ray-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -328,7 +449,7 @@ def run_ours(args, rank, ws, local, dist):
         B.check(rc, "jfnk_solve")
         return st.as_dict()
 
-    o = opts()
+    o = opts(profile=0)
     for _ in range(args.warmup):
         flush.zero_()
         solve_device(o)
@@ -356,6 +477,10 @@ def run_ours(args, rank, ws, local, dist):
         dist.barrier()
     total_ms = float(sum(times))
     pts = float(sum(s["ray_points"] for s in stats))
+    # roofline: a separate profiled solve (in-graph CUDA events around the
+    # formal kernel of every tick), outside the timed region
+    flush.zero_()
+    prof = solve_device(opts(profile=1))
     # e2e: host buffers through the public API (pinned in / out), wall clock
     n_host = torch.from_numpy(atm.lte().ravel().copy()).pin_memory()
     n_out = torch.empty_like(n_host).pin_memory()
@@ -363,7 +488,7 @@ def run_ours(args, rank, ws, local, dist):
     oe = opts(profile=0)
     oe.init = B.JFNK_INIT_USER
     st2 = B.jfnk_stats()
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(max(1, min(10, args.steps // 2))):
         flush.zero_()
         torch.cuda.synchronize()
         n_out.copy_(n_host)
@@ -381,15 +506,14 @@ def run_ours(args, rank, ws, local, dist):
     lat = np.array(times)
     cols_per_s = ws * args.steps / (total_ms * 1e-3)
     s0 = stats[-1]
-    # roofline of the formal-solution kernel (dominant)
-    launches = sum(s["formal_launches"] for s in stats)
-    kern_ms = sum(s["formal_ms"] for s in stats)
+    # roofline of the formal-solution kernel (dominant), from the profiled solve
+    launches = prof["formal_launches"]
+    kern_ms = prof["formal_ms"] + prof["formal_tan_ms"]
     fp64 = precision == B.JFNK_FP64
-    n_jvp = sum(s["jvp_calls"] for s in stats)
-    n_all = sum(s["F_calls"] for s in stats)
-    roofline = alu_roofline(B, ctx, fp64, n_all - n_jvp, n_jvp, atm.ray_points, kern_ms, launches,
-                            clocks, s0["formal_kernel"], local)
-    roofline["share_of_step"] = kern_ms / total_ms
+    roofline = alu_roofline(B, ctx, fp64, prof["F_calls"] - prof["jvp_calls"], prof["jvp_calls"],
+                            atm.ray_points, kern_ms, launches, clocks, prof["formal_kernel"], local)
+    roofline["share_of_step"] = kern_ms / (total_ms / args.steps)
+    roofline["timed_in"] = "a separate profiled solve (in-graph events around the formal kernel of every tick)"
     gpu_launches = int(sum(s["kernel_launches"] for s in stats))
     line = {"metric": METRIC, "value": value, "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -413,12 +537,38 @@ def run_ours(args, rank, ws, local, dist):
     print(json.dumps(line), flush=True)
 
 
+def batch_config(columns, nq, precision):
+    nz = [c.n_depth for c in columns]
+    return {"workload": f"batched 1.5D: {len(columns)} Ca II-like columns, depths {min(nz)}-{max(nz)}, "
+                        f"{nq} frequencies, 5 mu, T noise 5 %, {precision}, one batched solve per step",
+            "columns": len(columns), "init": "LTE, then <= 5 limited RH92 iterations (switch below 0.1 "
+                                             "change), then JFNK to the paper's stopping rule",
+            "rtol": 1e-2, "ftol": 1e-4, "fdrop": 1e-2,
+            "l2": "flushed by a 256 MiB device write before every timed step (the batch's tables and "
+                  "work buffers are also far larger than L2)"}
+
+
+BATCH_START = dict(rh92_warmup=5, rh92_switch=0.1)
+
+
 def run_batch(args, rank, ws, local, dist):
-    """Batched 1.5D workload: every column of the batch solved together (mixed precision),
-    against the plain FP64 path that solves one column per launch sequence."""
+    """Batched 1.5D workload (config 4): every column of the batch solved
+    together in one persistent batch plan (mixed precision), against the plain
+    FP64 path that solves one column per launch sequence, with the oracle on
+    the host cores beside it."""
+    import ctypes as C
     import torch
     from paper_2406_17234_gb300 import binding as B
     wl = W.config4(n_columns=args.columns, seed=rank_seed(20240624, rank))
+    # the oracle's sample solves start first and run on the host cores while the GPU works
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        workers = max(1, min(16, os.cpu_count() or 1))
+        pool = oracle_pool(workers)
+        t_cpu0 = time.perf_counter()
+        futs = [pool.submit(_oracle_column_solve, wl.atom, c, wl.n_mu, BATCH_START)
+                for c in wl.columns[:workers]]
+        cpu = (pool, futs, workers, t_cpu0)
     torch.cuda.set_device(local)
     ctx = B.Context(local)
     atom = B.Atom(ctx, wl.atom)
@@ -428,10 +578,7 @@ def run_batch(args, rank, ws, local, dist):
     setup_s = time.perf_counter() - t0
     plan = B.BatchPlan(ctx, atms, precision=B.JFNK_MIXED)
     free1, _ = torch.cuda.mem_get_info()
-    # hybrid start (Sect. 5): at most 5 per-depth limited RH92 iterations,
-    # fewer once the population change is below 0.1, then Algorithm 2
-    start = dict(rh92_warmup=5, rh92_switch=0.1)
-    opts = B.default_options(precision=B.JFNK_MIXED, profile=1, **start)
+    opts = B.default_options(precision=B.JFNK_MIXED, profile=0, **BATCH_START)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -440,6 +587,7 @@ def run_batch(args, rank, ws, local, dist):
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
+    torch.cuda.synchronize()
     clk = clocks_start() if rank == 0 else None
     times, allstats = [], []
     torch.cuda.nvtx.range_push("timed")
@@ -454,54 +602,106 @@ def run_batch(args, rank, ws, local, dist):
         times.append(e0.elapsed_time(e1))
         allstats.append(st)
     torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
     clocks = clocks_stop(clk, local) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    n_gpu = [n.copy() for n in plan.ns]
     total_ms = float(sum(times))
     pts = float(sum(s["ray_points"] for st in allstats for s in st))
     conv = sum(1 for st in allstats for s in st if s["status"] == 0)
+    # profiled pass (untimed): in-graph CUDA events around the two sweep
+    # launches of every tick, on the streams they run on
+    _, pst = plan.run(B.default_options(precision=B.JFNK_MIXED, profile=1, **BATCH_START), raise_on_fail=False)
+    rp = [a.ray_points for a in atms]
+    jvp_pts = float(sum(s["jvp_calls"] * r for s, r in zip(pst, rp)))
+    val_pts = float(sum((s["F_calls"] - s["jvp_calls"]) * r for s, r in zip(pst, rp)))
+    # e2e: jfnk_batch_run with pinned host buffers (populations in, populations out)
+    Ns = [a.n_depth * a.n_levels for a in atms]
+    offs = np.concatenate([[0], np.cumsum(Ns)])
+    h_in = torch.from_numpy(np.concatenate([a.lte().ravel() for a in atms])).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    nps = (C.c_void_p * len(atms))(*[h_out.data_ptr() + 8 * int(o) for o in offs[:-1]])
+    oe = B.default_options(precision=B.JFNK_MIXED, profile=0, **BATCH_START)
+    oe.init = B.JFNK_INIT_USER
+    st_e2e = (B.jfnk_stats * len(atms))()
+    e2e_times, e2e_pts = [], 0.0
+    for _ in range(min(3, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        h_out.copy_(h_in)
+        ta = time.perf_counter()
+        rc = ctx.lib.jfnk_batch_run(plan.h, C.byref(oe), nps, None, st_e2e, B.JFNK_MEM_HOST, None)
+        e2e_times.append(time.perf_counter() - ta)
+        if rc in (B.JFNK_E_INVALID, B.JFNK_E_CUDA, B.JFNK_E_NOMEM):
+            B.check(rc, "jfnk_batch_run (host buffers)")
+        e2e_pts += sum(s.ray_points for s in st_e2e)
     # plain FP64 path: one column per launch sequence, a sample of the same columns
     nsample = min(8, len(atms))
     fp64_t = []
     for a in atms[:nsample]:
-        B.solve(a, B.default_options(**start), raise_on_fail=False)        # warm (allocation, tuning)
+        B.solve(a, B.default_options(**BATCH_START), raise_on_fail=False)        # warm (allocation, tuning)
         flush.zero_()
         torch.cuda.synchronize()
         ta = time.perf_counter()
-        _, _, s1 = B.solve(a, B.default_options(**start), raise_on_fail=False)
+        _, _, s1 = B.solve(a, B.default_options(**BATCH_START), raise_on_fail=False)
         fp64_t.append(time.perf_counter() - ta)
     fp64_cols_s = nsample / sum(fp64_t)
-    mx, sm = reduce_ranks(dist, [total_ms, pts, conv])
-    total_ms, pts, conv = mx[0], sm[1], sm[2]
+    mx, sm = reduce_ranks(dist, [total_ms, pts, conv, sum(e2e_times), e2e_pts])
+    total_ms, pts, conv, e2e_s, e2e_pts = mx[0], sm[1], sm[2], mx[3], sm[4]
     if rank != 0:
         return
+    peaks = measured_peaks(B, ctx)
+    tan_ms = float(sum(s["formal_tan_ms"] for s in pst[:1]))
+    base_ms = float(sum(s["formal_ms"] for s in pst[:1]))
+    launches = int(pst[0]["formal_launches"])
+    kern = {"tangent": kernel_roofline("k_formal_sweep (tangent, JVP evaluations)", "jvp", False, jvp_pts,
+                                       tan_ms, launches, peaks, "formal_fp32_tan"),
+            "base": kernel_roofline("k_formal_sweep (base and RH92 evaluations)", "value", False, val_pts,
+                                    base_ms, launches, peaks, "formal_fp32_base")}
+    dom = max(kern.values(), key=lambda k: k["avg_launch_us"])
+    prof_total = sum(s for s in [tan_ms, base_ms])
+    roofline = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": "G ray-points/s", "frac": dom["frac"], "traffic": dom["traffic"],
+                "avg_launch_us": dom["avg_launch_us"], "launches": dom["launches"],
+                "peak_source": peak_source(False, peaks), "kernels": kern,
+                "both_sweeps": {"achieved": (jvp_pts + val_pts) / (prof_total * 1e-3) / 1e9,
+                                "frac": (jvp_pts + val_pts) / (prof_total * 1e-3) /
+                                        (1.0 / ((val_pts / peak_rate("value", False, peaks) +
+                                                 jvp_pts / peak_rate("jvp", False, peaks)) /
+                                                (jvp_pts + val_pts)))},
+                "measured_peaks": peaks, "timed_in": "a separate profiled batched solve (in-graph events)"}
     st0 = allstats[-1]
-    launches = sum(s["formal_launches"] for s in st0[:1]) * args.steps
-    kern_ms = sum(st[0]["formal_ms"] for st in allstats)
-    n_jvp = sum(s["jvp_calls"] for st in allstats for s in st)
-    n_all = sum(s["F_calls"] for st in allstats for s in st)
-    roofline = alu_roofline(B, ctx, False, n_all - n_jvp, n_jvp, pts / max(1, launches), kern_ms, launches,
-                            clocks, st0[0]["formal_kernel"], local)
-    roofline["share_of_step"] = kern_ms / total_ms
-    nz = [a.n_depth for a in atms]
     line = {"metric": METRIC, "value": pts / (total_ms * 1e-3), "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": MIXED_DTYPE, "data": "synthetic",
-            "config": {"workload": f"batched 1.5D: {len(atms)} Ca II-like columns, depths "
-                                   f"{min(nz)}-{max(nz)}, {atms[0].n_nu} frequencies, 5 mu, T noise 5 %, "
-                                   "mixed precision, one batched solve per step",
-                       "columns": len(atms), "init": "LTE, then <= 5 limited RH92 iterations (switch below 0.1 change), then JFNK",
-                       "l2": "flushed by a 256 MiB device write before every timed step"},
+            "config": batch_config(wl.columns, atms[0].n_nu, "mixed precision"),
             "columns_per_s": conv / (total_ms * 1e-3),
             "converged_fraction": conv / (len(atms) * args.steps * ws),
             "fp64_one_column_per_launch_columns_per_s": fp64_cols_s,
             "speedup_vs_fp64_per_column": (conv / (total_ms * 1e-3)) / (fp64_cols_s * ws),
-            "formal_kernel": {"avg_launch_ms": kern_ms / max(1, launches), "launches": launches,
-                              "share_of_step": kern_ms / total_ms, "qb": st0[0]["formal_qb"],
-                              "threads": st0[0]["formal_threads"]},
-            "max_ticks": max(s["F_calls"] for s in st0), "setup_s": setup_s,
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+            "solve": {"F_calls_max": max(s["F_calls"] for s in st0),
+                      "F_calls_median": float(np.median([s["F_calls"] for s in st0])),
+                      "F_norm_drop_max": max(s["F_norm"] / s["F_norm0"] for s in st0 if s["F_norm0"] > 0)},
+            "setup_s": setup_s,
             "device_memory_gb": {"tables_and_batch": (free0 - free1) / 1e9, "device_total": total_mem / 1e9},
-            "roofline": roofline, "gpu_launches": int(st0[0]["kernel_launches"]) * args.steps,
+            "roofline": roofline,
+            "e2e": {"value": e2e_pts / e2e_s, "unit": "ray-points/s",
+                    "h2d_bytes_per_step": int(offs[-1]) * 8, "d2h_bytes_per_step": int(offs[-1]) * 8,
+                    "steps": len(e2e_times), "call": "jfnk_batch_run with pinned host populations in and out"},
+            "gpu_launches": int(st0[0]["kernel_launches"]) * args.steps,
             "clocks": clocks}
+    if cpu is not None:
+        pool, futs, workers, t_cpu0 = cpu
+        cb, res = cpu_baseline_batch(wl, BATCH_START, pool, futs, workers, t_cpu0)
+        pool.shutdown()
+        line["cpu_baseline"] = cb
+        errs = [float(np.max(np.abs(n_gpu[c] / r["n"] - 1.0))) for c, r in enumerate(res) if r["converged"]]
+        line["oracle_error"] = {"max_rel": max(errs), "columns": len(errs),
+                                "what": "GPU mixed batch vs FP64 oracle, both solved to the paper's stopping "
+                                        "rule, populations of the sampled columns (max over elements)"}
     print(json.dumps(line), flush=True)
 
 

@@ -191,12 +191,15 @@ typedef struct {
   double F_norm0;       /* ||F||_inf at the first JFNK base point                   */
   double dn_norm;       /* last population change                                  */
   double ray_points;    /* formal-solution ray-points evaluated (F_calls x rays)   */
-  double formal_ms;     /* profile: summed duration of the formal-solution kernel  */
+  double formal_ms;     /* profile: summed duration of the formal-solution kernel
+                           (mixed mode: of the base-type sweep launches)           */
   int formal_launches;  /* profile: number of timed launches (active ticks)        */
   int kernel_launches;  /* CUDA kernels launched by the solve (graph nodes included) */
   int formal_qb;        /* fused kernel: frequencies per block (0 for the others)   */
   int formal_threads;   /* threads per block (warps per block: JFNK_FORMAL_SWEEP_WARP) */
   int formal_kernel;    /* jfnk_formal_kernel that ran the formal solution          */
+  double formal_tan_ms; /* profile, mixed mode: summed duration of the tangent-sweep
+                           launches (the JVP evaluations' formal solutions)       */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -309,9 +312,12 @@ int jfnk_batch_destroy(jfnk_batch* b);
  * A column whose buffers exceed the array (roughly nq * nz * (8 n_mu + 9) * 8
  * bytes) is rejected with JFNK_E_INVALID and a message giving the size needed.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. Every call shares
+ * device); make that first call before any stream capture (a first call on a
+ * stream that is being captured returns JFNK_E_INVALID). Every call shares
  * the array: calls that overlap on the GPU race and must be serialised by the
- * caller. */
+ * caller. The enqueued kernels read the atmosphere's tables: synchronise
+ * ``stream`` before destroying the atmosphere (jfnk_destroy_atmosphere returns
+ * the tables to a pool on another stream, not ordered after this one). */
 #define JFNK_STATIC_SCRATCH_BYTES (32u << 20)
 int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const double* n,
                          const double* J_dagger, double* F, double* J_new, void* stream);

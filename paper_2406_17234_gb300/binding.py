@@ -82,7 +82,8 @@ class jfnk_stats(C.Structure):
                 ("F_calls", C.c_int), ("jvp_calls", C.c_int), ("F_norm", C.c_double),
                 ("F_norm0", C.c_double), ("dn_norm", C.c_double), ("ray_points", C.c_double),
                 ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int),
-                ("formal_qb", C.c_int), ("formal_threads", C.c_int), ("formal_kernel", C.c_int)]
+                ("formal_qb", C.c_int), ("formal_threads", C.c_int), ("formal_kernel", C.c_int),
+                ("formal_tan_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

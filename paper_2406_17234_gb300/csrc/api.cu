@@ -208,6 +208,7 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   int rc = ensure_graph(b, s, profile);
   if (rc) return rc;
   b->tick_ms.clear();
+  b->tick_tan_ms.clear();
   b->replays = 0;
   b->compactions = 0;
   // the full view, restored before returning
@@ -226,13 +227,14 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
     if (cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) { rc = fail(JFNK_E_CUDA, "status poll failed"); break; }
     if (profile) {
-      // the formal kernels' own durations (summed when the two sweeps overlap)
+      // the formal kernels' own durations (base-type and tangent sweeps apart)
       const int ne = tick_events(*b);
       for (int t = 0; t < b->graph_ticks; ++t) {
         float ms = 0.f, ms2 = 0.f;
         cudaEventElapsedTime(&ms, b->tick_ev[(size_t)ne * t], b->tick_ev[(size_t)ne * t + 1]);
         if (ne == 4) cudaEventElapsedTime(&ms2, b->tick_ev[(size_t)ne * t + 2], b->tick_ev[(size_t)ne * t + 3]);
-        b->tick_ms.push_back(ms + ms2);
+        b->tick_ms.push_back(ms);
+        b->tick_tan_ms.push_back(ms2);
       }
     }
     std::vector<int> running;
@@ -384,8 +386,9 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
   int active = 0;
   for (int c = 0; c < b->ncols; ++c) active = std::max(active, st[c].ticks);
   active = std::min(active, (int)b->tick_ms.size());
-  double kernel_ms = 0.0;
+  double kernel_ms = 0.0, tan_ms = 0.0;
   for (int t = 0; t < active; ++t) kernel_ms += b->tick_ms[t];
+  for (int t = 0; t < active && t < (int)b->tick_tan_ms.size(); ++t) tan_ms += b->tick_tan_ms[t];
   for (int c = 0; c < b->ncols; ++c) {
     const SolverState& x = st[c];
     int status = x.status == 1 ? JFNK_E_TIMEOUT : x.status;
@@ -401,6 +404,7 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.dn_norm = x.err;
       S.ray_points = (double)x.F_calls * cols[c]->d.ray_points;
       S.formal_ms = kernel_ms;
+      S.formal_tan_ms = tan_ms;
       S.formal_launches = active;
       S.kernel_launches = (int)(b->replays * b->graph_kernels) + 2;   // + state init, mode reset
       S.formal_qb = b->formal_kind == FORMAL_FUSED ? b->formal_qb : 0;

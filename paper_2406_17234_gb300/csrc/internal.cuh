@@ -130,7 +130,8 @@ struct Batch {
   // base kernels of the other columns, and join before the assembly
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-  std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve
+  std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve (base-type sweep)
+  std::vector<float> tick_tan_ms;     // per-tick tangent-sweep durations (mixed mode)
   int* h_status = nullptr;            // pinned host mirror of d_status
   // launch view over the columns still running (straggler compaction)
   ColDesc* d_view = nullptr;          // device array [ncols] of the view's descriptors

@@ -29,10 +29,20 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 static char* g_static_addr[256] = {nullptr};
 static std::mutex g_static_mu;
 
-static int static_scratch(int device, char** out) {
+static int static_scratch(int device, cudaStream_t s, char** out) {
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (device < 0 || device >= 256) return fail(JFNK_E_INVALID, "device index out of range");
   if (!g_static_addr[device]) {
+    // the one-time lookup may load the module on this device: refuse it in
+    // the middle of a stream capture rather than disturb the capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess)
+      return fail(JFNK_E_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(JFNK_E_INVALID,
+                  "the first jfnk_residual_static call on a device must not be made while its stream is "
+                  "being captured (it looks up the static scratch's device address once)");
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess)
@@ -89,10 +99,10 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
                 "column too large for the static scratch of jfnk_residual_static (needs " +
                     std::to_string(L.cursor) + " bytes, limit " +
                     std::to_string(kStaticScratchBytes) + "); use jfnk_residual");
-  char* base = nullptr;
-  int rc = static_scratch(ctx->device, &base);
-  if (rc) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* base = nullptr;
+  int rc = static_scratch(ctx->device, s, &base);
+  if (rc) return rc;
 
   ColDesc cd{};
   cd.t = M.tables;

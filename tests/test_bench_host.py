@@ -27,6 +27,25 @@ def test_traffic_is_reported_only_for_the_profiled_code():
     b = _bench()
     d = json.load(open(os.path.join(ROOT, "profiles", "formal_traffic.json")))
     for key in b.KERNEL_SOURCES:
+        if key not in d:                      # never captured: no traffic figure
+            assert b.measured_traffic(key) is None
+            continue
         expect = d[key]["bytes_per_ray_point"] if d[key]["source_hash"] == b.source_hash(key) else None
         assert b.measured_traffic(key) == expect
         assert d[key]["bytes_per_ray_point"] > 0
+
+
+def test_roofline_peaks_from_measured_rates():
+    """The roofline of each evaluation kind follows the unit counts and the
+    measured pipe rates: FP32-bound for the JVP, MUFU-bound for the value
+    evaluation at 128 FP32 lanes against 16 MUFU per clock; FP64 with exp
+    costed in FMA-instruction time."""
+    b = _bench()
+    sm_clk = 152 * 2.07e9
+    peaks = {"fp32_fma_per_s": 128 * sm_clk, "mufu_per_s": 16 * sm_clk,
+             "fp64_fma_per_s": 1e12, "fp64_exp_per_s": 1e11}
+    assert abs(b.peak_rate("jvp", False, peaks) / (sm_clk * 128 / 26) - 1) < 1e-12
+    assert abs(b.peak_rate("value", False, peaks) / (sm_clk * 16 / 2) - 1) < 1e-12
+    assert abs(b.peak_rate("value", True, peaks) / (1e12 / (10 + 2 * 10)) - 1) < 1e-12
+    r = b.kernel_roofline("k", "jvp", False, 1e9, 2.0, 4, peaks)
+    assert abs(r["achieved"] - 1e9 / 2e-3 / 1e9) < 1e-9 and abs(r["avg_launch_us"] - 500.0) < 1e-9
