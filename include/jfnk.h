@@ -172,7 +172,10 @@ typedef struct {
   int rh92_warmup;      /* > 0: hybrid start, at most this many RH92 iterations    */
   double rh92_switch;   /* switch to JFNK when the RH92 change is below (1e-2)     */
   int max_ticks;        /* F-class evaluations allowed per column (20000)          */
-  int profile;          /* 1: time the formal-solution kernel of every active tick */
+  int profile;          /* 1: time the formal-solution kernel of every active tick
+                           (mixed mode: the tangent and base-type sweeps then run
+                           one after the other instead of side by side, so that
+                           each is timed alone; the results are the same)       */
   int formal_variant;   /* mixed mode: 0 autotuned, JFNK_FORMAL_SWEEP_THREAD or
                            JFNK_FORMAL_SWEEP_WARP forced (identical results)      */
   int precond;          /* 1: block-Jacobi, first solution of Sect. 2.5.2 (default);
@@ -382,7 +385,7 @@ int jfnk_server_destroy(jfnk_server* sv);
 /* ---- measurement ----------------------------------------------------------- */
 /* Throughput probe of one arithmetic pipe on the context's device, for roofline
  * denominators: kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add,
- * 2 = FP64 exp(), 3 = FP32 __expf (MUFU). Runs a fixed dependent-chain workload
+ * 2 = FP64 exp(), 3 = MUFU base-2 exponential (ex2.approx.ftz.f32). Runs a fixed dependent-chain workload
  * over every SM and returns operations per second (an FMA counts as 2 flops;
  * an exp as 1 operation). */
 int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s);

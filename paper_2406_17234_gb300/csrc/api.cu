@@ -162,7 +162,9 @@ int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out) 
   int rc = JFNK_OK;
   for (int t = 0; t < kTicksPerGraph && !rc; ++t) {
     cudaEvent_t* ev = profile ? &b->tick_ev[(size_t)ne * t] : nullptr;
-    rc = launch_evaluation(*b, s, ev ? ev[0] : nullptr, ev ? ev[1] : nullptr, b->side,
+    // a profiled tick runs the tangent and base-type chains one after the
+    // other on s (no side stream), so that each sweep's events time it alone
+    rc = launch_evaluation(*b, s, ev ? ev[0] : nullptr, ev ? ev[1] : nullptr, profile ? nullptr : b->side,
                            ev && ne == 4 ? ev[2] : nullptr, ev && ne == 4 ? ev[3] : nullptr);
     if (!rc) rc = launch_krylov_step(*b, s);   // P^k was factorised by the assembly
   }

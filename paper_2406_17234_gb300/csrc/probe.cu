@@ -36,13 +36,21 @@ __global__ void k_probe_exp64(double* out) {
   if (s == 12345.678) out[0] = s;
 }
 
+// MUFU throughput: dependent chains of the hardware base-2 exponential, issued
+// as inline PTX so that the compiler can neither fold nor merge them.
+__device__ __forceinline__ float ex2_mufu(float x) {
+  float y;
+  asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __global__ void k_probe_exp32(float* out) {
   float x[kChains];
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) x[c] = -1e-3f * (threadIdx.x + c);
+  for (int c = 0; c < kChains; ++c) x[c] = 1e-3f * (threadIdx.x + c);
   for (int it = 0; it < kIters; ++it) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = -__expf(x[c]);
+    for (int c = 0; c < kChains; ++c) x[c] = ex2_mufu(-x[c]);   // stays in [1/2, 1)
   }
   float s = 0;
 #pragma unroll

@@ -980,13 +980,23 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     return JFNK_OK;
   }
   if (b.formal_kind == FORMAL_SWEEP) {
-    // (float tangent direction,) opacity, then the per-frequency sweeps
+    // (float tangent direction,) opacity, then the per-frequency sweeps; with
+    // events (a profiled tick) the tangent sweep is bracketed by ev2/ev3 and
+    // the base-type sweep by ev0/ev1, each timed alone on this one stream
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
     int rc0 = launch_opacity_mixed(b, s, 0);
     if (rc0) return rc0;
-    if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
-    int rc = launch_formal_sweep(b, s);
-    if (rc) return rc;
+    int rc;
+    if (ev2) {
+      JFNK_CUDA(cudaEventRecordWithFlags(ev2, s, cudaEventRecordExternal));
+      if ((rc = launch_formal_sweep(b, s, 2))) return rc;
+      if (ev3) JFNK_CUDA(cudaEventRecordWithFlags(ev3, s, cudaEventRecordExternal));
+      if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+      if ((rc = launch_formal_sweep(b, s, 1))) return rc;
+    } else {
+      if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+      if ((rc = launch_formal_sweep(b, s))) return rc;
+    }
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   } else if (b.formal_kind == FORMAL_FUSED) {
     // opacity, then the fused formal solution with in-block ray sums

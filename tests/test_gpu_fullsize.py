@@ -123,7 +123,10 @@ def test_fullsize_residual_and_jvp(ctx, wls, cfg, precision):
     r = ora_residual(m, n, Jd)
     gross = _gross(m, n, r.R_up, r.R_dn)
     bar = 1e-10 if precision == 0 else 1e-4
-    assert np.all(np.abs(F - r.F) <= bar * gross + 1e-12 * np.abs(r.F))
+    excess = np.abs(F - r.F) / (bar * gross + 1e-12 * np.abs(r.F))
+    k, l = np.unravel_index(int(np.argmax(excess)), excess.shape)
+    assert excess[k, l] <= 1.0, (f"depth {k} level {l}: F {F[k, l]:.6e} oracle {r.F[k, l]:.6e} "
+                                 f"gross {gross[k, l]:.3e} istar {r.istar[k]} n {n[k].tolist()}")
     k = np.arange(m.nz)
     np.testing.assert_allclose(F[k, r.istar], r.F[k, r.istar], rtol=1e-13)
     np.testing.assert_allclose(Jn, r.J, rtol=bar, atol=(1e-14 if precision == 0 else 1e-9) * np.max(r.J))
