@@ -50,7 +50,7 @@ def parse():
                    help="timed steps (default: 40 single-column solves, 10 batched solves or oracle steps)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="batch", choices=["batch", "ca", "two-level", "h", "serve"])
+    p.add_argument("--workload", default="batch", choices=["batch", "ca", "two-level", "h", "serve", "rtol"])
     p.add_argument("--columns", type=int, default=4096, help="batch workload: number of columns")
     p.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     p.add_argument("--rate", type=float, default=2000.0, help="serve workload: Poisson arrival rate [1/s]")
@@ -705,6 +705,80 @@ def run_batch(args, rank, ws, local, dist):
     print(json.dumps(line), flush=True)
 
 
+RTOLS = (1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1)
+
+
+def run_rtol(args, rank, ws, local, dist):
+    """The experiment of Sect. 2.3 / Fig. 5 and Sect. 3.3 on the synthetic
+    columns: formal solutions (F-class evaluations) to the paper's stopping
+    rule for JFNK with GMRES and with BiCGSTAB over a range of Krylov
+    tolerances r_tol, and for the reference method alone (RH92 iterations
+    until the population change is below the same 1e-4), one column per solve
+    on the GPU. Config 2 (Ca II-like, FP64, from LTE) and config 3 (H I-like,
+    mixed, JFNK after the hybrid RH92 start). Accuracy reached = max relative
+    difference from the same column solved far past the stopping rule
+    (FP64, r_tol 1e-6, ftol 1e-10)."""
+    import torch
+    from paper_2406_17234_gb300 import binding as B
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    ctx = B.Context(local)
+    cases = [("config 2 (Ca II-like, 82 depths, FP64, from LTE)", W.config2(), B.JFNK_FP64, {}),
+             ("config 3 (H I-like, 82 depths, mixed, hybrid start)", W.config3(), B.JFNK_MIXED,
+              dict(rh92_warmup=60, rh92_switch=0.03))]
+    out, headline, total_ms = {}, None, 0.0
+
+    def timed_solve(atm, o):
+        B.solve(atm, o, raise_on_fail=False)              # warm: buffers, tuning, graphs
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n, _, st = B.solve(atm, o, raise_on_fail=False)
+        e1.record()
+        e1.synchronize()
+        return n, st, e0.elapsed_time(e1)
+
+    for name, wl, prec, start in cases:
+        atom = B.Atom(ctx, wl.atom)
+        atm = B.Atmosphere(ctx, atom, wl.columns[0], n_mu=wl.n_mu)
+        ref, _, sref = B.solve(atm, B.default_options(rtol=1e-6, ftol=1e-10, **start))
+        rows = {}
+        for kname, kr in (("gmres", B.JFNK_KRYLOV_GMRES), ("bicgstab", B.JFNK_KRYLOV_BICGSTAB)):
+            for rt in RTOLS:
+                n, st, ms = timed_solve(atm, B.default_options(precision=prec, rtol=rt, krylov=kr, **start))
+                total_ms += ms
+                rows.setdefault(kname, {})[f"{rt:g}"] = {
+                    "F_calls": st["F_calls"], "jvp_calls": st["jvp_calls"], "newton_iters": st["newton_iters"],
+                    "rh92_iters": st["rh92_iters"], "status": st["status"], "ms": ms,
+                    "F_norm_drop": st["F_norm"] / st["F_norm0"] if st["F_norm0"] > 0 else None,
+                    "max_rel_err": float(np.max(np.abs(n / ref - 1.0)))}
+        for key, pr in (("rh92", prec), ("rh92_fp64", B.JFNK_FP64)):
+            if key == "rh92_fp64" and prec == B.JFNK_FP64:
+                continue
+            n, st, ms = timed_solve(atm, B.default_options(precision=pr, solver=B.JFNK_SOLVER_RH92, maxiter=5000))
+            total_ms += ms
+            rows[key] = {"F_calls": st["F_calls"], "status": st["status"], "ms": ms,
+                         "F_norm_drop": st["F_norm"] / st["F_norm0"] if st["F_norm0"] > 0 else None,
+                         "max_rel_err": float(np.max(np.abs(n / ref - 1.0)))}
+        best = min((v["F_calls"], k, rt) for k in ("gmres", "bicgstab") for rt, v in rows[k].items()
+                   if v["status"] == 0)
+        rows["summary"] = {"best_jfnk": {"krylov": best[1], "rtol": float(best[2]), "F_calls": best[0]},
+                           "rh92_over_best_jfnk_F_calls": rows["rh92"]["F_calls"] / best[0],
+                           "reference_F_calls": sref["F_calls"]}
+        out[name] = rows
+        if headline is None:
+            headline = rows["gmres"]["0.01"]["F_calls"]
+    line = {"metric": "formal solutions to the paper's stopping rule (JFNK-GMRES, r_tol 1e-2, config 2)",
+            "value": headline, "unit": "F-class evaluations", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": total_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (config 2) / " + MIXED_DTYPE + " (config 3)", "data": "synthetic",
+            "config": {"workload": "r_tol sweep: JFNK-GMRES, JFNK-BiCGSTAB and RH92 alone, configs 2 and 3",
+                       "rtol": list(RTOLS), "stopping": "1/2 ||dn/n||_inf < 1e-4 (and ||F|| drop 1e-2 for JFNK)"},
+            "sweep": out}
+    print(json.dumps(line), flush=True)
+
+
 def serve_options(atom):
     """Start options per atom kind of the serving stream: the H I-like columns
     need a longer RH92 warm-up (Sect. 3.5 hybrid) than the others."""
@@ -800,6 +874,16 @@ def run_serve(args, rank, ws, local, dist):
                 "solve_p50": float(np.median([r["t_done"] - r["t_admit"] for r in done]) * 1e3)},
             "producer_threads": args.producers,
             "converged_fraction": len(conv) / n, "ray_points_per_s": pts / wall,
+            "not_converged": [{"id": int(r["id"]), "atom": wl.atoms[r["id"]].name,
+                               "n_depth": int(wl.columns[r["id"]].n_depth),
+                               "n_nu_lines_conts": int(sum(l.n_nu for l in wl.atoms[r["id"]].lines)
+                                                       + sum(c.n_nu for c in wl.atoms[r["id"]].conts)),
+                               "status": int(r["status"]), "F_calls": int(r["stats"]["F_calls"]),
+                               "newton_iters": int(r["stats"]["newton_iters"]),
+                               "rh92_iters": int(r["stats"]["rh92_iters"]),
+                               "F_norm_drop": (r["stats"]["F_norm"] / r["stats"]["F_norm0"]
+                                               if r["stats"]["F_norm0"] > 0 else None)}
+                              for r in done if r["status"] != 0][:50],
             "offered_rate": args.rate, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -813,6 +897,8 @@ def main():
         run_batch(args, rank, ws, local, dist)
     elif args.workload == "serve":
         run_serve(args, rank, ws, local, dist)
+    elif args.workload == "rtol":
+        run_rtol(args, rank, ws, local, dist)
     else:
         run_ours(args, rank, ws, local, dist)
     if dist is not None:

@@ -157,6 +157,21 @@ typedef enum {
   JFNK_JVP_CENTRAL = 3
 } jfnk_jvp_scheme;
 
+/* Krylov solver of the Newton steps (Sect. 2.3): GMRES (Arnoldi with CGS2,
+ * Givens rotations, restart after krylov_max vectors, one JVP per iteration)
+ * or BiCGSTAB (van der Vorst 1992: two JVPs per iteration, at most 200
+ * iterations per Newton step; needs krylov_max >= 5, its six vectors live in
+ * the GMRES basis buffer). Both left-preconditioned, x_0 = 0, stopping when
+ * the preconditioned residual falls below rtol times its initial norm. */
+typedef enum { JFNK_KRYLOV_GMRES = 0, JFNK_KRYLOV_BICGSTAB = 1 } jfnk_krylov;
+
+/* The nonlinear solver: Algorithm 2 (after the optional RH92 start), or the
+ * paper's reference method alone, RH92 iterations (Rybicki & Hummer 1992, full
+ * preconditioning) until the population change 1/2 ||(n' - n)/(n' + n)||_inf
+ * falls below ftol, at most maxiter iterations (limited per depth like the
+ * Newton corrections when clamp is set). */
+typedef enum { JFNK_SOLVER_JFNK = 0, JFNK_SOLVER_RH92 = 1 } jfnk_solver_kind;
+
 /* Solver options (Algorithm 2; defaults from jfnk_default_options). */
 typedef struct {
   double ftol;          /* 1/2 ||(n - n_prev)/(n + n_prev)||_inf threshold (1e-4)  */
@@ -178,10 +193,20 @@ typedef struct {
                            each is timed alone; the results are the same)       */
   int formal_variant;   /* mixed mode: 0 autotuned, JFNK_FORMAL_SWEEP_THREAD or
                            JFNK_FORMAL_SWEEP_WARP forced (identical results)      */
-  int precond;          /* 1: block-Jacobi, first solution of Sect. 2.5.2 (default);
-                           0: none (GMRES on J x = -F)                            */
+  int precond;          /* block-Jacobi preconditioner after the solutions of
+                           Sect. 2.5.2: 1 first (background-scattering derivative
+                           neglected; default), 2 second (chi_sca dJ/dn lagged from
+                           the previous preconditioner build, zero at the start),
+                           3 third (local self-consistent scattering term);
+                           0: none (the Krylov solver works on J x = -F)          */
   int jvp;              /* Jacobian-vector products: JFNK_JVP_TANGENT (default) or a
                            finite difference of Fig. 2 (jfnk_jvp_scheme)          */
+  int krylov;           /* jfnk_krylov: JFNK_KRYLOV_GMRES (default) or BICGSTAB    */
+  int solver;           /* jfnk_solver_kind: JFNK_SOLVER_JFNK (default) or RH92    */
+  int line_search;      /* 0: off (default); k > 0: backtracking on ||F||_inf after
+                           each Newton update (Sect. 2.2.2), step 1, 1/2, 1/4, ...
+                           until ||F||_inf falls below its value at the previous
+                           base point, at most k halvings (each one F evaluation) */
 } jfnk_options;
 
 typedef struct {
@@ -263,6 +288,16 @@ int jfnk_jvp(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
  * set to -1 (Sect. 2.5.1-2.5.2, first solution), unfactored, P[k][i][j]. */
 int jfnk_block_jacobi(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const double* n,
                       const double* J_dagger, double* P, jfnk_mem where, void* stream);
+
+/* The preconditioner blocks of any of the three solutions of Sect. 2.5.2
+ * (variant 1, 2 or 3), unfactored, P[k][i][j], for tests of the variants.
+ * dJdn_prev [nq*nz*nl] (q-major, then depth, then level; nullable = zero) is
+ * the lagged estimate d J_nu^k/d n_j^k that variant 2 uses; dJdn_out (same
+ * layout, nullable) receives variant 2's renewed estimate. Other arguments as
+ * jfnk_block_jacobi. JFNK_E_INVALID for another variant. */
+int jfnk_block_jacobi_variant(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, int variant,
+                              const double* n, const double* J_dagger, const double* dJdn_prev,
+                              double* P, double* dJdn_out, jfnk_mem where, void* stream);
 
 /* One RH92 population update (Rybicki & Hummer 1992 with full preconditioning,
  * the paper's reference method): n_out from the formal solution at n. The
@@ -367,8 +402,8 @@ int jfnk_server_bytes(jfnk_server* sv, const jfnk_atmos* a, size_t* bytes);
  * must stay alive until the result has been polled. n_out (host, nz*nl
  * doubles, nullable) receives the populations before the result is reported.
  * opts (nullable: the server's) sets this column's tolerances, limits and
- * hybrid start; its precision must be the server's and its krylov_max at most
- * the server's. JFNK_E_INVALID when ``a`` exceeds the slot shape or the pool,
+ * hybrid start; its precision must be the server's, its krylov_max at most
+ * the server's, and its precond not 2 (the server keeps no lagged estimate). JFNK_E_INVALID when ``a`` exceeds the slot shape or the pool,
  * or for such options. May be called from another thread than
  * jfnk_server_step. */
 int jfnk_server_submit(jfnk_server* sv, const jfnk_atmos* a, long long id, double* n_out,

@@ -27,7 +27,7 @@ import numpy as np
 
 from . import krylov
 from .model import Model, initial_J
-from .precond import apply_inverse, block_jacobi, lu_factor_blocks
+from .precond import apply_inverse, block_jacobi, dJ_dn, lu_factor_blocks
 from .residual import COMPLEX_EPS, jvp_complex, jvp_fd, residual
 
 
@@ -90,8 +90,12 @@ def jfnk(m: Model, n0, J0=None, ftol: float = 1e-4, fdrop: float = 1e-2, rtol: f
          maxiter: int = 100, m_max: int = 50, max_restarts: int = 20, krylov_solver: str = "gmres",
          jvp: str = "complex", fd_choice: str = "eps1", precond: bool = True, clamp: bool = True,
          complex_eps: float = COMPLEX_EPS, line_search: bool = False,
-         max_halvings: int = 12) -> SolveResult:
-    """Algorithm 2."""
+         max_halvings: int = 12, precond_variant: int = 1) -> SolveResult:
+    """Algorithm 2. ``precond_variant`` selects the solution of Sect. 2.5.2 the
+    block-Jacobi preconditioner follows (1, 2 or 3; see ``precond.dJ_dn``); the
+    lagged estimate of variant 2 starts at zero and is renewed at every base
+    evaluation. ``line_search``: backtracking on ||F||_inf, alpha = 1, 1/2, 1/4,
+    ... (at most ``max_halvings`` halvings, Sect. 2.2.2), each trial one F call."""
     n = np.array(n0, dtype=float)
     Jdag = initial_J(m) if J0 is None else np.array(J0, dtype=float)
     N = n.size
@@ -104,13 +108,17 @@ def jfnk(m: Model, n0, J0=None, ftol: float = 1e-4, fdrop: float = 1e-2, rtol: f
     hist = [dict(iter=0, F_norm=F0, dn_norm=np.nan, F_calls=1, n=n.copy())]
     niter = 0
     converged = False
+    D_lag = None
     while niter < maxiter:
         if err <= ftol and fnorm <= fdrop * F0:
             converged = True
             break
         istar = res.istar
         if precond:
-            lus = lu_factor_blocks(block_jacobi(m, n, res))
+            Pb = block_jacobi(m, n, res, variant=precond_variant, D_prev=D_lag)
+            if precond_variant == 2:
+                D_lag = dJ_dn(m, n, res, 2, D_lag)
+            lus = lu_factor_blocks(Pb)
             Pinv = lambda x: apply_inverse(lus, x).ravel()
         else:
             Pinv = lambda x: np.asarray(x).ravel()

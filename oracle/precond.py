@@ -12,6 +12,11 @@ rate quadrature weight omega_t 4 pi / (h nu), s_it = +1 (-1) when i is the
 lower (upper) level of t, dJ/dchi^k and dJ/deta^k the angle averages of the
 App. A.2 coefficients, and the conservation row replaced by -1 (Sect. 2.5.1).
 
+The second and third solutions of Sect. 2.5.2 (``variant`` 2 and 3) add the
+background-scattering term chi_sca d J/d n_j to d eta/d n_j: lagged from the
+previous preconditioner build (2), or solved locally (3). ``dJ_dn`` holds the
+three readings.
+
 Reading of beta_j (the printed sum_{s>j} V_js (1 - g_js) is garbled):
 beta_j = d chi / d n_j = sum_{t: lo=j} V_t - sum_{t: up=j} g_t V_t, derived from
 Eq. chi; gamma_j = d eta / d n_j = sum_{t: up=j} (2 h nu^3 / c^2) g_t V_t.
@@ -28,15 +33,13 @@ import scipy.linalg as sla
 from .model import FOURPI, H, Model
 
 
-def block_jacobi(m: Model, n, res) -> np.ndarray:
-    """P[k] (nl x nl) from a residual evaluation made with ``want_lambda``."""
-    n = np.real(np.asarray(n))
+def _alpha_beta_gamma(m: Model, n):
+    """alpha_i = sum_t s_it W_t chi_t, beta_j = d chi/d n_j, gamma_j = d eta/d n_j, each [nl, nq, nz]."""
     nl, nq, nz = m.nl, m.nq, m.nz
     Wnu = FOURPI / (H * m.nu)
     alpha = np.zeros((nl, nq, nz))
     beta = np.zeros((nl, nq, nz))
     gamma = np.zeros((nl, nq, nz))
-    P = np.zeros((nz, nl, nl))
     for t, tr in enumerate(m.trans):
         lo, up = tr.lo, tr.up
         chi_t = m.V[t] * (n[:, lo][None, :] - m.g[t] * n[:, up][None, :])
@@ -46,6 +49,39 @@ def block_jacobi(m: Model, n, res) -> np.ndarray:
         beta[lo] += m.V[t]
         beta[up] -= m.g[t] * m.V[t]
         gamma[up] += m.twohnu3c2[:, None] * m.g[t] * m.V[t]
+    return alpha, beta, gamma
+
+
+def dJ_dn(m: Model, n, res, variant: int = 1, D_prev=None) -> np.ndarray:
+    """Local estimate of d J_nu^k / d n_j^k, [nl, nq, nz], after one of the three
+    solutions of Sect. 2.5.2 (Lchi, Leta: angle averages of dI^k/dchi^k, dI^k/deta^k):
+      1: beta_j Lchi + gamma_j Leta (background-scattering derivative neglected);
+      2: beta_j Lchi + (gamma_j + chi_sca D_prev_j) Leta, D_prev the previous
+         estimate of d J/d n_j (lagged; zero when none);
+      3: (beta_j Lchi + gamma_j Leta) / (1 - chi_sca Leta), the local terms of the
+         self-consistent solution (coefficient r_k of Sect. 2.5.2)."""
+    n = np.real(np.asarray(n))
+    _, beta, gamma = _alpha_beta_gamma(m, n)
+    lx, le = np.real(res.lam_chi)[None], np.real(res.lam_eta)[None]
+    sca = m.chi_sca[None, None, :]
+    if variant == 1:
+        return beta * lx + gamma * le
+    if variant == 2:
+        Dp = np.zeros_like(beta) if D_prev is None else D_prev
+        return beta * lx + (gamma + sca * Dp) * le
+    if variant == 3:
+        return (beta * lx + gamma * le) / (1.0 - sca * le)
+    raise ValueError("variant must be 1, 2 or 3")
+
+
+def block_jacobi(m: Model, n, res, variant: int = 1, D_prev=None) -> np.ndarray:
+    """P[k] (nl x nl) from a residual evaluation made with ``want_lambda``."""
+    n = np.real(np.asarray(n))
+    nl, nz = m.nl, m.nz
+    P = np.zeros((nz, nl, nl))
+    alpha, _, _ = _alpha_beta_gamma(m, n)
+    for t, tr in enumerate(m.trans):
+        lo, up = tr.lo, tr.up
         # Gamma: direct dependence of kappa_t on n_lo, n_up
         up_rate = m.Cmat[:, lo, up] + res.R_up[t]
         dn_rate = m.Cmat[:, up, lo] + res.R_dn[t]
@@ -53,7 +89,7 @@ def block_jacobi(m: Model, n, res) -> np.ndarray:
         P[:, lo, up] -= dn_rate
         P[:, up, lo] -= up_rate
         P[:, up, up] += dn_rate
-    zeta = beta * np.real(res.lam_chi)[None] + gamma * np.real(res.lam_eta)[None]
+    zeta = dJ_dn(m, n, res, variant, D_prev)
     P += np.einsum("iqk,jqk->kij", alpha, zeta)
     P[np.arange(nz), res.istar, :] = -1.0
     return P

@@ -36,6 +36,10 @@ JFNK_JVP_TANGENT = 0
 JFNK_JVP_FORWARD_EPS1 = 1
 JFNK_JVP_FORWARD_EPS2 = 2
 JFNK_JVP_CENTRAL = 3
+JFNK_KRYLOV_GMRES = 0
+JFNK_KRYLOV_BICGSTAB = 1
+JFNK_SOLVER_JFNK = 0
+JFNK_SOLVER_RH92 = 1
 JFNK_FORMAL_PER_RAY = 0
 JFNK_FORMAL_FUSED = 1
 JFNK_FORMAL_SWEEP_THREAD = 2
@@ -74,7 +78,8 @@ class jfnk_options(C.Structure):
                 ("maxiter", C.c_int), ("krylov_max", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("init", C.c_int), ("clamp", C.c_int),
                 ("rh92_warmup", C.c_int), ("rh92_switch", C.c_double), ("max_ticks", C.c_int),
-                ("profile", C.c_int), ("formal_variant", C.c_int), ("precond", C.c_int), ("jvp", C.c_int)]
+                ("profile", C.c_int), ("formal_variant", C.c_int), ("precond", C.c_int), ("jvp", C.c_int),
+                ("krylov", C.c_int), ("solver", C.c_int), ("line_search", C.c_int)]
 
 
 class jfnk_stats(C.Structure):
@@ -121,6 +126,8 @@ _SIGNATURES = {
                            C.c_void_p, C.c_int, C.c_void_p]),
     "jfnk_block_jacobi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int, C.c_void_p]),
+    "jfnk_block_jacobi_variant": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "jfnk_rh92_update": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "jfnk_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(jfnk_options), C.c_void_p,
@@ -337,6 +344,21 @@ def block_jacobi(atm: Atmosphere, n, Jdag=None, precision: int = JFNK_FP64):
     check(atm.ctx.lib.jfnk_block_jacobi(atm.ctx.h, atm.h, precision, _ptr(n), _ptr(Jd), _ptr(P),
                                         JFNK_MEM_HOST, None), "jfnk_block_jacobi")
     return P
+
+
+def block_jacobi_variant(atm: Atmosphere, n, variant: int, Jdag=None, dJdn_prev=None,
+                         precision: int = JFNK_FP64):
+    """Preconditioner blocks of solution ``variant`` of Sect. 2.5.2; returns
+    (P [nz, nl, nl], the renewed lagged d J/d n [nq, nz, nl] for variant 2)."""
+    n = _f64(n)
+    P = np.zeros((atm.n_depth, atm.n_levels, atm.n_levels))
+    D = np.zeros((atm.n_nu, atm.n_depth, atm.n_levels)) if variant == 2 else None
+    Dp = None if dJdn_prev is None else _f64(dJdn_prev)
+    check(atm.ctx.lib.jfnk_block_jacobi_variant(atm.ctx.h, atm.h, precision, variant, _ptr(n),
+                                                _ptr(None if Jdag is None else _f64(Jdag)), _ptr(Dp),
+                                                _ptr(P), _ptr(D), JFNK_MEM_HOST, None),
+          "jfnk_block_jacobi_variant")
+    return P, D
 
 
 def rh92_update(atm: Atmosphere, n, Jdag=None, precision: int = JFNK_FP64):

@@ -81,13 +81,22 @@ static int check_common(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, jfnk_
   return JFNK_OK;
 }
 
-// One explicit evaluation of the single-column batch in mode ``mode``.
+// One explicit evaluation of the single-column batch in mode ``mode``; a base
+// evaluation builds the preconditioner blocks of solution ``variant``.
 static int explicit_eval(jfnk_ctx* ctx, const jfnk_atmos* a, Batch* b, int mode, const double* n,
-                         const double* Jdag, jfnk_mem where, cudaStream_t s) {
+                         const double* Jdag, jfnk_mem where, cudaStream_t s, int variant = 1) {
   const ColDesc& c = b->h_cols[0];
   const AtmosData& M = a->d;
   const size_t N = (size_t)M.nz * M.nl, QZ = (size_t)M.nq * M.nz;
   int rc;
+  {
+    jfnk_options o;
+    jfnk_default_options(&o);
+    o.precond = variant;
+    SolverOpts so;
+    options_to_device(&o, &so);
+    JFNK_CUDA(cudaMemcpyAsync(b->d_opts, &so, sizeof(so), cudaMemcpyHostToDevice, s));
+  }
   if (n && (rc = copy_in(c.w.n, n, N * 8, where, s))) return rc;
   if (Jdag) {
     if ((rc = copy_in(c.w.Jdag, Jdag, QZ * 8, where, s))) return rc;
@@ -112,6 +121,9 @@ void options_to_device(const jfnk_options* o, SolverOpts* so) {
   so->max_ticks = o->max_ticks;
   so->precond = o->precond;
   so->jvp = o->jvp;
+  so->krylov = o->krylov;
+  so->solver = o->solver;
+  so->line_search = o->line_search;
 }
 
 int validate_options(const jfnk_options* o) {
@@ -123,11 +135,18 @@ int validate_options(const jfnk_options* o) {
   if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return fail(JFNK_E_INVALID, "unknown precision");
   if (o->init != JFNK_INIT_LTE && o->init != JFNK_INIT_USER && o->init != JFNK_INIT_ZERO_RADIATION)
     return fail(JFNK_E_INVALID, "init must be JFNK_INIT_LTE, JFNK_INIT_USER or JFNK_INIT_ZERO_RADIATION");
-  if (o->precond != 0 && o->precond != 1) return fail(JFNK_E_INVALID, "precond must be 0 or 1");
+  if (o->precond < 0 || o->precond > 3) return fail(JFNK_E_INVALID, "precond must be 0, 1, 2 or 3");
+  if (o->line_search < 0 || o->line_search > 60) return fail(JFNK_E_INVALID, "line_search must be in [0, 60]");
   if (o->jvp < JFNK_JVP_TANGENT || o->jvp > JFNK_JVP_CENTRAL) return fail(JFNK_E_INVALID, "unknown jvp scheme");
   if (o->jvp != JFNK_JVP_TANGENT && o->precision != JFNK_FP64)
     return fail(JFNK_E_INVALID, "difference JVPs need precision JFNK_FP64");
   if (o->rh92_warmup < 0) return fail(JFNK_E_INVALID, "rh92_warmup must be >= 0");
+  if (o->krylov != JFNK_KRYLOV_GMRES && o->krylov != JFNK_KRYLOV_BICGSTAB)
+    return fail(JFNK_E_INVALID, "krylov must be JFNK_KRYLOV_GMRES or JFNK_KRYLOV_BICGSTAB");
+  if (o->krylov == JFNK_KRYLOV_BICGSTAB && o->krylov_max < 5)
+    return fail(JFNK_E_INVALID, "BiCGSTAB keeps its six vectors in the Krylov basis: krylov_max must be >= 5");
+  if (o->solver != JFNK_SOLVER_JFNK && o->solver != JFNK_SOLVER_RH92)
+    return fail(JFNK_E_INVALID, "solver must be JFNK_SOLVER_JFNK or JFNK_SOLVER_RH92");
   if (o->formal_variant != 0 && o->formal_variant != JFNK_FORMAL_SWEEP_THREAD &&
       o->formal_variant != JFNK_FORMAL_SWEEP_WARP)
     return fail(JFNK_E_INVALID, "formal_variant must be 0, JFNK_FORMAL_SWEEP_THREAD or JFNK_FORMAL_SWEEP_WARP");
@@ -301,6 +320,24 @@ static int set_sweep_config(Batch* b, int variant, int size) {
   return JFNK_OK;
 }
 
+int ensure_dJdn(Batch* b, cudaStream_t s) {
+  if (b->has_dJdn) return JFNK_OK;
+  DeviceArena& ar = b->dJ_arena;
+  ar.reset();
+  std::vector<size_t> off(b->ncols);
+  for (int c = 0; c < b->ncols; ++c) {
+    const ColTables& T = b->h_cols[c].t;
+    off[c] = ar.take<double>((size_t)T.nq * T.nz * T.nl);
+  }
+  int rc = ar.allocate();
+  if (rc) return rc;
+  for (int c = 0; c < b->ncols; ++c) b->h_cols[c].w.dJdn = ar.ptr<double>(off[c]);
+  JFNK_CUDA(cudaMemcpyAsync(b->d_cols, b->h_cols.data(), sizeof(ColDesc) * b->ncols, cudaMemcpyHostToDevice, s));
+  b->has_dJdn = true;
+  drop_graphs(b);   // the tick graph gains the estimate's renewal kernel
+  return JFNK_OK;
+}
+
 static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
                          const jfnk_options* o, double* const* n_in, double* const* J_in,
                          jfnk_mem where, cudaStream_t s) {
@@ -309,7 +346,12 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
   JFNK_CUDA(cudaMemcpyAsync(b->d_opts, &so, sizeof(so), cudaMemcpyHostToDevice, s));
   int rc = batch_set_forced_mode(b, -1, s);
   if (rc) return rc;
-  const int phase = o->rh92_warmup > 0 ? PH_RH92 : PH_BASE;
+  if (o->precond == 2) {
+    // the lagged estimate starts at zero in every solve
+    if ((rc = ensure_dJdn(b, s))) return rc;
+    JFNK_CUDA(cudaMemsetAsync(b->dJ_arena.base, 0, b->dJ_arena.bytes, s));
+  }
+  const int phase = (o->rh92_warmup > 0 || o->solver == JFNK_SOLVER_RH92) ? PH_RH92 : PH_BASE;
   k_init_state<<<(b->ncols + 127) / 128, 128, 0, s>>>(b->d_state, b->ncols, phase);
   JFNK_CUDA(cudaGetLastError());
   JFNK_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int) * b->ncols, s));
@@ -461,6 +503,9 @@ void jfnk_default_options(jfnk_options* o) {
   o->formal_variant = 0;
   o->precond = 1;
   o->jvp = JFNK_JVP_TANGENT;
+  o->krylov = JFNK_KRYLOV_GMRES;
+  o->solver = JFNK_SOLVER_JFNK;
+  o->line_search = 0;
 }
 
 int jfnk_init(int device, jfnk_ctx** out) {
@@ -681,6 +726,35 @@ int jfnk_block_jacobi(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const d
     if (r) return r;
     const AtmosData& M = a->d;
     return copy_out(P, b->h_cols[0].w.P, (size_t)M.nz * M.nl * M.nl * 8, where, s);
+  });
+}
+
+int jfnk_block_jacobi_variant(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, int variant,
+                              const double* n, const double* J_dagger, const double* dJdn_prev,
+                              double* P, double* dJdn_out, jfnk_mem where, void* stream) {
+  int rc = check_common(ctx, a, precision, where);
+  if (rc) return rc;
+  if (!n || !P) return fail(JFNK_E_INVALID, "n and P are required");
+  if (variant < 1 || variant > 3) return fail(JFNK_E_INVALID, "variant must be 1, 2 or 3");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Batch* b;
+  if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;
+  return on_ctx_stream(ctx, stream, where, [&](cudaStream_t s) {
+    const AtmosData& M = a->d;
+    const size_t nD = (size_t)M.nq * M.nz * M.nl;
+    int r;
+    if (variant == 2) {
+      if ((r = ensure_dJdn(b, s))) return r;
+      if (dJdn_prev) {
+        if ((r = copy_in(b->h_cols[0].w.dJdn, dJdn_prev, nD * 8, where, s))) return r;
+      } else {
+        JFNK_CUDA(cudaMemsetAsync(b->h_cols[0].w.dJdn, 0, nD * 8, s));
+      }
+    }
+    if ((r = explicit_eval(ctx, a, b, EV_BASE, n, J_dagger, where, s, variant))) return r;
+    if ((r = copy_out(P, b->h_cols[0].w.P, (size_t)M.nz * M.nl * M.nl * 8, where, s))) return r;
+    if (variant == 2 && dJdn_out && (r = copy_out(dJdn_out, b->h_cols[0].w.dJdn, nD * 8, where, s))) return r;
+    return 0;
   });
 }
 

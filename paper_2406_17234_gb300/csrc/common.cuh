@@ -94,6 +94,8 @@ struct ColTables {
   const double* dz;       // [nz-1] |z_k - z_{k+1}|
   const double* mu;       // [nmu]
   const double* wmu;      // [nmu]
+  const float4* ang32;    // [nmu] (1/(2 mu), w_mu/2, 2 mu, 0), each the FP64 value rounded once
+  const float2* dz32;     // [nz-1] (|dz|, 1/|dz|) likewise
   const double* chi_c;    // [nq][nz]
   const double* eta_c;    // [nq][nz]
   const double* chi_sca;  // [nz]
@@ -108,7 +110,18 @@ struct SolverOpts {
   int maxiter, krylov_max, max_restarts, clamp, rh92_warmup, max_ticks;
   int precond;   // 1: apply P^{-1} (block Jacobi); 0: no preconditioning
   int jvp;       // 0 exact tangent; 1 forward eps_1; 2 forward eps_2; 3 central eps_2
+  int krylov;    // 0 GMRES; 1 BiCGSTAB
+  int solver;    // 0 Algorithm 2 (after an optional RH92 start); 1 RH92 iterations only
+  int line_search;   // 0 off; k > 0 at most k halvings of a Newton correction
 };
+
+// Preconditioner variant (solution of Sect. 2.5.2) a base evaluation builds for
+// column cd: its own options, else the batch's, else the first solution.
+struct ColDesc;
+
+// BiCGSTAB vectors of a column in the Krylov basis buffer (slots of N doubles).
+enum BicgSlot : int { BS_R = 0, BS_RHAT = 1, BS_P = 2, BS_V = 3, BS_S = 4, BS_T = 5 };
+constexpr int kBicgMaxIter = 200;   // iterations per Newton step
 
 // Per-column solver state (device memory, written by the Krylov kernel only).
 struct SolverState {
@@ -130,6 +143,14 @@ struct SolverState {
   int fd_scheme;       // JVPs: 0 exact tangent, 1/2 forward difference, 3 central difference
   int fd_side;         // central difference: +1 before F(n + eps u), -1 before F(n - eps u)
   double fd_eps;       // difference step of the current JVP
+  int bstage;          // BiCGSTAB: 0 the pending product is A p, 1 it is A s
+  int bit;             // BiCGSTAB iterations of this Newton step
+  double rho, alpha, omega;   // BiCGSTAB scalars
+  int ls_pending;      // line search: the next base evaluation is a trial point
+  int ls_left;         // halvings left
+  double ls_step;      // fraction of the Newton correction taken
+  double ls_Fprev;     // ||F||_inf at the base point the correction came from
+  double rh_damp;      // RH92 step fraction (0 = full), halved after a non-finite iteration
 };
 
 // Work buffers of one column (device pointers). ``real`` buffers hold float in
@@ -192,6 +213,8 @@ struct ColWork {
   float* etab32;    // [nq][nz] its background part eta_c + chi_sca J^dagger (mixed mode)
   double* np;       // [N] populations of a finite-difference evaluation (n + s eps u)
   double* fdp;      // [N] F(n + eps u) of a central difference
+  double* dJdn;     // [nq][nz][nl] lagged d J/d n_j of the second preconditioner
+                    // solution (null until a solve asks for it)
   SolverState* st;
 };
 
@@ -208,6 +231,12 @@ struct ColDesc {
   int mixed;         // 1: FP32 formal solution (buffers are float)
   const SolverOpts* opts;   // this column's solver options (null: the batch's)
 };
+
+__device__ __forceinline__ int precond_variant(const ColDesc& cd, const SolverOpts* bopts) {
+  const SolverOpts* o = cd.opts ? cd.opts : bopts;
+  const int v = o ? o->precond : 1;
+  return (v == 2 && !cd.w.dJdn) ? 1 : (v < 1 ? 1 : v);
+}
 
 // Mixed mode: S, J^dagger, J_new and the RH92 emissivity hold float pairs
 // (hi, lo) in the bytes of their FP64 arrays.

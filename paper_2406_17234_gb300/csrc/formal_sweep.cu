@@ -20,6 +20,8 @@
 // intensity form I with the re-anchoring of D on I - S); only the order of
 // the ray sums differs: each hemisphere is summed over its angles first and
 // the two hemisphere sums are then added.
+#include <type_traits>
+
 #include "formal_coef.cuh"
 
 namespace jfnk {
@@ -36,9 +38,22 @@ size_t sweep_scratch_bytes(int nq, int nz) {
 // App. A.1 coefficients of a step of optical depth x (r = 1/x): e = exp(-x),
 // w = (1 - e)/x, a = 1 - w, bq = (w - e)/x; below x = 0.1 each comes from its
 // Taylor series (truncated after x^5, below 3e-10 relative).
+// e^(-x) on the MUFU as 2^(-x log2 e) (flush-to-zero: e below 2^-126 is 0).
+__device__ __forceinline__ float exp_neg(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(mul(x, -1.4426950408889634f)));
+  return y;
+}
+
+// Which form of the coefficients a step takes: chosen per step (CM_EITHER),
+// or known for every angle of the depth (CM_SERIES: all steps below 0.1;
+// CM_DIRECT: none), the same choice as CM_EITHER makes for each step.
+enum CoefMode { CM_EITHER = 0, CM_SERIES = 1, CM_DIRECT = 2 };
+
+template <int CM = CM_EITHER>
 __device__ __forceinline__ void pl_coef_rn(float x, float r, float& e, float& w, float& a, float& bq) {
-  e = __expf(-x);
-  if (x < 0.1f) {
+  e = exp_neg(x);
+  if (CM == CM_SERIES || (CM == CM_EITHER && x < 0.1f)) {
     w = fma3(fma3(fma3(fma3(fma3(-1.0f / 720.0f, x, 1.0f / 120.0f), x, -1.0f / 24.0f), x, 1.0f / 6.0f), x, -0.5f), x, 1.0f);
     a = mul(x, fma3(fma3(fma3(fma3(fma3(-1.0f / 5040.0f, x, 1.0f / 720.0f), x, -1.0f / 120.0f), x, 1.0f / 24.0f), x, -1.0f / 6.0f), x, 0.5f));
     bq = fma3(fma3(fma3(fma3(1.0f / 144.0f, x, -1.0f / 30.0f), x, 1.0f / 8.0f), x, -1.0f / 3.0f), x, 0.5f);
@@ -80,7 +95,7 @@ struct RayOut {
 // better-conditioned value: D carries an absolute error of the order of the
 // largest |D| met upstream (attenuated along the ray), I - S one of the order
 // of |I| + |S|.
-template <bool TAN>
+template <bool TAN, int CM = CM_EITHER>
 __device__ __forceinline__ RayOut ray_step(const StepIn& in, float inv2mu, float two_mu, float hw, float& D,
                                            float& I, float& M, float& dD) {
   RayOut o;
@@ -88,7 +103,7 @@ __device__ __forceinline__ RayOut ray_step(const StepIn& in, float inv2mu, float
   const float dtau = mul(in.tz, inv2mu);
   const float rdt = mul(in.rz, two_mu);
   float e, w, a, bq;
-  pl_coef_rn(dtau, rdt, e, w, a, bq);
+  pl_coef_rn<CM>(dtau, rdt, e, w, a, bq);
   const float Du = D;
   float Dn = fma3(Du, e, mul(w, in.dSin));
   if (TAN) {
@@ -118,10 +133,25 @@ __device__ __forceinline__ RayOut ray_step(const StepIn& in, float inv2mu, float
   return o;
 }
 
-// Sum of eight angle contributions in the fixed tree of a 3-level xor
-// butterfly over 8 lanes (absent angles contribute 0).
-__device__ __forceinline__ float tree8(const float* x) {
-  return add(add(add(x[0], x[4]), add(x[2], x[6])), add(add(x[1], x[5]), add(x[3], x[7])));
+// Sum of the angle contributions in the fixed tree of a 3-level xor butterfly
+// over 8 lanes, (x0 + x4) + (x2 + x6) and (x1 + x5) + (x3 + x7), with the terms
+// of angles m >= MU (zero by construction, known at compile time) left out:
+// x + 0 = x, so the sum has the butterfly's value.
+struct Part {
+  float v;
+  bool on;
+};
+__device__ __forceinline__ Part padd(Part a, Part b) {
+  if (a.on && b.on) return Part{add(a.v, b.v), true};
+  return a.on ? a : b;
+}
+template <int MU>
+__device__ __forceinline__ float tree_mu(const float* x) {
+  Part p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = Part{i < MU ? x[i] : 0.f, i < MU};
+  const Part s = padd(padd(padd(p[0], p[4]), padd(p[2], p[6])), padd(padd(p[1], p[5]), padd(p[3], p[7])));
+  return s.on ? s.v : 0.f;
 }
 __device__ __forceinline__ float butterfly8(float v) {
   v = add(v, __shfl_xor_sync(0xffffffffu, v, 4));
@@ -153,8 +183,9 @@ __device__ __forceinline__ void write_tan(const ColDesc& cd, size_t o, float dS,
 // Stages |dz| and 1/|dz| of the block's column in shared memory.
 __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float* s_idz) {
   for (int k = threadIdx.x; k < T.nz - 1; k += blockDim.x) {
-    s_dz[k] = (float)T.dz[k];
-    s_idz[k] = (float)(1.0 / T.dz[k]);
+    const float2 d = T.dz32[k];
+    s_dz[k] = d.x;
+    s_idz[k] = d.y;
   }
 }
 
@@ -167,7 +198,8 @@ __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float*
 // of the same Newton step;
 // those then read depth-major float arrays only (one 128-byte line per warp
 // and depth) and run entirely in FP32.
-template <int MU, bool TAN, bool UP>
+// EXACT: the column has exactly MU angles (no per-angle guards).
+template <int MU, bool TAN, bool UP, bool EXACT>
 __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const float* __restrict__ s_dz,
                                              const float* __restrict__ s_idz) {
   const ColTables& T = cd.t;
@@ -190,10 +222,11 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   float inv2mu[MU], hw[MU], two_mu[MU];
 #pragma unroll
   for (int m = 0; m < MU; ++m) {
-    const bool on = m < nmu;
-    inv2mu[m] = on ? (float)(0.5 / T.mu[m]) : 0.f;
-    hw[m] = on ? (float)(0.5 * T.wmu[m]) : 0.f;
-    two_mu[m] = on ? (float)(2.0 * T.mu[m]) : 0.f;
+    const bool on = EXACT || m < nmu;
+    const float4 a = on ? T.ang32[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+    inv2mu[m] = a.x;
+    hw[m] = a.y;
+    two_mu[m] = a.z;
   }
   // tangent opacity of depth kk, left by the opacity kernel
   auto tan_in = [&](int kk, float& dc, float& dS) {
@@ -227,7 +260,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     I[m] = I0;
     M[m] = fabsf(D0);
     dD[m] = dD0;
-    if (m < nmu) {
+    if (EXACT || m < nmu) {
       xD[m] = mul(hw[m], D0);
       xa[m] = fabsf(xD[m]);
       xI[m] = mul(hw[m], I0);
@@ -237,12 +270,13 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   auto emit = [&](int k, df Sk, float dS) {
     float* pp = part + (size_t)k * pitch;
     if (TAN) {
-      const float td = tree8(xd);
+      const float td = tree_mu<MU>(xd);
       if (!UP) pp[0] = td;
       else write_tan(cd, (size_t)k * pitch + q, dS, add(td, pp[0]));
       return;
     }
-    const float tD = tree8(xD), ta = tree8(xa), tI = tree8(xI), tx = tree8(xx), te = tree8(xe);
+    const float tD = tree_mu<MU>(xD), ta = tree_mu<MU>(xa), tI = tree_mu<MU>(xI), tx = tree_mu<MU>(xx),
+                te = tree_mu<MU>(xe);
     if (!UP) {
       pp[0] = tD;
       pp[pstride] = ta;
@@ -316,17 +350,29 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       in.rc0 = rcp_approx(c0);
       in.dcs = in.ddSin = 0.f;
     }
+    auto angles = [&](auto cm) {
+      constexpr int CM = decltype(cm)::value;
 #pragma unroll
-    for (int m = 0; m < MU; ++m) {
-      if (m < nmu) {
-        const RayOut r = ray_step<TAN>(in, inv2mu[m], two_mu[m], hw[m], D[m], I[m], M[m], dD[m]);
-        xD[m] = r.xD;
-        xa[m] = fabsf(r.xD);
-        xI[m] = r.xI;
-        xx[m] = r.xx;
-        xe[m] = r.xe;
-        xd[m] = r.xd;
+      for (int m = 0; m < MU; ++m) {
+        if (EXACT || m < nmu) {
+          const RayOut r = ray_step<TAN, CM>(in, inv2mu[m], two_mu[m], hw[m], D[m], I[m], M[m], dD[m]);
+          xD[m] = r.xD;
+          xa[m] = fabsf(r.xD);
+          xI[m] = r.xI;
+          xx[m] = r.xx;
+          xe[m] = r.xe;
+          xd[m] = r.xd;
+        }
       }
+    };
+    if (EXACT) {
+      // the angles' optical depths tz/(2 mu) fall with m (mu ascending): one
+      // test on the first and last angle settles the form for all of them
+      if (!(mul(in.tz, inv2mu[MU - 1]) < 0.1f)) angles(std::integral_constant<int, CM_DIRECT>());
+      else if (mul(in.tz, inv2mu[0]) < 0.1f) angles(std::integral_constant<int, CM_SERIES>());
+      else angles(std::integral_constant<int, CM_EITHER>());
+    } else {
+      angles(std::integral_constant<int, CM_EITHER>());
     }
     emit(k, Sk, dS0);
     Sp = Sk;
@@ -338,7 +384,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   if (UP && !TAN) {
 #pragma unroll
     for (int m = 0; m < MU; ++m)
-      if (m < nmu) cd.w.Iem[(size_t)q * nmu + m] = __dmul_rn((double)I[m], c2);
+      if (EXACT || m < nmu) cd.w.Iem[(size_t)q * nmu + m] = __dmul_rn((double)I[m], c2);
   }
 }
 
@@ -359,8 +405,13 @@ __global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict_
   __syncthreads();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
-  sweep_thread<MU, TAN, false>(cd, q, s_dz, s_idz);
-  sweep_thread<MU, TAN, true>(cd, q, s_dz, s_idz);
+  if (T.nmu == MU) {   // uniform over the block: every angle slot is in use
+    sweep_thread<MU, TAN, false, true>(cd, q, s_dz, s_idz);
+    sweep_thread<MU, TAN, true, true>(cd, q, s_dz, s_idz);
+  } else {
+    sweep_thread<MU, TAN, false, false>(cd, q, s_dz, s_idz);
+    sweep_thread<MU, TAN, true, false>(cd, q, s_dz, s_idz);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -401,9 +452,10 @@ __device__ __forceinline__ void sweep_warp(const ColDesc& cd, int q, float* __re
   const float c2f = T.c2f[qq];
   const df c2p = df_load(T.c2p, qq);
   const bool on = m < nmu;
-  const float inv2mu = on ? (float)(0.5 / T.mu[m]) : 0.f;
-  const float hw = on ? (float)(0.5 * T.wmu[m]) : 0.f;
-  const float two_mu = on ? (float)(2.0 * T.mu[m]) : 0.f;
+  const float4 ang = on ? T.ang32[m] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float inv2mu = ang.x;
+  const float hw = ang.y;
+  const float two_mu = ang.z;
   float* hp = wp + (size_t)(qi * 2 + hemi) * kWarpParts * nz;   // this hemisphere's sums [v][k]
   const bool writer = !TAN && !up && m == 0 && valid;           // depth-major copies
   auto tan_in = [&](int kk, float& dc, float& dS) {

@@ -137,6 +137,10 @@ struct Batch {
   ColDesc* d_view = nullptr;          // device array [ncols] of the view's descriptors
   cudaGraphExec_t graph_view = nullptr;
   int compactions = 0;                // view rebuilds in the last solve
+  // lagged d J/d n of the second preconditioner solution, allocated on the
+  // first solve that asks for it ([nq][nz][nl] per column, in one arena)
+  DeviceArena dJ_arena;
+  bool has_dJdn = false;
   ~Batch();
 };
 
@@ -156,6 +160,8 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr,
                       cudaStream_t side = nullptr, cudaEvent_t ev2 = nullptr, cudaEvent_t ev3 = nullptr);
 // Creates the side stream and the fork/join events of a mixed-mode batch.
 int ensure_side_stream(Batch* b);
+// Allocates and binds the lagged d J/d n buffers of every column (once).
+int ensure_dJdn(Batch* b, cudaStream_t s);
 // Launch of the Krylov/Newton state machine step.
 int launch_krylov_step(const Batch& b, cudaStream_t s);
 // Fused formal solution + ray sums (formal_fused.cu).

@@ -536,7 +536,7 @@ __device__ __forceinline__ int rate_mode(const ColDesc& cd, int t, int tile) {
 // RH92 sums in FP32, and Jeff = J - Psi* eta from the pairs because it cancels
 // in optically thick layers.
 __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const int tile, const int rank,
-                           const RateSmem& sm, cg::cluster_group& cluster) {
+                           const RateSmem& sm, cg::cluster_group& cluster, const SolverOpts* bopts) {
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -575,6 +575,8 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
     // rate sums in pair arithmetic, preconditioner sums
     // A^kk_{t,j} = sum W chi_t (beta_j Lchi + gamma_j Leta) in FP32
     const float nlo_f = (float)n_lo, nup_f = (float)n_up;
+    const int pv = precond_variant(cd, bopts);
+    const float sca_f = (float)T.chi_sca[k];
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
@@ -582,8 +584,16 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
       s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
       const float Vf = T.V32[pk], gf = T.G32[pk];
-      const float Wc = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
+      const float Wc0 = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
       const float Lx = cd.w.Lchi32[o], Le = cd.w.Leta32[o];
+      // third solution of Sect. 2.5.2: d J/d n over 1 - chi_sca Leta
+      const float Wc = pv == 3 ? Wc0 / (1.0f - sca_f * Le) : Wc0;
+      if (pv == 2) {
+        // second solution: + chi_sca (d J/d n_j)^dagger Leta for every level
+        const float f = Wc0 * sca_f * Le;
+        const double* Dq = cd.w.dJdn + (size_t)o * nl;
+        for (int j = 0; j < nl; ++j) sm.f(wid, j, lane) = fmaf(f, (float)Dq[j], sm.f(wid, j, lane));
+      }
       const float cLx = Wc * Lx, cU = Wc * (T.c2f[q] * Le - Lx);
       for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
         const int ts = T.q_t[s];
@@ -596,14 +606,24 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
       }
     }
   } else if (base_mode) {
+    const int pv = precond_variant(cd, bopts);
+    const double sca = T.chi_sca[k];
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
       const size_t pk = (size_t)(wbase + q - q0) * nz + k, o = (size_t)q * nz + k;
       const double Jq = J[o];
       const double wv = T.WV[pk], wgv = T.WgV[pk];
       a0 = fma(wv, Jq, a0);
       a1 = fma(wgv, Jq, a1);
-      const double Wc = wv * n_lo - wgv * n_up;     // W chi_t
+      const double Wc0 = wv * n_lo - wgv * n_up;     // W chi_t
       const double Lx = cd.w.Lchi[o], Le = cd.w.Leta[o], c2 = T.c2[q];
+      // third solution of Sect. 2.5.2: d J/d n over 1 - chi_sca Leta
+      const double Wc = pv == 3 ? Wc0 / (1.0 - sca * Le) : Wc0;
+      if (pv == 2) {
+        // second solution: + chi_sca (d J/d n_j)^dagger Leta for every level
+        const double f = Wc0 * sca * Le;
+        const double* Dq = cd.w.dJdn + o * nl;
+        for (int j = 0; j < nl; ++j) sm.d(wid, 2 + j, lane) += f * Dq[j];
+      }
       for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
         const int ts = T.q_t[s];
         const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
@@ -715,7 +735,7 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
 // column c0 + l * step, so that columns in another evaluation kind cost one
 // load each instead of a cluster launch.
 __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __restrict__ cols, int ncols,
-                                                           int racc, int fslots) {
+                                                           int racc, int fslots, const SolverOpts* bopts) {
   extern __shared__ __align__(16) unsigned char rate_smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -736,7 +756,7 @@ __global__ void __launch_bounds__(32 * kRateWarps) k_rates(const ColDesc* __rest
       const int l = __ffs(act) - 1;
       act &= act - 1;
       const int mode = __shfl_sync(0xffffffffu, ml, l);
-      rates_tile(cols[c0 + l * step], mode, t, tile, rank, sm, cluster);
+      rates_tile(cols[c0 + l * step], mode, t, tile, rank, sm, cluster, bopts);
     }
   }
 }
@@ -774,8 +794,45 @@ static int launch_rates(const Batch& b, cudaStream_t s) {
   attr[0].val.clusterDim.z = split;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_rates, (const ColDesc*)b.d_cols, b.ncols, racc, fslots));
+  JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_rates, (const ColDesc*)b.d_cols, b.ncols, racc, fslots,
+                               (const SolverOpts*)b.d_opts));
   return JFNK_OK;
+}
+
+// Second solution of Sect. 2.5.2: after a base evaluation (whose rate kernel
+// has used the previous estimate) the lagged d J_nu^k/d n_j^k is renewed as
+// beta_j Lchi + (gamma_j + chi_sca D_j) Leta, beta_j = d chi/d n_j,
+// gamma_j = d eta/d n_j from the transitions active at nu; thread per (nu, k).
+__global__ void k_dJdn_update(const ColDesc* __restrict__ cols, const SolverOpts* bopts) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (eval_mode(cd) != EV_BASE || precond_variant(cd, bopts) != 2) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nl = T.nl;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.nq * nz; i += gridDim.x * blockDim.x) {
+    const int q = i / nz, k = i - q * nz;
+    double beta[kMaxL], gamma[kMaxL];
+    for (int j = 0; j < nl; ++j) beta[j] = gamma[j] = 0.0;
+    for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+      const int t = T.q_t[s];
+      const size_t pk = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+      const double V = T.V[pk], gV = T.G[pk] * V;
+      beta[T.t_lo[t]] += V;
+      beta[T.t_up[t]] -= gV;
+      gamma[T.t_up[t]] += T.c2[q] * gV;
+    }
+    const double Lx = cd.mixed ? (double)cd.w.Lchi32[i] : cd.w.Lchi[i];
+    const double Le = cd.mixed ? (double)cd.w.Leta32[i] : cd.w.Leta[i];
+    const double sca = T.chi_sca[k];
+    double* D = cd.w.dJdn + (size_t)i * nl;
+    for (int j = 0; j < nl; ++j) D[j] = beta[j] * Lx + (gamma[j] + sca * D[j]) * Le;
+  }
+}
+
+static void launch_dJdn_update(const Batch& b, cudaStream_t s) {
+  if (!b.has_dJdn) return;
+  const long pts = (long)b.max_nq * b.max_nz;
+  k_dJdn_update<<<dim3((unsigned)std::min<long>((pts + 255) / 256, 1024), b.ncols), 256, 0, s>>>(
+      b.d_cols, b.d_opts);
 }
 
 // ---------------------------------------------------------------------------
@@ -974,6 +1031,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     if ((rc = launch_formal_sweep(b, s, 1))) return rc;
     if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
     if ((rc = launch_rates(b, s))) return rc;
+    launch_dJdn_update(b, s);
     JFNK_CUDA(cudaStreamWaitEvent(s, b.join_ev, 0));
     k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
     JFNK_CUDA(cudaGetLastError());
@@ -1016,6 +1074,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   {
     int rc = launch_rates(b, s);
     if (rc) return rc;
+    launch_dJdn_update(b, s);
     if (b.mixed) launch_rates_tan32(b, s);
   }
   k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);

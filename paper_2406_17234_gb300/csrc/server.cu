@@ -210,6 +210,8 @@ int jfnk_server_create(jfnk_ctx* ctx, const jfnk_server_desc* d, jfnk_server** o
   if (rc) return rc;
   if (d->opts.init != JFNK_INIT_LTE) return fail(JFNK_E_INVALID, "server requests start from LTE");
   if (d->opts.formal_variant != 0) return fail(JFNK_E_INVALID, "server chooses its formal kernel itself");
+  if (d->opts.precond == 2)
+    return fail(JFNK_E_INVALID, "the server does not keep the lagged estimate of preconditioner variant 2");
   if (d->max_slots < 1 || d->max_depth < 2 || d->max_depth > JFNK_MAX_DEPTH || d->max_freq < 1 ||
       d->max_levels < 2 || d->max_levels > JFNK_MAX_LEVELS || d->max_trans < 1 || d->max_trans > kMaxT ||
       d->max_mu < 1 || d->max_mu > JFNK_MAX_MU)
@@ -320,15 +322,15 @@ int jfnk_server_submit(jfnk_server* sv, const jfnk_atmos* a, long long id, doubl
   const jfnk_options* o = opts ? opts : &sv->desc.opts;
   if ((rc = validate_options(o))) return rc;
   if (o->precision != sv->desc.opts.precision || o->krylov_max > sv->kmax || o->init != JFNK_INIT_LTE ||
-      o->formal_variant != 0)
+      o->formal_variant != 0 || o->precond == 2)
     return fail(JFNK_E_INVALID,
-                "request options: precision, krylov_max, init or formal_variant do not fit the server");
+                "request options: precision, krylov_max, init, formal_variant or precond do not fit the server");
   ServerReq r;
   r.a = a;
   r.id = id;
   r.n_out = n_out;
   options_to_device(o, &r.o);
-  r.rh92 = o->rh92_warmup > 0;
+  r.rh92 = o->rh92_warmup > 0 || o->solver == JFNK_SOLVER_RH92;
   r.bytes = column_bytes(a->d, sv->kind, sv->mixed, sv->kmax, nullptr);
   if (r.bytes > sv->pool.bytes) return fail(JFNK_E_INVALID, "column larger than the server's memory pool");
   r.t_submit = sv->clock();

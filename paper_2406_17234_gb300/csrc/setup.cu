@@ -469,6 +469,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
   size_t o_W2 = ar.take<float2>(nwin), o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
   size_t o_linc = ar.take<int>((size_t)nl * (nt + 1));
+  size_t o_ang32 = ar.take<float4>(nmu), o_dz32 = ar.take<float2>(nz - 1);
   const size_t host_prefix = ar.cursor;
   size_t o_V = ar.take<double>((size_t)nwin * nz), o_G = ar.take<double>((size_t)nwin * nz);
   size_t o_chic = ar.take<double>((size_t)nq * nz), o_etac = ar.take<double>((size_t)nq * nz);
@@ -580,6 +581,14 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
     }
   }
   JFNK_CUDA(up(o_linc, linc.data(), linc.size() * 4));
+  // the sweep kernels' per-angle and per-layer constants, rounded once from FP64
+  std::vector<float4> ang32(nmu);
+  for (int m = 0; m < nmu; ++m)
+    ang32[m] = make_float4((float)(0.5 / mu[m]), (float)(0.5 * wmu[m]), (float)(2.0 * mu[m]), 0.f);
+  std::vector<float2> dz32(nz - 1);
+  for (int k = 0; k + 1 < nz; ++k) dz32[k] = make_float2((float)dzv[k], (float)(1.0 / dzv[k]));
+  JFNK_CUDA(up(o_ang32, ang32.data(), nmu * sizeof(float4)));
+  JFNK_CUDA(up(o_dz32, dz32.data(), (nz - 1) * sizeof(float2)));
   JFNK_CUDA(up(o_dz, dzv.data(), (nz - 1) * 8));
   JFNK_CUDA(up(o_mu, mu.data(), nmu * 8));
   JFNK_CUDA(up(o_wmu, wmu.data(), nmu * 8));
@@ -652,6 +661,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   tb_.qmeta = ar.ptr<int>(o_qmeta);
   tb_.lvl_inc = ar.ptr<int>(o_linc);
   tb_.mu = ar.ptr<double>(o_mu); tb_.wmu = ar.ptr<double>(o_wmu);
+  tb_.ang32 = ar.ptr<float4>(o_ang32); tb_.dz32 = ar.ptr<float2>(o_dz32);
   tb_.chi_c = ar.ptr<double>(o_chic); tb_.eta_c = ar.ptr<double>(o_etac);
   tb_.chi_sca = ar.ptr<double>(o_sca); tb_.Bn = ar.ptr<double>(o_B); tb_.C = ar.ptr<double>(o_C);
   tb_.ntot = ar.ptr<double>(o_ntot); tb_.nstar = ar.ptr<double>(o_nstar);

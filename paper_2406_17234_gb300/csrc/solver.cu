@@ -240,7 +240,19 @@ __device__ bool small_solve(double* A, double* b, int nl) {
 // population change measure of the depth (or NaN on a singular system). With
 // clamp the correction is limited like a Newton correction (Sect. 2.2.2), so
 // that no population of the depth falls below a tenth of its old value.
-__device__ double rh92_depth(const ColDesc& cd, int k, bool clamp) {
+//
+// The preconditioned rate equations M n' + c0 = 0 (plus the conservation row)
+// are affine in n' and equal the residual F at n' = n, so n' = n + d with
+// M d = -F(n) and sum d = n_tot - sum n, the same update. With ``correction``
+// (mixed mode, once the iteration has settled) the correction d is solved
+// from the residual the evaluation assembled in float-pair and FP64
+// arithmetic, so that the FP32 sums in M (Psi*, the cross-coupling terms)
+// affect the speed of convergence only and not the fixed point, which is then
+// F(n) = 0 to the residual's accuracy (in optically thick lines the net rates
+// cancel far below FP32 resolution of the gross rates). Far from the
+// solution the direct form is the more robust one (M and c0 carry the same
+// rounding), so the mixed mode starts with it.
+__device__ double rh92_depth(const ColDesc& cd, int k, bool clamp, bool correction, double damp, double* out) {
   const ColTables& T = cd.t;
   const int nl = T.nl, nt = T.nt, nz = T.nz;
   double M[kMaxL * kMaxL], c0[kMaxL];
@@ -263,12 +275,20 @@ __device__ double rh92_depth(const ColDesc& cd, int k, bool clamp) {
     c0[up] -= r[3];
   }
   const int is = cd.w.istar[k];
-  double rhs[kMaxL];
-  for (int i = 0; i < nl; ++i) rhs[i] = -c0[i];
-  for (int j = 0; j < nl; ++j) M[is * nl + j] = 1.0;
-  rhs[is] = T.ntot[k];
-  if (!small_solve(M, rhs, nl)) return nan("");
   double* n = cd.w.n + k * nl;
+  double rhs[kMaxL];
+  if (correction) {
+    const double* F = cd.w.F + (size_t)k * nl;   // F[is] = n_tot - sum n
+    for (int i = 0; i < nl; ++i) rhs[i] = -F[i];
+    rhs[is] = F[is];
+  } else {
+    for (int i = 0; i < nl; ++i) rhs[i] = -c0[i];
+    rhs[is] = T.ntot[k];
+  }
+  for (int j = 0; j < nl; ++j) M[is * nl + j] = 1.0;
+  if (!small_solve(M, rhs, nl)) return nan("");
+  if (correction)
+    for (int l = 0; l < nl; ++l) rhs[l] += n[l];   // n' = n + d
   double alpha = 1.0;
   if (clamp)
     for (int l = 0; l < nl; ++l) {
@@ -276,10 +296,12 @@ __device__ double rh92_depth(const ColDesc& cd, int k, bool clamp) {
       if (d < 0.0) alpha = fmin(alpha, 0.9 * n[l] / (-d));
     }
   double err = 0.0;
+  double* o = out + (size_t)k * nl;
   for (int l = 0; l < nl; ++l) {
-    const double nn = clamp ? n[l] + alpha * (rhs[l] - n[l]) : rhs[l];
+    double nn = clamp ? n[l] + alpha * (rhs[l] - n[l]) : rhs[l];
+    if (damp < 1.0) nn = n[l] + damp * (nn - n[l]);
     err = fmax(err, 0.5 * fabs((nn - n[l]) / (nn + n[l])));
-    n[l] = nn;
+    o[l] = nn;
   }
   return err;
 }
@@ -348,6 +370,67 @@ __device__ void fd_prepare(const ColDesc& cd, SolverState* st, int scheme, const
   }
 }
 
+// <a, b> over the N entries of a column, summed by the whole block.
+__device__ double block_dot(const double* a, const double* b, int N, double* sh) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) acc += a[i] * b[i];
+  return block_sum(acc, sh);
+}
+
+// BiCGSTAB (van der Vorst 1992) on the left-preconditioned Newton system
+// P^{-1} J x = -P^{-1} F with x_0 = 0 and the shadow residual r^ = r_0: each
+// iteration is two state-machine steps, one per Jacobian-vector product
+// (v = A p, then t = A s). Opening an iteration: rho' = <r^, r>,
+// beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v). Returns false
+// on a breakdown (rho' = 0), after which the Newton step takes the current x.
+__device__ bool bicg_open(const ColDesc& cd, SolverState* st, double* sh) {
+  const int N = cd.t.nz * cd.t.nl;
+  double* Vb = cd.w.Vb;
+  const double* r = Vb + (size_t)BS_R * N;
+  const double* rh = Vb + (size_t)BS_RHAT * N;
+  double* p = Vb + (size_t)BS_P * N;
+  const double* v = Vb + (size_t)BS_V * N;
+  const double rho = st->rho, alpha = st->alpha, omega = st->omega;
+  const double rn = block_dot(rh, r, N, sh);
+  if (!(rn != 0.0) || !(rn == rn)) return false;
+  const double beta = (rn / rho) * (alpha / omega);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->rho = rn;
+    st->bstage = 0;
+    st->j = BS_P;
+  }
+  return true;
+}
+
+// n = n_prev + alpha_k (step x^k) per depth, with the per-depth limiting of
+// Sect. 2.2.2 when clamp is set (alpha_k = min(1, 0.9 min n_prev/|step dx|) over
+// the negative entries), from the base populations saved in w.nprev; returns
+// the population change 1/2 ||(n - n_prev)/(n + n_prev)||_inf of the column.
+__device__ double newton_apply(const ColDesc& cd, bool clamp, double step, double* sh) {
+  const int nz = cd.t.nz, nl = cd.t.nl;
+  const double* x = cd.w.x;
+  const double* np0 = cd.w.nprev;
+  double* n = cd.w.n;
+  double err = 0.0;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    double alpha = 1.0;
+    if (clamp)
+      for (int l = 0; l < nl; ++l) {
+        const double dx = step * x[k * nl + l];
+        if (dx < 0.0) alpha = fmin(alpha, 0.9 * np0[k * nl + l] / (-dx));
+      }
+    for (int l = 0; l < nl; ++l) {
+      const double np = np0[k * nl + l];
+      const double nn = np + alpha * (step * x[k * nl + l]);
+      n[k * nl + l] = nn;
+      err = fmax(err, 0.5 * fabs((nn - np) / (nn + np)));
+    }
+  }
+  return block_max(err, sh);
+}
+
 constexpr int kKrylovThreads = 512;
 
 __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __restrict__ cols,
@@ -366,6 +449,18 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
   __shared__ double s_val;
   const int phase = st->phase;
   if (phase == PH_DONE) return;
+  if ((phase == PH_JVP || phase == PH_RESTART) && st->ticks + 1 >= o.max_ticks) {
+    // the tick budget runs out inside a Krylov solve: this product was the last
+    if (threadIdx.x == 0) {
+      st->F_calls++;
+      st->jvp_calls++;
+      st->ticks++;
+      st->status = JFNK_E_TIMEOUT;
+      st->phase = PH_DONE;
+      status_out[blockIdx.x] = st->status;
+    }
+    return;
+  }
   const int nz = cd.t.nz, nl = cd.t.nl, N = nz * nl;
   const int kmax = o.krylov_max;
   double* w = cd.w.w;
@@ -376,19 +471,63 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
   double start_beta = 0.0;
 
   if (phase == PH_RH92) {
+    // mixed mode: the correction form once the change has fallen below 1e-2
+    const bool corr = cd.mixed && st->rh92_iter > 0 && st->err < 1e-2;
+    const double damp = st->rh_damp > 0.0 ? st->rh_damp : 1.0;
+    const int it0 = st->rh92_iter;
+    __syncthreads();
+    // the new populations are staged in w.x and committed only when every
+    // depth's update is finite
     double err = 0.0;
     for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-      double e = rh92_depth(cd, k, o.clamp != 0);
+      double e = rh92_depth(cd, k, o.clamp != 0, corr, damp, cd.w.x);
       err = (e == e) ? fmax(err, e) : INFINITY;
     }
     err = block_max(err, sh);
+    if (!(err < INFINITY) && it0 > 0 && damp > 1.0 / 64.0) {
+      // a non-finite evaluation or update (a marginal column driven into an
+      // unphysical state by the previous step): back to the populations of the
+      // last iteration that evaluated finitely, and half the RH92 step from
+      // there; J^dagger is still that evaluation's mean intensity
+      for (int i = threadIdx.x; i < N; i += blockDim.x) cd.w.n[i] = cd.w.nprev[i];
+      if (threadIdx.x == 0) {
+        st->F_calls++;
+        st->ticks++;
+        st->rh_damp = 0.5 * damp;
+        if (st->ticks >= o.max_ticks) { st->status = JFNK_E_TIMEOUT; st->phase = PH_DONE; }
+        status_out[blockIdx.x] = st->status;
+      }
+      return;
+    }
+    if (err < INFINITY) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        cd.w.nprev[i] = cd.w.n[i];
+        cd.w.n[i] = cd.w.x[i];
+      }
+    }
+    if (threadIdx.x == 0) st->rh_damp = fmin(1.0, 2.0 * damp);
+    // ||F||_inf of the evaluation the update was formed from (reported by
+    // RH92-only solves)
+    double fm = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) fm = fmax(fm, fabs(cd.w.F[i]));
+    fm = block_max(fm, sh);
     if (threadIdx.x == 0) {
       st->jsel ^= 1;   // J(n) becomes the lagged J^dagger
       st->F_calls++;
       st->ticks++;
       st->rh92_iter++;
       st->err = err;
+      if (o.solver == JFNK_SOLVER_RH92) {
+        st->Fnorm = fm;
+        if (st->rh92_iter == 1) st->F0norm = fm;
+      }
       if (!(err < INFINITY)) { st->status = JFNK_E_NAN; st->phase = PH_DONE; }
+      else if (o.solver == JFNK_SOLVER_RH92) {
+        // the reference method alone: converged on the population change
+        if (err < o.ftol) { st->status = JFNK_OK; st->phase = PH_DONE; }
+        else if (st->rh92_iter >= o.maxiter) { st->status = JFNK_E_MAXITER; st->phase = PH_DONE; }
+        else if (st->ticks >= o.max_ticks) { st->status = JFNK_E_TIMEOUT; st->phase = PH_DONE; }
+      }
       else if (err < o.rh92_switch || st->rh92_iter >= o.rh92_warmup) st->phase = PH_BASE;
       else if (st->ticks >= o.max_ticks) { st->status = JFNK_E_TIMEOUT; st->phase = PH_DONE; }
       status_out[blockIdx.x] = st->status;
@@ -405,6 +544,31 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       fm = fmax(fm, fabs(f));
     }
     fm = block_max(bad ? INFINITY : fm, sh);
+    if (o.line_search > 0 && st->ls_pending) {
+      // this base evaluation is a trial point of the line search (Sect. 2.2.2):
+      // accepted when ||F||_inf fell below its value at the previous base point,
+      // else the correction is halved from the previous populations and tried
+      // again (the lagged J^dagger stays that of the previous base point); the
+      // last allowed trial is kept either way
+      const bool better = (fm < INFINITY) && fm < st->ls_Fprev;
+      const int left = st->ls_left;
+      const double step = st->ls_step;
+      __syncthreads();
+      if (!better && left > 0) {
+        const double e = newton_apply(cd, o.clamp != 0, 0.5 * step, sh);
+        if (threadIdx.x == 0) {
+          st->F_calls++;
+          st->ticks++;
+          st->ls_step = 0.5 * step;
+          st->ls_left = left - 1;
+          st->err = e;
+          if (st->ticks >= o.max_ticks) { st->status = JFNK_E_TIMEOUT; st->phase = PH_DONE; }
+          status_out[blockIdx.x] = st->status;
+        }
+        return;
+      }
+      if (threadIdx.x == 0) st->ls_pending = 0;
+    }
     if (threadIdx.x == 0) {
       st->F_calls++;
       st->ticks++;
@@ -442,6 +606,122 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
       return;
     }
     start_beta = beta;
+    if (o.krylov == JFNK_KRYLOV_BICGSTAB) {
+      // r = r^ = P^{-1}(-F), p = v = 0, rho = alpha = omega = 1
+      double* Vr = Vb + (size_t)BS_R * N;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        Vr[i] = w[i];
+        Vb[(size_t)BS_RHAT * N + i] = w[i];
+        Vb[(size_t)BS_P * N + i] = 0.0;
+        Vb[(size_t)BS_V * N + i] = 0.0;
+      }
+      if (threadIdx.x == 0) {
+        st->rho = st->alpha = st->omega = 1.0;
+        st->bit = 0;
+      }
+      __syncthreads();
+      if (bicg_open(cd, st, sh)) {
+        if (o.jvp) fd_prepare(cd, st, o.jvp, Vb + (size_t)BS_P * N, +1, sh);
+        if (threadIdx.x == 0) { st->phase = PH_JVP; status_out[blockIdx.x] = st->status; }
+        return;
+      }
+      next = NX_NEWTON;   // breakdown at the start: the Newton step keeps x = 0
+    }
+  } else if (o.krylov == JFNK_KRYLOV_BICGSTAB) {
+    // a Jacobian-vector product of BiCGSTAB (A p or A s) is in dF
+    const int scheme = st->fd_scheme;
+    if (scheme) {
+      const int side = st->fd_side;
+      const double eps = st->fd_eps;
+      const double* u = Vb + (size_t)st->j * N;
+      __syncthreads();   // every thread has read the state before it changes
+      if (scheme == 3 && side > 0) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+          cd.w.fdp[i] = cd.w.dF[i];
+          cd.w.np[i] = cd.w.n[i] - eps * u[i];
+        }
+        if (threadIdx.x == 0) {
+          st->fd_side = -1;
+          st->F_calls++;
+          st->ticks++;
+          status_out[blockIdx.x] = st->status;
+        }
+        return;
+      }
+      for (int i = threadIdx.x; i < N; i += blockDim.x)
+        cd.w.dF[i] = scheme == 3 ? (cd.w.fdp[i] - cd.w.dF[i]) / (2.0 * eps) : (cd.w.dF[i] - cd.w.F[i]) / eps;
+      __syncthreads();
+    }
+    const int stage = st->bstage;
+    const double r0n = st->r0norm;
+    __syncthreads();
+    if (threadIdx.x == 0) { st->F_calls++; st->jvp_calls++; st->ticks++; }
+    double* r = Vb + (size_t)BS_R * N;
+    const double* rh = Vb + (size_t)BS_RHAT * N;
+    const double* p = Vb + (size_t)BS_P * N;
+    double* v = Vb + (size_t)BS_V * N;
+    double* sv = Vb + (size_t)BS_S * N;
+    double* t = Vb + (size_t)BS_T * N;
+    bool fin = false, bad = false;
+    if (stage == 0) {
+      // v = P^{-1} J p, alpha = rho/<r^, v>, s = r - alpha v
+      apply_pinv(cd, cd.w.dF, 1.0, nullptr, 0.0, v, o.precond != 0);
+      __syncthreads();
+      const double alpha = st->rho / block_dot(rh, v, N, sh);
+      for (int i = threadIdx.x; i < N; i += blockDim.x) sv[i] = r[i] - alpha * v[i];
+      __syncthreads();
+      const double sn = sqrt(block_dot(sv, sv, N, sh));
+      bad = !(alpha == alpha) || !(sn == sn);
+      if (!bad && sn < o.rtol * r0n) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += alpha * p[i];
+        fin = true;
+      } else if (!bad) {
+        if (threadIdx.x == 0) {
+          st->alpha = alpha;
+          st->bstage = 1;
+          st->j = BS_S;
+        }
+        if (o.jvp) fd_prepare(cd, st, o.jvp, sv, +1, sh);
+        if (threadIdx.x == 0) { st->phase = PH_JVP; status_out[blockIdx.x] = st->status; }
+        return;
+      }
+    } else {
+      // t = P^{-1} J s, omega = <t, s>/<t, t>, x += alpha p + omega s, r = s - omega t
+      apply_pinv(cd, cd.w.dF, 1.0, nullptr, 0.0, t, o.precond != 0);
+      __syncthreads();
+      const double ts = block_dot(t, sv, N, sh), tt = block_dot(t, t, N, sh);
+      const double omega = tt > 0.0 ? ts / tt : 0.0;
+      const double alpha = st->alpha;
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        x[i] += alpha * p[i] + omega * sv[i];
+        r[i] = sv[i] - omega * t[i];
+      }
+      __syncthreads();
+      const double rn = sqrt(block_dot(r, r, N, sh));
+      const int it = st->bit + 1;
+      bad = !(omega == omega) || !(rn == rn);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        st->omega = omega;
+        st->bit = it;
+      }
+      __syncthreads();
+      fin = bad || rn < o.rtol * r0n || omega == 0.0 || it >= kBicgMaxIter;
+      if (!fin) {
+        if (bicg_open(cd, st, sh)) {
+          if (o.jvp) fd_prepare(cd, st, o.jvp, Vb + (size_t)BS_P * N, +1, sh);
+          if (threadIdx.x == 0) { st->phase = PH_JVP; status_out[blockIdx.x] = st->status; }
+          return;
+        }
+        fin = true;   // breakdown: the Newton step takes the current x
+      }
+    }
+    if (bad) {
+      if (threadIdx.x == 0) { st->status = JFNK_E_NAN; st->phase = PH_DONE; status_out[blockIdx.x] = st->status; }
+      return;
+    }
+    __syncthreads();
+    next = NX_NEWTON;
   } else {
     // a Jacobian-vector product J u is in dF (u = V_j or u = x); with a
     // difference scheme dF holds F(n + side eps u) and the quotient is formed here
@@ -625,30 +905,20 @@ __global__ void __launch_bounds__(kKrylovThreads) k_krylov(const ColDesc* __rest
     return;
   }
 
-  // Newton update with per-depth limiting (Sect. 2.2.2): n += alpha_k x^k
-  double err = 0.0;
-  double* n = cd.w.n;
-  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-    double alpha = 1.0;
-    if (o.clamp)
-      for (int l = 0; l < nl; ++l) {
-        const double dx = x[k * nl + l];
-        if (dx < 0.0) alpha = fmin(alpha, 0.9 * n[k * nl + l] / (-dx));
-      }
-    for (int l = 0; l < nl; ++l) {
-      const double np = n[k * nl + l];
-      const double nn = np + alpha * x[k * nl + l];
-      cd.w.nprev[k * nl + l] = np;
-      n[k * nl + l] = nn;
-      err = fmax(err, 0.5 * fabs((nn - np) / (nn + np)));
-    }
-  }
-  err = block_max(err, sh);
+  // Newton update with per-depth limiting (Sect. 2.2.2): n += alpha_k x^k,
+  // from the base populations kept in w.nprev (a line search may halve it)
+  for (int i = threadIdx.x; i < N; i += blockDim.x) cd.w.nprev[i] = cd.w.n[i];
+  __syncthreads();
+  const double err = newton_apply(cd, o.clamp != 0, 1.0, sh);
   if (threadIdx.x == 0) {
     st->jsel ^= 1;   // J(n^p) becomes J^dagger_{p+1}
     st->err = err;
     st->newton_iter++;
     st->phase = PH_BASE;
+    st->ls_pending = o.line_search > 0;
+    st->ls_left = o.line_search;
+    st->ls_step = 1.0;
+    st->ls_Fprev = st->Fnorm;   // ||F||_inf at the base point n^p
     status_out[blockIdx.x] = st->status;
   }
 }
@@ -663,7 +933,7 @@ __global__ void k_rh92_apply(const ColDesc* __restrict__ cols) {
   const ColDesc& cd = cols[blockIdx.y];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= cd.t.nz) return;
-  rh92_depth(cd, k, false);   // the plain update: jfnk_rh92_update applies no limiting
+  rh92_depth(cd, k, false, false, 1.0, cd.w.n);   // the plain update: jfnk_rh92_update applies no limiting
 }
 
 // Zero-radiation initial guess (Sect. 2.2.1): the rate equations with I = 0,

@@ -220,3 +220,70 @@ def test_pure_absorption_limit_ignores_J_dagger():
     m0 = OM.build_model(atom, _isothermal_column(thomson=False, ntot_scale=0.0), 2)
     chi, eta = opacity_emissivity(m0, np.zeros((m0.nz, m0.nl)), m0.B * 3.0)
     np.testing.assert_allclose(eta / chi, m0.B, rtol=1e-14)
+
+
+def test_preconditioner_variants_reduce_to_the_first_without_scattering(tiny):
+    """Sect. 2.5.2: the second and third solutions differ from the first only
+    through chi_sca; without background scattering all three give the same
+    blocks (which equal the dense Jacobian's diagonal blocks, pinned above)."""
+    from dataclasses import replace
+    m = replace(tiny, chi_sca=np.zeros_like(tiny.chi_sca))
+    rng = np.random.default_rng(5)
+    n = W.perturbed_populations(m.nstar, rng, 0.3)
+    res = residual(m, n, OM.initial_J(m), want_lambda=True)
+    P1 = block_jacobi(m, n, res, variant=1)
+    D = rng.normal(size=(m.nl, m.nq, m.nz))
+    np.testing.assert_array_equal(block_jacobi(m, n, res, variant=2, D_prev=D), P1)
+    np.testing.assert_array_equal(block_jacobi(m, n, res, variant=3), P1)
+
+
+def test_lagged_scattering_estimate_converges_to_the_local_solution(tiny):
+    """The lagged d J/d n of the second solution, renewed with fixed local
+    operators, is a contraction (factor chi_sca Leta < 1) whose fixed point is
+    the third solution's local self-consistent estimate."""
+    from oracle.precond import dJ_dn
+    from dataclasses import replace
+    m = replace(tiny, chi_sca=tiny.chi_sca * 3e3)
+    n = m.nstar
+    res = residual(m, n, OM.initial_J(m), want_lambda=True)
+    D3 = dJ_dn(m, n, res, 3)
+    D = None
+    for _ in range(80):
+        D = dJ_dn(m, n, res, 2, D)
+    np.testing.assert_allclose(D, D3, rtol=1e-12, atol=1e-14 * np.max(np.abs(D3)))
+
+
+def test_local_scattering_solution_approaches_the_consistent_jacobian(tiny):
+    """With J^dagger made self-consistent (J = Lambda[S(n, J)], iterated to
+    convergence inside the residual), the diagonal blocks of the resulting
+    dense complex-step Jacobian carry the scattering feedback that the first
+    solution drops: on a strongly scattering column the third solution's
+    blocks (local feedback kept) are several times closer to them."""
+    from dataclasses import replace
+    m = replace(tiny, chi_sca=tiny.chi_sca * 3e3)
+    n = W.perturbed_populations(m.nstar, np.random.default_rng(4), 0.2)
+
+    def consistent_J(nc, iters=150):
+        J = OM.initial_J(m).astype(complex)
+        for _ in range(iters):
+            J = residual(m, nc, J).J
+        return J
+
+    Jc = consistent_J(n.astype(complex))
+    np.testing.assert_allclose(residual(m, n, Jc).J, Jc, rtol=1e-12)   # converged
+    res = residual(m, n, Jc.real, want_lambda=True)
+    N, nl = n.size, m.nl
+    Jm = np.zeros((N, N))
+    for c in range(N):
+        e = np.zeros(N)
+        e[c] = 1.0
+        nc = n + 1j * 1e-200 * e.reshape(n.shape)
+        Jm[:, c] = (residual(m, nc, consistent_J(nc), istar=res.istar).F.imag / 1e-200).ravel()
+
+    def dev(P):
+        return max(np.max(np.abs(P[k] - Jm[k * nl:(k + 1) * nl, k * nl:(k + 1) * nl]))
+                   / np.max(np.abs(Jm[k * nl:(k + 1) * nl, k * nl:(k + 1) * nl])) for k in range(m.nz))
+
+    d1, d3 = dev(block_jacobi(m, n, res, variant=1)), dev(block_jacobi(m, n, res, variant=3))
+    assert d1 > 0.02
+    assert d3 < 0.25 * d1
