@@ -9,6 +9,11 @@ one obvious loop or array expression per formula.
 Pins (tests/test_oracle_model.py): Gauss-Legendre exactness, Voigt limits and
 direct quadrature of the Voigt integral, Saha/Boltzmann ratios, detailed
 balance of the collision rates, unit normalisation of the line profiles.
+
+A moving column (line-of-sight velocity v, Sect. 3.4) gives every direction
+of propagation mu_d its own line profile, centred at nu_0 (1 + mu_d v/c) and
+renormalised on the line's window like the static one (reading: continua are
+not shifted); ``Vdir`` holds them. Pins in tests/test_oracle_velocity.py.
 """
 from __future__ import annotations
 
@@ -116,6 +121,9 @@ class Model:
     Cmat: np.ndarray       # [nz, nl, nl] collision rate i -> j
     nstar: np.ndarray      # [nz, nl] LTE populations
     active: np.ndarray     # [nt, nq] bool window mask
+    vlos: np.ndarray = None    # [nz] line-of-sight velocity (> 0 upward), None for a static column
+    mu_dir: np.ndarray = None  # [2 nmu] signed direction cosines: +mu (outgoing) then -mu (ingoing)
+    Vdir: np.ndarray = None    # [nt, 2 nmu, nq, nz] V_ij seen by each direction (moving column only)
 
     @property
     def ray_points(self) -> int:
@@ -191,6 +199,27 @@ def build_model(atom, col, n_mu: int = 5) -> Model:
             Cup = ne * d.q0 * np.sqrt(T) * np.exp(-(Ej - Ei) * EV / (KB * T))
             Cmat[:, d.i, d.j] += Cup
             Cmat[:, d.j, d.i] += Cup * ratio
+    # a moving column: each direction sees its own Doppler-shifted line profile
+    vlos = getattr(col, "vlos", None)
+    Vdir, mu_dir = None, None
+    if vlos is not None and np.any(vlos != 0.0):
+        mu_dir = np.concatenate([mu, -mu])
+        Vdir = np.zeros((nt, 2 * n_mu, nq, nz))
+        for t, (kind, d, nu0, grid) in enumerate(per):
+            tr = trans[t]
+            if kind != "bb":
+                Vdir[t] = V[t][None]                    # continua: no Doppler shift
+                continue
+            win = nu[tr.q0:tr.q1 + 1]
+            w = omega[t, tr.q0:tr.q1 + 1]
+            dnud = nu0 / C * np.sqrt(2.0 * KB * T / (atom.mass_amu * AMU) + vturb ** 2)
+            for dd in range(2 * n_mu):
+                # profile of the gas moving at vlos seen along direction mu_d:
+                # centred at nu0 (1 + mu_d v / c), renormalised on the window
+                v = (win[:, None] - nu0 * (1.0 + mu_dir[dd] * vlos[None, :] / C)) / dnud[None, :]
+                phi = voigt_H(d.damping, v) / (np.sqrt(np.pi) * dnud[None, :])
+                phi = phi / np.sum(w[:, None] * phi, axis=0, keepdims=True)
+                Vdir[t, dd, tr.q0:tr.q1 + 1, :] = (np.pi * QE ** 2 / (ME * C)) * d.f * phi
     B = planck(nu[:, None], T[None, :])
     kap = np.full(nq, col.kappa)
     if col.kappa_power != 0.0:
@@ -204,7 +233,8 @@ def build_model(atom, col, n_mu: int = 5) -> Model:
                  z=col.z.copy(), dz=dz, T=T.copy(), ne=ne.copy(), ntot=col.ntot.copy(),
                  trans=trans, omega=omega, V=V, g=g,
                  twohnu3c2=2.0 * H * nu ** 3 / C ** 2, chi_c=chi_c, chi_sca=chi_sca,
-                 eta_c=eta_c, B=B, Cmat=Cmat, nstar=nstar, active=active)
+                 eta_c=eta_c, B=B, Cmat=Cmat, nstar=nstar, active=active,
+                 vlos=None if Vdir is None else np.array(vlos, dtype=float), mu_dir=mu_dir, Vdir=Vdir)
 
 
 def initial_J(model: Model) -> np.ndarray:

@@ -74,11 +74,38 @@ def dJ_dn(m: Model, n, res, variant: int = 1, D_prev=None) -> np.ndarray:
     raise ValueError("variant must be 1, 2 or 3")
 
 
+def _moving_radiative_block(m: Model, n, res) -> np.ndarray:
+    """A^kk of a moving column: every direction d has its own opacity and
+    profile, so sum_nu sum_d h_d alpha_{i,d} (beta_{j,d} dI_d/dchi_d + gamma_{j,d} dI_d/deta_d)
+    with alpha_{i,d} = sum_t s_it W chi_{t,d} and beta, gamma from Vdir (first solution)."""
+    from .residual import direction_weights
+    nl, nq, nz, nd = m.nl, m.nq, m.nz, 2 * m.nmu
+    Wnu = FOURPI / (H * m.nu)
+    h = direction_weights(m)
+    alpha = np.zeros((nl, nd, nq, nz))
+    beta = np.zeros((nl, nd, nq, nz))
+    gamma = np.zeros((nl, nd, nq, nz))
+    for t, tr in enumerate(m.trans):
+        lo, up = tr.lo, tr.up
+        Vd = m.Vdir[t]
+        chi_t = Vd * (n[:, lo][None, None, :] - m.g[t][None] * n[:, up][None, None, :])
+        Wchi = (m.omega[t] * Wnu)[None, :, None] * chi_t
+        alpha[lo] += Wchi
+        alpha[up] -= Wchi
+        beta[lo] += Vd
+        beta[up] -= m.g[t][None] * Vd
+        gamma[up] += m.twohnu3c2[None, :, None] * m.g[t][None] * Vd
+    zeta = beta * np.real(res.lam_chi_dir)[None] + gamma * np.real(res.lam_eta_dir)[None]
+    return np.einsum("d,idqk,jdqk->kij", h, alpha, zeta)
+
+
 def block_jacobi(m: Model, n, res, variant: int = 1, D_prev=None) -> np.ndarray:
     """P[k] (nl x nl) from a residual evaluation made with ``want_lambda``."""
     n = np.real(np.asarray(n))
     nl, nz = m.nl, m.nz
     P = np.zeros((nz, nl, nl))
+    if m.Vdir is not None and variant != 1:
+        raise NotImplementedError("moving columns: the first solution of Sect. 2.5.2 only")
     alpha, _, _ = _alpha_beta_gamma(m, n)
     for t, tr in enumerate(m.trans):
         lo, up = tr.lo, tr.up
@@ -89,8 +116,11 @@ def block_jacobi(m: Model, n, res, variant: int = 1, D_prev=None) -> np.ndarray:
         P[:, lo, up] -= dn_rate
         P[:, up, lo] -= up_rate
         P[:, up, up] += dn_rate
-    zeta = dJ_dn(m, n, res, variant, D_prev)
-    P += np.einsum("iqk,jqk->kij", alpha, zeta)
+    if m.Vdir is not None:
+        P += _moving_radiative_block(m, n, res)
+    else:
+        zeta = dJ_dn(m, n, res, variant, D_prev)
+        P += np.einsum("iqk,jqk->kij", alpha, zeta)
     P[np.arange(nz), res.istar, :] = -1.0
     return P
 

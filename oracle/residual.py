@@ -21,6 +21,9 @@ the conservation rows and J^dagger taken from the real point; forward,
 backward and central differences (Eqs. fordif-centdif) with the step choices
 eps_1 and eps_2 of the Fig. 2 caption.
 
+A moving column (line-of-sight velocity, Sect. 3.4) takes the per-direction
+path of ``_residual_moving``.
+
 Pins (tests/test_oracle_residual.py): detailed balance at LTE populations with
 J = B (every net rate vanishes), collision-only detailed balance, linearity of
 the complex-step JVP, agreement with brute-force central differences, and the
@@ -56,6 +59,10 @@ class ResidualResult:
     I_emergent: np.ndarray    # [nq, nmu] outgoing intensity at the top
     lam_chi: Optional[np.ndarray] = None   # [nq, nz] 1/2 sum_mu w (dI^k/dchi^k) both hemispheres
     lam_eta: Optional[np.ndarray] = None   # [nq, nz] 1/2 sum_mu w (dI^k/deta^k)
+    # moving column: chi, eta are per direction [2 nmu, nq, nz]; the local
+    # derivatives of each direction's intensity, not angle-averaged
+    lam_chi_dir: Optional[np.ndarray] = None   # [2 nmu, nq, nz] dI_d^k/dchi_d^k
+    lam_eta_dir: Optional[np.ndarray] = None   # [2 nmu, nq, nz] dI_d^k/deta_d^k
 
 
 def opacity_emissivity(m: Model, n, Jdag):
@@ -68,6 +75,68 @@ def opacity_emissivity(m: Model, n, Jdag):
         chi = chi + m.V[t] * (ni - m.g[t] * nj)
         eta = eta + m.twohnu3c2[:, None] * m.g[t] * m.V[t] * nj
     return chi, eta
+
+
+def opacity_emissivity_dir(m: Model, n, Jdag):
+    """Eqs. chi and eta for a moving column, per direction d (the profile of
+    transition t seen along mu_d is Vdir[t, d]): [2 nmu, nq, nz] each."""
+    nd = 2 * m.nmu
+    zero = np.zeros((nd, 1, 1), dtype=np.result_type(n, Jdag))
+    chi = (m.chi_c + m.chi_sca[None, :])[None] + zero
+    eta = (m.eta_c + m.chi_sca[None, :] * Jdag)[None] + zero
+    for t, tr in enumerate(m.trans):
+        ni = n[:, tr.lo][None, None, :]
+        nj = n[:, tr.up][None, None, :]
+        chi = chi + m.Vdir[t] * (ni - m.g[t][None] * nj)
+        eta = eta + m.twohnu3c2[None, :, None] * m.g[t][None] * m.Vdir[t] * nj
+    return chi, eta
+
+
+def direction_weights(m: Model) -> np.ndarray:
+    """1/2 w_mu of each direction (outgoing, then ingoing): J = sum_d h_d I_d."""
+    return 0.5 * np.concatenate([m.wmu, m.wmu])
+
+
+def _residual_moving(m: Model, n, Jdag, istar, want_lambda: bool) -> "ResidualResult":
+    """Algorithm 1 for a moving column (Sect. 3.4): every direction carries its
+    own opacity and source function, the formal solution runs per ray with
+    them, J = sum_d h_d I_d feeds the background scattering, and the rate
+    integrals weight each direction's intensity with the profile it sees:
+    R_ij = sum_nu W sum_d h_d V_d I_d, R_ji = sum_nu W g sum_d h_d V_d (2 h nu^3/c^2 + I_d)."""
+    chi, eta = opacity_emissivity_dir(m, n, Jdag)
+    S = eta / chi
+    nmu, nd = m.nmu, 2 * m.nmu
+    dtype = np.result_type(chi, S, float)
+    I = np.zeros((nd, m.nq, m.nz), dtype=dtype)
+    lx = np.zeros_like(I) if want_lambda else None
+    le = np.zeros_like(I) if want_lambda else None
+    for a in range(nmu):
+        mu_a = m.mu[a:a + 1]
+        up = solve_rays(chi[a], S[a], m.dz, mu_a, m.B[:, -1], want_derivs=want_lambda)
+        dn = solve_rays(chi[nmu + a], S[nmu + a], m.dz, mu_a, m.B[:, -1], want_derivs=want_lambda)
+        I[a] = up[0][:, 0, :]
+        I[nmu + a] = dn[1][:, 0, :]
+        if want_lambda:
+            lx[a], le[a] = up[2][0][:, 0, :], up[2][1][:, 0, :]
+            lx[nmu + a], le[nmu + a] = dn[2][2][:, 0, :], dn[2][3][:, 0, :]
+    h = direction_weights(m)
+    J = np.einsum("d,dqk->qk", h, I)
+    Wq = FOURPI / (H * m.nu)
+    R_up = np.zeros((m.nt, m.nz), dtype=dtype)
+    R_dn = np.zeros((m.nt, m.nz), dtype=dtype)
+    for t in range(m.nt):
+        W = m.omega[t][:, None] * Wq[:, None]                     # [nq, 1]
+        hv = h[:, None, None] * m.Vdir[t]                         # [nd, nq, nz]
+        R_up[t] = np.sum(W * np.sum(hv * I, axis=0), axis=0)
+        R_dn[t] = np.sum(W * m.g[t] * np.sum(hv * (m.twohnu3c2[None, :, None] + I), axis=0), axis=0)
+    F = assemble(m, n, R_up, R_dn, istar)
+    res = ResidualResult(F=F, J=J, R_up=R_up, R_dn=R_dn, istar=istar, chi=chi, eta=eta,
+                         I_emergent=np.stack([I[a][:, 0] for a in range(nmu)], axis=1))
+    if want_lambda:
+        res.lam_chi_dir, res.lam_eta_dir = lx, le
+        res.lam_chi = np.einsum("d,dqk->qk", h, lx)
+        res.lam_eta = np.einsum("d,dqk->qk", h, le)
+    return res
 
 
 def conservation_rows(n) -> np.ndarray:
@@ -101,6 +170,8 @@ def residual(m: Model, n, Jdag, istar=None, want_lambda: bool = False) -> Residu
     n = np.asarray(n)
     if istar is None:
         istar = conservation_rows(n)
+    if m.Vdir is not None:
+        return _residual_moving(m, n, Jdag, istar, want_lambda)
     chi, eta = opacity_emissivity(m, n, Jdag)
     S = eta / chi
     out = solve_rays(chi, S, m.dz, m.mu, m.B[:, -1], want_derivs=want_lambda)

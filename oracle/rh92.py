@@ -61,6 +61,8 @@ class RH92Result:
 
 def rh92_update(m: Model, n, res):
     """One preconditioned rate-equation solve per depth, from a residual evaluation at n."""
+    if m.Vdir is not None:
+        raise NotImplementedError("RH92 is written here for static columns (angle-averaged Psi*)")
     Wnu = FOURPI / (H * m.nu)
     psi = res.lam_eta                                   # [nq, nz] angle-averaged Psi*
     eta_bg = res.eta.copy()

@@ -104,6 +104,7 @@ class Column:
     kappa_max: float = 1.0      # cap on the UV rise factor
     thomson: bool = False    # add electron scattering sigma_T n_e
     vturb: Optional[np.ndarray] = None  # micro-turbulence [cm/s]; None = 0
+    vlos: Optional[np.ndarray] = None   # line-of-sight velocity [cm/s], > 0 upward (towards the top); None = static
 
     @property
     def n_depth(self) -> int:
@@ -225,6 +226,53 @@ def chromosphere(n_depth: int = 82, m_top: float = 1e-5, m_bot: float = 10.0,
         z[k] = z[k - 1] - (m[k] - m[k - 1]) * 0.5 * (1.0 / rho[k - 1] + 1.0 / rho[k])
     return Column(z=z, T=T, ne=ne, ntot=abundance * nH, rho=rho, kappa=1.0,
                   kappa_nu_ref=_C / 400e-7, kappa_power=6.0, kappa_max=1e3, thomson=True)
+
+
+def optimized_depth_grid(col: Column, n_depth: Optional[int] = None, wt_tau: float = 1.0,
+                         wt_T: float = 1.0, wt_v: float = 1.0, v_scale: float = 2e5) -> Column:
+    """Depth grid that places points where the column's structure changes
+    (Sect. 3.4, after the depth optimisation of the Multi code extended to
+    velocity gradients): the new points equidistribute the arc length of
+    (wt_tau log10 m, wt_T log10 T, wt_v v / v_scale) along the old grid (m the
+    column mass, standing in for the optical depth scale), with the same number
+    of points unless ``n_depth`` is given; every quantity is interpolated
+    linearly in the old depth index. An input recipe: both the library and the
+    oracle receive the re-gridded column."""
+    nz = col.n_depth if n_depth is None else int(n_depth)
+    m = np.cumsum(np.concatenate([[0.0], 0.5 * (col.rho[1:] + col.rho[:-1]) * np.abs(np.diff(col.z))]))
+    m = m + max(m[1], 1e-30)                       # strictly positive column mass
+    v = np.zeros(col.n_depth) if col.vlos is None else col.vlos
+    feats = np.stack([wt_tau * np.log10(m), wt_T * np.log10(col.T), wt_v * v / v_scale], axis=1)
+    arc = np.concatenate([[0.0], np.cumsum(np.sqrt(np.sum(np.diff(feats, axis=0) ** 2, axis=1)))])
+    target = np.linspace(0.0, arc[-1], nz)
+    idx = np.interp(target, arc, np.arange(col.n_depth))    # fractional old index of each new point
+
+    def lin(a):
+        return None if a is None else np.interp(idx, np.arange(col.n_depth), a)
+
+    return replace(col, z=lin(col.z), T=lin(col.T), ne=lin(col.ne), ntot=lin(col.ntot), rho=lin(col.rho),
+                   vturb=lin(col.vturb), vlos=lin(col.vlos))
+
+
+def velocity_chromosphere(n_depth: int = 82, v_top: float = 6e5, x_jump: float = -3.8, width: float = 0.08,
+                          abundance: float = 2.2e-6, optimize: bool = True) -> Column:
+    """The synthetic chromosphere with a sharp line-of-sight velocity gradient
+    at the base of the chromosphere (Sect. 3.4: a jump near the lower
+    chromosphere, positive velocity above it): v = v_top / (1 + exp((x - x_jump)
+    / width)) with x = log10 column mass, zero below the jump; then re-gridded
+    by ``optimized_depth_grid`` so that the jump is resolved by several points."""
+    base = chromosphere(4 * n_depth, abundance=abundance)
+    x = np.log10(np.logspace(-5, 1, 4 * n_depth))
+    v = v_top / (1.0 + np.exp((x - x_jump) / width))
+    col = replace(base, vlos=v)
+    return optimized_depth_grid(col, n_depth) if optimize else chromosphere(n_depth, abundance=abundance)
+
+
+def config2_velocity(seed: int = 0, n_depth: int = 82, nu_scale: float = 1.0) -> Workload:
+    """Config 2 with the velocity gradient of Sect. 3.4 (FP64)."""
+    atom = ca_like_atom(seed, nu_scale)
+    return Workload(name="Ca II-like 6-level, 82-depth chromosphere with a velocity gradient", atom=atom,
+                    columns=[velocity_chromosphere(n_depth)], n_mu=5, precision="fp64", init="lte")
 
 
 def _line_window(a: float) -> float:
@@ -384,7 +432,8 @@ def tiny_workload(n_depth: int = 6, n_nu_line: int = 5, n_nu_cont: int = 3,
     return Workload(name="tiny three-level", atom=atom, columns=[col], n_mu=2)
 
 
-__all__ = ["Line", "Continuum", "Atom", "Column", "Workload", "config1", "config2",
+__all__ = ["Line", "Continuum", "Atom", "Column", "Workload", "config1", "config2", "config2_velocity",
+           "velocity_chromosphere", "optimized_depth_grid",
            "config3", "config4", "config5", "two_level_atom", "two_level_slab",
            "chromosphere", "ca_like_atom", "h_like_atom", "perturbed_populations",
            "tiny_workload", "replace"]
