@@ -50,7 +50,8 @@ def parse():
                    help="timed steps (default: 40 single-column solves, 10 batched solves or oracle steps)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="batch", choices=["batch", "ca", "two-level", "h", "serve", "rtol"])
+    p.add_argument("--workload", default="batch",
+                   choices=["batch", "ca", "two-level", "h", "ca-velocity", "serve", "rtol"])
     p.add_argument("--columns", type=int, default=4096, help="batch workload: number of columns")
     p.add_argument("--requests", type=int, default=10000, help="serve workload: number of requests")
     p.add_argument("--rate", type=float, default=2000.0, help="serve workload: Poisson arrival rate [1/s]")
@@ -62,7 +63,7 @@ def parse():
     if args.steps is None:
         # a single-column solve takes tens of ms: 40 of them give the clock
         # sampler a timed region of about a second
-        single = args.workload in ("ca", "two-level", "h")
+        single = args.workload in ("ca", "two-level", "h", "ca-velocity")
         args.steps = 40 if (single and args.impl == "ours") else 10
     return args
 
@@ -70,6 +71,8 @@ def parse():
 def workload(name):
     if name == "two-level":
         return W.config1(), "fp64"
+    if name == "ca-velocity":
+        return W.config2_velocity(), "fp64"
     if name == "h":
         return W.config3(), "mixed"
     return W.config2(), "fp64"
@@ -299,7 +302,8 @@ def cpu_baseline_batch(wl, start, pool, futures, workers, t0):
 # the tangent adds the differentiated recurrence).
 ALG_OPS = {"value": (10, 2), "jvp": (26, 2)}
 FORMAL_KERNELS = {0: "k_formal<double> + k_ray_sum (per-ray buffers)", 1: "k_formal_fused<double>",
-                  2: "k_formal_sweep (thread per frequency)", 3: "k_formal_sweep_warp (warp per frequency pair)"}
+                  2: "k_formal_sweep (thread per frequency)", 3: "k_formal_sweep_warp (warp per frequency pair)",
+                  4: "k_mv_formal (moving column, thread per ray)"}
 
 
 def measured_peaks(B, ctx):

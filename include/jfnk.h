@@ -131,6 +131,14 @@ typedef struct {
   double kappa, kappa_nu_ref, kappa_power, kappa_max;
   int thomson;
   int n_mu;                     /* Gauss-Legendre points on ]0,1[, 1..JFNK_MAX_MU */
+  const double* vlos;           /* [n_depth] line-of-sight velocity [cm/s], > 0 towards
+                                   the top (Sect. 3.4); NULL or all zero: static. A
+                                   moving column's lines are Doppler-shifted per
+                                   direction: every ray has its own profile, opacity
+                                   and source function (FP64 evaluations and
+                                   Algorithm 2 with GMRES or BiCGSTAB, exact or
+                                   difference JVPs, the first preconditioner
+                                   solution; no RH92 and no mixed precision)     */
 } jfnk_atmos_desc;
 
 /* Formal-solution kernel of a batch (all give the solution of Eqs. Iplus/
@@ -139,7 +147,8 @@ typedef enum {
   JFNK_FORMAL_PER_RAY = 0,       /* per-ray buffers, separate ray-sum kernel      */
   JFNK_FORMAL_FUSED = 1,         /* FP64: block per frequency group, shared memory */
   JFNK_FORMAL_SWEEP_THREAD = 2,  /* mixed: thread per frequency, all angles        */
-  JFNK_FORMAL_SWEEP_WARP = 3     /* mixed: warp per frequency pair, lane per ray   */
+  JFNK_FORMAL_SWEEP_WARP = 3,    /* mixed: warp per frequency pair, lane per ray   */
+  JFNK_FORMAL_MOVING = 4         /* moving columns: thread per ray, per-ray opacity */
 } jfnk_formal_kernel;
 
 /* Jacobian-vector products inside GMRES (Sect. 2.4, Fig. 2). The default is
@@ -264,7 +273,9 @@ int jfnk_atmos_info(const jfnk_atmos* a, int* n_depth, int* n_nu, int* n_levels,
  * 2 collision rates C[k][i][j] [nz*nl*nl], 3 V_t on its window [sum_t w_t * nz]
  * (transition-major, window-point-major, depth fastest), 4 g_t likewise,
  * 5 quadrature weights omega_t on the window [sum_t w_t], 6 chi_c [nq*nz],
- * 7 eta_c [nq*nz]. ``count`` is the capacity of ``out`` in doubles. */
+ * 7 eta_c [nq*nz], 8 (moving columns) V_t seen along each direction
+ * [2 n_mu][sum_t w_t][nz] (outgoing mu_1..mu_n, then ingoing). ``count`` is
+ * the capacity of ``out`` in doubles. */
 int jfnk_atmos_table(const jfnk_atmos* a, int which, double* out, size_t count);
 
 /* ---- the hot path --------------------------------------------------------- */

@@ -44,6 +44,7 @@ JFNK_FORMAL_PER_RAY = 0
 JFNK_FORMAL_FUSED = 1
 JFNK_FORMAL_SWEEP_THREAD = 2
 JFNK_FORMAL_SWEEP_WARP = 3
+JFNK_FORMAL_MOVING = 4
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -70,7 +71,7 @@ class jfnk_atmos_desc(C.Structure):
     _fields_ = [("n_depth", C.c_int), ("z", _dp), ("T", _dp), ("ne", _dp), ("ntot", _dp),
                 ("rho", _dp), ("vturb", _dp), ("kappa", C.c_double), ("kappa_nu_ref", C.c_double),
                 ("kappa_power", C.c_double), ("kappa_max", C.c_double), ("thomson", C.c_int),
-                ("n_mu", C.c_int)]
+                ("n_mu", C.c_int), ("vlos", _dp)]
 
 
 class jfnk_options(C.Structure):
@@ -266,12 +267,14 @@ class Atmosphere:
         lib = ctx.lib
         keep = [_f64(col.z), _f64(col.T), _f64(col.ne), _f64(col.ntot), _f64(col.rho)]
         vt = None if getattr(col, "vturb", None) is None else _f64(col.vturb)
-        self._keep = keep + [vt]
+        vl = None if getattr(col, "vlos", None) is None else _f64(col.vlos)
+        self._keep = keep + [vt, vl]
         p = [k.ctypes.data_as(_dp) for k in keep]
         d = jfnk_atmos_desc(len(keep[0]), p[0], p[1], p[2], p[3], p[4],
                             vt.ctypes.data_as(_dp) if vt is not None else None,
                             col.kappa, getattr(col, "kappa_nu_ref", 0.0), getattr(col, "kappa_power", 0.0),
-                            getattr(col, "kappa_max", 1.0), 1 if col.thomson else 0, n_mu)
+                            getattr(col, "kappa_max", 1.0), 1 if col.thomson else 0, n_mu,
+                            vl.ctypes.data_as(_dp) if vl is not None else None)
         h = C.c_void_p()
         check(lib.jfnk_create_atmosphere(ctx.h, atom.h, C.byref(d), C.byref(h)), "jfnk_create_atmosphere")
         self.h = h

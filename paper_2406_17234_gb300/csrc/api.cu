@@ -341,6 +341,10 @@ int ensure_dJdn(Batch* b, cudaStream_t s) {
 static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
                          const jfnk_options* o, double* const* n_in, double* const* J_in,
                          jfnk_mem where, cudaStream_t s) {
+  if (b->formal_kind == FORMAL_MOVING &&
+      (o->rh92_warmup > 0 || o->solver != JFNK_SOLVER_JFNK || o->precond > 1))
+    return fail(JFNK_E_INVALID,
+                "moving columns: Algorithm 2 without an RH92 start, with the first preconditioner solution or none");
   SolverOpts so;
   options_to_device(o, &so);
   JFNK_CUDA(cudaMemcpyAsync(b->d_opts, &so, sizeof(so), cudaMemcpyHostToDevice, s));
@@ -455,7 +459,8 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.formal_threads = b->formal_threads;
       S.formal_kernel = b->formal_kind == FORMAL_SWEEP
                             ? (b->sweep_variant == 2 ? JFNK_FORMAL_SWEEP_WARP : JFNK_FORMAL_SWEEP_THREAD)
-                            : (b->formal_kind == FORMAL_FUSED ? JFNK_FORMAL_FUSED : JFNK_FORMAL_PER_RAY);
+                            : (b->formal_kind == FORMAL_FUSED ? JFNK_FORMAL_FUSED
+                               : (b->formal_kind == FORMAL_MOVING ? JFNK_FORMAL_MOVING : JFNK_FORMAL_PER_RAY));
     }
     if (status != JFNK_OK && *worst == JFNK_OK) *worst = status;
   }
@@ -662,6 +667,9 @@ int jfnk_atmos_table(const jfnk_atmos* a, int which, double* out, size_t count) 
     case 5: src = T.t_w; n = (size_t)M.nwin; break;
     case 6: src = T.chi_c; n = (size_t)M.nq * M.nz; break;
     case 7: src = T.eta_c; n = (size_t)M.nq * M.nz; break;
+    case 8:
+      if (!T.Vd) return fail(JFNK_E_INVALID, "table 8 exists for moving columns only");
+      src = T.Vd; n = 2 * (size_t)M.nmu * M.nwin * M.nz; break;
     default: return fail(JFNK_E_INVALID, "unknown table");
   }
   if (count < n) return fail(JFNK_E_INVALID, "output buffer too small");
@@ -736,6 +744,7 @@ int jfnk_block_jacobi_variant(jfnk_ctx* ctx, const jfnk_atmos* a, int precision,
   if (rc) return rc;
   if (!n || !P) return fail(JFNK_E_INVALID, "n and P are required");
   if (variant < 1 || variant > 3) return fail(JFNK_E_INVALID, "variant must be 1, 2 or 3");
+  if (a->d.moving && variant != 1) return fail(JFNK_E_INVALID, "moving columns: the first solution only");
   std::lock_guard<std::mutex> lk(ctx->mu);
   Batch* b;
   if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;
@@ -764,6 +773,7 @@ int jfnk_rh92_update(jfnk_ctx* ctx, const jfnk_atmos* a, int precision, const do
   int rc = check_common(ctx, a, precision, where);
   if (rc) return rc;
   if (!n || !n_out) return fail(JFNK_E_INVALID, "n and n_out are required");
+  if (a->d.moving) return fail(JFNK_E_INVALID, "RH92 is not available for moving columns");
   std::lock_guard<std::mutex> lk(ctx->mu);
   Batch* b;
   if ((rc = get_single(a, precision == JFNK_MIXED, &b))) return rc;

@@ -94,6 +94,8 @@ struct ColTables {
   const double* dz;       // [nz-1] |z_k - z_{k+1}|
   const double* mu;       // [nmu]
   const double* wmu;      // [nmu]
+  const double* Vd;       // [2 nmu][nwin][nz] V_ij seen along each direction (outgoing
+                          // mu_1..mu_n, then ingoing): a moving column; null when static
   const float4* ang32;    // [nmu] (1/(2 mu), w_mu/2, 2 mu, 0), each the FP64 value rounded once
   const float2* dz32;     // [nz-1] (|dz|, 1/|dz|) likewise
   const double* chi_c;    // [nq][nz]
@@ -213,6 +215,15 @@ struct ColWork {
   float* etab32;    // [nq][nz] its background part eta_c + chi_sca J^dagger (mixed mode)
   double* np;       // [N] populations of a finite-difference evaluation (n + s eps u)
   double* fdp;      // [N] F(n + eps u) of a central difference
+  // moving column (per-ray path, FP64): [2 nmu][nq][nz] each
+  double* mchi;     // opacity of each direction
+  double* mS;       // source function of each direction
+  double* mdchi;    // their tangents
+  double* mdS;
+  double* mI;       // intensity of each ray
+  double* mdI;      // its tangent
+  double* mLX;      // dI^k/dchi^k of each ray (base evaluations)
+  double* mLE;      // dI^k/deta^k
   double* dJdn;     // [nq][nz][nl] lagged d J/d n_j of the second preconditioner
                     // solution (null until a solve asks for it)
   SolverState* st;

@@ -51,6 +51,7 @@ struct AtomData {
 
 struct AtmosData {
   int nz = 0, nq = 0, nl = 0, nt = 0, nmu = 0, nwin = 0;
+  bool moving = false;                // a line-of-sight velocity field (per-direction profiles)
   double ray_points = 0;
   DeviceArena arena;
   ColTables tables{};
@@ -98,7 +99,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
 
 // Formal-solution kernels: per-ray buffers + ray-sum kernel (any size),
 // in-block fused kernel (FP64), per-frequency sweep kernel (mixed precision).
-enum FormalKind { FORMAL_UNFUSED = 0, FORMAL_FUSED = 1, FORMAL_SWEEP = 2 };
+enum FormalKind { FORMAL_UNFUSED = 0, FORMAL_FUSED = 1, FORMAL_SWEEP = 2, FORMAL_MOVING = 3 };
 
 // A batch of columns with their work buffers, resident on the device.
 struct Batch {
@@ -182,6 +183,10 @@ int sweep_autotune(Batch* b, cudaStream_t s);
 // filled by the host or the tables) to float pairs in place (to_pairs), or
 // their J_new back to FP64; FP64 columns are left alone.
 int launch_j_pairs(const ColDesc* d_cols, int ncols, size_t max_qz, cudaStream_t s, bool to_pairs);
+// Moving columns (velocity.cu): one F-class evaluation of every column of a
+// batch whose formal kind is FORMAL_MOVING (opacity per direction, formal
+// solution per ray, moments, rate integrals; then the common assembly).
+int launch_moving_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // Kernel attributes of the current device, set once per context (residual.cu).
 int prepare_kernels();
 // Opacity kernel of the mixed mode (tangent columns skipped when the sweeps form it).

@@ -1037,6 +1037,15 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     JFNK_CUDA(cudaGetLastError());
     return JFNK_OK;
   }
+  if (b.formal_kind == FORMAL_MOVING) {
+    // per-ray opacity, formal solution and rate integrals (velocity.cu), then
+    // the common assembly
+    int rc = launch_moving_evaluation(b, s, ev0, ev1);
+    if (rc) return rc;
+    k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
+    JFNK_CUDA(cudaGetLastError());
+    return JFNK_OK;
+  }
   if (b.formal_kind == FORMAL_SWEEP) {
     // (float tangent direction,) opacity, then the per-frequency sweeps; with
     // events (a profiled tick) the tangent sweep is bracketed by ev2/ev3 and

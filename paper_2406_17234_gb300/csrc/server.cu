@@ -319,6 +319,7 @@ int jfnk_server_submit(jfnk_server* sv, const jfnk_atmos* a, long long id, doubl
   if (a->ctx != sv->ctx) return fail(JFNK_E_INVALID, "atmosphere belongs to another context");
   int rc = check_shape(sv, a);
   if (rc) return rc;
+  if (a->d.moving) return fail(JFNK_E_INVALID, "the server solves static columns only");
   const jfnk_options* o = opts ? opts : &sv->desc.opts;
   if ((rc = validate_options(o))) return rc;
   if (o->precision != sv->desc.opts.precision || o->krylov_max > sv->kmax || o->init != JFNK_INIT_LTE ||

@@ -299,6 +299,33 @@ __global__ void k_window_tables(int nt, const TransDev* tr, const int* t_q0, con
   }
 }
 
+// A moving column: the line profile seen along each direction d (signed
+// cosine mu_d: +mu for the outgoing rays, -mu for the ingoing ones) is centred
+// at nu_0 (1 + mu_d v/c) (Sect. 3.4); continua are not shifted. Unnormalised.
+__global__ void k_window_tables_dir(int nt, const TransDev* tr, const int* t_q0, const int* t_base,
+                                    const int* win_t, int nwin, int nz, int nmu, const double* nu,
+                                    const double* T, const double* vturb, const double* vlos,
+                                    const double* mu, AtomDev at, const double* V, double* Vd) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)nwin * nz;
+  if (i >= 2 * (size_t)nmu * per) return;
+  const int dd = (int)(i / per);
+  const size_t pk = i - (size_t)dd * per;
+  const int p = (int)(pk / nz), k = (int)(pk % nz);
+  const int t = win_t[p];
+  const TransDev d = tr[t];
+  if (d.kind != 0) {
+    Vd[i] = V[pk];
+    return;
+  }
+  const double mud = dd < nmu ? mu[dd] : -mu[dd - nmu];
+  const int q = t_q0[t] + (p - t_base[t]);
+  const double vt = vturb ? vturb[k] : 0.0;
+  const double dnud = d.nu0 / kC * sqrt(2.0 * kKB * T[k] / (at.mass * kAMU) + vt * vt);
+  const double x = (nu[q] - d.nu0 * (1.0 + mud * vlos[k] / kC)) / dnud;
+  Vd[i] = (kPi * kQE * kQE / (kME * kC)) * d.f * voigt_H(d.damping, x) / (1.7724538509055160273 * dnud);
+}
+
 // Float copies of the (normalised) window tables for mixed-mode tangents.
 __global__ void k_float_copy(int nwin, int nz, const double* V, const double* G, float* V32, float* G32,
                              float* V32T, float* G32T) {
@@ -312,11 +339,16 @@ __global__ void k_float_copy(int nwin, int nz, const double* V, const double* G,
   G32T[k * nwin + p] = g;
 }
 
-// Renormalise each line profile so that sum_q omega_t(q) phi(q, k) = 1.
+// Renormalise each line profile so that sum_q omega_t(q) phi(q, k) = 1 (for
+// every direction's copy when ndir > 1: the tables follow one another).
 __global__ void k_normalise_lines(int nt, const TransDev* tr, const int* t_q0, const int* t_q1,
-                                  const int* t_base, const double* t_w, int nz, double* V) {
+                                  const int* t_base, const double* t_w, int nz, double* V, int ndir = 1,
+                                  size_t dir_stride = 0) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nt * nz) return;
+  if (i >= nt * nz * ndir) return;
+  const int dd = i / (nt * nz);
+  i -= dd * nt * nz;
+  V += (size_t)dd * dir_stride;
   int t = i / nz, k = i % nz;
   const TransDev d = tr[t];
   if (d.kind != 0) return;
@@ -447,6 +479,13 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   }
   const int nq = A.nq, nl = A.nl, nt = A.nt, nwin = A.nwin, nmu = d->n_mu;
   M->nz = nz; M->nq = nq; M->nl = nl; M->nt = nt; M->nmu = nmu; M->nwin = nwin;
+  M->moving = false;
+  if (d->vlos)
+    for (int k = 0; k < nz; ++k) {
+      if (!std::isfinite(d->vlos[k]) || std::fabs(d->vlos[k]) >= 0.1 * kC)
+        return fail(JFNK_E_INVALID, "vlos must be finite and below c/10");
+      if (d->vlos[k] != 0.0) M->moving = true;
+    }
   M->ray_points = (double)nq * 2.0 * nmu * nz;
   // one device arena for every table
   DeviceArena& ar = M->arena;
@@ -470,6 +509,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   size_t o_W2 = ar.take<float2>(nwin), o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
   size_t o_linc = ar.take<int>((size_t)nl * (nt + 1));
   size_t o_ang32 = ar.take<float4>(nmu), o_dz32 = ar.take<float2>(nz - 1);
+  size_t o_vlos = ar.take<double>(M->moving ? nz : 0);
   const size_t host_prefix = ar.cursor;
   size_t o_V = ar.take<double>((size_t)nwin * nz), o_G = ar.take<double>((size_t)nwin * nz);
   size_t o_chic = ar.take<double>((size_t)nq * nz), o_etac = ar.take<double>((size_t)nq * nz);
@@ -482,6 +522,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   size_t o_V2 = ar.take<float2>((size_t)nwin * nz), o_gV2 = ar.take<float2>((size_t)nwin * nz),
          o_chibg2 = ar.take<float2>((size_t)nq * nz), o_etac2 = ar.take<float2>((size_t)nq * nz),
          o_chisca2 = ar.take<float2>(nz);
+  size_t o_Vd = ar.take<double>(M->moving ? 2 * (size_t)nmu * nwin * nz : 0);
   int rc = ar.allocate();
   if (rc) return rc;
   // host-side staging
@@ -588,6 +629,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   std::vector<float2> dz32(nz - 1);
   for (int k = 0; k + 1 < nz; ++k) dz32[k] = make_float2((float)dzv[k], (float)(1.0 / dzv[k]));
   JFNK_CUDA(up(o_ang32, ang32.data(), nmu * sizeof(float4)));
+  if (M->moving) JFNK_CUDA(up(o_vlos, d->vlos, nz * 8));
   JFNK_CUDA(up(o_dz32, dz32.data(), (nz - 1) * sizeof(float2)));
   JFNK_CUDA(up(o_dz, dzv.data(), (nz - 1) * 8));
   JFNK_CUDA(up(o_mu, mu.data(), nmu * 8));
@@ -618,6 +660,16 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   k_normalise_lines<<<(nt * nz + tb - 1) / tb, tb, 0, s>>>(
       nt, ar.ptr<TransDev>(o_tr), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tq1), ar.ptr<int>(o_tbase),
       ar.ptr<double>(o_tw), nz, ar.ptr<double>(o_V));
+  if (M->moving) {
+    const size_t nd = 2 * (size_t)nmu, per = (size_t)nwin * nz;
+    k_window_tables_dir<<<(int)((nd * per + tb - 1) / tb), tb, 0, s>>>(
+        nt, ar.ptr<TransDev>(o_tr), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tbase), ar.ptr<int>(o_winT), nwin, nz, nmu,
+        ar.ptr<double>(o_nu), T, d->vturb ? ar.ptr<double>(o_vt) : nullptr, ar.ptr<double>(o_vlos),
+        ar.ptr<double>(o_mu), at, ar.ptr<double>(o_V), ar.ptr<double>(o_Vd));
+    k_normalise_lines<<<(int)((nd * nt * nz + tb - 1) / tb), tb, 0, s>>>(
+        nt, ar.ptr<TransDev>(o_tr), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tq1), ar.ptr<int>(o_tbase),
+        ar.ptr<double>(o_tw), nz, ar.ptr<double>(o_Vd), (int)nd, per);
+  }
   k_rate_weights<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
       nwin, nz, ar.ptr<int>(o_winT), ar.ptr<int>(o_tq0), ar.ptr<int>(o_tbase), ar.ptr<double>(o_tw),
       ar.ptr<double>(o_rw), ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<double>(o_gV),
@@ -662,6 +714,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   tb_.lvl_inc = ar.ptr<int>(o_linc);
   tb_.mu = ar.ptr<double>(o_mu); tb_.wmu = ar.ptr<double>(o_wmu);
   tb_.ang32 = ar.ptr<float4>(o_ang32); tb_.dz32 = ar.ptr<float2>(o_dz32);
+  tb_.Vd = M->moving ? ar.ptr<double>(o_Vd) : nullptr;
   tb_.chi_c = ar.ptr<double>(o_chic); tb_.eta_c = ar.ptr<double>(o_etac);
   tb_.chi_sca = ar.ptr<double>(o_sca); tb_.Bn = ar.ptr<double>(o_B); tb_.C = ar.ptr<double>(o_C);
   tb_.ntot = ar.ptr<double>(o_ntot); tb_.nstar = ar.ptr<double>(o_nstar);

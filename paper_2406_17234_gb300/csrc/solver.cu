@@ -37,7 +37,7 @@ void DeviceArena::release() {
 struct ColLayout {
   size_t n, v, v32, chiT, S32T, dSkT, dchiT, dS32T, dJ32T, Jdag, Jnew, istar, chi, S, dSk, dchi, dS, ddSk, H, HI, dH,
       LX, LE, part, J, dJ, Lchi, Leta, Lchi32, Leta32, Rup, Rdn, dRup, dRdn, Apart, rh, F, dF, P, piv, Iem, Vb, Hh, cs, sn, gv, x,
-      w, nprev, np, fdp, eta, etab32, n2;
+      w, nprev, np, fdp, eta, etab32, n2, mchi, mS, mdchi, mdS, mI, mdI, mLX, mLE;
 };
 
 size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout* out) {
@@ -78,6 +78,11 @@ size_t column_bytes(const AtmosData& M, int kind, int mixed, int kmax, ColLayout
   o.np = ar.take<double>(N); o.fdp = ar.take<double>(N);
   o.eta = ar.take<double>(nq * nz); o.etab32 = ar.take<float>(mixed ? nq * nz : 0);
   o.n2 = ar.take<float2>(mixed ? N : 0);
+  // moving columns: per-ray opacity, source function, intensity, tangents and local derivatives
+  const size_t MR = kind == FORMAL_MOVING ? 2 * nmu * nq * nz : 0;
+  o.mchi = ar.take<double>(MR); o.mS = ar.take<double>(MR); o.mdchi = ar.take<double>(MR);
+  o.mdS = ar.take<double>(MR); o.mI = ar.take<double>(MR); o.mdI = ar.take<double>(MR);
+  o.mLX = ar.take<double>(MR); o.mLE = ar.take<double>(MR);
   if (out) *out = o;
   return ar.cursor;
 }
@@ -122,6 +127,11 @@ void column_bind(char* base, const AtmosData& M, int kind, int mixed, int kmax, 
   w.np = (double*)P(o.np); w.fdp = (double*)P(o.fdp);
   w.eta = (double*)P(o.eta); w.etab32 = mixed ? (float*)P(o.etab32) : nullptr;
   w.n2 = mixed ? (float2*)P(o.n2) : nullptr;
+  if (kind == FORMAL_MOVING) {
+    w.mchi = (double*)P(o.mchi); w.mS = (double*)P(o.mS); w.mdchi = (double*)P(o.mdchi);
+    w.mdS = (double*)P(o.mdS); w.mI = (double*)P(o.mI); w.mdI = (double*)P(o.mdI);
+    w.mLX = (double*)P(o.mLX); w.mLE = (double*)P(o.mLE);
+  }
   w.st = st;
 }
 
@@ -143,13 +153,18 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     b->max_nmu = std::max(b->max_nmu, c->nmu);
   }
   b->max_overlap = mov;
+  bool moving = false;
+  for (auto* c : cols) moving = moving || c->moving;
+  if (moving && mixed)
+    return fail(JFNK_E_INVALID, "moving columns (a velocity field) are solved in JFNK_FP64 only");
   {
     int dev = 0;
     JFNK_CUDA(cudaGetDevice(&dev));
     JFNK_CUDA(cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev));
   }
-  b->formal_qb = mixed ? 0 : fused_default_qb(b->max_nz, b->max_nmu, false);
-  b->formal_kind = mixed ? FORMAL_SWEEP : (b->formal_qb > 0 ? FORMAL_FUSED : FORMAL_UNFUSED);
+  b->formal_qb = mixed || moving ? 0 : fused_default_qb(b->max_nz, b->max_nmu, false);
+  b->formal_kind = moving ? FORMAL_MOVING
+                          : (mixed ? FORMAL_SWEEP : (b->formal_qb > 0 ? FORMAL_FUSED : FORMAL_UNFUSED));
   std::vector<size_t> off(nc);
   for (int c = 0; c < nc; ++c)
     off[c] = ar.take<char>(column_bytes(*cols[c], b->formal_kind, mixed, kmax, nullptr));
@@ -171,6 +186,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   JFNK_CUDA(cudaMemcpy(b->d_cols, b->h_cols.data(), nc * sizeof(ColDesc), cudaMemcpyHostToDevice));
   JFNK_CUDA(cudaMemset(b->d_state, 0, nc * sizeof(SolverState)));
   if (b->formal_kind == FORMAL_SWEEP) return sweep_prepare(b);
+  if (b->formal_kind == FORMAL_MOVING) return JFNK_OK;
   return fused_prepare(b);
 }
 

@@ -78,6 +78,7 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
                                     void* stream) {
   if (!ctx || !a || !n || !F) return fail(JFNK_E_INVALID, "ctx, atmosphere, n and F are required");
   if (a->ctx != ctx) return fail(JFNK_E_INVALID, "atmosphere belongs to another context");
+  if (a->d.moving) return fail(JFNK_E_INVALID, "moving columns need jfnk_residual (per-ray buffers)");
   JFNK_CUDA(cudaSetDevice(ctx->device));
   const AtmosData& M = a->d;
   const size_t nz = M.nz, nq = M.nq, nl = M.nl, nt = M.nt, nmu = M.nmu;

@@ -1,0 +1,231 @@
+// Moving columns (a line-of-sight velocity field, Sect. 3.4): each direction
+// of propagation sees its own Doppler-shifted line profile, so opacity and
+// source function are per direction rather than shared by the rays of a
+// frequency, the formal solution runs per ray with them, and the rate
+// integrals weight every ray's intensity with the profile that ray sees:
+//
+//   chi_d = chi_c + chi_sca + sum_t V_t,d (n_lo - g n_up),
+//   eta_d = eta_c + chi_sca J^dagger + sum_t (2 h nu^3/c^2) g V_t,d n_up,
+//   R_ij = sum_nu W sum_d h_d V_t,d I_d,  R_ji = sum_nu W g sum_d h_d V_t,d (2 h nu^3/c^2 + I_d),
+//   J = sum_d h_d I_d (for the background scattering), h_d = w_mu/2,
+//
+// with W = omega_t(nu) 4 pi/(h nu). The block-Jacobi blocks (first solution
+// of Sect. 2.5.2) take per ray the local derivatives dI^k/dchi^k and
+// dI^k/deta^k of App. A.2 with that ray's beta and gamma. FP64 throughout; the
+// per-ray intensities, their tangents and local derivatives are stored
+// ([2 n_mu][nq][nz] each), the assembly and the Krylov/Newton step are the
+// static path's.
+#include "formal_coef.cuh"
+
+namespace jfnk {
+
+namespace {
+
+__device__ __forceinline__ int mv_mode(const ColDesc& cd) {
+  if (cd.forced_mode >= 0) return cd.forced_mode;
+  switch (cd.w.st->phase) {
+    case PH_BASE: return EV_BASE;
+    case PH_JVP:
+    case PH_RESTART: return cd.w.st->fd_scheme ? EV_FD : EV_TANGENT;
+    default: return EV_SKIP;   // RH92 is not defined here (rejected at the API)
+  }
+}
+
+__device__ __forceinline__ const double* mv_dir(const ColDesc& cd) {
+  if (cd.forced_mode >= 0) return cd.w.v;
+  const int N = cd.t.nz * cd.t.nl;
+  return cd.w.st->phase == PH_RESTART ? cd.w.x : cd.w.Vb + (size_t)cd.w.st->j * N;
+}
+
+// h_d = w_mu/2 of direction d (outgoing mu_1..mu_n, then ingoing)
+__device__ __forceinline__ double mv_h(const ColTables& T, int d) {
+  return 0.5 * T.wmu[d < T.nmu ? d : d - T.nmu];
+}
+
+}  // namespace
+
+// Opacity and source function (or their tangents) of every (direction, nu, depth).
+__global__ void k_mv_opacity(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = mv_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nl = T.nl, nd = 2 * T.nmu;
+  const size_t per = (size_t)nq * nz;
+  const double* n = eval_pops(cd, mode);
+  const double* v = mode == EV_TANGENT ? mv_dir(cd) : nullptr;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd * per; i += (size_t)gridDim.x * blockDim.x) {
+    const int d = (int)(i / per);
+    const size_t qk = i - (size_t)d * per;
+    const int q = (int)(qk / nz), k = (int)(qk - (size_t)q * nz);
+    const double* Vd = T.Vd + (size_t)d * T.nwin * nz;
+    double a = 0.0, e = 0.0;   // sum V (x_lo - g x_up), sum (2 h nu^3/c^2) g V x_up
+    const double* x = (mode == EV_TANGENT ? v : n) + (size_t)k * nl;
+    for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+      const int t = T.q_t[s];
+      const size_t pk = (size_t)(T.t_base[t] + q - T.t_q0[t]) * nz + k;
+      const double V = Vd[pk], gV = T.G[pk] * V;
+      a += V * x[T.t_lo[t]] - gV * x[T.t_up[t]];
+      e += gV * x[T.t_up[t]];
+    }
+    e *= T.c2[q];
+    if (mode == EV_TANGENT) {
+      // tangent at the base point (J^dagger is not perturbed)
+      const double chi = cd.w.mchi[i], S = cd.w.mS[i];
+      cd.w.mdchi[i] = a;
+      cd.w.mdS[i] = (e - S * a) / chi;
+    } else {
+      const double chi = T.chi_c[qk] + T.chi_sca[k] + a;
+      const double eta = T.eta_c[qk] + T.chi_sca[k] * jdag_ptr(cd)[qk] + e;
+      cd.w.mchi[i] = chi;
+      cd.w.mS[i] = eta / chi;
+    }
+  }
+}
+
+// Formal solution of every ray (Eqs. Iplus/Iminus with the App. A.1
+// coefficients; I = B_nu(T_bottom) entering at the bottom, 0 at the top), one
+// thread per (direction, nu): the intensity form of the recurrence,
+//   I^k = I^u e + a S^k + b S^u,  dtau = h (chi^k + chi^u), h = |dz|/(2 mu),
+// and in base evaluations the local derivatives of App. A.2,
+//   dI^k/dchi^k = -(S^k/chi^k) a + h (e (S^u - I^u) - (S^u - S^k) b/dtau),  dI^k/deta^k = a/chi^k,
+// or in tangent evaluations the differentiated recurrence (de = -e ddtau,
+// da = (b/dtau) ddtau, db = (e - b/dtau) ddtau, ddtau = h (dchi^k + dchi^u)).
+__global__ void k_mv_formal(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = mv_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nmu = T.nmu;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= 2 * nmu * nq) return;
+  const int d = r / nq, q = r - d * nq;
+  const bool up = d < nmu;
+  const double mu = T.mu[up ? d : d - nmu];
+  const size_t row = ((size_t)d * nq + q) * nz;
+  const double* chi = cd.w.mchi + row;
+  const double* S = cd.w.mS + row;
+  const bool tan = (mode == EV_TANGENT), base = (mode == EV_BASE);
+  const double* dchi = tan ? cd.w.mdchi + row : nullptr;
+  const double* dS = tan ? cd.w.mdS + row : nullptr;
+  const double* Ib = cd.w.mI + row;   // the base point's intensities (tangent evaluations)
+  double* Iout = tan ? cd.w.mdI + row : cd.w.mI + row;
+  const int k0 = up ? nz - 1 : 0, step = up ? -1 : 1;
+  double I = up ? T.Bn[(size_t)q * nz + nz - 1] : 0.0;   // boundary values (dI = 0 there)
+  if (tan) I = 0.0;
+  Iout[k0] = I;
+  if (base) {
+    cd.w.mLX[row + k0] = 0.0;
+    cd.w.mLE[row + k0] = 0.0;
+  }
+  for (int k = k0 + step; k >= 0 && k < nz; k += step) {
+    const int u = k - step;
+    const double h = T.dz[up ? k : k - 1] / (2.0 * mu);
+    const double dtau = h * (chi[k] + chi[u]);
+    double e, w, a, bq;
+    pl_coef_f(dtau, 1.0 / dtau, e, w, a, bq);
+    const double b = bq * dtau;
+    if (tan) {
+      const double ddtau = h * (dchi[k] + dchi[u]);
+      I = I * e - Ib[u] * e * ddtau + a * dS[k] + bq * ddtau * S[k] + b * dS[u] + (e - bq) * ddtau * S[u];
+    } else {
+      const double Iu = I;
+      I = Iu * e + a * S[k] + b * S[u];
+      if (base) {
+        cd.w.mLX[row + k] = -(S[k] / chi[k]) * a + h * (e * (S[u] - Iu) - (S[u] - S[k]) * bq);
+        cd.w.mLE[row + k] = a / chi[k];
+      }
+    }
+    Iout[k] = I;
+  }
+  if (base && up) cd.w.Iem[(size_t)q * nmu + d] = I;   // the outgoing intensity at the top
+}
+
+// J = sum_d h_d I_d of a base evaluation, written into J_new.
+__global__ void k_mv_moments(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (mv_mode(cd) != EV_BASE) return;
+  const ColTables& T = cd.t;
+  const size_t per = (size_t)T.nq * T.nz;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= per) return;
+  double J = 0.0;
+  for (int d = 0; d < 2 * T.nmu; ++d) J += mv_h(T, d) * cd.w.mI[(size_t)d * per + i];
+  jnew_ptr(cd)[i] = J;
+}
+
+// Rate integrals of transition t at depth k (one thread each): R_ij, R_ji from
+// the rays' intensities (their tangents in tangent evaluations) and, in base
+// evaluations, the block-Jacobi sums A_tj = sum_nu W sum_d h_d chi_t,d
+// (beta_j,d dI_d/dchi_d + gamma_j,d dI_d/deta_d).
+__global__ void k_mv_rates(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  const int mode = mv_mode(cd);
+  if (mode == EV_SKIP) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nq = T.nq, nl = T.nl, nd = 2 * T.nmu;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.nt * nz) return;
+  const int t = i / nz, k = i - t * nz;
+  const bool tan = (mode == EV_TANGENT), base = (mode == EV_BASE);
+  const int q0 = T.t_q0[t], q1 = T.t_q1[t], wb = T.t_base[t];
+  const double* n = eval_pops(cd, mode) + (size_t)k * nl;
+  const double nlo = n[T.t_lo[t]], nup = n[T.t_up[t]];
+  const size_t per = (size_t)nq * nz, vper = (size_t)T.nwin * nz;
+  const double* Iray = tan ? cd.w.mdI : cd.w.mI;
+  double ru = 0.0, rd = 0.0, A[kMaxL];
+  for (int j = 0; j < nl; ++j) A[j] = 0.0;
+  for (int q = q0; q <= q1; ++q) {
+    const int p = wb + q - q0;
+    const size_t pk = (size_t)p * nz + k, qk = (size_t)q * nz + k;
+    const double W = T.t_w[p] * T.rw[q], g = T.G[pk], c2 = T.c2[q];
+    double su = 0.0, sd = 0.0;
+    for (int d = 0; d < nd; ++d) {
+      const double hv = mv_h(T, d) * T.Vd[(size_t)d * vper + pk];
+      const double Id = Iray[(size_t)d * per + qk];
+      su += hv * Id;
+      sd += hv * (tan ? Id : c2 + Id);
+      if (base) {
+        // chi_t,d W h_d times beta_j,d dI/dchi + gamma_j,d dI/deta over the
+        // transitions active at nu
+        const double c = W * hv * (nlo - g * nup);
+        const double lx = cd.w.mLX[(size_t)d * per + qk], le = cd.w.mLE[(size_t)d * per + qk];
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          const double Vs = T.Vd[(size_t)d * vper + ps], gVs = T.G[ps] * Vs;
+          A[T.t_lo[ts]] += c * (Vs * lx);
+          A[T.t_up[ts]] += c * (-gVs * lx + c2 * gVs * le);
+        }
+      }
+    }
+    ru += W * su;
+    rd += W * g * sd;
+  }
+  const size_t o = (size_t)t * nz + k;
+  if (tan) {
+    cd.w.dRup[o] = ru;
+    cd.w.dRdn[o] = rd;
+  } else {
+    cd.w.Rup[o] = ru;
+    cd.w.Rdn[o] = rd;
+    if (base)
+      for (int j = 0; j < nl; ++j) cd.w.Apart[o * nl + j] = A[j];
+  }
+}
+
+int launch_moving_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  const int nc = b.ncols;
+  const long pts = 2L * b.max_nmu * b.max_nq * b.max_nz;
+  const int tb = 256;
+  k_mv_opacity<<<dim3((unsigned)std::min<long>((pts + tb - 1) / tb, 4096), nc), tb, 0, s>>>(b.d_cols);
+  if (ev0) JFNK_CUDA(cudaEventRecordWithFlags(ev0, s, cudaEventRecordExternal));
+  k_mv_formal<<<dim3((2 * b.max_nmu * b.max_nq + 127) / 128, nc), 128, 0, s>>>(b.d_cols);
+  if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
+  k_mv_moments<<<dim3((b.max_nq * b.max_nz + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
+  k_mv_rates<<<dim3((b.max_nt * b.max_nz + 63) / 64, nc), 64, 0, s>>>(b.d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
+}  // namespace jfnk
