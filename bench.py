@@ -674,7 +674,11 @@ def run_batch(args, rank, ws, local, dist):
                                         (1.0 / ((val_pts / peak_rate("value", False, peaks) +
                                                  jvp_pts / peak_rate("jvp", False, peaks)) /
                                                 (jvp_pts + val_pts)))},
-                "measured_peaks": peaks, "timed_in": "a separate profiled batched solve (in-graph events)"}
+                "measured_peaks": peaks, "timed_in": "a separate profiled batched solve (in-graph events)",
+                "launch": {"threads": int(pst[0]["formal_threads"]), "variant": int(pst[0]["formal_kernel"]),
+                           "blocks_per_sm_cap_tangent": int(pst[0]["formal_occ"]),
+                           "blocks_per_sm_cap_base": int(pst[0]["formal_occ_base"]),
+                           "tangent_opacity_in_sweep": int(pst[0]["formal_fuse"])}}
     st0 = allstats[-1]
     line = {"metric": METRIC, "value": pts / (total_ms * 1e-3), "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

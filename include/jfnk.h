@@ -148,7 +148,10 @@ typedef enum {
   JFNK_FORMAL_FUSED = 1,         /* FP64: block per frequency group, shared memory */
   JFNK_FORMAL_SWEEP_THREAD = 2,  /* mixed: thread per frequency, all angles        */
   JFNK_FORMAL_SWEEP_WARP = 3,    /* mixed: warp per frequency pair, lane per ray   */
-  JFNK_FORMAL_MOVING = 4         /* moving columns: thread per ray, per-ray opacity */
+  JFNK_FORMAL_MOVING = 4,        /* moving columns: thread per ray, per-ray opacity */
+  JFNK_FORMAL_SWEEP_THREAD_FUSED = 5 /* mixed: thread per frequency, the tangent sweep
+                                    forming the JVP evaluations' opacity tangent itself
+                                    (at most 8 transitions overlap at any frequency) */
 } jfnk_formal_kernel;
 
 /* Jacobian-vector products inside GMRES (Sect. 2.4, Fig. 2). The default is
@@ -200,8 +203,9 @@ typedef struct {
                            (mixed mode: the tangent and base-type sweeps then run
                            one after the other instead of side by side, so that
                            each is timed alone; the results are the same)       */
-  int formal_variant;   /* mixed mode: 0 autotuned, JFNK_FORMAL_SWEEP_THREAD or
-                           JFNK_FORMAL_SWEEP_WARP forced (identical results)      */
+  int formal_variant;   /* mixed mode: 0 autotuned, JFNK_FORMAL_SWEEP_THREAD,
+                           JFNK_FORMAL_SWEEP_WARP or JFNK_FORMAL_SWEEP_THREAD_FUSED
+                           forced (identical results)                             */
   int precond;          /* block-Jacobi preconditioner after the solutions of
                            Sect. 2.5.2: 1 first (background-scattering derivative
                            neglected; default), 2 second (chi_sca dJ/dn lagged from
@@ -237,6 +241,13 @@ typedef struct {
   int formal_kernel;    /* jfnk_formal_kernel that ran the formal solution          */
   double formal_tan_ms; /* profile, mixed mode: summed duration of the tangent-sweep
                            launches (the JVP evaluations' formal solutions)       */
+  int formal_occ;       /* thread-per-frequency sweep: resident blocks per SM allowed
+                           to the tangent sweep (0: no cap; chosen by the autotuner) */
+  int formal_occ_base;  /* the same for the base-type sweep                        */
+  int formal_fuse;      /* thread-per-frequency sweep: 0 when a separate kernel forms
+                           the opacity tangent of the JVP evaluations, 1 when the
+                           tangent sweep's inward pass forms it, 2 the same held to
+                           80 registers (chosen by the autotuner)                */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */

@@ -45,6 +45,7 @@ JFNK_FORMAL_FUSED = 1
 JFNK_FORMAL_SWEEP_THREAD = 2
 JFNK_FORMAL_SWEEP_WARP = 3
 JFNK_FORMAL_MOVING = 4
+JFNK_FORMAL_SWEEP_THREAD_FUSED = 5
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -89,7 +90,8 @@ class jfnk_stats(C.Structure):
                 ("F_norm0", C.c_double), ("dn_norm", C.c_double), ("ray_points", C.c_double),
                 ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int),
                 ("formal_qb", C.c_int), ("formal_threads", C.c_int), ("formal_kernel", C.c_int),
-                ("formal_tan_ms", C.c_double)]
+                ("formal_tan_ms", C.c_double), ("formal_occ", C.c_int), ("formal_occ_base", C.c_int),
+                ("formal_fuse", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

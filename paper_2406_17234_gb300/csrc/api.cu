@@ -148,8 +148,10 @@ int validate_options(const jfnk_options* o) {
   if (o->solver != JFNK_SOLVER_JFNK && o->solver != JFNK_SOLVER_RH92)
     return fail(JFNK_E_INVALID, "solver must be JFNK_SOLVER_JFNK or JFNK_SOLVER_RH92");
   if (o->formal_variant != 0 && o->formal_variant != JFNK_FORMAL_SWEEP_THREAD &&
-      o->formal_variant != JFNK_FORMAL_SWEEP_WARP)
-    return fail(JFNK_E_INVALID, "formal_variant must be 0, JFNK_FORMAL_SWEEP_THREAD or JFNK_FORMAL_SWEEP_WARP");
+      o->formal_variant != JFNK_FORMAL_SWEEP_WARP && o->formal_variant != JFNK_FORMAL_SWEEP_THREAD_FUSED)
+    return fail(JFNK_E_INVALID,
+                "formal_variant must be 0, JFNK_FORMAL_SWEEP_THREAD, JFNK_FORMAL_SWEEP_WARP or "
+                "JFNK_FORMAL_SWEEP_THREAD_FUSED");
   return JFNK_OK;
 }
 
@@ -311,11 +313,13 @@ static void drop_graphs(Batch* b) {
   }
 }
 
-// Selects a sweep variant and block size; captured graphs with other shapes are dropped.
-static int set_sweep_config(Batch* b, int variant, int size) {
-  if (b->sweep_variant == variant && b->formal_threads == size) return JFNK_OK;
+// Selects a sweep variant, block size and opacity-tangent placement; captured
+// graphs with other shapes are dropped.
+static int set_sweep_config(Batch* b, int variant, int size, int fuse) {
+  if (b->sweep_variant == variant && b->formal_threads == size && b->sweep_fuse == fuse) return JFNK_OK;
   b->sweep_variant = variant;
   b->formal_threads = size;
+  b->sweep_fuse = fuse;
   drop_graphs(b);
   return JFNK_OK;
 }
@@ -382,7 +386,10 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
     const int v = o->formal_variant == JFNK_FORMAL_SWEEP_WARP ? 2 : 1;
     const int size = v == 2 ? sweep_warp_size(b->max_nz) : 128;
     if (size == 0) return fail(JFNK_E_INVALID, "JFNK_FORMAL_SWEEP_WARP: the column is too deep for its shared memory");
-    if ((rc = set_sweep_config(b, v, size))) return rc;
+    const int fuse = o->formal_variant == JFNK_FORMAL_SWEEP_THREAD_FUSED ? 1 : 0;
+    if (fuse && b->max_overlap > kQMetaT)
+      return fail(JFNK_E_INVALID, "JFNK_FORMAL_SWEEP_THREAD_FUSED: more than 8 transitions overlap at a frequency");
+    if ((rc = set_sweep_config(b, v, size, fuse))) return rc;
   } else if (!b->tuned && b->formal_kind != FORMAL_UNFUSED) {
     // tune the formal kernel once per batch, on its own columns: a base
     // evaluation at the initial state, then tangent data along v = n
@@ -399,10 +406,11 @@ static int prepare_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols,
     b->tuned = true;
     b->tuned_variant = b->sweep_variant;
     b->tuned_size = b->formal_threads;
+    b->tuned_fuse = b->sweep_fuse;
     drop_graphs(b);   // graphs captured with other launch shapes are stale
     if ((rc = batch_set_forced_mode(b, -1, s))) return rc;
   } else if (b->tuned && b->formal_kind == FORMAL_SWEEP) {
-    if ((rc = set_sweep_config(b, b->tuned_variant, b->tuned_size))) return rc;
+    if ((rc = set_sweep_config(b, b->tuned_variant, b->tuned_size, b->tuned_fuse))) return rc;
   }
   // mark every column as running for the host poll
   std::vector<int> ones(b->ncols, 1);
@@ -453,12 +461,16 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.ray_points = (double)x.F_calls * cols[c]->d.ray_points;
       S.formal_ms = kernel_ms;
       S.formal_tan_ms = tan_ms;
+      S.formal_occ = b->formal_kind == FORMAL_SWEEP && b->sweep_variant != 2 ? b->sweep_occ : 0;
+      S.formal_occ_base = b->formal_kind == FORMAL_SWEEP && b->sweep_variant != 2 ? b->sweep_occ_base : 0;
+      S.formal_fuse = b->formal_kind == FORMAL_SWEEP && sweep_fused(*b) ? b->sweep_fuse : 0;
       S.formal_launches = active;
       S.kernel_launches = (int)(b->replays * b->graph_kernels) + 2;   // + state init, mode reset
       S.formal_qb = b->formal_kind == FORMAL_FUSED ? b->formal_qb : 0;
       S.formal_threads = b->formal_threads;
       S.formal_kernel = b->formal_kind == FORMAL_SWEEP
-                            ? (b->sweep_variant == 2 ? JFNK_FORMAL_SWEEP_WARP : JFNK_FORMAL_SWEEP_THREAD)
+                            ? (b->sweep_variant == 2 ? JFNK_FORMAL_SWEEP_WARP
+                               : (sweep_fused(*b) ? JFNK_FORMAL_SWEEP_THREAD_FUSED : JFNK_FORMAL_SWEEP_THREAD))
                             : (b->formal_kind == FORMAL_FUSED ? JFNK_FORMAL_FUSED
                                : (b->formal_kind == FORMAL_MOVING ? JFNK_FORMAL_MOVING : JFNK_FORMAL_PER_RAY));
     }

@@ -21,6 +21,7 @@
 // the ray sums differs: each hemisphere is summed over its angles first and
 // the two hemisphere sums are then added.
 #include <type_traits>
+#include <vector>
 
 #include "formal_coef.cuh"
 
@@ -198,8 +199,11 @@ __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float*
 // of the same Newton step;
 // those then read depth-major float arrays only (one 128-byte line per warp
 // and depth) and run entirely in FP32.
-// EXACT: the column has exactly MU angles (no per-angle guards).
-template <int MU, bool TAN, bool UP, bool EXACT>
+// EXACT: the column has exactly MU angles (no per-angle guards). FUSE
+// (tangent, inward pass): the opacity tangent dchi, dS of each depth is formed
+// here from the line tables, with the arithmetic of the separate opacity
+// kernel (tan_acc, tan_dS: the same bits), and stored for the outward pass.
+template <int MU, bool TAN, bool UP, bool EXACT, bool FUSE = false>
 __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const float* __restrict__ s_dz,
                                              const float* __restrict__ s_idz) {
   const ColTables& T = cd.t;
@@ -228,19 +232,84 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     hw[m] = a.y;
     two_mu[m] = a.z;
   }
-  // tangent opacity of depth kk, left by the opacity kernel
+  // the transitions active at nu (packed window point << 8 | lo << 4 | up),
+  // constant along the column: loaded once
+  int pm[kQMetaT];
+  int nact = 0;
+  if (FUSE && TAN && !UP) {
+#pragma unroll
+    for (int j = 0; j < kQMetaT; ++j) {
+      pm[j] = __ldg(T.qmeta + (size_t)j * nq + q);
+      if (pm[j] >= 0 && nact == j) nact = j + 1;
+    }
+  }
+  // FUSE: the table entries of the next depth's first kFusePre transitions
+  // (all of them at most frequencies), loaded one depth ahead so that their
+  // latency hides behind the current depth's rays
+  constexpr int kFusePre = 2;
+  float fV[kFusePre], fG[kFusePre], fl[kFusePre], fu[kFusePre], fS = 0.f;
+  auto tan_issue = [&](int kk) {
+    const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
+    const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
+    const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
+#pragma unroll
+    for (int j = 0; j < kFusePre; ++j) {
+      if (j >= nact) break;
+      const int m = pm[j];
+      fV[j] = __ldg(Vk + (m >> 8));
+      fG[j] = __ldg(Gk + (m >> 8));
+      fl[j] = __ldg(vk + ((m >> 4) & 15));
+      fu[j] = __ldg(vk + (m & 15));
+    }
+    fS = __ldg(S32T + (size_t)kk * pitch);
+  };
+  // ... and the opacity tangent formed from them and the rest of the depth's
+  // transitions (same order as the opacity kernel; chi_k: the float opacity of
+  // that depth), stored for the outward pass
+  auto tan_finish = [&](int kk, float chik, float& dc, float& dS) {
+    TanAcc ta;
+#pragma unroll
+    for (int j = 0; j < kFusePre; ++j) {
+      if (j >= nact) break;
+      tan_acc(ta, fV[j], fG[j], fl[j], fu[j]);
+    }
+    if (nact > kFusePre) {
+      const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
+      const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
+      const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
+#pragma unroll
+      for (int j = kFusePre; j < kQMetaT; ++j) {
+        if (j >= nact) break;
+        const int m = pm[j];
+        tan_acc(ta, __ldg(Vk + (m >> 8)), __ldg(Gk + (m >> 8)), __ldg(vk + ((m >> 4) & 15)), __ldg(vk + (m & 15)));
+      }
+    }
+    dc = ta.dchi;
+    dS = tan_dS(ta, fS, chik);
+    const size_t o = (size_t)kk * pitch + q;
+    cd.w.dchiT[o] = dc;
+    cd.w.dS32T[o] = dS;
+  };
+  // tangent opacity of depth kk, left by the opacity kernel or (outward pass
+  // of a fused sweep) by the inward pass
   auto tan_in = [&](int kk, float& dc, float& dS) {
     const size_t o = (size_t)kk * pitch;
     dc = dchiT[o];
     dS = dS32T[o];
   };
+  constexpr bool FT = FUSE && TAN && !UP;
 
   // boundary depth: I = 0 at the top, I = B at the bottom (Sect. 2.1)
   const int k0 = UP ? nz - 1 : 0;
   df Sp = df_load(S2, k0);
   float cp = TAN ? chiT[k0 * pitch] : chi[k0];
   float dSp = 0.f, dcp = 0.f;
-  if (TAN) tan_in(k0, dcp, dSp);
+  if (FT) {
+    tan_issue(k0);
+    tan_finish(k0, cp, dcp, dSp);
+  } else if (TAN) {
+    tan_in(k0, dcp, dSp);
+  }
   float Su = Sp.hi;
   if (!TAN && !UP) {
     chiT[0] = cp;
@@ -298,7 +367,8 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     if (TAN) {
       c_n = chiT[(size_t)kk * pitch];
       dSl_n = dSkT[(size_t)(UP ? kk : kk - 1) * pitch];
-      tan_in(kk, dc_n, dS_n);
+      if (FT) tan_issue(kk);
+      else tan_in(kk, dc_n, dS_n);
     } else if (UP) {
       // the outward sweep of a base evaluation reads the float copies its own
       // inward sweep left (coalesced; the same values, no pair difference)
@@ -316,7 +386,9 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   for (int s = 1; s < nz; ++s) {
     const int k = kn;
     const int kd = UP ? k : k - 1;   // layer between k and its upstream neighbour
-    const float c0 = c_n, dc0 = dc_n, dS0 = dS_n, dSl = dSl_n, Sf = Sf_n;
+    const float c0 = c_n, dSl = dSl_n, Sf = Sf_n;
+    float dc0 = dc_n, dS0 = dS_n;
+    if (FT) tan_finish(k, c0, dc0, dS0);
     const df Sk = S_n;
     if (s + 1 < nz) {
       kn = UP ? k - 1 : k + 1;
@@ -389,9 +461,10 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
 }
 
 // One kernel per evaluation kind (its own register allocation): blocks of
-// columns in the other kind return at once.
-template <int MU, bool TAN>
-__global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict__ cols) {
+// columns in the other kind return at once. FUSE: the tangent kernel forms
+// the opacity tangent itself (no separate opacity-tangent launch).
+template <int MU, bool TAN, bool FUSE>
+__device__ __forceinline__ void formal_sweep_block(const ColDesc* __restrict__ cols) {
   extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode_f(cd);
@@ -406,12 +479,23 @@ __global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict_
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   if (T.nmu == MU) {   // uniform over the block: every angle slot is in use
-    sweep_thread<MU, TAN, false, true>(cd, q, s_dz, s_idz);
+    sweep_thread<MU, TAN, false, true, FUSE>(cd, q, s_dz, s_idz);
     sweep_thread<MU, TAN, true, true>(cd, q, s_dz, s_idz);
   } else {
-    sweep_thread<MU, TAN, false, false>(cd, q, s_dz, s_idz);
+    sweep_thread<MU, TAN, false, false, FUSE>(cd, q, s_dz, s_idz);
     sweep_thread<MU, TAN, true, false>(cd, q, s_dz, s_idz);
   }
+}
+
+template <int MU, bool TAN, bool FUSE = false>
+__global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict__ cols) {
+  formal_sweep_block<MU, TAN, FUSE>(cols);
+}
+
+// The fused tangent kernel held to 80 registers (three 256-thread blocks per SM).
+template <int MU>
+__global__ void __launch_bounds__(256, 3) k_formal_sweep_tan_capped(const ColDesc* __restrict__ cols) {
+  formal_sweep_block<MU, true, true>(cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -621,28 +705,56 @@ static int sweep_mu_class(int nmu) {
   return 8;
 }
 
-template <int MU>
-static void launch_mu(const Batch& b, cudaStream_t s, int threads, int which) {
-  dim3 g((b.max_nq + threads - 1) / threads, b.ncols);
-  const size_t bytes = sizeof(float) * 2 * (size_t)b.max_nz;
-  if (which != 1) k_formal_sweep<MU, true><<<g, threads, bytes, s>>>(b.d_cols);
-  if (which != 2) k_formal_sweep<MU, false><<<g, threads, bytes, s>>>(b.d_cols);
+// Dynamic shared memory of a sweep block: its |dz| tables, padded so that at
+// most ``occ`` blocks fit on a multiprocessor when occ > 0. Fewer resident
+// columns keep the outward pass's re-reads of the inward pass's inputs in L2.
+static size_t sweep_smem(int max_nz, int occ) {
+  const size_t need = sizeof(float) * 2 * (size_t)max_nz;
+  if (occ <= 0) return need;
+  const size_t cap = (size_t)227 * 1024;
+  const size_t pad = (size_t)228 * 1024 / occ - 1024;
+  return std::min(cap, std::max(need, pad));
 }
 
-// variant 1: ``size`` threads per block; variant 2: ``size`` warps per block;
-// which: 0 every column, 1 base-type evaluations, 2 tangent ones
-static int launch_sweep_cfg(const Batch& b, cudaStream_t s, int variant, int size, int which = 0) {
+template <int MU>
+static void launch_mu(const Batch& b, cudaStream_t s, int threads, int which, int occ_tan, int occ_base, int fuse) {
+  dim3 g((b.max_nq + threads - 1) / threads, b.ncols);
+  if (which != 1) {
+    const size_t sm = sweep_smem(b.max_nz, occ_tan);
+    if (fuse == 2) k_formal_sweep_tan_capped<MU><<<g, threads, sm, s>>>(b.d_cols);
+    else if (fuse == 1) k_formal_sweep<MU, true, true><<<g, threads, sm, s>>>(b.d_cols);
+    else k_formal_sweep<MU, true><<<g, threads, sm, s>>>(b.d_cols);
+  }
+  if (which != 2) k_formal_sweep<MU, false><<<g, threads, sweep_smem(b.max_nz, occ_base), s>>>(b.d_cols);
+}
+
+template <int MU>
+static int allow_smem_mu() {
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep<MU, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep<MU, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024));
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep_tan_capped<MU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024));
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep<MU, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  return JFNK_OK;
+}
+
+// variant 1: ``size`` threads per block, at most occ_tan / occ_base blocks per
+// SM (0: no cap); variant 2: ``size`` warps per block; which: 0 every column,
+// 1 base-type evaluations, 2 tangent ones
+static int launch_sweep_cfg(const Batch& b, cudaStream_t s, int variant, int size, int which = 0, int occ_tan = 0,
+                            int occ_base = 0, int fuse = 0) {
   if (variant == 2) {
     const int fpb = 2 * size;   // frequencies per block
     dim3 g((b.max_nq + fpb - 1) / fpb, b.ncols);
     k_formal_sweep_warp<<<g, 32 * size, warp_variant_smem(b.max_nz, size), s>>>(b.d_cols, which);
   } else {
     switch (sweep_mu_class(b.max_nmu)) {
-      case 2: launch_mu<2>(b, s, size, which); break;
-      case 3: launch_mu<3>(b, s, size, which); break;
-      case 4: launch_mu<4>(b, s, size, which); break;
-      case 5: launch_mu<5>(b, s, size, which); break;
-      default: launch_mu<8>(b, s, size, which); break;
+      case 2: launch_mu<2>(b, s, size, which, occ_tan, occ_base, fuse); break;
+      case 3: launch_mu<3>(b, s, size, which, occ_tan, occ_base, fuse); break;
+      case 4: launch_mu<4>(b, s, size, which, occ_tan, occ_base, fuse); break;
+      case 5: launch_mu<5>(b, s, size, which, occ_tan, occ_base, fuse); break;
+      default: launch_mu<8>(b, s, size, which, occ_tan, occ_base, fuse); break;
     }
   }
   JFNK_CUDA(cudaGetLastError());
@@ -657,6 +769,10 @@ int sweep_prepare(Batch* b) {
   const size_t bytes = warp_variant_smem(b->max_nz, 8);
   JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::min(bytes, (size_t)227 * 1024)));
+  int rc;
+  if ((rc = allow_smem_mu<2>()) || (rc = allow_smem_mu<3>()) || (rc = allow_smem_mu<4>()) ||
+      (rc = allow_smem_mu<5>()) || (rc = allow_smem_mu<8>()))
+    return rc;
   if (b->sweep_variant == 0) {
     b->sweep_variant = 1;
     b->formal_threads = 128;
@@ -664,9 +780,11 @@ int sweep_prepare(Batch* b) {
   return JFNK_OK;
 }
 
+bool sweep_fused(const Batch& b) { return b.sweep_fuse > 0 && b.sweep_variant != 2 && b.max_overlap <= kQMetaT; }
+
 int launch_formal_sweep(const Batch& b, cudaStream_t s, int which) {
   return launch_sweep_cfg(b, s, b.sweep_variant == 2 ? 2 : 1, b.formal_threads > 0 ? b.formal_threads : 128,
-                          which);
+                          which, b.sweep_occ, b.sweep_occ_base, sweep_fused(b) ? b.sweep_fuse : 0);
 }
 
 int sweep_warp_size(int nz) {
@@ -675,35 +793,74 @@ int sweep_warp_size(int nz) {
   return 0;
 }
 
-// Autotuner of the sweep kernels, timed in tangent mode on the batch's own
-// columns: variant 1 with 32..256 threads per block, variant 2 with 1..8 warps
-// per block (where its shared memory fits). Both variants give bit-identical
-// results, so the choice changes the speed only.
+// Autotuner of the sweep kernels, timed on the batch's own columns: the
+// tangent sweep (the columns in tangent mode) over variant 1 with 32..256
+// threads per block and a cap of 2..8 resident blocks per SM or none, and
+// variant 2 with 1..8 warps per block (where its shared memory fits); then,
+// for variant 1, the base-type sweep's cap (columns in base mode). Both
+// variants give bit-identical results, so the choice changes the speed only.
 int sweep_autotune(Batch* b, cudaStream_t s) {
   cudaEvent_t e0, e1;
   JFNK_CUDA(cudaEventCreate(&e0));
   JFNK_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int bv = 1, bs = 128;
-  const std::pair<int, int> cands[] = {{1, 32}, {1, 64}, {1, 128}, {1, 256}, {2, 1}, {2, 2}, {2, 4}, {2, 8}};
   int rc = JFNK_OK;
+  // a tangent candidate without fusion is timed with the separate opacity-tangent launch it needs
+  auto once = [&](int variant, int size, int which, int ot, int ob, int fuse) -> int {
+    if (which == 2 && !fuse) {
+      int r = launch_opacity_tan(*b, s);
+      if (r) return r;
+    }
+    return launch_sweep_cfg(*b, s, variant, size, which, ot, ob, fuse);
+  };
+  auto timed = [&](int variant, int size, int which, int ot, int ob, float* ms, int fuse = 0) -> int {
+    int r = once(variant, size, which, ot, ob, fuse);   // warm-up
+    if (r) return r;
+    if (cudaEventRecord(e0, s) != cudaSuccess) return fail(JFNK_E_CUDA, "autotune event");
+    for (int i = 0; i < 3 && !r; ++i) r = once(variant, size, which, ot, ob, fuse);
+    if (r) return r;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return fail(JFNK_E_CUDA, "autotune timing");
+    return JFNK_OK;
+  };
+  struct Cand { int variant, size, occ, fuse; };
+  std::vector<Cand> cands;
+  const bool can_fuse = b->max_overlap <= kQMetaT;
+  for (int t : {32, 64, 128, 256})
+    for (int occ : {0, 2, 4, 8})
+      for (int f = 0; f <= (can_fuse ? 2 : 0); ++f) cands.push_back({1, t, occ, f});
+  for (int w : {1, 2, 4, 8}) cands.push_back({2, w, 0, 0});
+  float best = 1e30f;
+  Cand bc{1, 128, 0, 0};
   for (const auto& c : cands) {
-    if (c.first == 2 && !warp_variant_fits(b->max_nz, c.second)) continue;
-    if ((rc = launch_sweep_cfg(*b, s, c.first, c.second))) break;   // warm-up
-    JFNK_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3 && !rc; ++r) rc = launch_sweep_cfg(*b, s, c.first, c.second);
-    if (rc) break;
-    JFNK_CUDA(cudaEventRecord(e1, s));
-    JFNK_CUDA(cudaEventSynchronize(e1));
+    if (c.variant == 2 && !warp_variant_fits(b->max_nz, c.size)) continue;
+    if (c.variant == 1 && c.occ > 0 && c.size * c.occ > 2048) continue;
     float ms = 0.f;
-    JFNK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) { best = ms; bv = c.first; bs = c.second; }
+    if ((rc = timed(c.variant, c.size, 2, c.occ, 0, &ms, c.fuse))) break;
+    if (ms < best) { best = ms; bc = c; }
+  }
+  int best_base = 0;
+  if (!rc && bc.variant == 1) {
+    // the base-type sweep's cap, on the same columns in base mode
+    if (!(rc = batch_set_forced_mode(b, EV_BASE, s))) {
+      float bb = 1e30f;
+      for (int occ : {0, 2, 3, 4, 6, 8}) {
+        if (occ > 0 && bc.size * occ > 2048) continue;
+        float ms = 0.f;
+        if ((rc = timed(1, bc.size, 1, bc.occ, occ, &ms))) break;
+        if (ms < bb) { bb = ms; best_base = occ; }
+      }
+      if (!rc) rc = batch_set_forced_mode(b, EV_TANGENT, s);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  b->sweep_variant = bv;
-  b->formal_threads = bs;
+  b->sweep_variant = bc.variant;
+  b->formal_threads = bc.size;
+  b->sweep_occ = bc.variant == 1 ? bc.occ : 0;
+  b->sweep_occ_base = bc.variant == 1 ? best_base : 0;
+  b->sweep_fuse = bc.variant == 1 ? bc.fuse : 0;
   return JFNK_OK;
 }
 

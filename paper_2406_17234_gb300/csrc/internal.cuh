@@ -120,7 +120,12 @@ struct Batch {
   int formal_qb = 0;                  // frequencies per block of the fused formal kernel
   int formal_threads = 0;             // fused: threads per block; sweep: threads (variant 1) or warps (2)
   int sweep_variant = 0;              // sweep kernel: 1 thread per frequency, 2 warp per frequency pair
-  int tuned_variant = 0, tuned_size = 0;   // autotuner's choice (a forced variant may replace it for a solve)
+  int sweep_fuse = 0;                 // thread variant: the tangent sweep forms the opacity tangent itself
+                                      // (1; 2: held to 80 registers), 0: a separate kernel does
+  int sweep_occ = 0, sweep_occ_base = 0;   // thread variant: blocks per SM allowed (0: no cap) for the
+                                           // tangent and base-type sweeps (shared-memory padding)
+  int tuned_variant = 0, tuned_size = 0, tuned_fuse = 0;   // autotuner's choice (a forced variant may
+                                                          // replace it for a solve)
   int max_overlap = 0;                // most transitions active at one frequency over the batch
   int n_sm = 1;                       // multiprocessors of the batch's device
   bool tuned = false;                 // autotuner has run on this batch
@@ -176,6 +181,11 @@ size_t sweep_scratch_bytes(int nq, int nz);
 int sweep_prepare(Batch* b);
 // which: 0 every column, 1 base-type evaluations only, 2 tangent ones only
 int launch_formal_sweep(const Batch& b, cudaStream_t s, int which = 0);
+// The tangent sweep of this batch forms the opacity tangent itself (so the
+// separate opacity-tangent kernel is not launched).
+bool sweep_fused(const Batch& b);
+// The separate mixed-mode opacity-tangent kernel (residual.cu).
+int launch_opacity_tan(const Batch& b, cudaStream_t s);
 // Warps per block of the warp variant whose shared memory fits depth nz (0: none).
 int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);

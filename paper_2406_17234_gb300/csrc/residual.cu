@@ -987,6 +987,12 @@ static dim3 opacity_grid(const Batch& b, int tb) {
   return dim3((unsigned)std::max(1L, std::min(need, share)), b.ncols);
 }
 
+int launch_opacity_tan(const Batch& b, cudaStream_t s) {
+  k_opacity_tan32<<<opacity_grid(b, 256), 256, 0, s>>>(b.d_cols);
+  JFNK_CUDA(cudaGetLastError());
+  return JFNK_OK;
+}
+
 int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
   const int tb = 256;
   k_pop_pairs<<<dim3((b.max_N + tb - 1) / tb, b.ncols), tb, 0, s>>>(b.d_cols);
@@ -1018,7 +1024,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     JFNK_CUDA(cudaEventRecord(b.fork_ev, s));
     JFNK_CUDA(cudaStreamWaitEvent(side, b.fork_ev, 0));
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, side>>>(b.d_cols);
-    k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, side>>>(b.d_cols);
+    if (!sweep_fused(b)) k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, side>>>(b.d_cols);
     if (ev2) JFNK_CUDA(cudaEventRecordWithFlags(ev2, side, cudaEventRecordExternal));
     int rc = launch_formal_sweep(b, side, 2);
     if (rc) return rc;
@@ -1051,7 +1057,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     // events (a profiled tick) the tangent sweep is bracketed by ev2/ev3 and
     // the base-type sweep by ev0/ev1, each timed alone on this one stream
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
-    int rc0 = launch_opacity_mixed(b, s, 0);
+    int rc0 = launch_opacity_mixed(b, s, sweep_fused(b) ? 1 : 0);
     if (rc0) return rc0;
     int rc;
     if (ev2) {

@@ -154,19 +154,25 @@ __global__ void k_mv_moments(const ColDesc* __restrict__ cols) {
   jnew_ptr(cd)[i] = J;
 }
 
-// Rate integrals of transition t at depth k (one thread each): R_ij, R_ji from
-// the rays' intensities (their tangents in tangent evaluations) and, in base
+// Rate integrals of transition t at depth k: R_ij, R_ji from the rays'
+// intensities (their tangents in tangent evaluations) and, in base
 // evaluations, the block-Jacobi sums A_tj = sum_nu W sum_d h_d chi_t,d
-// (beta_j,d dI_d/dchi_d + gamma_j,d dI_d/deta_d).
-__global__ void k_mv_rates(const ColDesc* __restrict__ cols) {
-  const ColDesc& cd = cols[blockIdx.y];
+// (beta_j,d dI_d/dchi_d + gamma_j,d dI_d/deta_d). A block takes one
+// transition and 32 depths (lanes: coalesced rows of the tables and of the
+// ray arrays); its warps split the frequency window and their partial sums
+// are added in a fixed order.
+constexpr int kMvRateWarps = 4;
+
+__global__ void __launch_bounds__(32 * kMvRateWarps) k_mv_rates(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.z];
   const int mode = mv_mode(cd);
   if (mode == EV_SKIP) return;
   const ColTables& T = cd.t;
+  const int t = blockIdx.y;
   const int nz = T.nz, nq = T.nq, nl = T.nl, nd = 2 * T.nmu;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T.nt * nz) return;
-  const int t = i / nz, k = i - t * nz;
+  if (t >= T.nt || (int)blockIdx.x * 32 >= nz) return;   // uniform over the block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = min((int)blockIdx.x * 32 + lane, nz - 1);
   const bool tan = (mode == EV_TANGENT), base = (mode == EV_BASE);
   const int q0 = T.t_q0[t], q1 = T.t_q1[t], wb = T.t_base[t];
   const double* n = eval_pops(cd, mode) + (size_t)k * nl;
@@ -175,7 +181,7 @@ __global__ void k_mv_rates(const ColDesc* __restrict__ cols) {
   const double* Iray = tan ? cd.w.mdI : cd.w.mI;
   double ru = 0.0, rd = 0.0, A[kMaxL];
   for (int j = 0; j < nl; ++j) A[j] = 0.0;
-  for (int q = q0; q <= q1; ++q) {
+  for (int q = q0 + wid; q <= q1; q += kMvRateWarps) {
     const int p = wb + q - q0;
     const size_t pk = (size_t)p * nz + k, qk = (size_t)q * nz + k;
     const double W = T.t_w[p] * T.rw[q], g = T.G[pk], c2 = T.c2[q];
@@ -202,15 +208,30 @@ __global__ void k_mv_rates(const ColDesc* __restrict__ cols) {
     ru += W * su;
     rd += W * g * sd;
   }
+  // partial sums of the warps, added in warp order by warp 0
+  __shared__ double s_part[kMvRateWarps][2 + kMaxL][32];
+  s_part[wid][0][lane] = ru;
+  s_part[wid][1][lane] = rd;
+  if (base)
+    for (int j = 0; j < nl; ++j) s_part[wid][2 + j][lane] = A[j];
+  __syncthreads();
+  if (wid != 0 || (int)blockIdx.x * 32 + lane >= nz) return;
+  const int nacc = base ? 2 + nl : 2;
+  double acc[2 + kMaxL];
+  for (int j = 0; j < nacc; ++j) {
+    double v = s_part[0][j][lane];
+    for (int w = 1; w < kMvRateWarps; ++w) v += s_part[w][j][lane];
+    acc[j] = v;
+  }
   const size_t o = (size_t)t * nz + k;
   if (tan) {
-    cd.w.dRup[o] = ru;
-    cd.w.dRdn[o] = rd;
+    cd.w.dRup[o] = acc[0];
+    cd.w.dRdn[o] = acc[1];
   } else {
-    cd.w.Rup[o] = ru;
-    cd.w.Rdn[o] = rd;
+    cd.w.Rup[o] = acc[0];
+    cd.w.Rdn[o] = acc[1];
     if (base)
-      for (int j = 0; j < nl; ++j) cd.w.Apart[o * nl + j] = A[j];
+      for (int j = 0; j < nl; ++j) cd.w.Apart[o * nl + j] = acc[2 + j];
   }
 }
 
@@ -223,7 +244,7 @@ int launch_moving_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cu
   k_mv_formal<<<dim3((2 * b.max_nmu * b.max_nq + 127) / 128, nc), 128, 0, s>>>(b.d_cols);
   if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   k_mv_moments<<<dim3((b.max_nq * b.max_nz + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
-  k_mv_rates<<<dim3((b.max_nt * b.max_nz + 63) / 64, nc), 64, 0, s>>>(b.d_cols);
+  k_mv_rates<<<dim3((b.max_nz + 31) / 32, b.max_nt, nc), 32 * kMvRateWarps, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }

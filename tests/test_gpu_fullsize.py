@@ -183,12 +183,13 @@ def test_config3_fullsize_mixed_and_fp64(ctx, wls):
     assert _rel(nmx, n64) < 1e-3
 
 
-@pytest.mark.parametrize("variant", ["JFNK_FORMAL_SWEEP_THREAD", "JFNK_FORMAL_SWEEP_WARP"])
+@pytest.mark.parametrize("variant", ["JFNK_FORMAL_SWEEP_THREAD", "JFNK_FORMAL_SWEEP_WARP",
+                                     "JFNK_FORMAL_SWEEP_THREAD_FUSED"])
 def test_config4_batch_columns_against_oracle(ctx, wls, variant):
     """Columns of the 4,096-column batch (its 64- and 256-depth extremes and
     two more) solved together in one mixed batch plan with the benchmark's
     options (5 angles, hybrid start of at most 5 RH92 iterations, paper
-    stopping rule), each within 1e-3 of the oracle; both sweep kernels."""
+    stopping rule), each within 1e-3 of the oracle; every sweep kernel."""
     wl = wls["c4"]
     idx = _c4_indices(wl)
     atom = B.Atom(ctx, wl.atom)

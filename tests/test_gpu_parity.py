@@ -220,7 +220,8 @@ def test_limited_hybrid_solve(ctx, precision):
 @pytest.mark.parametrize("n_mu", [3, 5])
 @pytest.mark.parametrize("start", ["lte", "hybrid"])
 def test_sweep_variants_are_bit_identical(ctx, n_mu, start):
-    """The two mixed-mode formal kernels (thread per frequency; warp per
+    """The mixed-mode formal kernels (thread per frequency, with the opacity
+    tangent from its own kernel or formed in the tangent sweep; warp per
     frequency pair) give bit-identical solves, so the autotuner's choice
     changes the speed only."""
     wl = W.config4(n_columns=3, nz_min=60, nz_max=90, nu_scale=0.1)
@@ -228,14 +229,15 @@ def test_sweep_variants_are_bit_identical(ctx, n_mu, start):
     atms = [B.Atmosphere(ctx, atom, c, n_mu=n_mu) for c in wl.columns]
     init = dict(rh92_warmup=10, rh92_switch=0.1) if start == "hybrid" else {}
     outs = []
-    for v in (B.JFNK_FORMAL_SWEEP_THREAD, B.JFNK_FORMAL_SWEEP_WARP):
+    for v in (B.JFNK_FORMAL_SWEEP_THREAD, B.JFNK_FORMAL_SWEEP_WARP, B.JFNK_FORMAL_SWEEP_THREAD_FUSED):
         opts = B.default_options(precision=B.JFNK_MIXED, formal_variant=v, **init)
         ns, st = B.batch_solve(ctx, atms, opts, raise_on_fail=False)
         assert all(s["formal_kernel"] == v for s in st)
         outs.append((ns, st))
-    for na, nb, sa, sb in zip(outs[0][0], outs[1][0], outs[0][1], outs[1][1]):
-        assert sa["status"] == sb["status"] and sa["F_calls"] == sb["F_calls"]
-        np.testing.assert_array_equal(na, nb)
+    for other in outs[1:]:
+        for na, nb, sa, sb in zip(outs[0][0], other[0], outs[0][1], other[1]):
+            assert sa["status"] == sb["status"] and sa["F_calls"] == sb["F_calls"]
+            np.testing.assert_array_equal(na, nb)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
