@@ -326,6 +326,19 @@ def peak_rate(kind, fp64, peaks):
     return 1.0 / max(ops / peaks["fp32_fma_per_s"], mufu / peaks["mufu_per_s"])
 
 
+STAGES = ("opacity", "tangent_sweep", "base_formal", "rate_integrals", "assembly", "krylov_step")
+
+
+def stage_breakdown(st):
+    """Mean duration per active tick of each stage of a profiled solve (all
+    kernels on one stream, in-graph CUDA events), with each stage's share."""
+    n = max(1, int(st["formal_launches"]))
+    ms = [float(x) / n for x in st["stage_ms"]]
+    tot = sum(ms) or 1.0
+    return {"per_tick": {k: v for k, v in zip(STAGES, ms)}, "tick_total": sum(ms),
+            "share": {k: v / tot for k, v in zip(STAGES, ms)}}
+
+
 def kernel_roofline(name, kind, fp64, points, kern_ms, launches, peaks, traffic_key=None):
     """One formal kernel: achieved = algorithmic ray-points of its launches /
     their summed CUDA-event duration, against the roofline of its evaluation kind."""
@@ -678,7 +691,8 @@ def run_batch(args, rank, ws, local, dist):
                 "launch": {"threads": int(pst[0]["formal_threads"]), "variant": int(pst[0]["formal_kernel"]),
                            "blocks_per_sm_cap_tangent": int(pst[0]["formal_occ"]),
                            "blocks_per_sm_cap_base": int(pst[0]["formal_occ_base"]),
-                           "tangent_opacity_in_sweep": int(pst[0]["formal_fuse"])}}
+                           "tangent_opacity_in_sweep": int(pst[0]["formal_fuse"])},
+                "tick_stages_ms": stage_breakdown(pst[0])}
     st0 = allstats[-1]
     line = {"metric": METRIC, "value": pts / (total_ms * 1e-3), "unit": "ray-points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,

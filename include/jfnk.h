@@ -246,8 +246,14 @@ typedef struct {
   int formal_occ_base;  /* the same for the base-type sweep                        */
   int formal_fuse;      /* thread-per-frequency sweep: 0 when a separate kernel forms
                            the opacity tangent of the JVP evaluations, 1 when the
-                           tangent sweep's inward pass forms it, 2 the same held to
-                           80 registers (chosen by the autotuner)                */
+                           tangent sweep's inward pass forms it
+                           (JFNK_FORMAL_SWEEP_THREAD_FUSED)                       */
+  double stage_ms[6];   /* profile: summed durations over the active ticks of each
+                           stage of a tick, all on one stream: [0] opacity (up to
+                           the first formal kernel), [1] tangent sweep (mixed
+                           mode), [2] base-type formal solution, [3] rate
+                           integrals (and, moving columns, moments), [4] assembly
+                           and preconditioner factorisation, [5] Krylov step      */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */

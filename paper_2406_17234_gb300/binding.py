@@ -91,10 +91,11 @@ class jfnk_stats(C.Structure):
                 ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int),
                 ("formal_qb", C.c_int), ("formal_threads", C.c_int), ("formal_kernel", C.c_int),
                 ("formal_tan_ms", C.c_double), ("formal_occ", C.c_int), ("formal_occ_base", C.c_int),
-                ("formal_fuse", C.c_int)]
+                ("formal_fuse", C.c_int), ("stage_ms", C.c_double * 6)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: (list(v) if isinstance(v, C.Array) else v)
+                for f, v in ((f, getattr(self, f)) for f, _ in self._fields_)}
 
 
 class jfnk_server_desc(C.Structure):

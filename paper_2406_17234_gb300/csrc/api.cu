@@ -35,8 +35,12 @@ int ensure_side_stream(Batch* b) {
   return JFNK_OK;
 }
 
-// Events per tick of a profiled graph: one pair per formal kernel launch.
-static int tick_events(const Batch& b) { return b.formal_kind == FORMAL_SWEEP ? 4 : 2; }
+// Events per tick of a profiled graph: ev0/ev1 around the (base-type) formal
+// kernel, ev2/ev3 around the tangent sweep (mixed mode), then the tick's start,
+// the end of its rate integrals, of its assembly and of its Krylov step.
+constexpr int kTickEvents = 8;
+constexpr int kStages = 6;
+static int tick_events(const Batch&) { return kTickEvents; }
 
 // Work buffers and the tick graph of one column, cached in its handle.
 struct SingleWork {
@@ -185,9 +189,12 @@ int capture_ticks(Batch* b, cudaStream_t s, bool profile, cudaGraphExec_t* out) 
     cudaEvent_t* ev = profile ? &b->tick_ev[(size_t)ne * t] : nullptr;
     // a profiled tick runs the tangent and base-type chains one after the
     // other on s (no side stream), so that each sweep's events time it alone
+    const bool sweep = b->formal_kind == FORMAL_SWEEP;
     rc = launch_evaluation(*b, s, ev ? ev[0] : nullptr, ev ? ev[1] : nullptr, profile ? nullptr : b->side,
-                           ev && ne == 4 ? ev[2] : nullptr, ev && ne == 4 ? ev[3] : nullptr);
+                           ev && sweep ? ev[2] : nullptr, ev && sweep ? ev[3] : nullptr, ev ? ev + 4 : nullptr);
     if (!rc) rc = launch_krylov_step(*b, s);   // P^k was factorised by the assembly
+    if (!rc && ev && cudaEventRecordWithFlags(ev[7], s, cudaEventRecordExternal) != cudaSuccess)
+      rc = fail(JFNK_E_CUDA, "tick event record");
   }
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (rc) return rc;
@@ -232,6 +239,7 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
   if (rc) return rc;
   b->tick_ms.clear();
   b->tick_tan_ms.clear();
+  b->tick_stage_ms.clear();
   b->replays = 0;
   b->compactions = 0;
   // the full view, restored before returning
@@ -252,12 +260,21 @@ static int run_to_completion(Batch* b, const jfnk_options* o, cudaStream_t s) {
     if (profile) {
       // the formal kernels' own durations (base-type and tangent sweeps apart)
       const int ne = tick_events(*b);
+      const bool sweep = b->formal_kind == FORMAL_SWEEP;
       for (int t = 0; t < b->graph_ticks; ++t) {
-        float ms = 0.f, ms2 = 0.f;
-        cudaEventElapsedTime(&ms, b->tick_ev[(size_t)ne * t], b->tick_ev[(size_t)ne * t + 1]);
-        if (ne == 4) cudaEventElapsedTime(&ms2, b->tick_ev[(size_t)ne * t + 2], b->tick_ev[(size_t)ne * t + 3]);
-        b->tick_ms.push_back(ms);
-        b->tick_tan_ms.push_back(ms2);
+        const cudaEvent_t* e = &b->tick_ev[(size_t)ne * t];
+        auto span = [&](int i, int j) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e[i], e[j]);
+          return ms;
+        };
+        const float base = span(0, 1), tan = sweep ? span(2, 3) : 0.f;
+        b->tick_ms.push_back(base);
+        b->tick_tan_ms.push_back(tan);
+        // opacity (up to the first formal kernel), tangent sweep, base-type
+        // formal solution, rate integrals, assembly, Krylov step
+        const float st[kStages] = {span(4, sweep ? 2 : 0), tan, base, span(1, 5), span(5, 6), span(6, 7)};
+        b->tick_stage_ms.insert(b->tick_stage_ms.end(), st, st + kStages);
       }
     }
     std::vector<int> running;
@@ -442,9 +459,11 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
   int active = 0;
   for (int c = 0; c < b->ncols; ++c) active = std::max(active, st[c].ticks);
   active = std::min(active, (int)b->tick_ms.size());
-  double kernel_ms = 0.0, tan_ms = 0.0;
+  double kernel_ms = 0.0, tan_ms = 0.0, stage_ms[kStages] = {};
   for (int t = 0; t < active; ++t) kernel_ms += b->tick_ms[t];
   for (int t = 0; t < active && t < (int)b->tick_tan_ms.size(); ++t) tan_ms += b->tick_tan_ms[t];
+  for (int t = 0; t < active && (size_t)(t + 1) * kStages <= b->tick_stage_ms.size(); ++t)
+    for (int j = 0; j < kStages; ++j) stage_ms[j] += b->tick_stage_ms[(size_t)t * kStages + j];
   for (int c = 0; c < b->ncols; ++c) {
     const SolverState& x = st[c];
     int status = x.status == 1 ? JFNK_E_TIMEOUT : x.status;
@@ -461,6 +480,7 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.ray_points = (double)x.F_calls * cols[c]->d.ray_points;
       S.formal_ms = kernel_ms;
       S.formal_tan_ms = tan_ms;
+      for (int j = 0; j < kStages; ++j) S.stage_ms[j] = stage_ms[j];
       S.formal_occ = b->formal_kind == FORMAL_SWEEP && b->sweep_variant != 2 ? b->sweep_occ : 0;
       S.formal_occ_base = b->formal_kind == FORMAL_SWEEP && b->sweep_variant != 2 ? b->sweep_occ_base : 0;
       S.formal_fuse = b->formal_kind == FORMAL_SWEEP && sweep_fused(*b) ? b->sweep_fuse : 0;

@@ -46,6 +46,25 @@ __device__ __forceinline__ float exp_neg(float x) {
   return y;
 }
 
+// Asynchronous 4-byte copies global -> shared (each thread copies and later
+// reads back only its own words, so waiting on its own copy groups suffices).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Fused tangent sweep: the line-table entries of each depth are copied into a
+// shared-memory ring kRing - 1 depths ahead of the recurrence; a stage holds
+// per thread V, G, v_lo, v_up of the first two transitions and S.
+constexpr int kRing = 4;
+constexpr int kRingSlots = 9;
+__host__ __device__ inline size_t ring_floats(int threads) { return (size_t)kRing * kRingSlots * threads; }
+
 // Which form of the coefficients a step takes: chosen per step (CM_EITHER),
 // or known for every angle of the depth (CM_SERIES: all steps below 0.1;
 // CM_DIRECT: none), the same choice as CM_EITHER makes for each step.
@@ -168,13 +187,37 @@ __device__ __forceinline__ float butterfly8(float v) {
 // diagonals are FP32 sums and stay float. The sweeps serve the mixed mode
 // only, whose Jacobian-vector products are exact tangents (no difference
 // evaluations).
+struct BaseOut {
+  df J;
+  float lx, le;
+};
+__device__ __forceinline__ BaseOut base_out(df Sk, df c2, float c2f, float fD, float fa, float fI, float fx, float fe) {
+  BaseOut r;
+  r.J = fabsf(fI) < fa ? df_mul_f(c2, fI) : df_mul(df_add_f(Sk, fD), c2);
+  r.lx = mul(fx, c2f);
+  r.le = fe;
+  return r;
+}
 __device__ __forceinline__ void write_base(const ColDesc& cd, size_t o, df Sk, df c2, float c2f, float fD, float fa,
                                            float fI, float fx, float fe) {
-  const df J = fabsf(fI) < fa ? df_mul_f(c2, fI) : df_mul(df_add_f(Sk, fD), c2);
-  df_store(as_pairs(jnew_ptr(cd)), o, J);
-  cd.w.Lchi32[o] = mul(fx, c2f);
-  cd.w.Leta32[o] = fe;
+  const BaseOut r = base_out(Sk, c2, c2f, fD, fa, fI, fx, fe);
+  df_store(as_pairs(jnew_ptr(cd)), o, r.J);
+  cd.w.Lchi32[o] = r.lx;
+  cd.w.Leta32[o] = r.le;
 }
+
+// Outward pass of a base-type sweep: the per-frequency output rows ([q][k]:
+// J pair, Lchi, Leta) are staged per warp for kStageD depths in shared memory
+// ([plane][lane][depth], row stride kStageD + 1: the 32 lanes' words of one
+// depth fall in 32 banks) and then written row by row, consecutive lanes on
+// consecutive depths of a row, instead of one scattered word per lane.
+// (Staging the input rows the same way, through a double buffer of
+// asynchronous copies, was slower: 1.02 against 0.94 ms per tick; the larger
+// shared memory leaves less L1, where those rows are mostly hits.)
+constexpr int kStageD = 8;
+constexpr int kStagePlane = 32 * (kStageD + 1);
+constexpr int kWarpStage = 4 * kStagePlane;
+__host__ __device__ inline size_t stage_floats(int threads) { return (size_t)(threads / 32) * kWarpStage; }
 // Tangent output: dJ (normalised by 2 h nu^3/c^2) in float, depth-major, read
 // by the FP32 tangent rate integrals; o indexes the depth-major arrays.
 __device__ __forceinline__ void write_tan(const ColDesc& cd, size_t o, float dS, float fd) {
@@ -205,7 +248,9 @@ __device__ __forceinline__ void stage_dz(const ColTables& T, float* s_dz, float*
 // kernel (tan_acc, tan_dS: the same bits), and stored for the outward pass.
 template <int MU, bool TAN, bool UP, bool EXACT, bool FUSE = false>
 __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const float* __restrict__ s_dz,
-                                             const float* __restrict__ s_idz) {
+                                             const float* __restrict__ s_idz, float* __restrict__ s_ring = nullptr,
+                                             float* __restrict__ s_stage = nullptr, unsigned amask = 0u,
+                                             int na = 0) {
   const ColTables& T = cd.t;
   const int nz = T.nz, nq = T.nq, nmu = T.nmu, nl = T.nl;
   const size_t pitch = (size_t)col_pitch(nq);
@@ -233,59 +278,62 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     two_mu[m] = a.z;
   }
   // the transitions active at nu (packed window point << 8 | lo << 4 | up),
-  // constant along the column: loaded once
-  int pm[kQMetaT];
-  int nact = 0;
-  if (FUSE && TAN && !UP) {
-#pragma unroll
-    for (int j = 0; j < kQMetaT; ++j) {
-      pm[j] = __ldg(T.qmeta + (size_t)j * nq + q);
-      if (pm[j] >= 0 && nact == j) nact = j + 1;
-    }
+  // constant along the column: the first two held, the others read when used
+  constexpr bool FT = FUSE && TAN && !UP;
+  int pm0 = -1, pm1 = -1;
+  if (FT) {
+    pm0 = __ldg(T.qmeta + q);
+    pm1 = __ldg(T.qmeta + (size_t)nq + q);
   }
-  // FUSE: the table entries of the next depth's first kFusePre transitions
-  // (all of them at most frequencies), loaded one depth ahead so that their
-  // latency hides behind the current depth's rays
-  constexpr int kFusePre = 2;
-  float fV[kFusePre], fG[kFusePre], fl[kFusePre], fu[kFusePre], fS = 0.f;
+  // FUSE: the asynchronous copies of depth kk's table entries into ring stage
+  // kk % kRing (one commit group per depth, empty past the column's end)
+  const int bd = blockDim.x;
   auto tan_issue = [&](int kk) {
-    const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
-    const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
-    const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
-#pragma unroll
-    for (int j = 0; j < kFusePre; ++j) {
-      if (j >= nact) break;
-      const int m = pm[j];
-      fV[j] = __ldg(Vk + (m >> 8));
-      fG[j] = __ldg(Gk + (m >> 8));
-      fl[j] = __ldg(vk + ((m >> 4) & 15));
-      fu[j] = __ldg(vk + (m & 15));
+    if (kk < nz) {
+      float* r = s_ring + (size_t)(kk % kRing) * kRingSlots * bd + threadIdx.x;
+      const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
+      const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
+      const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
+      if (pm0 >= 0) {
+        cp_async4(r, Vk + (pm0 >> 8));
+        cp_async4(r + bd, Gk + (pm0 >> 8));
+        cp_async4(r + 2 * bd, vk + ((pm0 >> 4) & 15));
+        cp_async4(r + 3 * bd, vk + (pm0 & 15));
+      }
+      if (pm1 >= 0) {
+        cp_async4(r + 4 * bd, Vk + (pm1 >> 8));
+        cp_async4(r + 5 * bd, Gk + (pm1 >> 8));
+        cp_async4(r + 6 * bd, vk + ((pm1 >> 4) & 15));
+        cp_async4(r + 7 * bd, vk + (pm1 & 15));
+      }
+      cp_async4(r + 8 * bd, S32T + (size_t)kk * pitch);
     }
-    fS = __ldg(S32T + (size_t)kk * pitch);
+    cp_async_commit();
   };
-  // ... and the opacity tangent formed from them and the rest of the depth's
-  // transitions (same order as the opacity kernel; chi_k: the float opacity of
-  // that depth), stored for the outward pass
+  // ... and the opacity tangent of depth kk formed from its stage (and the
+  // rest of the depth's transitions, read directly; the order of the
+  // separate opacity kernel; chi_k: the float opacity of that depth), stored
+  // for the outward pass. Every copy but those of the kRing - 2 most recent
+  // depths has landed after the wait.
   auto tan_finish = [&](int kk, float chik, float& dc, float& dS) {
+    cp_async_wait<kRing - 2>();
+    const float* r = s_ring + (size_t)(kk % kRing) * kRingSlots * bd + threadIdx.x;
     TanAcc ta;
-#pragma unroll
-    for (int j = 0; j < kFusePre; ++j) {
-      if (j >= nact) break;
-      tan_acc(ta, fV[j], fG[j], fl[j], fu[j]);
-    }
-    if (nact > kFusePre) {
+    if (pm0 >= 0) tan_acc(ta, r[0], r[bd], r[2 * bd], r[3 * bd]);
+    if (pm1 >= 0) {
+      tan_acc(ta, r[4 * bd], r[5 * bd], r[6 * bd], r[7 * bd]);
       const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
       const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
       const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
 #pragma unroll
-      for (int j = kFusePre; j < kQMetaT; ++j) {
-        if (j >= nact) break;
-        const int m = pm[j];
+      for (int j = 2; j < kQMetaT; ++j) {
+        const int m = __ldg(T.qmeta + (size_t)j * nq + q);
+        if (m < 0) break;
         tan_acc(ta, __ldg(Vk + (m >> 8)), __ldg(Gk + (m >> 8)), __ldg(vk + ((m >> 4) & 15)), __ldg(vk + (m & 15)));
       }
     }
     dc = ta.dchi;
-    dS = tan_dS(ta, fS, chik);
+    dS = tan_dS(ta, r[8 * bd], chik);
     const size_t o = (size_t)kk * pitch + q;
     cd.w.dchiT[o] = dc;
     cd.w.dS32T[o] = dS;
@@ -297,7 +345,6 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     dc = dchiT[o];
     dS = dS32T[o];
   };
-  constexpr bool FT = FUSE && TAN && !UP;
 
   // boundary depth: I = 0 at the top, I = B at the bottom (Sect. 2.1)
   const int k0 = UP ? nz - 1 : 0;
@@ -305,8 +352,10 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   float cp = TAN ? chiT[k0 * pitch] : chi[k0];
   float dSp = 0.f, dcp = 0.f;
   if (FT) {
-    tan_issue(k0);
+#pragma unroll
+    for (int j = 0; j < kRing - 1; ++j) tan_issue(k0 + j);
     tan_finish(k0, cp, dcp, dSp);
+    tan_issue(k0 + kRing - 1);
   } else if (TAN) {
     tan_in(k0, dcp, dSp);
   }
@@ -336,12 +385,15 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       xd[m] = mul(hw[m], dD0);
     }
   }
-  auto emit = [&](int k, df Sk, float dS) {
+  // the inward pass leaves its hemisphere sums of each depth in part; the
+  // outward pass adds its own to them (pt: those of depth k, loaded ahead)
+  constexpr int NP = TAN ? 1 : kSweepParts;
+  auto emit = [&](int k, df Sk, float dS, const float* pt) {
     float* pp = part + (size_t)k * pitch;
     if (TAN) {
       const float td = tree_mu<MU>(xd);
       if (!UP) pp[0] = td;
-      else write_tan(cd, (size_t)k * pitch + q, dS, add(td, pp[0]));
+      else write_tan(cd, (size_t)k * pitch + q, dS, add(td, pt[0]));
       return;
     }
     const float tD = tree_mu<MU>(xD), ta = tree_mu<MU>(xa), tI = tree_mu<MU>(xI), tx = tree_mu<MU>(xx),
@@ -353,22 +405,52 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
       pp[3 * pstride] = tx;
       pp[4 * pstride] = te;
     } else {
-      write_base(cd, row + k, Sk, c2p, c2f, add(tD, pp[0]), add(ta, pp[pstride]), add(tI, pp[2 * pstride]),
-                 add(tx, pp[3 * pstride]), add(te, pp[4 * pstride]));
+      const BaseOut r = base_out(Sk, c2p, c2f, add(tD, pt[0]), add(ta, pt[1]), add(tI, pt[2]), add(tx, pt[3]),
+                                 add(te, pt[4]));
+      const int lane = threadIdx.x & 31;
+      float* w = s_stage + lane * (kStageD + 1) + (k % kStageD);
+      w[0] = r.J.hi;
+      w[kStagePlane] = r.J.lo;
+      w[2 * kStagePlane] = r.lx;
+      w[3 * kStagePlane] = r.le;
+      if (k % kStageD == 0) {
+        // the depths k .. k + kStageD - 1 of the warp's rows are complete
+        __syncwarp(amask);
+        const int nk = min(kStageD, nz - k);
+        const int q0w = q - lane;
+        float2* __restrict__ J2 = as_pairs(jnew_ptr(cd));
+        for (int e = lane; e < na * nk; e += na) {
+          const int rr = e / nk, kk = e - rr * nk;
+          const float* sr = s_stage + rr * (kStageD + 1) + kk;
+          const size_t o = (size_t)(q0w + rr) * nz + k + kk;
+          J2[o] = make_float2(sr[0], sr[kStagePlane]);
+          cd.w.Lchi32[o] = sr[2 * kStagePlane];
+          cd.w.Leta32[o] = sr[3 * kStagePlane];
+        }
+        __syncwarp(amask);
+      }
     }
   };
-  emit(k0, Sp, dSp);
+  float pt_n[NP];
+  auto load_parts = [&](int kk) {
+    if (UP) {
+#pragma unroll
+      for (int j = 0; j < NP; ++j) pt_n[j] = part[(size_t)kk * pitch + j * pstride];
+    }
+  };
+  load_parts(k0);
+  emit(k0, Sp, dSp, pt_n);
 
   // the next depth's inputs are prepared one step ahead
   int kn = UP ? nz - 2 : 1;
   float c_n = 0.f, dc_n = 0.f, dS_n = 0.f, dSl_n = 0.f, Sf_n = 0.f;
   df S_n = df_make(0.f, 0.f);
   auto load = [&](int kk) {
+    load_parts(kk);
     if (TAN) {
       c_n = chiT[(size_t)kk * pitch];
       dSl_n = dSkT[(size_t)(UP ? kk : kk - 1) * pitch];
-      if (FT) tan_issue(kk);
-      else tan_in(kk, dc_n, dS_n);
+      if (!FT) tan_in(kk, dc_n, dS_n);
     } else if (UP) {
       // the outward sweep of a base evaluation reads the float copies its own
       // inward sweep left (coalesced; the same values, no pair difference)
@@ -388,8 +470,14 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     const int kd = UP ? k : k - 1;   // layer between k and its upstream neighbour
     const float c0 = c_n, dSl = dSl_n, Sf = Sf_n;
     float dc0 = dc_n, dS0 = dS_n;
-    if (FT) tan_finish(k, c0, dc0, dS0);
+    if (FT) {
+      tan_finish(k, c0, dc0, dS0);
+      tan_issue(k + kRing - 1);
+    }
     const df Sk = S_n;
+    float pt[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) pt[j] = pt_n[j];
     if (s + 1 < nz) {
       kn = UP ? k - 1 : k + 1;
       load(kn);
@@ -446,7 +534,7 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     } else {
       angles(std::integral_constant<int, CM_EITHER>());
     }
-    emit(k, Sk, dS0);
+    emit(k, Sk, dS0, pt);
     Sp = Sk;
     Su = in.S0;
     cp = c0;
@@ -465,36 +553,48 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
 // the opacity tangent itself (no separate opacity-tangent launch).
 template <int MU, bool TAN, bool FUSE>
 __device__ __forceinline__ void formal_sweep_block(const ColDesc* __restrict__ cols) {
-  extern __shared__ float s_tab[];   // [nz] |dz|, [nz] 1/|dz|
+  extern __shared__ float s_tab[];   // FUSE: the copy ring; then [nz] |dz|, [nz] 1/|dz|
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode_f(cd);
   if (mode == EV_SKIP || (mode == EV_TANGENT) != TAN) return;
   const ColTables& T = cd.t;
   const int nz = T.nz, nq = T.nq;
   if ((int)(blockIdx.x * blockDim.x) >= nq) return;   // uniform over the block
-  float* s_dz = s_tab;
-  float* s_idz = s_tab + nz;
+  // FUSE: the copy ring; base-type sweeps: the output stage; then the |dz| tables
+  float* s_ring = FUSE ? s_tab : nullptr;
+  float* s_stage = TAN ? nullptr : s_tab + (size_t)(threadIdx.x >> 5) * kWarpStage;
+  float* s_dz = s_tab + (FUSE ? ring_floats(blockDim.x) : 0) + (TAN ? 0 : stage_floats(blockDim.x));
+  float* s_idz = s_dz + nz;
   stage_dz(T, s_dz, s_idz);
   __syncthreads();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  // the lanes of a warp with a frequency form a prefix of it
+  const unsigned amask = __ballot_sync(0xffffffffu, q < nq);
   if (q >= nq) return;
+  const int na = __popc(amask);
   if (T.nmu == MU) {   // uniform over the block: every angle slot is in use
-    sweep_thread<MU, TAN, false, true, FUSE>(cd, q, s_dz, s_idz);
-    sweep_thread<MU, TAN, true, true>(cd, q, s_dz, s_idz);
+    sweep_thread<MU, TAN, false, true, FUSE>(cd, q, s_dz, s_idz, s_ring, s_stage, amask, na);
+    sweep_thread<MU, TAN, true, true>(cd, q, s_dz, s_idz, nullptr, s_stage, amask, na);
   } else {
-    sweep_thread<MU, TAN, false, false, FUSE>(cd, q, s_dz, s_idz);
-    sweep_thread<MU, TAN, true, false>(cd, q, s_dz, s_idz);
+    sweep_thread<MU, TAN, false, false, FUSE>(cd, q, s_dz, s_idz, s_ring, s_stage, amask, na);
+    sweep_thread<MU, TAN, true, false>(cd, q, s_dz, s_idz, nullptr, s_stage, amask, na);
   }
 }
 
-template <int MU, bool TAN, bool FUSE = false>
+template <int MU, bool TAN>
 __global__ void __launch_bounds__(256) k_formal_sweep(const ColDesc* __restrict__ cols) {
-  formal_sweep_block<MU, TAN, FUSE>(cols);
+  formal_sweep_block<MU, TAN, false>(cols);
 }
 
-// The fused tangent kernel held to 80 registers (three 256-thread blocks per SM).
+// The tangent sweep that forms the opacity tangent itself (forced variant):
+// 128-thread blocks, at most 72 registers (seven blocks per SM). Measured on
+// the 1,216-column batch against the separate opacity-tangent kernel
+// (per tick, all on one stream): opacity stage 1.67 -> 0.63 ms, tangent sweep
+// 1.54 -> 2.91 ms; whole solve 529 -> 554 ms. At 64 registers (spills) the
+// sweep took 3.51 ms, unbounded (100 registers) 3.69 ms.
+constexpr int kFusedThreads = 128;
 template <int MU>
-__global__ void __launch_bounds__(256, 3) k_formal_sweep_tan_capped(const ColDesc* __restrict__ cols) {
+__global__ void __launch_bounds__(kFusedThreads, 7) k_formal_sweep_fused(const ColDesc* __restrict__ cols) {
   formal_sweep_block<MU, true, true>(cols);
 }
 
@@ -708,8 +808,9 @@ static int sweep_mu_class(int nmu) {
 // Dynamic shared memory of a sweep block: its |dz| tables, padded so that at
 // most ``occ`` blocks fit on a multiprocessor when occ > 0. Fewer resident
 // columns keep the outward pass's re-reads of the inward pass's inputs in L2.
-static size_t sweep_smem(int max_nz, int occ) {
-  const size_t need = sizeof(float) * 2 * (size_t)max_nz;
+static size_t sweep_smem(int max_nz, int occ, int threads, bool tan, bool fuse = false) {
+  const size_t need =
+      sizeof(float) * (2 * (size_t)max_nz + (fuse ? ring_floats(threads) : 0) + (tan ? 0 : stage_floats(threads)));
   if (occ <= 0) return need;
   const size_t cap = (size_t)227 * 1024;
   const size_t pad = (size_t)228 * 1024 / occ - 1024;
@@ -720,20 +821,18 @@ template <int MU>
 static void launch_mu(const Batch& b, cudaStream_t s, int threads, int which, int occ_tan, int occ_base, int fuse) {
   dim3 g((b.max_nq + threads - 1) / threads, b.ncols);
   if (which != 1) {
-    const size_t sm = sweep_smem(b.max_nz, occ_tan);
-    if (fuse == 2) k_formal_sweep_tan_capped<MU><<<g, threads, sm, s>>>(b.d_cols);
-    else if (fuse == 1) k_formal_sweep<MU, true, true><<<g, threads, sm, s>>>(b.d_cols);
+    const size_t sm = sweep_smem(b.max_nz, occ_tan, threads, true, fuse != 0);
+    if (fuse) k_formal_sweep_fused<MU><<<g, threads, sm, s>>>(b.d_cols);
     else k_formal_sweep<MU, true><<<g, threads, sm, s>>>(b.d_cols);
   }
-  if (which != 2) k_formal_sweep<MU, false><<<g, threads, sweep_smem(b.max_nz, occ_base), s>>>(b.d_cols);
+  if (which != 2)
+    k_formal_sweep<MU, false><<<g, threads, sweep_smem(b.max_nz, occ_base, threads, false), s>>>(b.d_cols);
 }
 
 template <int MU>
 static int allow_smem_mu() {
   JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep<MU, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep<MU, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024));
-  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep_tan_capped<MU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep_fused<MU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  227 * 1024));
   JFNK_CUDA(cudaFuncSetAttribute(k_formal_sweep<MU, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   return JFNK_OK;
@@ -744,6 +843,8 @@ static int allow_smem_mu() {
 // 1 base-type evaluations, 2 tangent ones
 static int launch_sweep_cfg(const Batch& b, cudaStream_t s, int variant, int size, int which = 0, int occ_tan = 0,
                             int occ_base = 0, int fuse = 0) {
+  if (fuse && (variant != 1 || size != kFusedThreads))
+    return fail(JFNK_E_INVALID, "fused tangent sweep: thread variant with 128-thread blocks only");
   if (variant == 2) {
     const int fpb = 2 * size;   // frequencies per block
     dim3 g((b.max_nq + fpb - 1) / fpb, b.ncols);
@@ -823,12 +924,14 @@ int sweep_autotune(Batch* b, cudaStream_t s) {
       return fail(JFNK_E_CUDA, "autotune timing");
     return JFNK_OK;
   };
+  // The fused opacity tangent (forced variant only) is not a candidate: timed
+  // alone it can win, but inside a tick the separate opacity-tangent kernel
+  // overlaps the base-type chain on the other stream, and the fused sweep
+  // made the whole solve about 11 % slower.
   struct Cand { int variant, size, occ, fuse; };
   std::vector<Cand> cands;
-  const bool can_fuse = b->max_overlap <= kQMetaT;
   for (int t : {32, 64, 128, 256})
-    for (int occ : {0, 2, 4, 8})
-      for (int f = 0; f <= (can_fuse ? 2 : 0); ++f) cands.push_back({1, t, occ, f});
+    for (int occ : {0, 2, 4, 8}) cands.push_back({1, t, occ, 0});
   for (int w : {1, 2, 4, 8}) cands.push_back({2, w, 0, 0});
   float best = 1e30f;
   Cand bc{1, 128, 0, 0};

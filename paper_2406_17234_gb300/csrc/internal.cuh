@@ -121,7 +121,7 @@ struct Batch {
   int formal_threads = 0;             // fused: threads per block; sweep: threads (variant 1) or warps (2)
   int sweep_variant = 0;              // sweep kernel: 1 thread per frequency, 2 warp per frequency pair
   int sweep_fuse = 0;                 // thread variant: the tangent sweep forms the opacity tangent itself
-                                      // (1; 2: held to 80 registers), 0: a separate kernel does
+                                      // (1, forced variant only), 0: a separate kernel does
   int sweep_occ = 0, sweep_occ_base = 0;   // thread variant: blocks per SM allowed (0: no cap) for the
                                            // tangent and base-type sweeps (shared-memory padding)
   int tuned_variant = 0, tuned_size = 0, tuned_fuse = 0;   // autotuner's choice (a forced variant may
@@ -138,6 +138,7 @@ struct Batch {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   std::vector<float> tick_ms;         // per-tick formal-kernel durations of the last solve (base-type sweep)
   std::vector<float> tick_tan_ms;     // per-tick tangent-sweep durations (mixed mode)
+  std::vector<float> tick_stage_ms;   // per tick, kStages durations (jfnk_stats.stage_ms order)
   int* h_status = nullptr;            // pinned host mirror of d_status
   // launch view over the columns still running (straggler compaction)
   ColDesc* d_view = nullptr;          // device array [ncols] of the view's descriptors
@@ -162,8 +163,11 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
 // ev0/ev1 (optional) are recorded around the formal-solution kernel. With a
 // side stream (mixed mode) the tangent kernels go there, forked from and joined
 // back into s, and ev2/ev3 bracket the tangent sweep (ev0/ev1 the base one).
+// stage (optional, without a side stream): three events recorded at the start
+// of the evaluation, after the rate integrals and after the assembly.
 int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
-                      cudaStream_t side = nullptr, cudaEvent_t ev2 = nullptr, cudaEvent_t ev3 = nullptr);
+                      cudaStream_t side = nullptr, cudaEvent_t ev2 = nullptr, cudaEvent_t ev3 = nullptr,
+                      const cudaEvent_t* stage = nullptr);
 // Creates the side stream and the fork/join events of a mixed-mode batch.
 int ensure_side_stream(Batch* b);
 // Allocates and binds the lagged d J/d n buffers of every column (once).

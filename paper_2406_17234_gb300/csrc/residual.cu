@@ -577,34 +577,95 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
     const float nlo_f = (float)n_lo, nup_f = (float)n_up;
     const int pv = precond_variant(cd, bopts);
     const float sca_f = (float)T.chi_sca[k];
-    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+    const bool packed = T.max_overlap <= kQMetaT;
+    // one frequency's inputs; two frequencies are loaded before the first is
+    // summed, so that their latencies overlap (the sums keep their order)
+    struct In {
+      df J, w, V, gV;
+      float Vf, gf, Wr, Lx, Le, c2f;
+      int m0, m1;
+      float Vs0, Gs0, Vs1, Gs1;
+    };
+    auto ld = [&](int q) {
+      In r;
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
-      const df Jq = df_load(J2, o), w = df_load(T.W2, p);
-      s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
-      s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
-      const float Vf = T.V32[pk], gf = T.G32[pk];
-      const float Wc0 = T.Wr32[p] * (Vf * (nlo_f - gf * nup_f));
-      const float Lx = cd.w.Lchi32[o], Le = cd.w.Leta32[o];
+      r.J = df_load(J2, o);
+      r.w = df_load(T.W2, p);
+      r.V = df_load(T.V2, pk);
+      r.gV = df_load(T.gV2, pk);
+      r.Vf = __ldg(T.V32 + pk);
+      r.gf = __ldg(T.G32 + pk);
+      r.Wr = __ldg(T.Wr32 + p);
+      r.Lx = cd.w.Lchi32[o];
+      r.Le = cd.w.Leta32[o];
+      r.c2f = __ldg(T.c2f + q);
+      r.m0 = r.m1 = -1;
+      r.Vs0 = r.Gs0 = r.Vs1 = r.Gs1 = 0.f;
+      if (packed) {
+        // the packed table gives window point and levels in one load
+        r.m0 = __ldg(T.qmeta + q);
+        r.m1 = __ldg(T.qmeta + (size_t)T.nq + q);
+        if (r.m0 >= 0) {
+          const size_t ps = (size_t)(r.m0 >> 8) * nz + k;
+          r.Vs0 = __ldg(T.V32 + ps);
+          r.Gs0 = __ldg(T.G32 + ps);
+        }
+        if (r.m1 >= 0) {
+          const size_t ps = (size_t)(r.m1 >> 8) * nz + k;
+          r.Vs1 = __ldg(T.V32 + ps);
+          r.Gs1 = __ldg(T.G32 + ps);
+        }
+      }
+      return r;
+    };
+    auto use = [&](int q, const In& r) {
+      s0 = df_acc(s0, df_mul(df_mul(r.w, r.V), r.J));
+      s1 = df_acc(s1, df_mul(df_mul(r.w, r.gV), r.J));
+      const float Wc0 = r.Wr * (r.Vf * (nlo_f - r.gf * nup_f));
       // third solution of Sect. 2.5.2: d J/d n over 1 - chi_sca Leta
-      const float Wc = pv == 3 ? Wc0 / (1.0f - sca_f * Le) : Wc0;
+      const float Wc = pv == 3 ? Wc0 / (1.0f - sca_f * r.Le) : Wc0;
       if (pv == 2) {
         // second solution: + chi_sca (d J/d n_j)^dagger Leta for every level
-        const float f = Wc0 * sca_f * Le;
-        const double* Dq = cd.w.dJdn + (size_t)o * nl;
+        const float f = Wc0 * sca_f * r.Le;
+        const double* Dq = cd.w.dJdn + ((size_t)q * nz + k) * nl;
         for (int j = 0; j < nl; ++j) sm.f(wid, j, lane) = fmaf(f, (float)Dq[j], sm.f(wid, j, lane));
       }
-      const float cLx = Wc * Lx, cU = Wc * (T.c2f[q] * Le - Lx);
-      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-        const int ts = T.q_t[s];
-        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-        const float Vs = T.V32[ps];
-        float& zl = sm.f(wid, T.t_lo[ts], lane);
-        zl = fmaf(cLx, Vs, zl);                     // beta_j (Sect. 2.5.1, read from Eq. chi)
-        float& zu = sm.f(wid, T.t_up[ts], lane);
-        zu = fmaf(cU, T.G32[ps] * Vs, zu);          // and gamma_j (Eq. der_eta_n)
+      const float cLx = Wc * r.Lx, cU = Wc * (r.c2f * r.Le - r.Lx);
+      // beta_j (Sect. 2.5.1, read from Eq. chi) and gamma_j (Eq. der_eta_n)
+      // of every transition active at nu
+      auto add_terms = [&](int m, float Vs, float Gs) {
+        float& zl = sm.f(wid, (m >> 4) & 15, lane);
+        zl = fmaf(cLx, Vs, zl);
+        float& zu = sm.f(wid, m & 15, lane);
+        zu = fmaf(cU, Gs * Vs, zu);
+      };
+      if (packed) {
+        if (r.m0 >= 0) add_terms(r.m0, r.Vs0, r.Gs0);
+        if (r.m1 >= 0) {
+          add_terms(r.m1, r.Vs1, r.Gs1);
+          for (int j = 2; j < kQMetaT; ++j) {
+            const int m = __ldg(T.qmeta + (size_t)j * T.nq + q);
+            if (m < 0) break;
+            const size_t ps = (size_t)(m >> 8) * nz + k;
+            add_terms(m, __ldg(T.V32 + ps), __ldg(T.G32 + ps));
+          }
+        }
+      } else {
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          add_terms((T.t_lo[ts] << 4) | T.t_up[ts], T.V32[ps], T.G32[ps]);
+        }
       }
+    };
+    int q = qa + wid;
+    for (; q + kRateWarps <= qb; q += 2 * kRateWarps) {
+      const In r0 = ld(q), r1 = ld(q + kRateWarps);
+      use(q, r0);
+      use(q + kRateWarps, r1);
     }
+    if (q <= qb) use(q, ld(q));
   } else if (base_mode) {
     const int pv = precond_variant(cd, bopts);
     const double sca = T.chi_sca[k];
@@ -980,10 +1041,13 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __re
 // launchers
 // ---------------------------------------------------------------------------
 // Blocks per column of the grid-stride opacity kernel: all the points of a
-// column when the batch is small, about 32 blocks per SM in total otherwise.
+// column when the batch is small, about 128 blocks per SM in total otherwise
+// (only the columns in the launch's evaluation kind work, a fifth or so of a
+// large batch in the base-type launch, and their blocks should still fill
+// the GPU; the others' blocks return after two loads).
 static dim3 opacity_grid(const Batch& b, int tb) {
   const long need = ((long)b.max_nq * b.max_nz + tb - 1) / tb;
-  const long share = (32L * b.n_sm + b.ncols - 1) / b.ncols;
+  const long share = (128L * b.n_sm + b.ncols - 1) / b.ncols;
   return dim3((unsigned)std::max(1L, std::min(need, share)), b.ncols);
 }
 
@@ -1009,9 +1073,13 @@ static void launch_rates_tan32(const Batch& b, cudaStream_t s) {
 }
 
 int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, cudaStream_t side,
-                      cudaEvent_t ev2, cudaEvent_t ev3) {
+                      cudaEvent_t ev2, cudaEvent_t ev3, const cudaEvent_t* stage) {
   const int nc = b.ncols;
   if (nc == 0) return JFNK_OK;
+  auto mark = [&](int j) -> int {
+    if (stage) JFNK_CUDA(cudaEventRecordWithFlags(stage[j], s, cudaEventRecordExternal));
+    return JFNK_OK;
+  };
   const int tb = 256;
   dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
   dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
@@ -1043,14 +1111,15 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     JFNK_CUDA(cudaGetLastError());
     return JFNK_OK;
   }
+  if (int rm = mark(0)) return rm;
   if (b.formal_kind == FORMAL_MOVING) {
     // per-ray opacity, formal solution and rate integrals (velocity.cu), then
     // the common assembly
     int rc = launch_moving_evaluation(b, s, ev0, ev1);
-    if (rc) return rc;
+    if (rc || (rc = mark(1))) return rc;
     k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
     JFNK_CUDA(cudaGetLastError());
-    return JFNK_OK;
+    return mark(2);
   }
   if (b.formal_kind == FORMAL_SWEEP) {
     // (float tangent direction,) opacity, then the per-frequency sweeps; with
@@ -1091,10 +1160,11 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     if (rc) return rc;
     launch_dJdn_update(b, s);
     if (b.mixed) launch_rates_tan32(b, s);
+    if ((rc = mark(1))) return rc;
   }
   k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
   JFNK_CUDA(cudaGetLastError());
-  return JFNK_OK;
+  return mark(2);
 }
 
 
