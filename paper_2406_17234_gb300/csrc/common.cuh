@@ -82,8 +82,7 @@ struct ColTables {
   const double* Rsp;      // [nt][nz] sum_q W g V 2 h nu^3/c^2: the spontaneous part of R_ji
   const float* V32;       // [nwin][nz] float copies (mixed-mode tangent evaluations)
   const float* G32;       // [nwin][nz]
-  const float* V32T;      // [nz][nwin] the same, depth-major
-  const float* G32T;      // [nz][nwin]
+  const float2* VG32T;    // [nz][nwin] the same pairs (V, G), depth-major
   const float* W32;       // [nwin] omega_t(nu_q) 4 pi/(h nu_q) 2 h nu_q^3/c^2 in float
   const float* Wr32;      // [nwin] omega_t(nu_q) 4 pi/(h nu_q) in float
   const float* c2f;       // [nq] 2 h nu^3/c^2 in float
@@ -91,6 +90,7 @@ struct ColTables {
                           // t << 1 | (1 if the level is the upper one), -1 after the last
   const int* qmeta;       // [kQMetaT][nq] transitions active at nu_q, packed as
                           // window point << 8 | lo << 4 | up; -1 past the last
+  const int* qtr;         // [kQMetaT][nq] the same transitions' indices t
   const double* dz;       // [nz-1] |z_k - z_{k+1}|
   const double* mu;       // [nmu]
   const double* wmu;      // [nmu]

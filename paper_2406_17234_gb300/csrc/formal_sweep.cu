@@ -291,18 +291,17 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
   auto tan_issue = [&](int kk) {
     if (kk < nz) {
       float* r = s_ring + (size_t)(kk % kRing) * kRingSlots * bd + threadIdx.x;
-      const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
-      const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
+      const float* __restrict__ VGk = reinterpret_cast<const float*>(T.VG32T + (size_t)kk * T.nwin);
       const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
       if (pm0 >= 0) {
-        cp_async4(r, Vk + (pm0 >> 8));
-        cp_async4(r + bd, Gk + (pm0 >> 8));
+        cp_async4(r, VGk + 2 * (pm0 >> 8));
+        cp_async4(r + bd, VGk + 2 * (pm0 >> 8) + 1);
         cp_async4(r + 2 * bd, vk + ((pm0 >> 4) & 15));
         cp_async4(r + 3 * bd, vk + (pm0 & 15));
       }
       if (pm1 >= 0) {
-        cp_async4(r + 4 * bd, Vk + (pm1 >> 8));
-        cp_async4(r + 5 * bd, Gk + (pm1 >> 8));
+        cp_async4(r + 4 * bd, VGk + 2 * (pm1 >> 8));
+        cp_async4(r + 5 * bd, VGk + 2 * (pm1 >> 8) + 1);
         cp_async4(r + 6 * bd, vk + ((pm1 >> 4) & 15));
         cp_async4(r + 7 * bd, vk + (pm1 & 15));
       }
@@ -322,14 +321,14 @@ __device__ __forceinline__ void sweep_thread(const ColDesc& cd, int q, const flo
     if (pm0 >= 0) tan_acc(ta, r[0], r[bd], r[2 * bd], r[3 * bd]);
     if (pm1 >= 0) {
       tan_acc(ta, r[4 * bd], r[5 * bd], r[6 * bd], r[7 * bd]);
-      const float* __restrict__ Vk = T.V32T + (size_t)kk * T.nwin;
-      const float* __restrict__ Gk = T.G32T + (size_t)kk * T.nwin;
+      const float2* __restrict__ VGk = T.VG32T + (size_t)kk * T.nwin;
       const float* __restrict__ vk = cd.w.v32 + (size_t)kk * nl;
 #pragma unroll
       for (int j = 2; j < kQMetaT; ++j) {
         const int m = __ldg(T.qmeta + (size_t)j * nq + q);
         if (m < 0) break;
-        tan_acc(ta, __ldg(Vk + (m >> 8)), __ldg(Gk + (m >> 8)), __ldg(vk + ((m >> 4) & 15)), __ldg(vk + (m & 15)));
+        const float2 a = __ldg(VGk + (m >> 8));
+        tan_acc(ta, a.x, a.y, __ldg(vk + ((m >> 4) & 15)), __ldg(vk + (m & 15)));
       }
     }
     dc = ta.dchi;

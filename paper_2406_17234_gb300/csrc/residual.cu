@@ -148,43 +148,87 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
   if (mode == EV_RH92) cd.w.eta[i] = eta;   // for the RH92 rate sums
 }
 
-// Mixed mode, tangent evaluations: dchi and dS in FP32 (tan_acc), one thread
-// per (k, nu) with nu fastest, so that every warp reads and writes coalesced
-// rows of the depth-major arrays and line tables; the transitions active at
-// nu come from the packed qmeta table (one dependent load, then the data).
-__global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict__ cols) {
+// Mixed mode, tangent evaluations: dchi and dS in FP32 (tan_acc). A thread
+// owns one frequency nu and a run of kOpTanDepths depths; consecutive threads
+// take consecutive frequencies, so every warp reads and writes coalesced rows
+// of the depth-major arrays and line tables. The transitions active at nu
+// come from the packed qmeta table, loaded once (the first two held, the
+// others read when present), and kOpTanBatch depths' table loads are issued
+// before any of their sums use them.
+constexpr int kOpTanDepths = 16;
+constexpr int kOpTanBatch = 2;   // depths whose loads are issued together
+__global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict__ cols, int nqb) {
   const ColDesc& cd = cols[blockIdx.y];
   if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
   const ColTables& T = cd.t;
   const int nq = T.nq, nz = T.nz, nl = T.nl, nwin = T.nwin;
+  const int qb = blockIdx.x % nqb, kc = blockIdx.x / nqb;
+  const int q = qb * blockDim.x + threadIdx.x, k0 = kc * kOpTanDepths;
+  if (q >= nq || k0 >= nz) return;
+  const int k1 = min(nz, k0 + kOpTanDepths);
   const size_t pitch = (size_t)col_pitch(nq);
-  const float* __restrict__ V32T = T.V32T;
-  const float* __restrict__ G32T = T.G32T;
-  const float* __restrict__ v32 = cd.w.v32;
-  const int* __restrict__ qmeta = T.qmeta;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nq * nz; i += gridDim.x * blockDim.x) {
-    const int k = i / nq, q = i - k * nq;
-    const float* V32 = V32T + (size_t)k * nwin;
-    const float* G32 = G32T + (size_t)k * nwin;
-    const float* v = v32 + k * nl;
-    TanAcc ta;
-#pragma unroll
-    for (int j = 0; j < kQMetaT; ++j) {
-      const int m = __ldg(qmeta + (size_t)j * nq + q);
-      if (m < 0) break;
-      const int p = m >> 8;
-      tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + ((m >> 4) & 15)), __ldg(v + (m & 15)));
+  const int m0 = __ldg(T.qmeta + q), m1 = __ldg(T.qmeta + (size_t)nq + q);
+  struct In {
+    float V0, G0, l0, u0, V1, G1, l1, u1, S, c;
+  };
+  auto ld = [&](int k) {
+    In r;
+    const float2* __restrict__ VG = T.VG32T + (size_t)k * nwin;
+    const float* __restrict__ v = cd.w.v32 + (size_t)k * nl;
+    const size_t o = (size_t)k * pitch + q;
+    r.S = __ldg(cd.w.S32T + o);
+    r.c = __ldg(cd.w.chiT + o);
+    r.V0 = r.G0 = r.l0 = r.u0 = r.V1 = r.G1 = r.l1 = r.u1 = 0.f;
+    if (m0 >= 0) {
+      const float2 a = __ldg(VG + (m0 >> 8));
+      r.V0 = a.x;
+      r.G0 = a.y;
+      r.l0 = __ldg(v + ((m0 >> 4) & 15));
+      r.u0 = __ldg(v + (m0 & 15));
     }
-    if (T.max_overlap > kQMetaT)
-      for (int s = T.q_off[q] + kQMetaT; s < T.q_off[q + 1]; ++s) {
-        const int t = T.q_t[s];
-        const int p = T.t_base[t] + q - T.t_q0[t];
-        tan_acc(ta, __ldg(V32 + p), __ldg(G32 + p), __ldg(v + T.t_lo[t]), __ldg(v + T.t_up[t]));
+    if (m1 >= 0) {
+      const float2 a = __ldg(VG + (m1 >> 8));
+      r.V1 = a.x;
+      r.G1 = a.y;
+      r.l1 = __ldg(v + ((m1 >> 4) & 15));
+      r.u1 = __ldg(v + (m1 & 15));
+    }
+    return r;
+  };
+  auto fin = [&](int k, const In& r) {
+    TanAcc ta;
+    if (m0 >= 0) tan_acc(ta, r.V0, r.G0, r.l0, r.u0);
+    if (m1 >= 0) {
+      tan_acc(ta, r.V1, r.G1, r.l1, r.u1);
+      const float2* __restrict__ VG = T.VG32T + (size_t)k * nwin;
+      const float* __restrict__ v = cd.w.v32 + (size_t)k * nl;
+#pragma unroll
+      for (int j = 2; j < kQMetaT; ++j) {
+        const int m = __ldg(T.qmeta + (size_t)j * nq + q);
+        if (m < 0) break;
+        const float2 a = __ldg(VG + (m >> 8));
+        tan_acc(ta, a.x, a.y, __ldg(v + ((m >> 4) & 15)), __ldg(v + (m & 15)));
       }
+      if (T.max_overlap > kQMetaT)
+        for (int s = T.q_off[q] + kQMetaT; s < T.q_off[q + 1]; ++s) {
+          const int t = T.q_t[s];
+          const float2 a = __ldg(VG + T.t_base[t] + q - T.t_q0[t]);
+          tan_acc(ta, a.x, a.y, __ldg(v + T.t_lo[t]), __ldg(v + T.t_up[t]));
+        }
+    }
     const size_t o = (size_t)k * pitch + q;
     cd.w.dchiT[o] = ta.dchi;
-    cd.w.dS32T[o] = tan_dS(ta, __ldg(cd.w.S32T + o), __ldg(cd.w.chiT + o));
+    cd.w.dS32T[o] = tan_dS(ta, r.S, r.c);
+  };
+  int k = k0;
+  for (; k + kOpTanBatch <= k1; k += kOpTanBatch) {
+    In r[kOpTanBatch];
+#pragma unroll
+    for (int i = 0; i < kOpTanBatch; ++i) r[i] = ld(k + i);
+#pragma unroll
+    for (int i = 0; i < kOpTanBatch; ++i) fin(k + i, r[i]);
   }
+  for (; k < k1; ++k) fin(k, ld(k));
 }
 
 // Mixed mode, tangent evaluations: the tangent rate integrals (Eqs. Rij/Rji
@@ -206,8 +250,7 @@ __global__ void __launch_bounds__(32 * kRateTanWarps) k_rates_tan32(const ColDes
   const int nz = T.nz, nwin = T.nwin;
   const size_t pitch = (size_t)col_pitch(T.nq);
   const int q0 = T.t_q0[t], q1 = T.t_q1[t], base = T.t_base[t];
-  const float* __restrict__ V32 = T.V32T + base - q0;
-  const float* __restrict__ G32 = T.G32T + base - q0;
+  const float2* __restrict__ VG = T.VG32T + base - q0;
   const float* __restrict__ W32 = T.W32 + base - q0;
   const float* __restrict__ dJ = cd.w.dJ32T;
   float a0[kRateTanDepths], a1[kRateTanDepths];
@@ -219,10 +262,11 @@ __global__ void __launch_bounds__(32 * kRateTanWarps) k_rates_tan32(const ColDes
     for (int d = 0; d < kRateTanDepths; ++d) {
       const int k = k0 + d * kRateTanWarps;
       if (k < nz) {
-        const float WV = W * __ldg(V32 + (size_t)k * nwin + q);
+        const float2 vg = __ldg(VG + (size_t)k * nwin + q);
+        const float WV = W * vg.x;
         const float x = __ldg(dJ + (size_t)k * pitch + q);
         a0[d] = fmaf(WV, x, a0[d]);
-        a1[d] = fmaf(WV * __ldg(G32 + (size_t)k * nwin + q), x, a1[d]);
+        a1[d] = fmaf(WV * vg.y, x, a1[d]);
       }
     }
   }
@@ -696,29 +740,93 @@ __device__ void rates_tile(const ColDesc& cd, const int mode, const int t, const
   } else if (mix) {
     // RH92 (full preconditioning): N_t(n') = sum W [chi_t(n') Jeff + chi_t(n) Psi eta(n') - eta_t(n')]
     const float nlo_f = (float)n_lo, nup_f = (float)n_up;
-    for (int q = qa + wid; q <= qb; q += kRateWarps) {
+    const bool packed = T.max_overlap <= kQMetaT;
+    const float2* __restrict__ eta2 = as_pairs(cd.w.eta);
+    // one frequency's inputs; two frequencies are loaded before the first is
+    // summed, so that their latencies overlap (the sums keep their order)
+    struct In {
+      df J, w, V, gV, eta;
+      float Le, Wf, Vf, gf, c2f, etab;
+      int m0, t0, m1, t1;
+      float GV0, GV1;
+    };
+    auto ld = [&](int q) {
+      In r;
       const int p = wbase + q - q0;
       const size_t pk = (size_t)p * nz + k, o = (size_t)q * nz + k;
-      const df Jq = df_load(J2, o), w = df_load(T.W2, p);
-      s0 = df_acc(s0, df_mul(df_mul(w, df_load(T.V2, pk)), Jq));
-      s1 = df_acc(s1, df_mul(df_mul(w, df_load(T.gV2, pk)), Jq));
-      const float Le = cd.w.Leta32[o];
-      // Jeff = J - Psi* eta cancels in optically thick layers: formed from the pairs
-      const float Jf = df_to_float(df_sub(Jq, df_mul_f(df_load(as_pairs(cd.w.eta), o), Le)));
-      const float Wf = T.Wr32[p], Vf = T.V32[pk], gf = T.G32[pk], c2f = T.c2f[q];
-      const float WVf = Wf * Vf;
-      f0 = fmaf(WVf, Jf, f0);
-      f1 = fmaf(WVf * gf, Jf, f1);
-      const float wcp = Wf * (Vf * (nlo_f - gf * nup_f)) * Le;
-      f3 = fmaf(wcp, cd.w.etab32[o], f3);
-      const float wcu = wcp * c2f;
-      for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
-        const int ts = T.q_t[s];
-        const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
-        float& z = sm.f(wid, ts, lane);
-        z = fmaf(wcu, T.G32[ps] * T.V32[ps], z);
+      r.J = df_load(J2, o);
+      r.w = df_load(T.W2, p);
+      r.V = df_load(T.V2, pk);
+      r.gV = df_load(T.gV2, pk);
+      r.eta = df_load(eta2, o);
+      r.Le = cd.w.Leta32[o];
+      r.Wf = __ldg(T.Wr32 + p);
+      r.Vf = __ldg(T.V32 + pk);
+      r.gf = __ldg(T.G32 + pk);
+      r.c2f = __ldg(T.c2f + q);
+      r.etab = cd.w.etab32[o];
+      r.m0 = r.m1 = r.t0 = r.t1 = -1;
+      r.GV0 = r.GV1 = 0.f;
+      if (packed) {
+        // the packed tables give window point and transition in two loads
+        r.m0 = __ldg(T.qmeta + q);
+        r.m1 = __ldg(T.qmeta + (size_t)T.nq + q);
+        r.t0 = __ldg(T.qtr + q);
+        r.t1 = __ldg(T.qtr + (size_t)T.nq + q);
+        if (r.m0 >= 0) {
+          const size_t ps = (size_t)(r.m0 >> 8) * nz + k;
+          r.GV0 = __ldg(T.G32 + ps) * __ldg(T.V32 + ps);
+        }
+        if (r.m1 >= 0) {
+          const size_t ps = (size_t)(r.m1 >> 8) * nz + k;
+          r.GV1 = __ldg(T.G32 + ps) * __ldg(T.V32 + ps);
+        }
       }
+      return r;
+    };
+    auto use = [&](int q, const In& r) {
+      s0 = df_acc(s0, df_mul(df_mul(r.w, r.V), r.J));
+      s1 = df_acc(s1, df_mul(df_mul(r.w, r.gV), r.J));
+      // Jeff = J - Psi* eta cancels in optically thick layers: formed from the pairs
+      const float Jf = df_to_float(df_sub(r.J, df_mul_f(r.eta, r.Le)));
+      const float WVf = r.Wf * r.Vf;
+      f0 = fmaf(WVf, Jf, f0);
+      f1 = fmaf(WVf * r.gf, Jf, f1);
+      const float wcp = r.Wf * (r.Vf * (nlo_f - r.gf * nup_f)) * r.Le;
+      f3 = fmaf(wcp, r.etab, f3);
+      const float wcu = wcp * r.c2f;
+      if (packed) {
+        if (r.m0 >= 0) {
+          float& z = sm.f(wid, r.t0, lane);
+          z = fmaf(wcu, r.GV0, z);
+        }
+        if (r.m1 >= 0) {
+          float& z = sm.f(wid, r.t1, lane);
+          z = fmaf(wcu, r.GV1, z);
+          for (int j = 2; j < kQMetaT; ++j) {
+            const int m = __ldg(T.qmeta + (size_t)j * T.nq + q);
+            if (m < 0) break;
+            const size_t ps = (size_t)(m >> 8) * nz + k;
+            float& zj = sm.f(wid, __ldg(T.qtr + (size_t)j * T.nq + q), lane);
+            zj = fmaf(wcu, __ldg(T.G32 + ps) * __ldg(T.V32 + ps), zj);
+          }
+        }
+      } else {
+        for (int s = T.q_off[q]; s < T.q_off[q + 1]; ++s) {
+          const int ts = T.q_t[s];
+          const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
+          float& z = sm.f(wid, ts, lane);
+          z = fmaf(wcu, T.G32[ps] * T.V32[ps], z);
+        }
+      }
+    };
+    int q = qa + wid;
+    for (; q + kRateWarps <= qb; q += 2 * kRateWarps) {
+      const In r0 = ld(q), r1 = ld(q + kRateWarps);
+      use(q, r0);
+      use(q + kRateWarps, r1);
     }
+    if (q <= qb) use(q, ld(q));
   } else {
     const double* Jd = jdag_ptr(cd);
     for (int q = qa + wid; q <= qb; q += kRateWarps) {
@@ -1051,8 +1159,14 @@ static dim3 opacity_grid(const Batch& b, int tb) {
   return dim3((unsigned)std::max(1L, std::min(need, share)), b.ncols);
 }
 
+// k_opacity_tan32: blocks of 256 frequencies x kOpTanDepths depths per column.
+static void launch_op_tan(const Batch& b, cudaStream_t s) {
+  const int nqb = (b.max_nq + 255) / 256, nkc = (b.max_nz + kOpTanDepths - 1) / kOpTanDepths;
+  k_opacity_tan32<<<dim3(nqb * nkc, b.ncols), 256, 0, s>>>(b.d_cols, nqb);
+}
+
 int launch_opacity_tan(const Batch& b, cudaStream_t s) {
-  k_opacity_tan32<<<opacity_grid(b, 256), 256, 0, s>>>(b.d_cols);
+  launch_op_tan(b, s);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
@@ -1061,7 +1175,7 @@ int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
   const int tb = 256;
   k_pop_pairs<<<dim3((b.max_N + tb - 1) / tb, b.ncols), tb, 0, s>>>(b.d_cols);
   k_opacity<float><<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols, 1);   // base and RH92 columns
-  if (!skip_tangent) k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, s>>>(b.d_cols);
+  if (!skip_tangent) launch_op_tan(b, s);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
@@ -1092,7 +1206,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     JFNK_CUDA(cudaEventRecord(b.fork_ev, s));
     JFNK_CUDA(cudaStreamWaitEvent(side, b.fork_ev, 0));
     k_dir32<<<dim3((b.max_N + tb - 1) / tb, nc), tb, 0, side>>>(b.d_cols);
-    if (!sweep_fused(b)) k_opacity_tan32<<<opacity_grid(b, tb), tb, 0, side>>>(b.d_cols);
+    if (!sweep_fused(b)) launch_op_tan(b, side);
     if (ev2) JFNK_CUDA(cudaEventRecordWithFlags(ev2, side, cudaEventRecordExternal));
     int rc = launch_formal_sweep(b, side, 2);
     if (rc) return rc;

@@ -328,15 +328,14 @@ __global__ void k_window_tables_dir(int nt, const TransDev* tr, const int* t_q0,
 
 // Float copies of the (normalised) window tables for mixed-mode tangents.
 __global__ void k_float_copy(int nwin, int nz, const double* V, const double* G, float* V32, float* G32,
-                             float* V32T, float* G32T) {
+                             float2* VG32T) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)nwin * nz) return;
   const size_t p = i / nz, k = i % nz;
   const float v = (float)V[i], g = (float)G[i];
   V32[i] = v;
   G32[i] = g;
-  V32T[k * nwin + p] = v;
-  G32T[k * nwin + p] = g;
+  VG32T[k * nwin + p] = make_float2(v, g);
 }
 
 // Renormalise each line profile so that sum_q omega_t(q) phi(q, k) = 1 (for
@@ -505,7 +504,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
          o_vt = ar.take<double>(nz);
   size_t o_tr = ar.take<TransDev>(nt), o_cd = ar.take<CollDev>(nt);
   size_t o_W32 = ar.take<float>(nwin), o_Wr32 = ar.take<float>(nwin), o_c2f = ar.take<float>(nq);
-  size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq);
+  size_t o_qmeta = ar.take<int>((size_t)kQMetaT * nq), o_qtr = ar.take<int>((size_t)kQMetaT * nq);
   size_t o_W2 = ar.take<float2>(nwin), o_c2p = ar.take<float2>(nq), o_rc2p = ar.take<float2>(nq);
   size_t o_linc = ar.take<int>((size_t)nl * (nt + 1));
   size_t o_ang32 = ar.take<float4>(nmu), o_dz32 = ar.take<float2>(nz - 1);
@@ -516,7 +515,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   size_t o_sca = ar.take<double>(nz), o_B = ar.take<double>((size_t)nq * nz);
   size_t o_C = ar.take<double>((size_t)nz * nl * nl), o_nstar = ar.take<double>((size_t)nz * nl);
   size_t o_V32 = ar.take<float>((size_t)nwin * nz), o_G32 = ar.take<float>((size_t)nwin * nz);
-  size_t o_V32T = ar.take<float>((size_t)nwin * nz), o_G32T = ar.take<float>((size_t)nwin * nz);
+  size_t o_VG32T = ar.take<float2>((size_t)nwin * nz);
   size_t o_WV = ar.take<double>((size_t)nwin * nz), o_WgV = ar.take<double>((size_t)nwin * nz),
          o_Rsp = ar.take<double>((size_t)nt * nz), o_gV = ar.take<double>((size_t)nwin * nz);
   size_t o_V2 = ar.take<float2>((size_t)nwin * nz), o_gV2 = ar.take<float2>((size_t)nwin * nz),
@@ -605,13 +604,15 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   JFNK_CUDA(up(o_W2, w2.data(), nwin * sizeof(float2)));
   JFNK_CUDA(up(o_c2p, c2p.data(), nq * sizeof(float2)));
   JFNK_CUDA(up(o_rc2p, rc2p.data(), nq * sizeof(float2)));
-  std::vector<int> qmeta((size_t)kQMetaT * nq, -1);
+  std::vector<int> qmeta((size_t)kQMetaT * nq, -1), qtr((size_t)kQMetaT * nq, -1);
   for (int q = 0; q < nq; ++q)
     for (int s = A.q_off[q], j = 0; s < A.q_off[q + 1] && j < kQMetaT; ++s, ++j) {
       const int t = A.q_t[s];
       qmeta[(size_t)j * nq + q] = ((A.t_base[t] + q - A.t_q0[t]) << 8) | (A.t_lo[t] << 4) | A.t_up[t];
+      qtr[(size_t)j * nq + q] = t;
     }
   JFNK_CUDA(up(o_qmeta, qmeta.data(), qmeta.size() * 4));
+  JFNK_CUDA(up(o_qtr, qtr.data(), qtr.size() * 4));
   // per level, its transitions in index order (lower level: +, upper: -)
   std::vector<int> linc((size_t)nl * (nt + 1), -1);
   for (int l = 0; l < nl; ++l) {
@@ -690,7 +691,7 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
                                                   ar.ptr<double>(o_C));
   k_float_copy<<<(int)(((size_t)nwin * nz + tb - 1) / tb), tb, 0, s>>>(
       nwin, nz, ar.ptr<double>(o_V), ar.ptr<double>(o_G), ar.ptr<float>(o_V32), ar.ptr<float>(o_G32),
-      ar.ptr<float>(o_V32T), ar.ptr<float>(o_G32T));
+      ar.ptr<float2>(o_VG32T));
   JFNK_CUDA(cudaGetLastError());
   JFNK_CUDA(cudaEventRecord(ctx->setup_done[lane], s));
   ColTables& tb_ = M->tables;
@@ -708,9 +709,10 @@ int build_atmosphere(jfnk_ctx* ctx, int lane, const AtomData& A, const jfnk_atmo
   tb_.chisca2 = ar.ptr<float2>(o_chisca2); tb_.c2p = ar.ptr<float2>(o_c2p); tb_.rc2p = ar.ptr<float2>(o_rc2p);
   tb_.WV = ar.ptr<double>(o_WV); tb_.WgV = ar.ptr<double>(o_WgV); tb_.Rsp = ar.ptr<double>(o_Rsp);
   tb_.V32 = ar.ptr<float>(o_V32); tb_.G32 = ar.ptr<float>(o_G32); tb_.W32 = ar.ptr<float>(o_W32);
-  tb_.V32T = ar.ptr<float>(o_V32T); tb_.G32T = ar.ptr<float>(o_G32T);
+  tb_.VG32T = ar.ptr<float2>(o_VG32T);
   tb_.Wr32 = ar.ptr<float>(o_Wr32); tb_.c2f = ar.ptr<float>(o_c2f);
   tb_.qmeta = ar.ptr<int>(o_qmeta);
+  tb_.qtr = ar.ptr<int>(o_qtr);
   tb_.lvl_inc = ar.ptr<int>(o_linc);
   tb_.mu = ar.ptr<double>(o_mu); tb_.wmu = ar.ptr<double>(o_wmu);
   tb_.ang32 = ar.ptr<float4>(o_ang32); tb_.dz32 = ar.ptr<float2>(o_dz32);
