@@ -1012,10 +1012,49 @@ static void launch_dJdn_update(const Batch& b, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 constexpr int kAsmWarps = 4;
 
+// Tangent evaluations: the directional derivative of F only (no block of the
+// preconditioner), one thread per depth so that the per-(transition, depth)
+// rates are read in coalesced rows; each level's sum runs over its own
+// transitions in index order, the additions of the warp-per-depth kernel.
+constexpr int kAsmTanThreads = 128;
+__global__ void __launch_bounds__(kAsmTanThreads) k_assemble_tan(const ColDesc* __restrict__ cols) {
+  const ColDesc& cd = cols[blockIdx.y];
+  if (eval_mode(cd) != EV_TANGENT) return;
+  const ColTables& T = cd.t;
+  const int nz = T.nz, nl = T.nl, nt = T.nt;
+  const int k = blockIdx.x * kAsmTanThreads + threadIdx.x;
+  if (k >= nz) return;
+  const double* n = cd.w.n + (size_t)k * nl;
+  const double* v = tangent_dir(cd) + (size_t)k * nl;
+  const double* C = T.C + (size_t)k * nl * nl;
+  const int is = cd.w.istar[k];
+  for (int l = 0; l < nl; ++l) {
+    double f = 0.0;
+    if (l == is) {
+      for (int j = 0; j < nl; ++j) f += v[j];
+      f = -f;
+    } else {
+      const int* inc = T.lvl_inc + l * (nt + 1);
+      for (int e = 0; e < nt; ++e) {
+        const int m = __ldg(inc + e);
+        if (m < 0) break;
+        const int t = m >> 1;
+        const int lo = __ldg(T.t_lo + t), up = __ldg(T.t_up + t);
+        const size_t o = (size_t)t * nz + k;
+        const double ur = C[lo * nl + up] + cd.w.Rup[o];
+        const double dr = C[up * nl + lo] + cd.w.Rdn[o];
+        const double kp = v[lo] * ur + n[lo] * cd.w.dRup[o] - v[up] * dr - n[up] * cd.w.dRdn[o];
+        f += (m & 1) ? -kp : kp;
+      }
+    }
+    cd.w.dF[(size_t)k * nl + l] = f;
+  }
+}
+
 __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __restrict__ cols) {
   const ColDesc& cd = cols[blockIdx.y];
   const int mode = eval_mode(cd);
-  if (mode == EV_SKIP) return;
+  if (mode == EV_SKIP || mode == EV_TANGENT) return;   // k_assemble_tan
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1180,6 +1219,13 @@ int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
   return JFNK_OK;
 }
 
+// The assembly: tangent evaluations thread per depth, the others warp per depth.
+static void launch_assemble(const Batch& b, cudaStream_t s) {
+  k_assemble_tan<<<dim3((b.max_nz + kAsmTanThreads - 1) / kAsmTanThreads, b.ncols), kAsmTanThreads, 0, s>>>(
+      b.d_cols);
+  k_assemble<<<dim3((b.max_nz + kAsmWarps - 1) / kAsmWarps, b.ncols), 32 * kAsmWarps, 0, s>>>(b.d_cols);
+}
+
 static void launch_rates_tan32(const Batch& b, cudaStream_t s) {
   k_rates_tan32<<<dim3((b.max_nz + kRateTanWarps * kRateTanDepths - 1) / (kRateTanWarps * kRateTanDepths),
                        b.max_nt, b.ncols),
@@ -1197,7 +1243,6 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
   const int tb = 256;
   dim3 g_qk((b.max_nq * b.max_nz + tb - 1) / tb, nc);
   dim3 g_ray((b.max_nq * 2 * b.max_nmu + 63) / 64, nc);
-  dim3 g_asm((b.max_nz + kAsmWarps - 1) / kAsmWarps, nc);
   if (b.formal_kind == FORMAL_SWEEP && side) {
     // Two independent chains over disjoint columns (a column is in one
     // evaluation kind per tick): tangent evaluations (FP32, issue-bound) on the
@@ -1221,7 +1266,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     if ((rc = launch_rates(b, s))) return rc;
     launch_dJdn_update(b, s);
     JFNK_CUDA(cudaStreamWaitEvent(s, b.join_ev, 0));
-    k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
+    launch_assemble(b, s);
     JFNK_CUDA(cudaGetLastError());
     return JFNK_OK;
   }
@@ -1231,7 +1276,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     // the common assembly
     int rc = launch_moving_evaluation(b, s, ev0, ev1);
     if (rc || (rc = mark(1))) return rc;
-    k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
+    launch_assemble(b, s);
     JFNK_CUDA(cudaGetLastError());
     return mark(2);
   }
@@ -1276,7 +1321,7 @@ int launch_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent
     if (b.mixed) launch_rates_tan32(b, s);
     if ((rc = mark(1))) return rc;
   }
-  k_assemble<<<g_asm, 32 * kAsmWarps, 0, s>>>(b.d_cols);
+  launch_assemble(b, s);
   JFNK_CUDA(cudaGetLastError());
   return mark(2);
 }
