@@ -306,12 +306,42 @@ FORMAL_KERNELS = {0: "k_formal<double> + k_ray_sum (per-ray buffers)", 1: "k_for
                   4: "k_mv_formal (moving column, thread per ray)"}
 
 
-def measured_peaks(B, ctx):
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM per clock (Blackwell SM: 4 x 32)
+
+
+def nominal_fp32_fma(device=0):
+    """FP32 FMA lane instructions per second from the unit count and the maximum
+    SM clock: multiprocessors x 128 lanes x the clock (MEASURED_PEAKS.json's
+    sm_max_mhz, else nvidia-smi's clocks.max.sm)."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = None
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                                  "-i", str(device)], capture_output=True, text=True, timeout=20).stdout
+            mhz = float(out.split()[0])
+        except Exception:
+            mhz = None
+    return None if mhz is None else n_sm * FP32_LANES_PER_SM * mhz * 1e6
+
+
+def measured_peaks(B, ctx, device=0):
     """Pipe rates measured on this GPU by the library's probe kernels
     (jfnk_probe_alu): FP32 and FP64 fused multiply-adds per second (lane
-    instructions) and MUFU exponentials per second."""
-    return {"fp32_fma_per_s": B.probe_alu(ctx, 1) / 2.0, "fp64_fma_per_s": B.probe_alu(ctx, 0) / 2.0,
-            "fp64_exp_per_s": B.probe_alu(ctx, 2), "mufu_per_s": B.probe_alu(ctx, 3)}
+    instructions) and MUFU exponentials per second. The FP32 rate taken as the
+    roofline denominator is the larger of the probe's and the nominal one, so a
+    probe that ran below the maximum clock cannot inflate a fraction."""
+    p = {"fp32_fma_per_s": B.probe_alu(ctx, 1) / 2.0, "fp64_fma_per_s": B.probe_alu(ctx, 0) / 2.0,
+         "fp64_exp_per_s": B.probe_alu(ctx, 2), "mufu_per_s": B.probe_alu(ctx, 3)}
+    nom = nominal_fp32_fma(device)
+    p["fp32_fma_probe_per_s"] = p["fp32_fma_per_s"]
+    p["fp32_fma_nominal_per_s"] = nom
+    if nom is not None:
+        p["fp32_fma_per_s"] = max(p["fp32_fma_per_s"], nom)
+    return p
 
 
 def peak_rate(kind, fp64, peaks):
@@ -356,8 +386,11 @@ def peak_source(fp64, peaks):
     if fp64:
         return (f"measured FP64 FMA {peaks['fp64_fma_per_s'] * 2 / 1e12:.3f} TFLOP/s and FP64 exp "
                 f"{peaks['fp64_exp_per_s'] / 1e9:.1f} G/s (jfnk_probe_alu kinds 0, 2)")
-    return (f"measured FP32 FMA {peaks['fp32_fma_per_s'] * 2 / 1e12:.1f} TFLOP/s and MUFU exp "
-            f"{peaks['mufu_per_s'] / 1e12:.3f} T/s (jfnk_probe_alu kinds 1, 3) with unit counts "
+    nom = peaks.get("fp32_fma_nominal_per_s")
+    return (f"FP32 FMA {peaks['fp32_fma_per_s'] * 2 / 1e12:.1f} TFLOP/s (the larger of the probe's "
+            f"{peaks.get('fp32_fma_probe_per_s', peaks['fp32_fma_per_s']) * 2 / 1e12:.1f} and the nominal "
+            f"{'n/a' if nom is None else f'{nom * 2 / 1e12:.1f}'}: SMs x 128 lanes x max clock) and measured "
+            f"MUFU exp {peaks['mufu_per_s'] / 1e12:.3f} T/s (jfnk_probe_alu kinds 1, 3) with unit counts "
             f"value {ALG_OPS['value']}, jvp {ALG_OPS['jvp']} (FP32 ops, MUFU ops) per ray-point")
 
 
@@ -366,7 +399,7 @@ def alu_roofline(B, ctx, fp64, n_value, n_jvp, pts_per_launch, kern_ms, launches
     tick, value and JVP evaluations mixed): achieved = ray-points per launch /
     mean launch time (in-graph CUDA events around the formal kernel of every
     tick), peak = the mix of the two kinds' rooflines at the measured rates."""
-    peaks = measured_peaks(B, ctx)
+    peaks = measured_peaks(B, ctx, device)
     w_v, w_j = n_value / max(1, n_value + n_jvp), n_jvp / max(1, n_value + n_jvp)
     peak = 1.0 / (w_v / peak_rate("value", fp64, peaks) + w_j / peak_rate("jvp", fp64, peaks))
     avg_s = kern_ms * 1e-3 / max(1, launches)
@@ -668,7 +701,7 @@ def run_batch(args, rank, ws, local, dist):
     total_ms, pts, conv, e2e_s, e2e_pts = mx[0], sm[1], sm[2], mx[3], sm[4]
     if rank != 0:
         return
-    peaks = measured_peaks(B, ctx)
+    peaks = measured_peaks(B, ctx, local)
     tan_ms = float(sum(s["formal_tan_ms"] for s in pst[:1]))
     base_ms = float(sum(s["formal_ms"] for s in pst[:1]))
     launches = int(pst[0]["formal_launches"])

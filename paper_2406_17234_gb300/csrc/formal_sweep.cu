@@ -20,6 +20,7 @@
 // intensity form I with the re-anchoring of D on I - S); only the order of
 // the ray sums differs: each hemisphere is summed over its angles first and
 // the two hemisphere sums are then added.
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -912,15 +913,22 @@ int sweep_autotune(Batch* b, cudaStream_t s) {
     }
     return launch_sweep_cfg(*b, s, variant, size, which, ot, ob, fuse);
   };
+  // a candidate's time: the fastest of five launches timed one by one, after a
+  // warm-up (single launches differ by a few per cent; the minimum is stable)
   auto timed = [&](int variant, int size, int which, int ot, int ob, float* ms, int fuse = 0) -> int {
     int r = once(variant, size, which, ot, ob, fuse);   // warm-up
     if (r) return r;
-    if (cudaEventRecord(e0, s) != cudaSuccess) return fail(JFNK_E_CUDA, "autotune event");
-    for (int i = 0; i < 3 && !r; ++i) r = once(variant, size, which, ot, ob, fuse);
-    if (r) return r;
-    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
-      return fail(JFNK_E_CUDA, "autotune timing");
+    float best = 1e30f;
+    for (int i = 0; i < 5; ++i) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return fail(JFNK_E_CUDA, "autotune event");
+      if ((r = once(variant, size, which, ot, ob, fuse))) return r;
+      float t = 0.f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+        return fail(JFNK_E_CUDA, "autotune timing");
+      best = std::min(best, t);
+    }
+    *ms = best;
     return JFNK_OK;
   };
   // The fused opacity tangent (forced variant only) is not a candidate: timed

@@ -6,13 +6,16 @@ namespace jfnk {
 
 constexpr int kChains = 8;
 constexpr int kIters = 4096;
+// FP32 and MUFU launches run 8x longer (about 2 ms), so that each launch is
+// timed at the clock the SMs hold under load rather than during a ramp
+constexpr int kIters32 = 8 * kIters;
 
-template <typename T>
+template <typename T, int ITERS>
 __global__ void k_probe_fma(T* out, T a, T b) {
   T x[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
-  for (int it = 0; it < kIters; ++it) {
+  for (int it = 0; it < ITERS; ++it) {
 #pragma unroll
     for (int c = 0; c < kChains; ++c) x[c] = x[c] * a + b;
   }
@@ -48,7 +51,7 @@ __global__ void k_probe_exp32(float* out) {
   float x[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) x[c] = 1e-3f * (threadIdx.x + c);
-  for (int it = 0; it < kIters; ++it) {
+  for (int it = 0; it < kIters32; ++it) {
 #pragma unroll
     for (int c = 0; c < kChains; ++c) x[c] = ex2_mufu(-x[c]);   // stays in [1/2, 1)
   }
@@ -109,11 +112,11 @@ extern "C" int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s) {
   cudaEventCreate(&e1);
   cudaStream_t s = ctx->stream;
   float best = 1e30f;
-  for (int rep = 0; rep < 4; ++rep) {
+  for (int rep = 0; rep < 10; ++rep) {
     cudaEventRecord(e0, s);
     switch (kind) {
-      case 0: k_probe_fma<double><<<blocks, threads, 0, s>>>(d, 0.999999, 1e-7); break;
-      case 1: k_probe_fma<float><<<blocks, threads, 0, s>>>((float*)d, 0.999999f, 1e-7f); break;
+      case 0: k_probe_fma<double, kIters><<<blocks, threads, 0, s>>>(d, 0.999999, 1e-7); break;
+      case 1: k_probe_fma<float, kIters32><<<blocks, threads, 0, s>>>((float*)d, 0.999999f, 1e-7f); break;
       case 2: k_probe_exp64<<<blocks, threads, 0, s>>>(d); break;
       case 3: k_probe_exp32<<<blocks, threads, 0, s>>>((float*)d); break;
     }
@@ -121,7 +124,7 @@ extern "C" int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s) {
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (rep > 0 && ms < best) best = ms;   // first launch is a warm-up
+    if (rep > 1 && ms < best) best = ms;   // the first two launches are warm-ups
   }
   cudaError_t err = cudaGetLastError();
   cudaEventDestroy(e0);
@@ -130,9 +133,10 @@ extern "C" int jfnk_probe_alu(jfnk_ctx* ctx, int kind, double* ops_per_s) {
   if (err != cudaSuccess) return fail(JFNK_E_CUDA, cudaGetErrorString(err));
   const double threads_total = (double)threads * blocks;
   double ops;
-  if (kind <= 1) ops = threads_total * kChains * kIters * 2.0;
+  if (kind == 0) ops = threads_total * kChains * kIters * 2.0;
+  else if (kind == 1) ops = threads_total * kChains * kIters32 * 2.0;
   else if (kind == 2) ops = threads_total * kChains * (kIters / 8);
-  else ops = threads_total * kChains * kIters;
+  else ops = threads_total * kChains * kIters32;
   *ops_per_s = ops / (best * 1e-3);
   return JFNK_OK;
 }

@@ -38,6 +38,11 @@ __device__ __forceinline__ const double* tangent_dir(const ColDesc& cd) {
 // ---------------------------------------------------------------------------
 // a1: opacity and source function per (nu, k), shared by every ray
 // ---------------------------------------------------------------------------
+// Prefetch of one line into L2 (no register is held while it is in flight).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <typename real>
 __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i);
 
@@ -49,8 +54,23 @@ __global__ void k_opacity(const ColDesc* __restrict__ cols, int skip_tangent) {
   const int mode = eval_mode(cd);
   if (mode == EV_SKIP || (skip_tangent && mode == EV_TANGENT)) return;
   const int n = cd.t.nq * cd.t.nz;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (sizeof(real) == sizeof(float) && mode != EV_TANGENT && i + stride < n) {
+      // the next point's background terms and first transition, into L2
+      const ColTables& T = cd.t;
+      const int j = i + stride, q = j / T.nz, k = j - q * T.nz;
+      prefetch_l2(as_pairs(jdag_ptr(cd)) + j);
+      prefetch_l2(T.etac2 + j);
+      prefetch_l2(T.chibg2 + j);
+      const int m = __ldg(T.qmeta + q);
+      if (m >= 0) {
+        prefetch_l2(T.V2 + (size_t)(m >> 8) * T.nz + k);
+        prefetch_l2(T.gV2 + (size_t)(m >> 8) * T.nz + k);
+      }
+    }
     opacity_point<real>(cd, mode, i);
+  }
 }
 
 template <typename real>
@@ -157,6 +177,8 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
 // before any of their sums use them.
 constexpr int kOpTanDepths = 16;
 constexpr int kOpTanBatch = 2;   // depths whose loads are issued together
+constexpr int kOpTanAhead = 4;   // depths ahead whose rows are prefetched into L2
+
 __global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict__ cols, int nqb) {
   const ColDesc& cd = cols[blockIdx.y];
   if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
@@ -220,8 +242,21 @@ __global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict
     cd.w.dchiT[o] = ta.dchi;
     cd.w.dS32T[o] = tan_dS(ta, r.S, r.c);
   };
+  auto pf = [&](int k) {
+    if (k >= k1) return;
+    const size_t o = (size_t)k * pitch + q;
+    prefetch_l2(cd.w.S32T + o);
+    prefetch_l2(cd.w.chiT + o);
+    const float2* __restrict__ VG = T.VG32T + (size_t)k * nwin;
+    if (m0 >= 0) prefetch_l2(VG + (m0 >> 8));
+    if (m1 >= 0) prefetch_l2(VG + (m1 >> 8));
+  };
+#pragma unroll
+  for (int i = 0; i < kOpTanAhead; ++i) pf(k0 + i);
   int k = k0;
   for (; k + kOpTanBatch <= k1; k += kOpTanBatch) {
+#pragma unroll
+    for (int i = 0; i < kOpTanBatch; ++i) pf(k + kOpTanAhead + i);
     In r[kOpTanBatch];
 #pragma unroll
     for (int i = 0; i < kOpTanBatch; ++i) r[i] = ld(k + i);
