@@ -176,10 +176,12 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
 // others read when present), and kOpTanBatch depths' table loads are issued
 // before any of their sums use them.
 constexpr int kOpTanDepths = 16;
-constexpr int kOpTanBatch = 2;   // depths whose loads are issued together
+constexpr int kOpTanBatch = 1;   // depths whose loads are issued together (the L2
+                                 // prefetch supplies the memory parallelism; fewer
+                                 // registers leave room for six blocks per SM)
 constexpr int kOpTanAhead = 4;   // depths ahead whose rows are prefetched into L2
 
-__global__ void __launch_bounds__(256) k_opacity_tan32(const ColDesc* __restrict__ cols, int nqb) {
+__global__ void __launch_bounds__(256, 6) k_opacity_tan32(const ColDesc* __restrict__ cols, int nqb) {
   const ColDesc& cd = cols[blockIdx.y];
   if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
   const ColTables& T = cd.t;
