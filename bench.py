@@ -864,7 +864,9 @@ def run_serve(args, rank, ws, local, dist):
     n = len(wl.columns)
     live = {}                     # id -> (atom, atmosphere) until retired
     lock = threading.Lock()
-    window = threading.Semaphore(4 * args.slots)   # requests built but not retired
+    # requests built but not retired (their tables live on the device): a few
+    # slots' worth of queue, capped so that large slot counts keep memory
+    window = threading.Semaphore(min(4 * args.slots, 2048))
     err = []
     t_start = sv.clock()
     arrivals = t_start + np.asarray(wl.arrivals)
