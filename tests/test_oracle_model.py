@@ -110,3 +110,15 @@ def test_line_grid_rule():
     assert x[80] == 0.0
     assert x[40] == pytest.approx(-3.0, rel=1e-12) and x[120] == pytest.approx(3.0, rel=1e-12)
     np.testing.assert_allclose(OM.line_offsets(41, 5.0, 5.0), np.linspace(-5, 5, 41), atol=1e-15)
+
+
+def test_dense_overlap_workload_overlaps_more_transitions_than_a_packed_list():
+    """The dense-overlap test atom has frequencies where all 12 lines are
+    active at once (the kernels' packed per-frequency lists hold 8), so the
+    GPU parity tests on it take the general transition lists."""
+    wl = W.dense_overlap_workload()
+    m = OM.build_model(wl.atom, wl.columns[0], wl.n_mu)
+    active = np.zeros(m.nu.size, int)
+    for t in m.trans:
+        active[t.q0:t.q1 + 1] += 1
+    assert active.max() == 12 > 8

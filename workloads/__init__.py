@@ -410,6 +410,33 @@ def perturbed_populations(nstar: np.ndarray, rng: np.random.Generator,
     return nstar * np.exp(rng.normal(0.0, rel, size=nstar.shape))
 
 
+def dense_overlap_workload(n_depth: int = 24, n_nu_line: int = 21, n_nu_cont: int = 8,
+                           seed: int = 11) -> Workload:
+    """An eight-level atom whose 12 lines all overlap: three nearly degenerate
+    lower levels (1e-5 eV apart) and four nearly degenerate upper levels near
+    3 eV, every lower-upper pair a line, so that at the lines' common centre
+    12 transitions are active at once (more than the eight a frequency's packed
+    transition list holds); 7 continua to an ionised level at 11.9 eV overlap
+    among themselves above their edges. Not a physical ion: it exercises the
+    general per-frequency transition lists of the kernels."""
+    rng = np.random.default_rng(seed)
+    E = np.array([0.0, 1e-5, 2e-5, 3.0, 3.0 + 1e-5, 3.0 + 2e-5, 3.0 + 3e-5, 11.9])
+    g = np.array([2.0, 2.0, 2.0, 4.0, 4.0, 4.0, 4.0, 1.0])
+    stage = np.array([1, 1, 1, 1, 1, 1, 1, 2])
+    lines = []
+    for i in range(3):
+        for j in range(3, 7):
+            a = 10.0 ** rng.uniform(-3.0, -2.0)
+            lines.append(Line(i=i, j=j, f=10.0 ** rng.uniform(-2.0, -0.5), damping=a,
+                              upsilon=rng.uniform(0.2, 1.0), n_nu=_odd(n_nu_line), q_core=3.0, q_wing=30.0))
+    conts = [Continuum(i=i, j=7, alpha0=rng.uniform(1e-19, 1e-18), q0=10.0 ** rng.uniform(-11.0, -10.0),
+                       n_nu=n_nu_cont, y_max=2.0) for i in range(7)]
+    atom = Atom(name="dense-overlap", E_eV=E, g=g, stage=stage, lines=lines, conts=conts,
+                mass_amu=40.08, vchar=_thermal_speed(6000.0, 40.08))
+    col = chromosphere(n_depth, m_top=1e-4, m_bot=1.0, abundance=2.2e-6)
+    return Workload(name="dense overlap", atom=atom, columns=[col], n_mu=3)
+
+
 def tiny_workload(n_depth: int = 6, n_nu_line: int = 5, n_nu_cont: int = 3,
                   seed: int = 7, two_level: bool = False) -> Workload:
     """Very small three-level (or two-level) problem for brute-force checks."""
@@ -436,4 +463,4 @@ __all__ = ["Line", "Continuum", "Atom", "Column", "Workload", "config1", "config
            "velocity_chromosphere", "optimized_depth_grid",
            "config3", "config4", "config5", "two_level_atom", "two_level_slab",
            "chromosphere", "ca_like_atom", "h_like_atom", "perturbed_populations",
-           "tiny_workload", "replace"]
+           "tiny_workload", "dense_overlap_workload", "replace"]
