@@ -563,6 +563,7 @@ def run_ours(args, rank, ws, local, dist):
     roofline = alu_roofline(B, ctx, fp64, prof["F_calls"] - prof["jvp_calls"], prof["jvp_calls"],
                             atm.ray_points, kern_ms, launches, clocks, prof["formal_kernel"], local)
     roofline["share_of_step"] = kern_ms / (total_ms / args.steps)
+    roofline["tick_stages_ms"] = stage_breakdown(prof)
     roofline["timed_in"] = "a separate profiled solve (in-graph events around the formal kernel of every tick)"
     gpu_launches = int(sum(s["kernel_launches"] for s in stats))
     line = {"metric": METRIC, "value": value, "unit": "ray-points/s", "n_gpus": ws,

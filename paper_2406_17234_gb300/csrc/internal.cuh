@@ -107,6 +107,7 @@ struct Batch {
   int mixed = 0;
   int kmax = 0;
   int max_nz = 0, max_nq = 0, max_nt = 0, max_N = 0, max_nmu = 0;
+  int max_nl = 0;   // largest level count (compacted views keep the full batch's)
   DeviceArena arena;
   ColDesc* d_cols = nullptr;          // device array [ncols]
   std::vector<ColDesc> h_cols;        // host mirror

@@ -1050,42 +1050,40 @@ static void launch_dJdn_update(const Batch& b, cudaStream_t s) {
 constexpr int kAsmWarps = 4;
 
 // Tangent evaluations: the directional derivative of F only (no block of the
-// preconditioner), one thread per depth so that the per-(transition, depth)
-// rates are read in coalesced rows; each level's sum runs over its own
-// transitions in index order, the additions of the warp-per-depth kernel.
+// preconditioner), one thread per (depth, level) with the level on the grid's
+// z axis, so that the per-(transition, depth) rates are read in coalesced
+// rows; each level's sum runs over its own transitions in index order, the
+// additions of the warp-per-depth kernel.
 constexpr int kAsmTanThreads = 128;
 __global__ void __launch_bounds__(kAsmTanThreads) k_assemble_tan(const ColDesc* __restrict__ cols) {
   const ColDesc& cd = cols[blockIdx.y];
   if (eval_mode(cd) != EV_TANGENT) return;
   const ColTables& T = cd.t;
   const int nz = T.nz, nl = T.nl, nt = T.nt;
-  const int k = blockIdx.x * kAsmTanThreads + threadIdx.x;
-  if (k >= nz) return;
+  const int k = blockIdx.x * kAsmTanThreads + threadIdx.x, l = blockIdx.z;
+  if (k >= nz || l >= nl) return;
   const double* n = cd.w.n + (size_t)k * nl;
   const double* v = tangent_dir(cd) + (size_t)k * nl;
   const double* C = T.C + (size_t)k * nl * nl;
-  const int is = cd.w.istar[k];
-  for (int l = 0; l < nl; ++l) {
-    double f = 0.0;
-    if (l == is) {
-      for (int j = 0; j < nl; ++j) f += v[j];
-      f = -f;
-    } else {
-      const int* inc = T.lvl_inc + l * (nt + 1);
-      for (int e = 0; e < nt; ++e) {
-        const int m = __ldg(inc + e);
-        if (m < 0) break;
-        const int t = m >> 1;
-        const int lo = __ldg(T.t_lo + t), up = __ldg(T.t_up + t);
-        const size_t o = (size_t)t * nz + k;
-        const double ur = C[lo * nl + up] + cd.w.Rup[o];
-        const double dr = C[up * nl + lo] + cd.w.Rdn[o];
-        const double kp = v[lo] * ur + n[lo] * cd.w.dRup[o] - v[up] * dr - n[up] * cd.w.dRdn[o];
-        f += (m & 1) ? -kp : kp;
-      }
+  double f = 0.0;
+  if (l == cd.w.istar[k]) {
+    for (int j = 0; j < nl; ++j) f += v[j];
+    f = -f;
+  } else {
+    const int* inc = T.lvl_inc + l * (nt + 1);
+    for (int e = 0; e < nt; ++e) {
+      const int m = __ldg(inc + e);
+      if (m < 0) break;
+      const int t = m >> 1;
+      const int lo = __ldg(T.t_lo + t), up = __ldg(T.t_up + t);
+      const size_t o = (size_t)t * nz + k;
+      const double ur = C[lo * nl + up] + cd.w.Rup[o];
+      const double dr = C[up * nl + lo] + cd.w.Rdn[o];
+      const double kp = v[lo] * ur + n[lo] * cd.w.dRup[o] - v[up] * dr - n[up] * cd.w.dRdn[o];
+      f += (m & 1) ? -kp : kp;
     }
-    cd.w.dF[(size_t)k * nl + l] = f;
   }
+  cd.w.dF[(size_t)k * nl + l] = f;
 }
 
 __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(const ColDesc* __restrict__ cols) {
@@ -1258,8 +1256,8 @@ int launch_opacity_mixed(const Batch& b, cudaStream_t s, int skip_tangent) {
 
 // The assembly: tangent evaluations thread per depth, the others warp per depth.
 static void launch_assemble(const Batch& b, cudaStream_t s) {
-  k_assemble_tan<<<dim3((b.max_nz + kAsmTanThreads - 1) / kAsmTanThreads, b.ncols), kAsmTanThreads, 0, s>>>(
-      b.d_cols);
+  k_assemble_tan<<<dim3((b.max_nz + kAsmTanThreads - 1) / kAsmTanThreads, b.ncols, std::max(1, b.max_nl)),
+                   kAsmTanThreads, 0, s>>>(b.d_cols);
   k_assemble<<<dim3((b.max_nz + kAsmWarps - 1) / kAsmWarps, b.ncols), 32 * kAsmWarps, 0, s>>>(b.d_cols);
 }
 

@@ -233,6 +233,7 @@ int jfnk_server_create(jfnk_ctx* ctx, const jfnk_server_desc* d, jfnk_server** o
   b.max_nt = d->max_trans;
   b.max_N = d->max_depth * d->max_levels;
   b.max_nmu = d->max_mu;
+  b.max_nl = d->max_levels;
   b.max_overlap = d->max_trans;
   b.n_sm = ctx->n_sm;
   b.formal_qb = sv->mixed ? 0 : fused_default_qb(d->max_depth, d->max_mu, false);

@@ -140,7 +140,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
   b->ncols = nc;
   b->mixed = mixed;
   b->kmax = kmax;
-  b->max_nz = b->max_nq = b->max_nt = b->max_N = b->max_nmu = 0;
+  b->max_nz = b->max_nq = b->max_nt = b->max_N = b->max_nmu = b->max_nl = 0;
   DeviceArena& ar = b->arena;
   ar.reset();
   int mov = 0;
@@ -151,6 +151,7 @@ int batch_create(Batch* b, const std::vector<const AtmosData*>& cols, int mixed,
     b->max_nt = std::max(b->max_nt, c->nt);
     b->max_N = std::max(b->max_N, c->nz * c->nl);
     b->max_nmu = std::max(b->max_nmu, c->nmu);
+    b->max_nl = std::max(b->max_nl, c->nl);
   }
   b->max_overlap = mov;
   bool moving = false;

@@ -145,6 +145,7 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
   b.max_nt = (int)nt;
   b.max_N = (int)N;
   b.max_nmu = (int)nmu;
+  b.max_nl = (int)nl;
   b.n_sm = ctx->n_sm;
   b.d_cols = reinterpret_cast<ColDesc*>(base + o_desc);
   if ((rc = launch_evaluation(b, s))) {

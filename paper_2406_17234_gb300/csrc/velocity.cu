@@ -15,9 +15,13 @@
 // per-ray intensities, their tangents and local derivatives are stored
 // ([2 n_mu][nq][nz] each), the assembly and the Krylov/Newton step are the
 // static path's.
+#include <cooperative_groups.h>
+
 #include "formal_coef.cuh"
 
 namespace jfnk {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -157,31 +161,42 @@ __global__ void k_mv_moments(const ColDesc* __restrict__ cols) {
 // Rate integrals of transition t at depth k: R_ij, R_ji from the rays'
 // intensities (their tangents in tangent evaluations) and, in base
 // evaluations, the block-Jacobi sums A_tj = sum_nu W sum_d h_d chi_t,d
-// (beta_j,d dI_d/dchi_d + gamma_j,d dI_d/deta_d). A block takes one
-// transition and 32 depths (lanes: coalesced rows of the tables and of the
-// ray arrays); its warps split the frequency window and their partial sums
-// are added in a fixed order.
+// (beta_j,d dI_d/dchi_d + gamma_j,d dI_d/deta_d). A cluster of kMvRateSplit
+// blocks takes one transition and 32 depths (lanes: coalesced rows of the
+// tables and of the ray arrays); its blocks split the frequency window into
+// chunks and their warps stride through a chunk, so that even one column
+// spreads its FP64 sums over the GPU; the partial sums are added in warp
+// order, then in rank order through distributed shared memory.
 constexpr int kMvRateWarps = 4;
+constexpr int kMvRateSplit = 8;   // blocks of a cluster splitting the frequency window
 
 __global__ void __launch_bounds__(32 * kMvRateWarps) k_mv_rates(const ColDesc* __restrict__ cols) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int split = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int tile = blockIdx.x / split;
   const ColDesc& cd = cols[blockIdx.z];
   const int mode = mv_mode(cd);
-  if (mode == EV_SKIP) return;
   const ColTables& T = cd.t;
   const int t = blockIdx.y;
   const int nz = T.nz, nq = T.nq, nl = T.nl, nd = 2 * T.nmu;
-  if (t >= T.nt || (int)blockIdx.x * 32 >= nz) return;   // uniform over the block
+  // uniform over the cluster (its blocks differ only in their frequency chunk)
+  if (mode == EV_SKIP || t >= T.nt || tile * 32 >= nz) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int k = min((int)blockIdx.x * 32 + lane, nz - 1);
+  const int k = min(tile * 32 + lane, nz - 1);
   const bool tan = (mode == EV_TANGENT), base = (mode == EV_BASE);
   const int q0 = T.t_q0[t], q1 = T.t_q1[t], wb = T.t_base[t];
+  const int nw = q1 - q0 + 1;
+  const int qa = q0 + (int)(((long)nw * rank) / split), qb = q0 + (int)(((long)nw * (rank + 1)) / split) - 1;
   const double* n = eval_pops(cd, mode) + (size_t)k * nl;
   const double nlo = n[T.t_lo[t]], nup = n[T.t_up[t]];
   const size_t per = (size_t)nq * nz, vper = (size_t)T.nwin * nz;
   const double* Iray = tan ? cd.w.mdI : cd.w.mI;
-  double ru = 0.0, rd = 0.0, A[kMaxL];
-  for (int j = 0; j < nl; ++j) A[j] = 0.0;
-  for (int q = q0 + wid; q <= q1; q += kMvRateWarps) {
+  // per-lane sums: [0] R_up, [1] R_dn, [2 + j] the preconditioner's A_j (base)
+  __shared__ double s_part[kMvRateWarps][2 + kMaxL][32];
+  if (base)
+    for (int j = 0; j < nl; ++j) s_part[wid][2 + j][lane] = 0.0;
+  double ru = 0.0, rd = 0.0;
+  for (int q = qa + wid; q <= qb; q += kMvRateWarps) {
     const int p = wb + q - q0;
     const size_t pk = (size_t)p * nz + k, qk = (size_t)q * nz + k;
     const double W = T.t_w[p] * T.rw[q], g = T.G[pk], c2 = T.c2[q];
@@ -200,39 +215,45 @@ __global__ void __launch_bounds__(32 * kMvRateWarps) k_mv_rates(const ColDesc* _
           const int ts = T.q_t[s];
           const size_t ps = (size_t)(T.t_base[ts] + q - T.t_q0[ts]) * nz + k;
           const double Vs = T.Vd[(size_t)d * vper + ps], gVs = T.G[ps] * Vs;
-          A[T.t_lo[ts]] += c * (Vs * lx);
-          A[T.t_up[ts]] += c * (-gVs * lx + c2 * gVs * le);
+          s_part[wid][2 + T.t_lo[ts]][lane] += c * (Vs * lx);
+          s_part[wid][2 + T.t_up[ts]][lane] += c * (-gVs * lx + c2 * gVs * le);
         }
       }
     }
     ru += W * su;
     rd += W * g * sd;
   }
-  // partial sums of the warps, added in warp order by warp 0
-  __shared__ double s_part[kMvRateWarps][2 + kMaxL][32];
   s_part[wid][0][lane] = ru;
   s_part[wid][1][lane] = rd;
-  if (base)
-    for (int j = 0; j < nl; ++j) s_part[wid][2 + j][lane] = A[j];
   __syncthreads();
-  if (wid != 0 || (int)blockIdx.x * 32 + lane >= nz) return;
+  // the block's warps in warp order, then the cluster's blocks in rank order
   const int nacc = base ? 2 + nl : 2;
-  double acc[2 + kMaxL];
-  for (int j = 0; j < nacc; ++j) {
-    double v = s_part[0][j][lane];
-    for (int w = 1; w < kMvRateWarps; ++w) v += s_part[w][j][lane];
-    acc[j] = v;
+  if (wid == 0)
+    for (int j = 0; j < nacc; ++j) {
+      double v = s_part[0][j][lane];
+      for (int w = 1; w < kMvRateWarps; ++w) v += s_part[w][j][lane];
+      s_part[0][j][lane] = v;
+    }
+  cluster.sync();
+  if (rank == 0 && wid == 0 && tile * 32 + lane < nz) {
+    double acc[2 + kMaxL];
+    for (int j = 0; j < nacc; ++j) acc[j] = s_part[0][j][lane];
+    for (int r = 1; r < split; ++r) {
+      const double* peer = cluster.map_shared_rank(&s_part[0][0][0], r);
+      for (int j = 0; j < nacc; ++j) acc[j] += peer[j * 32 + lane];
+    }
+    const size_t o = (size_t)t * nz + k;
+    if (tan) {
+      cd.w.dRup[o] = acc[0];
+      cd.w.dRdn[o] = acc[1];
+    } else {
+      cd.w.Rup[o] = acc[0];
+      cd.w.Rdn[o] = acc[1];
+      if (base)
+        for (int j = 0; j < nl; ++j) cd.w.Apart[o * nl + j] = acc[2 + j];
+    }
   }
-  const size_t o = (size_t)t * nz + k;
-  if (tan) {
-    cd.w.dRup[o] = acc[0];
-    cd.w.dRdn[o] = acc[1];
-  } else {
-    cd.w.Rup[o] = acc[0];
-    cd.w.Rdn[o] = acc[1];
-    if (base)
-      for (int j = 0; j < nl; ++j) cd.w.Apart[o * nl + j] = acc[2 + j];
-  }
+  cluster.sync();   // peers keep their shared memory until rank 0 has read it
 }
 
 int launch_moving_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
@@ -244,7 +265,22 @@ int launch_moving_evaluation(const Batch& b, cudaStream_t s, cudaEvent_t ev0, cu
   k_mv_formal<<<dim3((2 * b.max_nmu * b.max_nq + 127) / 128, nc), 128, 0, s>>>(b.d_cols);
   if (ev1) JFNK_CUDA(cudaEventRecordWithFlags(ev1, s, cudaEventRecordExternal));
   k_mv_moments<<<dim3((b.max_nq * b.max_nz + tb - 1) / tb, nc), tb, 0, s>>>(b.d_cols);
-  k_mv_rates<<<dim3((b.max_nz + 31) / 32, b.max_nt, nc), 32 * kMvRateWarps, 0, s>>>(b.d_cols);
+  {
+    // clusters of kMvRateSplit blocks along x split each transition's window
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(((b.max_nz + 31) / 32) * kMvRateSplit, b.max_nt, nc);
+    cfg.blockDim = dim3(32 * kMvRateWarps);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kMvRateSplit;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    JFNK_CUDA(cudaLaunchKernelEx(&cfg, k_mv_rates, (const ColDesc*)b.d_cols));
+  }
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
