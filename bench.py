@@ -725,7 +725,8 @@ def run_batch(args, rank, ws, local, dist):
                 "launch": {"threads": int(pst[0]["formal_threads"]), "variant": int(pst[0]["formal_kernel"]),
                            "blocks_per_sm_cap_tangent": int(pst[0]["formal_occ"]),
                            "blocks_per_sm_cap_base": int(pst[0]["formal_occ_base"]),
-                           "tangent_opacity_in_sweep": int(pst[0]["formal_fuse"])},
+                           "tangent_opacity_in_sweep": int(pst[0]["formal_fuse"]),
+                           "opacity_tangent_depths_per_thread": int(pst[0]["opacity_depths"])},
                 "tick_stages_ms": stage_breakdown(pst[0])}
     st0 = allstats[-1]
     line = {"metric": METRIC, "value": pts / (total_ms * 1e-3), "unit": "ray-points/s", "n_gpus": ws,

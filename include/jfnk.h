@@ -254,6 +254,8 @@ typedef struct {
                            mode), [2] base-type formal solution, [3] rate
                            integrals (and, moving columns, moments), [4] assembly
                            and preconditioner factorisation, [5] Krylov step      */
+  int opacity_depths;   /* mixed mode: depths per thread of the opacity-tangent kernel
+                           (its depth tile, chosen by the autotuner; 0: not tuned) */
 } jfnk_stats;
 
 /* ---- context ------------------------------------------------------------ */

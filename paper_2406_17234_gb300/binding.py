@@ -91,7 +91,8 @@ class jfnk_stats(C.Structure):
                 ("formal_ms", C.c_double), ("formal_launches", C.c_int), ("kernel_launches", C.c_int),
                 ("formal_qb", C.c_int), ("formal_threads", C.c_int), ("formal_kernel", C.c_int),
                 ("formal_tan_ms", C.c_double), ("formal_occ", C.c_int), ("formal_occ_base", C.c_int),
-                ("formal_fuse", C.c_int), ("stage_ms", C.c_double * 6)]
+                ("formal_fuse", C.c_int), ("stage_ms", C.c_double * 6),
+                ("opacity_depths", C.c_int)]
 
     def as_dict(self):
         return {f: (list(v) if isinstance(v, C.Array) else v)

@@ -481,6 +481,7 @@ static int finish_solve(Batch* b, const std::vector<const jfnk_atmos*>& cols, do
       S.formal_ms = kernel_ms;
       S.formal_tan_ms = tan_ms;
       for (int j = 0; j < kStages; ++j) S.stage_ms[j] = stage_ms[j];
+      S.opacity_depths = b->formal_kind == FORMAL_SWEEP ? b->optan_depths : 0;
       S.formal_occ = b->formal_kind == FORMAL_SWEEP && b->sweep_variant != 2 ? b->sweep_occ : 0;
       S.formal_occ_base = b->formal_kind == FORMAL_SWEEP && b->sweep_variant != 2 ? b->sweep_occ_base : 0;
       S.formal_fuse = b->formal_kind == FORMAL_SWEEP && sweep_fused(*b) ? b->sweep_fuse : 0;

@@ -914,8 +914,9 @@ int sweep_warp_size(int nz) {
 // tangent sweep (the columns in tangent mode) over variant 1 with 32..256
 // threads per block and a cap of 2..8 resident blocks per SM or none, and
 // variant 2 with 1..8 warps per block (where its shared memory fits); then,
-// for variant 1, the base-type sweep's cap (columns in base mode). Both
-// variants give bit-identical results, so the choice changes the speed only.
+// for variant 1, the base-type sweep's cap (columns in base mode). First the
+// opacity tangent's run of depths per thread. Every choice gives bit-identical
+// results, so it changes the speed only.
 int sweep_autotune(Batch* b, cudaStream_t s) {
   cudaEvent_t e0, e1;
   JFNK_CUDA(cudaEventCreate(&e0));
@@ -947,6 +948,37 @@ int sweep_autotune(Batch* b, cudaStream_t s) {
     *ms = best;
     return JFNK_OK;
   };
+  // the opacity tangent's run of depths per thread (the depth tile of its
+  // grid): the default of 16 unless another run gains 2 %
+  {
+    auto time_optan = [&](int dr, float* ms) -> int {
+      int r = launch_opacity_tan(*b, s, dr);   // warm-up
+      if (r) return r;
+      float best = 1e30f;
+      for (int i = 0; i < 5; ++i) {
+        if (cudaEventRecord(e0, s) != cudaSuccess) return fail(JFNK_E_CUDA, "autotune event");
+        if ((r = launch_opacity_tan(*b, s, dr))) return r;
+        float t = 0.f;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+          return fail(JFNK_E_CUDA, "autotune timing");
+        best = std::min(best, t);
+      }
+      *ms = best;
+      return JFNK_OK;
+    };
+    float bo = 0.f;
+    int bd = 16;
+    if (!(rc = time_optan(16, &bo))) {
+      bo *= 0.98f;
+      for (int dr : {4, 8, 32}) {
+        float ms = 0.f;
+        if ((rc = time_optan(dr, &ms))) break;
+        if (ms < bo) { bo = ms; bd = dr; }
+      }
+    }
+    b->optan_depths = bd;
+  }
   // The fused opacity tangent (forced variant only) is not a candidate: timed
   // alone it can win, but inside a tick the separate opacity-tangent kernel
   // overlaps the base-type chain on the other stream, and the fused sweep

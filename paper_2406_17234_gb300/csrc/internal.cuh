@@ -108,6 +108,7 @@ struct Batch {
   int kmax = 0;
   int max_nz = 0, max_nq = 0, max_nt = 0, max_N = 0, max_nmu = 0;
   int max_nl = 0;   // largest level count (compacted views keep the full batch's)
+  int optan_depths = 0;   // opacity tangent: depths per thread (autotuned; 0: the default)
   DeviceArena arena;
   ColDesc* d_cols = nullptr;          // device array [ncols]
   std::vector<ColDesc> h_cols;        // host mirror
@@ -190,7 +191,8 @@ int launch_formal_sweep(const Batch& b, cudaStream_t s, int which = 0);
 // separate opacity-tangent kernel is not launched).
 bool sweep_fused(const Batch& b);
 // The separate mixed-mode opacity-tangent kernel (residual.cu).
-int launch_opacity_tan(const Batch& b, cudaStream_t s);
+// depths: the run of depths per thread (0: the batch's tuned run).
+int launch_opacity_tan(const Batch& b, cudaStream_t s, int depths = 0);
 // Warps per block of the warp variant whose shared memory fits depth nz (0: none).
 int sweep_warp_size(int nz);
 int sweep_autotune(Batch* b, cudaStream_t s);

@@ -169,27 +169,28 @@ __device__ __forceinline__ void opacity_point(const ColDesc& cd, int mode, int i
 }
 
 // Mixed mode, tangent evaluations: dchi and dS in FP32 (tan_acc). A thread
-// owns one frequency nu and a run of kOpTanDepths depths; consecutive threads
+// owns one frequency nu and a run of ``depths`` depths (Batch::optan_depths,
+// chosen by the autotuner); consecutive threads
 // take consecutive frequencies, so every warp reads and writes coalesced rows
 // of the depth-major arrays and line tables. The transitions active at nu
 // come from the packed qmeta table, loaded once (the first two held, the
 // others read when present), and kOpTanBatch depths' table loads are issued
 // before any of their sums use them.
-constexpr int kOpTanDepths = 16;
+constexpr int kOpTanDepths = 16;   // default run of depths per thread
 constexpr int kOpTanBatch = 1;   // depths whose loads are issued together (the L2
                                  // prefetch supplies the memory parallelism; fewer
                                  // registers leave room for six blocks per SM)
 constexpr int kOpTanAhead = 4;   // depths ahead whose rows are prefetched into L2
 
-__global__ void __launch_bounds__(256, 6) k_opacity_tan32(const ColDesc* __restrict__ cols, int nqb) {
+__global__ void __launch_bounds__(256, 6) k_opacity_tan32(const ColDesc* __restrict__ cols, int nqb, int depths) {
   const ColDesc& cd = cols[blockIdx.y];
   if (!cd.mixed || eval_mode(cd) != EV_TANGENT) return;
   const ColTables& T = cd.t;
   const int nq = T.nq, nz = T.nz, nl = T.nl, nwin = T.nwin;
   const int qb = blockIdx.x % nqb, kc = blockIdx.x / nqb;
-  const int q = qb * blockDim.x + threadIdx.x, k0 = kc * kOpTanDepths;
+  const int q = qb * blockDim.x + threadIdx.x, k0 = kc * depths;
   if (q >= nq || k0 >= nz) return;
-  const int k1 = min(nz, k0 + kOpTanDepths);
+  const int k1 = min(nz, k0 + depths);
   const size_t pitch = (size_t)col_pitch(nq);
   const int m0 = __ldg(T.qmeta + q), m1 = __ldg(T.qmeta + (size_t)nq + q);
   struct In {
@@ -1233,14 +1234,16 @@ static dim3 opacity_grid(const Batch& b, int tb) {
   return dim3((unsigned)std::max(1L, std::min(need, share)), b.ncols);
 }
 
-// k_opacity_tan32: blocks of 256 frequencies x kOpTanDepths depths per column.
-static void launch_op_tan(const Batch& b, cudaStream_t s) {
-  const int nqb = (b.max_nq + 255) / 256, nkc = (b.max_nz + kOpTanDepths - 1) / kOpTanDepths;
-  k_opacity_tan32<<<dim3(nqb * nkc, b.ncols), 256, 0, s>>>(b.d_cols, nqb);
+// k_opacity_tan32: blocks of 256 frequencies x a run of depths per thread
+// (the batch's tuned run, else kOpTanDepths).
+static void launch_op_tan(const Batch& b, cudaStream_t s, int depths = 0) {
+  const int dr = depths > 0 ? depths : (b.optan_depths > 0 ? b.optan_depths : kOpTanDepths);
+  const int nqb = (b.max_nq + 255) / 256, nkc = (b.max_nz + dr - 1) / dr;
+  k_opacity_tan32<<<dim3(nqb * nkc, b.ncols), 256, 0, s>>>(b.d_cols, nqb, dr);
 }
 
-int launch_opacity_tan(const Batch& b, cudaStream_t s) {
-  launch_op_tan(b, s);
+int launch_opacity_tan(const Batch& b, cudaStream_t s, int depths) {
+  launch_op_tan(b, s, depths);
   JFNK_CUDA(cudaGetLastError());
   return JFNK_OK;
 }
