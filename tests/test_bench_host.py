@@ -49,3 +49,13 @@ def test_roofline_peaks_from_measured_rates():
     assert abs(b.peak_rate("value", True, peaks) / (1e12 / (10 + 2 * 10)) - 1) < 1e-12
     r = b.kernel_roofline("k", "jvp", False, 1e9, 2.0, 4, peaks)
     assert abs(r["achieved"] - 1e9 / 2e-3 / 1e9) < 1e-9 and abs(r["avg_launch_us"] - 500.0) < 1e-9
+
+
+def test_stage_breakdown_is_per_active_tick_with_shares():
+    b = _bench()
+    st = {"formal_launches": 4, "stage_ms": [4.0, 8.0, 2.0, 4.0, 1.0, 1.0]}
+    r = b.stage_breakdown(st)
+    assert list(r["per_tick"]) == list(b.STAGES)
+    assert r["per_tick"]["tangent_sweep"] == 2.0 and r["tick_total"] == 5.0
+    assert abs(sum(r["share"].values()) - 1.0) < 1e-12
+    assert b.stage_breakdown({"formal_launches": 0, "stage_ms": [0.0] * 6})["tick_total"] == 0.0

@@ -616,3 +616,28 @@ def test_rh92_only_mixed_reaches_the_oracle_fixed_point(ctx):
                                               ftol=1e-5, maxiter=2000))
     assert ref.converged and st["status"] == 0
     np.testing.assert_allclose(n, ref.n, rtol=1e-3)
+
+
+def test_profiled_batch_reports_its_stages_and_tuned_shapes(ctx):
+    """A profiled mixed batch solve: each tick's stages are timed on one stream
+    (the sweeps' own durations are two of them), the results are those of the
+    unprofiled solve, and the autotuned opacity-tangent depth tile is one of
+    its candidates."""
+    wl = W.config4(n_columns=6, nz_min=40, nz_max=70, nu_scale=0.1)
+    atom = B.Atom(ctx, wl.atom)
+    atms = [B.Atmosphere(ctx, atom, c, n_mu=3) for c in wl.columns]
+    start = dict(rh92_warmup=5, rh92_switch=0.1)
+    plan = B.BatchPlan(ctx, atms, precision=B.JFNK_MIXED)
+    n0, s0 = plan.run(B.default_options(precision=B.JFNK_MIXED, **start), raise_on_fail=False)
+    n0 = [x.copy() for x in n0]
+    n1, s1 = plan.run(B.default_options(precision=B.JFNK_MIXED, profile=1, **start), raise_on_fail=False)
+    st = s1[0]
+    stage = st["stage_ms"]
+    assert len(stage) == 6 and all(x >= 0.0 for x in stage) and sum(stage) > 0.0
+    assert abs(stage[1] - st["formal_tan_ms"]) <= 1e-9 * max(1.0, st["formal_tan_ms"])
+    assert abs(stage[2] - st["formal_ms"]) <= 1e-9 * max(1.0, st["formal_ms"])
+    assert st["opacity_depths"] in (4, 8, 16, 32)
+    for a, b_, sa, sb in zip(n0, n1, s0, s1):
+        assert sa["status"] == sb["status"] and sa["F_calls"] == sb["F_calls"]
+        np.testing.assert_array_equal(a, b_)
+    plan.close()
