@@ -377,8 +377,12 @@ int jfnk_batch_destroy(jfnk_batch* b);
  *   n [nz*nl], J_dagger [nq*nz] (nullable: B_nu(T)), F [nz*nl], J_new [nq*nz]
  *   (nullable): device pointers on the context's device; the work is enqueued
  *   on ``stream`` and the call returns without synchronising.
- * A column whose buffers exceed the array (roughly nq * nz * (8 n_mu + 9) * 8
- * bytes) is rejected with JFNK_E_INVALID and a message giving the size needed.
+ * The formal solution runs in the fused kernel of jfnk_residual, whose buffers
+ * take roughly nq * nz * 6 * 8 bytes; a column too deep for it (a frequency's
+ * rays over all depths beyond one block's shared memory) takes the per-ray
+ * kernels, about nq * nz * (8 n_mu + 9) * 8 bytes. A column whose buffers
+ * exceed the array is rejected with JFNK_E_INVALID and a message giving the
+ * size needed.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture (a first call on a
  * stream that is being captured returns JFNK_E_INVALID). Every call shares

@@ -83,14 +83,19 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
   const AtmosData& M = a->d;
   const size_t nz = M.nz, nq = M.nq, nl = M.nl, nt = M.nt, nmu = M.nmu;
   const size_t N = nz * nl, QZ = nq * nz;
+  // the fused formal kernel (the one jfnk_residual runs) needs no per-ray
+  // buffers; the per-ray path only when a frequency's rays exceed its shared memory
+  const int qb = fused_default_qb((int)nz, (int)nmu, false);
+  const bool fused = qb > 0;
+  const size_t per_ray = fused ? 0 : 2 * nmu * QZ;
   StaticLayout L;
   const size_t o_desc = L.take<ColDesc>(1);
   const size_t o_n = L.take<double>(N), o_Jdag = L.take<double>(QZ), o_Jnew = L.take<double>(QZ);
   const size_t o_istar = L.take<int>(nz);
-  const size_t o_chi = L.take<double>(QZ), o_S = L.take<double>(QZ), o_dSk = L.take<double>(QZ);
-  const size_t o_H = L.take<double>(2 * nmu * QZ), o_LX = L.take<double>(2 * nmu * QZ),
-               o_LE = L.take<double>(2 * nmu * QZ), o_HI = L.take<double>(2 * nmu * QZ);
-  const size_t o_J = L.take<double>(QZ), o_Lchi = L.take<double>(QZ), o_Leta = L.take<double>(QZ);
+  const size_t o_chi = L.take<double>(QZ), o_S = L.take<double>(QZ), o_dSk = L.take<double>(fused ? 0 : QZ);
+  const size_t o_H = L.take<double>(per_ray), o_LX = L.take<double>(per_ray), o_LE = L.take<double>(per_ray),
+               o_HI = L.take<double>(per_ray);
+  const size_t o_J = L.take<double>(fused ? 0 : QZ), o_Lchi = L.take<double>(QZ), o_Leta = L.take<double>(QZ);
   const size_t o_Rup = L.take<double>(nt * nz), o_Rdn = L.take<double>(nt * nz);
   const size_t o_Apart = L.take<double>(nt * nz * nl);
   const size_t o_F = L.take<double>(N), o_P = L.take<double>(nz * nl * nl);
@@ -116,12 +121,14 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
   w.istar = reinterpret_cast<int*>(base + o_istar);
   w.chi = base + o_chi;
   w.S = reinterpret_cast<double*>(base + o_S);
-  w.dSk = base + o_dSk;
-  w.H = base + o_H;
-  w.HI = base + o_HI;
-  w.LX = base + o_LX;
-  w.LE = base + o_LE;
-  w.J = reinterpret_cast<double*>(base + o_J);
+  if (!fused) {
+    w.dSk = base + o_dSk;
+    w.H = base + o_H;
+    w.HI = base + o_HI;
+    w.LX = base + o_LX;
+    w.LE = base + o_LE;
+    w.J = reinterpret_cast<double*>(base + o_J);
+  }
   w.Lchi = reinterpret_cast<double*>(base + o_Lchi);
   w.Leta = reinterpret_cast<double*>(base + o_Leta);
   w.Rup = reinterpret_cast<double*>(base + o_Rup);
@@ -147,6 +154,9 @@ extern "C" int jfnk_residual_static(jfnk_ctx* ctx, const jfnk_atmos* a, const do
   b.max_nmu = (int)nmu;
   b.max_nl = (int)nl;
   b.n_sm = ctx->n_sm;
+  b.formal_kind = fused ? FORMAL_FUSED : FORMAL_UNFUSED;
+  b.formal_qb = qb;
+  if (fused && (rc = fused_prepare(&b))) return rc;
   b.d_cols = reinterpret_cast<ColDesc*>(base + o_desc);
   if ((rc = launch_evaluation(b, s))) {
     b.d_cols = nullptr;

@@ -39,7 +39,9 @@ def test_static_residual_matches_regular_entry_point_twice():
         pytest.skip("no CUDA device")
     ctx = B.Context(0)
     lib = ctx.lib
-    cases = [W.config1(), W.config2(nu_scale=0.3, n_depth=50)]
+    # the last: the full H I-like column (about 2,000 frequencies), within the
+    # array since the fused formal kernel needs no per-ray buffers
+    cases = [W.config1(), W.config2(nu_scale=0.3, n_depth=50), W.config3()]
     rng = np.random.default_rng(2024)
     stream = torch.cuda.current_stream()
     for wl in cases:
@@ -70,7 +72,7 @@ def test_static_residual_rejects_oversized_columns():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     ctx = B.Context(0)
-    wl = W.config3()   # about 2,000 frequencies x 82 depths: beyond the fixed array
+    wl = W.config3(n_depth=420)   # about 2,000 frequencies x 420 depths: beyond the fixed array
     atom = B.Atom(ctx, wl.atom)
     atm = B.Atmosphere(ctx, atom, wl.columns[0], n_mu=wl.n_mu)
     n_d = torch.zeros(atm.n_depth * atm.n_levels, dtype=torch.float64, device="cuda")
