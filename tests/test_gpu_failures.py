@@ -11,7 +11,10 @@ carry on unchanged.
   * in a batch, a failing column does not change the others' results
     (bit-identical to their solves alone);
   * in the server, a request that fails is retired with its status and the
-    requests around it are served with their usual results.
+    requests around it are served with their usual results;
+  * a level that no transition touches makes every preconditioner block
+    singular: the solve stops with an error status and the context serves the
+    next solve as before.
 """
 import numpy as np
 import pytest
@@ -121,3 +124,32 @@ def test_server_retires_a_failing_request_and_serves_the_others(ctx):
         assert res[i]["status"] == 0
         n1, _, s1 = B.solve(cols[i][1], base)
         np.testing.assert_array_equal(res[i]["n"], n1)
+
+
+def test_singular_preconditioner_stops_with_a_status(ctx):
+    """An atom with an isolated bound level (no line or continuum touches it):
+    its rate-equation row is identically zero, so the block-Jacobi blocks of
+    Sect. 2.5.1 are singular (the level is never the conservation row, being
+    almost empty). The solve ends with an error status, not a hang or a
+    wrong 'converged', and a regular column solves as before afterwards."""
+    from dataclasses import replace
+    base = W.tiny_workload(n_depth=12, n_nu_line=9, n_nu_cont=5)
+    a = base.atom
+    E = np.array([a.E_eV[0], a.E_eV[1], 6.0, a.E_eV[2]])
+    g = np.array([a.g[0], a.g[1], 2.0, a.g[2]])
+    stage = np.array([a.stage[0], a.stage[1], a.stage[1], a.stage[2]])
+    lines = [replace(ln, j=ln.j) for ln in a.lines]                  # (0, 1)
+    conts = [replace(c, j=3) for c in a.conts]                         # (0, 3), (1, 3)
+    iso = replace(a, E_eV=E, g=g, stage=stage, lines=lines, conts=conts, name="isolated level")
+    atom = B.Atom(ctx, iso)
+    atm = B.Atmosphere(ctx, atom, base.columns[0], n_mu=base.n_mu)
+    n, _, st = B.solve(atm, B.default_options(), raise_on_fail=False)
+    assert st["status"] != 0
+    assert st["status"] in (B.JFNK_E_NAN, B.JFNK_E_MAXITER, B.JFNK_E_TIMEOUT)
+    # the context and a regular column are unaffected
+    wl = W.config2(nu_scale=0.15, n_depth=30)
+    atom2, atm2 = _col(ctx, wl)
+    n1, _, s1 = B.solve(atm2, B.default_options())
+    n2, _, s2 = B.solve(atm2, B.default_options())
+    assert s1["status"] == 0
+    np.testing.assert_array_equal(n1, n2)
